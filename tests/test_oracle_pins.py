@@ -1,0 +1,379 @@
+"""Pins of the FP64 oracle against values the paper and the mathematics fix.
+
+Every check here compares the oracle with something other than itself: a
+published known-answer vector, a closed form derived from Eq. 1 / Eq. 2 on a
+symmetric configuration, an exact invariant, or a hand-worked example.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_04383_gb300 import graphs
+from golden_io import contract_example, philox_kat
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    for ctr, key, expect in philox_kat():
+        assert oracle.philox4x32_10(ctr, key).tolist() == expect
+
+
+# --------------------------------------------------------------------------
+# k-hop S (Sec. 2.3 footnote): hand-counted neighbourhoods
+# --------------------------------------------------------------------------
+def test_S_grid_32x32_counts():
+    rp, col = graphs.grid(32, 32)
+    assert int(rp[-1]) == 2 * 1984
+    sp, scol, sd, rho = oracle.build_S(rp, col, 2)
+    # 1984 edges + 1920 straight distance-2 pairs + 1922 diagonal pairs,
+    # each stored in both directions
+    assert len(scol) == 2 * (1984 + 1920 + 1922) == 11652
+    assert np.all(sd[sd > 1] == 2.0)
+    assert np.count_nonzero(sd == 2.0) == 2 * (1920 + 1922)
+    # interior vertex: 4 neighbours (w=1) and 8 at distance 2 (w=1/4)
+    u = 5 * 32 + 5
+    assert sp[u + 1] - sp[u] == 12
+    assert rho[u] == pytest.approx(4 + 8 / 4.0)
+
+
+def test_S_path_and_coarse_lengths():
+    rp, col = graphs.path(5)
+    sp, scol, sd, rho = oracle.build_S(rp, col, 3)
+    assert scol[sp[0]:sp[1]].tolist() == [1, 2, 3]
+    assert sd[sp[0]:sp[1]].tolist() == [1.0, 2.0, 3.0]
+    # coarse level: edge length sqrt(c_u) + sqrt(c_v) (Sec. 3.2)
+    c = np.array([1.0, 4.0, 9.0, 16.0, 25.0])
+    sp, scol, sd, rho = oracle.build_S(rp, col, 2, c=c, coarse=True)
+    row0 = dict(zip(scol[sp[0]:sp[1]].tolist(), sd[sp[0]:sp[1]].tolist()))
+    assert row0 == {1: 1 + 2, 2: (1 + 2) + (2 + 3)}
+    row2 = dict(zip(scol[sp[2]:sp[3]].tolist(), sd[sp[2]:sp[3]].tolist()))
+    assert row2 == {0: 8.0, 1: 5.0, 3: 7.0, 4: 7.0 + 9.0}
+
+
+def test_S_shortest_path_prefers_cheaper_route():
+    # square 0-1-2-3-0 plus chord 0-2; with k=2 the pair (1,3) is reached via
+    # 0 or 2; the coarse lengths make one route cheaper
+    rp, col = graphs.csr_from_edges(4, [0, 1, 2, 3, 0], [1, 2, 3, 0, 2])
+    c = np.array([1.0, 1.0, 100.0, 1.0])
+    sp, scol, sd, _ = oracle.build_S(rp, col, 2, c=c, coarse=True)
+    row1 = dict(zip(scol[sp[1]:sp[2]].tolist(), sd[sp[1]:sp[2]].tolist()))
+    assert row1[3] == pytest.approx(2.0 + 2.0)  # via vertex 0 (sqrt c = 1)
+    assert row1[2] == pytest.approx(1.0 + 10.0)  # direct edge
+
+
+# --------------------------------------------------------------------------
+# Eq. 2 sweep: regular polygon closed form
+#   one exact sweep maps a regular n-gon of radius R to a regular n-gon at the
+#   same angles with radius
+#   R' = [sum_{v in S} w_v (R cos phi_v + d_v |sin(phi_v/2)|)
+#         + alpha (n - 1 - |S_u|) / (2R)] / rho
+# --------------------------------------------------------------------------
+def polygon(n, R, center=(0.0, 0.0)):
+    ang = 2 * np.pi * np.arange(n) / n
+    return np.stack([center[0] + R * np.cos(ang), center[1] + R * np.sin(ang)], 1)
+
+
+def polygon_radius_after_sweep(n, k, R, alpha):
+    num = rho = 0.0
+    cnt = 0
+    for m in range(1, k + 1):
+        phi = 2 * math.pi * m / n
+        w = 1.0 / m ** 2
+        num += 2 * w * (R * math.cos(phi) + m * abs(math.sin(phi / 2)))
+        rho += 2 * w
+        cnt += 2
+    return (num + alpha * (n - 1 - cnt) / (2 * R)) / rho
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("n", [7, 16, 51])
+@pytest.mark.parametrize("alpha", [1.0, 0.027, 0.008])
+def test_sweep_regular_polygon(k, n, alpha):
+    rp, col = graphs.cycle(n)
+    S = oracle.build_S(rp, col, k)
+    R = 1.3
+    x = polygon(n, R, center=(0.25, -0.5))
+    xn, st = oracle.sweep(x, S, alpha, rep_mode=0)
+    expect = polygon(n, polygon_radius_after_sweep(n, k, R, alpha), center=(0.25, -0.5))
+    np.testing.assert_allclose(xn, expect, rtol=0, atol=1e-12)
+    # stress of the input over S: n pairs at distance 1 (+ n at distance 2)
+    stress = n * (2 * R * math.sin(math.pi / n) - 1) ** 2
+    if k == 2:
+        stress += n * 0.25 * (2 * R * math.sin(2 * math.pi / n) - 2) ** 2
+    assert st[2] == pytest.approx(stress, rel=1e-12)
+
+
+def test_sweep_polygon_fixed_point_k1():
+    # R* = (1 + sqrt(1 + 2 alpha (n-3))) / (4 sin(pi/n)) is a fixed point
+    n, alpha = 24, 0.3
+    Rs = (1 + math.sqrt(1 + 2 * alpha * (n - 3))) / (4 * math.sin(math.pi / n))
+    rp, col = graphs.cycle(n)
+    S = oracle.build_S(rp, col, 1)
+    x = polygon(n, Rs)
+    xn, st = oracle.sweep(x, S, alpha, 0)
+    np.testing.assert_allclose(xn, x, atol=1e-12)
+    assert st[0] < 1e-20
+
+
+def test_sweep_two_vertices_map():
+    # K2 at distance D with target d: the vertices swap to distance |2d - D|
+    rp, col = graphs.path(2)
+    for D, d in [(0.5, 1.0), (3.0, 1.0), (1.7, 2.5)]:
+        S = oracle.build_S(rp, col, 1, elen=np.array([d, d]))
+        x = np.array([[0.0, 0.0], [D, 0.0]])
+        xn, _ = oracle.sweep(x, S, 0.7, 0)
+        np.testing.assert_allclose(xn, [[D - d, 0.0], [d, 0.0]], atol=1e-14)
+    # the two-vertex initial layout (distance d) is a fixed point
+    S = oracle.build_S(rp, col, 1, c=np.array([3.0, 5.0]), coarse=True)
+    D = math.sqrt(3) + math.sqrt(5)
+    x = np.array([[-D / 2, 0.0], [D / 2, 0.0]])
+    xn, st = oracle.sweep(x, S, 1.0, 0)
+    np.testing.assert_allclose(xn, x, atol=1e-14)
+
+
+def _random_graph(n, seed):
+    rp, col, pts, _ = graphs.rgg(n, 6.0, seed, tune=False)
+    return rp, col, pts
+
+
+@pytest.mark.parametrize("rep_mode", [0, 1])
+def test_sweep_translation_rotation_equivariance(rep_mode):
+    rp, col, pts = _random_graph(300, 3)
+    S = oracle.build_S(rp, col, 2)
+    x = graphs.uniform_positions(len(rp) - 1, 11, 0.0, 10.0)
+    theta = 0.0  # BH with theta = 0 must match the exact sweep
+    y, _ = oracle.sweep(x, S, 0.09, rep_mode, theta)
+    t = np.array([3.5, -7.25])
+    yt, _ = oracle.sweep(x + t, S, 0.09, rep_mode, theta)
+    np.testing.assert_allclose(yt, y + t, atol=1e-9)
+    a = 0.7
+    Rm = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    yr, _ = oracle.sweep(x @ Rm.T, S, 0.09, rep_mode, theta)
+    np.testing.assert_allclose(yr, y @ Rm.T, atol=1e-9)
+
+
+def test_sweep_bh_theta0_equals_exact():
+    rp, col, pts = _random_graph(400, 5)
+    S = oracle.build_S(rp, col, 2)
+    x = graphs.uniform_positions(len(rp) - 1, 2, 0.0, 20.0)
+    a, _ = oracle.sweep(x, S, 0.3, 0)
+    b, _ = oracle.sweep(x, S, 0.3, 1, 0.0)
+    np.testing.assert_allclose(a, b, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Barnes-Hut (Sec. 2.2)
+# --------------------------------------------------------------------------
+def test_bh_far_cluster_closed_form():
+    # u alone in its quadrant, a cluster B of N points with an off-centre
+    # centroid in the opposite quadrant: B is accepted as one cell and
+    # F(u) = N r(u, centroid(B)) exactly.
+    B = np.array([[10.0 + 0.001 * i, 10.0 + 0.0007 * i] for i in range(9)] + [[10.1, 10.1]])
+    x = np.vstack([[0.0, 0.0], B])
+    c = B.mean(axis=0)
+    expect = len(B) * (x[0] - c) / np.sum((x[0] - c) ** 2)
+    for theta in (0.05, 0.3, 0.4):
+        F = oracle.repulsion_bh(x, theta)
+        np.testing.assert_allclose(F[0], expect, rtol=1e-13)
+    # opened all the way (theta = 0): the exact sum, which differs
+    F0 = oracle.repulsion_bh(x, 0.0)
+    ex = oracle.repulsion_exact(x)
+    np.testing.assert_allclose(F0, ex, rtol=1e-13)
+    assert np.abs(F0[0] - expect).max() > 1e-9
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.5, 0.7])
+def test_bh_multipole_remainder_bound(theta):
+    # For an accepted cell of side w at centroid distance D > w / theta the
+    # first-order term vanishes and the remainder of each member v is
+    # |delta_v|^2 / (D^2 |x_u - x_v|) <= 2 theta^2 / |x_u - x_v|, so
+    # |F_BH(u) - F(u)| <= 2 theta^2 sum_{v != u} 1 / |x_u - x_v|.
+    rng = np.random.default_rng(7)
+    x = np.vstack([rng.random((700, 2)) * 5.0, rng.normal(8.0, 0.3, (300, 2))])
+    F = oracle.repulsion_bh(x, theta)
+    ex = oracle.repulsion_exact(x)
+    diff = x[:, None, :] - x[None, :, :]
+    dist = np.sqrt((diff ** 2).sum(-1))
+    np.fill_diagonal(dist, np.inf)
+    bound = 2 * theta ** 2 * (1.0 / dist).sum(1)
+    err = np.sqrt(((F - ex) ** 2).sum(1))
+    assert np.all(err <= bound * (1 + 1e-9))
+    assert err.max() > 0  # cells really were accepted
+
+
+def test_bh_coincident_points():
+    x = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 0.0], [1.0, 0.0], [0.5, 2.0]])
+    F = oracle.repulsion_bh(x, 0.5)
+    ex = oracle.repulsion_exact(x)
+    np.testing.assert_allclose(F, ex, atol=1e-12)
+    # coincident partner contributes nothing
+    np.testing.assert_allclose(ex[0], [-2.0 / 1.0 * 1 + -0.5 / 4.25, -2.0 / 4.25], atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Objective, Eq. 1
+# --------------------------------------------------------------------------
+def test_objective_two_vertices():
+    rp, col = graphs.path(2)
+    S = oracle.build_S(rp, col, 1)
+    for D in (0.3, 1.0, 2.5):
+        x = np.array([[0.0, 0.0], [D, 0.0]])
+        stress, lns, M = oracle.objective(x, S, 0.008)
+        assert stress == pytest.approx((D - 1.0) ** 2)
+        assert lns == 0.0 and M == pytest.approx((D - 1.0) ** 2)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("n", [9, 40])
+def test_objective_regular_polygon(k, n):
+    # sum over all unordered pairs of ln|x_i - x_j| on a regular n-gon:
+    # prod_{j=1}^{n-1} 2 sin(pi j / n) = n gives (n/2) ((n-1) ln R + ln n).
+    R, alpha = 2.2, 0.008
+    rp, col = graphs.cycle(n)
+    S = oracle.build_S(rp, col, k)
+    x = polygon(n, R)
+    stress, lns, M = oracle.objective(x, S, alpha)
+    total = 0.5 * n * ((n - 1) * math.log(R) + math.log(n))
+    exp_stress = 0.0
+    for m in range(1, k + 1):
+        dist = 2 * R * math.sin(math.pi * m / n)
+        total -= n * math.log(dist)
+        exp_stress += n * (dist - m) ** 2 / m ** 2
+    assert lns == pytest.approx(total, rel=1e-12)
+    assert stress == pytest.approx(exp_stress, rel=1e-12)
+    assert M == pytest.approx(exp_stress - alpha * total, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# SCLaP (Sec. 3.1): invariants and order-free cases
+# --------------------------------------------------------------------------
+def _cluster_weights(labels, c):
+    w = {}
+    for v, L in enumerate(labels):
+        w[L] = w.get(L, 0.0) + c[v]
+    return w
+
+
+def test_sclap_matching_pairs():
+    n = 40
+    rp, col = graphs.csr_from_edges(n, np.arange(0, n, 2), np.arange(1, n, 2))
+    lab = oracle.sclap(rp, col, np.ones(n), U=2.0, rounds=10, seed=1, level=0)
+    for v in range(0, n, 2):
+        assert lab[v] == lab[v + 1]
+    assert len(set(lab.tolist())) == n // 2
+
+
+def test_sclap_star_one_cluster():
+    n = 30
+    rp, col = graphs.csr_from_edges(n, np.zeros(n - 1, dtype=int), np.arange(1, n))
+    for seed in range(5):
+        lab = oracle.sclap(rp, col, np.ones(n), U=float(n), rounds=10, seed=seed, level=0)
+        assert len(set(lab.tolist())) == 1
+
+
+@pytest.mark.parametrize("U", [2.0, 3.0, 7.5])
+def test_sclap_size_bound_and_partition(U):
+    rp, col, _, _ = graphs.rgg(2000, 8.0, 9, tune=False)
+    n = len(rp) - 1
+    c = np.ones(n)
+    lab = oracle.sclap(rp, col, c, U=U, rounds=10, seed=3, level=0)
+    assert lab.shape == (n,) and lab.min() >= 0 and lab.max() < n
+    w = _cluster_weights(lab, c)
+    assert max(w.values()) <= U
+    assert len(w) < n  # something merged
+
+
+# --------------------------------------------------------------------------
+# Contraction (Sec. 3.1): hand-worked example and invariants
+# --------------------------------------------------------------------------
+def test_contract_hand_example():
+    g = contract_example()
+    mp, cc, crp, ccol, cew = oracle.contract(g["rp"], g["col"], np.ones(g["n"]), g["labels"],
+                                             ew=g["ew"])
+    assert mp.tolist() == g["map"].tolist()
+    assert cc.tolist() == g["c"].tolist()
+    assert crp.tolist() == g["crp"].tolist()
+    assert ccol.tolist() == g["ccol"].tolist()
+    assert cew.tolist() == g["cew"].tolist()
+
+
+def test_contract_invariants():
+    rp, col, _, _ = graphs.rgg(3000, 8.0, 21, tune=False)
+    n = len(rp) - 1
+    c = np.ones(n)
+    lab = oracle.sclap(rp, col, c, U=4.0, rounds=10, seed=5, level=1)
+    mp, cc, crp, ccol, cew = oracle.contract(rp, col, c, lab)
+    nc = len(cc)
+    assert cc.sum() == n
+    src = np.repeat(np.arange(n), np.diff(rp))
+    cut = mp[src] != mp[col]
+    assert cew.sum() == cut.sum()  # sum of omega over cut entries is preserved
+    csrc = np.repeat(np.arange(nc), np.diff(crp))
+    assert np.all(csrc != ccol)  # no self-loops
+    pairs = set(zip(csrc.tolist(), ccol.tolist()))
+    assert all((b, a) in pairs for a, b in pairs)  # symmetric
+    assert len(graphs.largest_component(crp, ccol)[2]) == nc  # connected
+
+
+# --------------------------------------------------------------------------
+# Prolongation (Sec. 3.2)
+# --------------------------------------------------------------------------
+def test_prolong_radius_and_moments():
+    nf, nc = 200000, 3
+    mp = np.arange(nf) % nc
+    xc = np.array([[0.0, 0.0], [10.0, 5.0], [-4.0, 2.0]])
+    cc = np.array([1.0, 4.0, 9.0])
+    xf = oracle.prolong(mp, xc, cc, seed=77, level=2)
+    off = xf - xc[mp]
+    r = np.sqrt((off ** 2).sum(1))
+    R = np.sqrt(cc)[mp]
+    assert np.all(r <= R)
+    # radius uniform in [0, R): mean R/2, var R^2/12; angle uniform
+    t = r / R
+    assert abs(t.mean() - 0.5) < 0.005 and abs(t.var() - 1 / 12) < 0.002
+    ang = np.arctan2(off[:, 1], off[:, 0])
+    assert abs(np.cos(ang).mean()) < 0.01 and abs(np.sin(ang).mean()) < 0.01
+    # reproducible, and different levels draw different numbers
+    assert np.array_equal(xf, oracle.prolong(mp, xc, cc, seed=77, level=2))
+    assert not np.array_equal(xf, oracle.prolong(mp, xc, cc, seed=77, level=3))
+
+
+# --------------------------------------------------------------------------
+# alpha schedule (Sec. 3.2, Sec. 4 'Algorithm Configuration')
+# --------------------------------------------------------------------------
+def test_alpha_rounds_values():
+    p = oracle.params()
+    assert oracle.alpha_rounds(p) == pytest.approx([1.0, 0.3, 0.09, 0.027, 0.0081, 0.008])
+
+
+def test_schedule_counts():
+    rp, col = graphs.path(2)
+    S = oracle.build_S(rp, col, 1)
+    x = np.array([[-0.5, 0.0], [0.5, 0.0]])   # fixed point: every round exits after 1
+    p = oracle.params()
+    _, sweeps = oracle.schedule(S, x, p, 0)
+    assert sweeps == 6
+    p = oracle.params(early_exit=0, max_iters_at_min=90)
+    _, sweeps = oracle.schedule(S, x, p, 0)
+    assert sweeps == 100
+
+
+def test_layout_small_multilevel_runs():
+    rp, col = graphs.grid(12, 12)
+    p = oracle.params(k=2, theta=0.5, coarsest_n=2, seed=4)
+    x, info = oracle.layout(rp, col, p)
+    assert x.shape == (144, 2) and np.all(np.isfinite(x))
+    levels = info["levels"]
+    assert levels[-1]["n"] <= 2
+    for a, b in zip(levels[:-1], levels[1:]):
+        assert b["n"] < a["n"]
+        assert b["c"].sum() == 144
+    # the layout is far better than the random start in Eq. 1
+    S = levels[0]["S"]
+    M_lay = oracle.objective(x, S, 0.008)[2]
+    M_rand = oracle.objective(graphs.uniform_positions(144, 1, 0, 12), S, 0.008)[2]
+    assert M_lay < M_rand
