@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MulMent layout (multilevel maxent-stress, Sec. 3).
+
+One step = one full multilevel layout of the workload graph through
+mm_layout (every level: prolongation + the alpha schedule of Eq. 2 sweeps,
+each sweep = Barnes-Hut tree rebuild + walk + fused gather/update +
+controller), with the hierarchy already built and resident in HBM.
+
+  value  = vertex updates (sum over sweeps of the level size) per second
+  e2e    = the same metric through the one-call host API mm_layout_host
+           (host CSR in, host layout out: H2D copy, hierarchy build, layout,
+           D2H copy all inside the timed region)
+
+Default workload: random geometric graph, 100,000 points uniform in the unit
+square, radius tuned for mean degree 8, largest component, k = 2,
+theta = 0.5, coarsening to <= 100 vertices.  L2 (129 MB) is flushed by a
+256 MB write before every timed step.
+
+Multi-GPU (torchrun, N > 1): replicas only -- every rank lays out its own
+copy; value = all ranks' vertex updates / max rank time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (Barnes-Hut sweeps of the finest level).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "vertex-updates/s per sweep; time-to-layout at oracle-matched maxent-stress"
+UNIT = "vertex-updates/s"
+
+WORKLOADS = {
+    "rgg100k": dict(kind="rgg", n=100000, deg=8.0, seed=1506, k=2, theta=0.5, coarsest_n=100,
+                    desc="random geometric graph, 100k points in the unit square, mean degree 8, "
+                         "largest component, k=2, Barnes-Hut theta=0.5, coarsen to <=100"),
+    "grid32": dict(kind="grid", nx=32, ny=32, k=2, exact=1, single=100,
+                   desc="32x32 grid, k=2, exact O(n^2) repulsion, uniform [0,1]^2 start, "
+                        "100 Jacobi sweeps (single level)"),
+    "rmat20": dict(kind="rmat", scale=20, ef=8, seed=1506, k=1, theta=0.6, coarsest_n=100,
+                   desc="R-MAT scale 20 (a=0.57 b=c=0.19), 8 edge samples per vertex, largest "
+                        "component, k=1, theta=0.6"),
+    "del20": dict(kind="delaunay", n=1 << 20, seed=1506, k=1, theta=0.6, coarsest_n=100,
+                  desc="Delaunay triangulation of 2^20 uniform points, k=1, theta=0.6"),
+}
+
+
+def make_graph(w):
+    from paper_1506_04383_gb300 import graphs
+    if w["kind"] == "rgg":
+        rp, col, _, _ = graphs.rgg(w["n"], w["deg"], w["seed"])
+    elif w["kind"] == "grid":
+        rp, col = graphs.grid(w["nx"], w["ny"])
+    elif w["kind"] == "rmat":
+        rp, col = graphs.rmat(w["scale"], w["ef"], w["seed"])
+    else:
+        rp, col, _ = graphs.delaunay(w["n"], w["seed"])
+    return rp, col
+
+
+def params_of(mm, w):
+    kw = dict(k=w["k"])
+    if w.get("single"):
+        kw.update(exact_repulsion=w.get("exact", 0), early_exit=0,
+                  max_iters_at_min=w["single"] - 10)
+    else:
+        kw.update(theta=w["theta"], coarsest_n=w["coarsest_n"])
+    return kw
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(w, rp, col, budget_s=15.0, per_step=None):
+    """The FP64 oracle as it stands: Barnes-Hut (or exact) Eq. 2 sweeps of the
+    finest level on the host cores.  Returns (vertex-updates/s, cores, sample)."""
+    import numpy as np
+    import oracle
+    from paper_1506_04383_gb300 import graphs
+    n = len(rp) - 1
+    S = oracle.build_S(rp, col, w["k"])
+    x = graphs.uniform_positions(n, 1506, 0.0, math.sqrt(n))
+    exact = bool(w.get("exact"))
+    theta = w.get("theta", 0.5)
+    sweeps, t0 = 0, time.perf_counter()
+    while True:
+        x, _ = oracle.sweep(x, S, 0.3, 0 if exact else 1, theta)
+        sweeps += 1
+        el = time.perf_counter() - t0
+        if (per_step and sweeps >= per_step) or (not per_step and el >= budget_s):
+            break
+    sample = (f"{sweeps} {'exact' if exact else 'Barnes-Hut theta=%g' % theta} Eq. 2 sweeps "
+              f"of the finest level (n={n}, |S|={len(S[1])}), FP64 oracle, OpenMP")
+    return n * sweeps / el, oracle.num_threads(), sample, el
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    rp, col = make_graph(w)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample, el = cpu_baseline(w, rp, col, per_step=1)
+        if i >= args.warmup:
+            steps.append((v, el))
+    value = sum(len(rp) - 1 for _ in steps) / sum(el for _, el in steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(el for _, el in steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": w["desc"], "n": len(rp) - 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rgg100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1506_04383_gb300 import build as _build, mm
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    mm.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    rp, col = make_graph(w)
+    n = len(rp) - 1
+    kw = params_of(mm, w)
+    p = mm.default_params(**kw)
+    drp = torch.from_numpy(rp).cuda()
+    dcol = torch.from_numpy(col).cuda()
+    x_init = None
+    if w.get("single"):
+        from paper_1506_04383_gb300 import graphs
+        x_init = torch.from_numpy(graphs.uniform_positions(n, 1506).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    h = mm.build_hierarchy(drp, dcol, p)
+    e1.record()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    xbuf = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        _, st = mm.layout(h, p, x_init=x_init, x_out=xbuf)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stats = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.fill_(1)
+            a.record()
+            _, st = mm.layout(h, p, x_init=x_init, x_out=xbuf)
+            b.record()
+            stats.append(st)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    vu = stats[-1]["vertex_updates"]
+    value = world * vu * args.steps / (total_ms / 1e3)
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # quality: objective of the final layout (Eq. 1 at alpha = 0.008)
+    _, _, M = mm.objective(h, 0, xbuf, 0.008)
+
+    # roofline of the dominant kernel on the finest level, live with events
+    prof = mm.sweep_profile(h, 0, xbuf, reps=10)
+    peaks, src = measured_peaks()
+    clk_sum = clk.summary()
+    roof = roofline(prof, peaks, src, clk_sum, n)
+
+    # end to end through the host API (pinned host buffers)
+    e2e = None
+    if args.e2e_steps > 0:
+        prp = torch.from_numpy(rp).pin_memory().numpy()
+        pcol = torch.from_numpy(col).pin_memory().numpy()
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xh, sth = mm.layout_host(prp, pcol, p)
+            t1 = time.perf_counter()
+            if i > 0:
+                times.append(t1 - t0)
+        e2e = {"value": sth["vertex_updates"] / statistics.mean(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(prp.nbytes + pcol.nbytes),
+               "d2h_bytes_per_step": int(xh.nbytes),
+               "time_to_layout_s": statistics.mean(times)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample, el = cpu_baseline(w, rp, col, budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": round(el, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "n": n,
+                       "m": int(len(col) // 2), "levels": stats[-1]["num_levels"],
+                       "level_n": stats[-1]["level_n"],
+                       "sweeps": stats[-1]["total_sweeps"],
+                       "level_sweeps": stats[-1]["level_sweeps"],
+                       "vertex_updates_per_step": vu, "l2": "flushed (256 MB write) before "
+                       "every timed step", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "time_to_layout_s": (build_ms + statistics.mean(step_ms)) / 1e3,
+            "hierarchy_build_ms": build_ms,
+            "objective_M": M,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk_sum,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(prof, peaks, src, clk, n):
+    """Dominant kernel of a finest-level sweep against its roofline.
+
+    traverse (Barnes-Hut walk): ALU bound; algorithmic work = 10 FP32 ops per
+    lane interaction (accepted cell or leaf point), peak = 152 SMs x 128 FP32
+    lanes x 2 (FMA) x SM clock.  gather: HBM bound; algorithmic bytes per
+    vertex = 4 (row_ptr) + 8 (x_u) + 8 (x'_u) + 8 (F_u) + 4 (rho_u) + 8 per S
+    entry (col, d); neighbour positions are L2 hits and not counted.
+    sort: HBM bound; 4 passes x (4 B key read in the histogram pass + 8 B
+    read + 8 B write in the scatter pass) per element.
+    """
+    st = prof["stage_ms"]
+    names = prof["stage_names"]
+    dom = max(range(len(st)), key=lambda i: st[i])
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nnzS = prof["nnz_S"]
+    kern = {}
+    t_trav = st[names.index("traverse")] / 1e3
+    flops = 10.0 * prof["interactions"]
+    kern["traverse"] = {"bound": "alu", "achieved": flops / t_trav / 1e12, "peak": alu_peak,
+                        "unit": "TFLOP/s", "traffic": None,
+                        "note": f"peak = 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"}
+    t_g = st[names.index("gather")] / 1e3
+    gbytes = n * 32.0 + nnzS * 8.0
+    kern["gather"] = {"bound": "hbm", "achieved": gbytes / t_g / 1e9, "peak": hbm, "unit": "GB/s",
+                      "traffic": None}
+    t_s = st[names.index("sort")] / 1e3
+    sbytes = 4 * (4.0 + 16.0) * n
+    kern["sort"] = {"bound": "hbm", "achieved": sbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "traffic": None}
+    for v in kern.values():
+        v["frac"] = v["achieved"] / v["peak"]
+        v["peak_source"] = src
+    name = names[dom]
+    out = dict(kern.get(name, kern["traverse"]))
+    out["kernel"] = name if name in kern else "traverse"
+    out["stage_ms"] = dict(zip(names, st))
+    out["others"] = {k: {kk: vv for kk, vv in v.items() if kk in ("achieved", "peak", "unit",
+                                                                   "frac", "bound")}
+                     for k, v in kern.items() if k != out["kernel"]}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

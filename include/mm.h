@@ -1,0 +1,326 @@
+/*
+ * mm.h -- C-ABI of the GB300 MulMent library (libmm.so).
+ *
+ * MulMent: multilevel maxent-stress graph layout (Meyerhenke, Noellenburg,
+ * Schulz, arXiv 1506.04383).  The library computes a 2-D layout x of an
+ * undirected connected graph by iterating the local update of Eq. 2 on every
+ * level of a coarsening hierarchy (Sec. 3), with the long-range entropy term
+ * approximated by a Barnes-Hut quadtree rebuilt on the GPU every iteration.
+ *
+ * Conventions for every call:
+ *   - Positions are float32 pairs, x[2*v] = x-coordinate, x[2*v+1] = y.
+ *   - Graphs are symmetric CSR: row_ptr[n+1] (int64), col[nnz] (int32), rows
+ *     sorted strictly ascending, no self-loops, every edge stored in both
+ *     directions.  The paper's input model (Sec. 2.1) is an undirected,
+ *     connected graph with unit node weights, unit edge weights and target
+ *     edge lengths d (default 1).
+ *   - "device" pointers are CUDA device memory of the current device; "host"
+ *     pointers are ordinary CPU memory.  The caller owns every buffer it
+ *     passes; inputs are only read during the call (the hierarchy copies what
+ *     it keeps); the library owns mm_hierarchy objects.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is ordered on it.  Calls that write host
+ *     outputs synchronise the stream before returning.
+ *   - Every call returns an mm_status; no exception or exit crosses the ABI.
+ *     mm_last_error() gives a message for the last failure on this thread.
+ *   - There is no CPU fallback: without a usable GPU the calls return
+ *     MM_ERR_CUDA.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mm_status;
+#define MM_OK 0
+#define MM_ERR_INVALID_ARG 1   /* malformed graph, bad level, bad sizes      */
+#define MM_ERR_NOT_CONNECTED 2 /* the input graph is not connected (Sec. 2.1)*/
+#define MM_ERR_CUDA 3          /* a CUDA runtime call failed                 */
+#define MM_ERR_OOM 4           /* device allocation failed                   */
+#define MM_ERR_NONFINITE 5     /* a sweep produced NaN or Inf coordinates    */
+#define MM_ERR_TIMEOUT 6       /* a bounded device wait gave up              */
+#define MM_ERR_UNSUPPORTED 7   /* valid request outside the implemented range*/
+
+#define MM_PARAMS_VERSION 1u
+#define MM_MAX_LEVELS 64
+
+/*
+ * Algorithm parameters.  Defaults (mm_default_params) are the paper's
+ * configuration (Sec. 4, "Algorithm Configuration"): f = 20, b = 2,
+ * alpha0 = 1, alpha := 0.3 alpha down to alpha_min = 0.008, at most a = 2
+ * iterations per alpha, at alpha_min iterate until the relative change is
+ * below 1e-4.  k, theta and coarsest_n select the general model and the
+ * Barnes-Hut approximation.
+ */
+typedef struct mm_params {
+  uint32_t struct_version;  /* must be MM_PARAMS_VERSION                      */
+  int32_t k;                /* S = pairs within k hops (1 or 2); k=1 is S=E   */
+  float theta;              /* Barnes-Hut opening parameter; 0 = exact via tree*/
+  int32_t exact_repulsion;  /* 1: exact O(n^2) entropy sum on every level     */
+  int32_t coarsest_n;       /* coarsen while n > coarsest_n (>= 2)            */
+  float f, b;               /* SCLaP W = min(b^(h+1), n/f) (Sec. 3.1)         */
+  int32_t lp_rounds;        /* SCLaP rounds l                                 */
+  int32_t iters_per_alpha;  /* a: iterations per alpha round                  */
+  double alpha0, alpha_factor, alpha_min;
+  double eps;               /* early alpha reduction threshold                */
+  double eps_final;         /* convergence threshold at alpha_min             */
+  int32_t max_iters_at_min; /* cap on iterations at alpha_min                 */
+  int32_t early_exit;       /* 0: run exactly a / max_iters_at_min iterations */
+  uint64_t seed;            /* Philox key for prolongation and clustering     */
+  int32_t max_levels;       /* hierarchy depth cap (<= MM_MAX_LEVELS)         */
+  int32_t max_stalls;       /* retries of a contraction that merged nothing   */
+  int32_t gather_lanes;     /* lanes per vertex in the S gather; 0 = auto     */
+  int32_t heavy_degree;     /* rows above this use a block each; 0 = auto     */
+  int32_t traverse_warps;   /* warps per block in the tree walk; 0 = auto     */
+  int32_t reserved[7];
+} mm_params;
+
+/* A graph on the device (the input of mm_build_hierarchy). */
+typedef struct mm_graph {
+  int32_t n;                /* vertices                                       */
+  int64_t nnz;              /* CSR entries (2 x edges)                        */
+  const int64_t* row_ptr;   /* device [n+1]                                   */
+  const int32_t* col;       /* device [nnz]                                   */
+  const float* edge_len;    /* device [nnz] target lengths d, or NULL for 1   */
+  int32_t num_graphs;       /* 1, or >1 for a block-diagonal batch            */
+  const int32_t* graph_ptr; /* host [num_graphs+1] vertex offsets, or NULL    */
+} mm_graph;
+
+/* Per-layout statistics written by mm_layout (host struct). */
+typedef struct mm_layout_stats {
+  int32_t num_levels;
+  int32_t total_sweeps;
+  int64_t vertex_updates;              /* sum over sweeps of the level size   */
+  int32_t level_n[MM_MAX_LEVELS];
+  int32_t level_sweeps[MM_MAX_LEVELS];
+  double final_alpha;
+  double final_rel_change;
+  double final_stress;                 /* stress over S of the finest level   */
+  int64_t kernel_launches;             /* library kernels launched by the call*/
+} mm_layout_stats;
+
+typedef struct mm_hierarchy mm_hierarchy;
+
+/* Fills p with the paper's defaults (see mm_params). */
+void mm_default_params(mm_params* p);
+
+/* Static description of a status code; never NULL. */
+const char* mm_status_string(mm_status s);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* mm_last_error(void);
+
+/*
+ * Builds the coarsening hierarchy of Sec. 3.1 on the device: level 0 is the
+ * input graph; level h+1 is the contraction of a size-constrained label
+ * propagation clustering of level h with U = max(max c, min(b^(h+1), n/f)).
+ * A contraction that shrinks the graph by at most 10 percent sets f := 0.7f.
+ * For every level it also builds the pair set S (k hops) with target
+ * distances d (Sec. 3.2: sqrt(c_u) + sqrt(c_v) per edge on coarse levels)
+ * and rho_u = sum_S d^-2 (Eq. 2), and sizes the per-sweep workspaces.
+ *   g       device graph (validated: CSR shape, symmetry, connectivity)
+ *   p       parameters (k, coarsest_n, f, b, lp_rounds, seed, ...)
+ *   out     receives the hierarchy; free with mm_free_hierarchy
+ * Errors: MM_ERR_INVALID_ARG (malformed graph or params),
+ * MM_ERR_NOT_CONNECTED, MM_ERR_OOM, MM_ERR_UNSUPPORTED (k not 1 or 2,
+ * more than 2^31 - 1 pair entries), MM_ERR_CUDA.  Synchronises `stream`.
+ */
+mm_status mm_build_hierarchy(const mm_graph* g, const mm_params* p,
+                             void* stream, mm_hierarchy** out);
+
+/* One level of a caller-supplied hierarchy (device pointers). */
+typedef struct mm_level_desc {
+  int32_t n;
+  int64_t nnz;
+  const int64_t* row_ptr;   /* device [n+1]                                   */
+  const int32_t* col;       /* device [nnz], symmetric CSR as for mm_graph    */
+  const float* omega;       /* device [nnz] edge weights, or NULL for 1       */
+  const float* node_c;      /* device [n] node weights c, or NULL for 1       */
+  const int32_t* map;       /* device [n] -> vertex of level+1; NULL on the   */
+                            /* last level                                     */
+} mm_level_desc;
+
+/*
+ * Same as mm_build_hierarchy, but the coarsening (Sec. 3.1) is supplied by
+ * the caller instead of computed: level 0 is the input graph (target lengths
+ * edge_len0, device [nnz] or NULL for 1); each coarser level's pairs use
+ * d = sqrt(c_u) + sqrt(c_v) (Sec. 3.2).  Every level's CSR is validated and
+ * every map entry must lie in [0, n of the next level).
+ */
+mm_status mm_build_hierarchy_levels(int32_t num_levels,
+                                    const mm_level_desc* levels,
+                                    const float* edge_len0, const mm_params* p,
+                                    void* stream, mm_hierarchy** out);
+
+/* Releases a hierarchy and its device memory.  NULL is ignored. */
+void mm_free_hierarchy(mm_hierarchy* h);
+
+/* Number of levels (level 0 = input graph). */
+mm_status mm_hierarchy_levels(const mm_hierarchy* h, int32_t* num_levels);
+
+/* Sizes of one level: vertices, CSR entries of E, entries of S (host out). */
+mm_status mm_level_info(const mm_hierarchy* h, int32_t level, int32_t* n,
+                        int64_t* nnz_E, int64_t* nnz_S);
+
+/*
+ * Copies one level's data into caller device buffers (each may be NULL):
+ * the level's CSR (row_ptr int64 [n+1], col [nnzE], omega [nnzE] edge
+ * weights of Sec. 3.1), node weights c [n], the map to the next coarser
+ * level [n] (undefined on the coarsest), and S (s_ptr int64 [n+1], s_col
+ * [nnzS], s_d [nnzS], rho [n]).
+ */
+mm_status mm_level_export(const mm_hierarchy* h, int32_t level,
+                          int64_t* row_ptr, int32_t* col, float* omega,
+                          float* c, int32_t* map, int64_t* s_ptr,
+                          int32_t* s_col, float* s_d, float* rho,
+                          void* stream);
+
+/*
+ * One Jacobi iteration of Eq. 2 on `level` (Sec. 3.2), general model over S:
+ *   x'_u = (1/rho_u) sum_{v in S_u} w_uv (x_v + d_uv (x_u-x_v)/|x_u-x_v|)
+ *        + (alpha/rho_u) sum_{v not in S_u, v != u} r(u,v),
+ * r(u,v) = (x_u-x_v)/|x_u-x_v|^2.  The entropy sum is the Barnes-Hut total
+ * over all v (quadtree rebuilt from x_in, opening parameter theta from the
+ * build parameters) minus the exact r-values over S, or the exact O(n^2) sum
+ * when the hierarchy was built with exact_repulsion = 1.  A coincident pair
+ * contributes a zero unit vector and a zero r-value.
+ *   x_in, x_out  device [2n], must not overlap
+ *   stats        host [3] or NULL: sum|x'-x|^2, sum|x|^2 and the stress of
+ *                x_in over the unordered pairs of S (Eq. 1); non-NULL
+ *                synchronises the stream.
+ * Errors: MM_ERR_INVALID_ARG, MM_ERR_NONFINITE (stats requested and the
+ * result is not finite), MM_ERR_CUDA.
+ */
+mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha,
+                   const float* x_in, float* x_out, double* stats,
+                   void* stream);
+
+/*
+ * The long-range sum F_u = sum_{v != u} r(u,v) over all vertices of `level`
+ * (the quantity Barnes-Hut approximates).  theta > 0: quadtree with that
+ * opening parameter; theta == 0: quadtree opened completely (exact);
+ * theta < 0: the tiled exact O(n^2) kernel.
+ *   x device [2n], F_out device [2n].
+ */
+mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x,
+                       float theta, float* F_out, void* stream);
+
+/*
+ * The multilevel layout of Sec. 3: initial layout of the coarsest level (two
+ * vertices at their target distance; more than two placed around the origin
+ * and refined), then for every finer level a random polar prolongation
+ * (angle in [0, 2pi), radius in [0, sqrt(c(v'))), Philox keyed by p->seed)
+ * followed by the alpha schedule of Sec. 3.2.  The whole schedule runs on the
+ * device (CUDA graph with a device-side loop); the host waits once.
+ *   p        schedule parameters (alpha0, alpha_factor, alpha_min, eps,
+ *            eps_final, iters_per_alpha, max_iters_at_min, early_exit, seed);
+ *            NULL = the parameters given to mm_build_hierarchy
+ *   x_init   device [2 n0] or NULL.  Non-NULL runs the schedule on level 0
+ *            only, starting from x_init (resume / dynamic update, Sec. 4.3).
+ *   x_out    device [2 n0]
+ *   stats    host or NULL
+ * Errors: MM_ERR_NONFINITE, MM_ERR_INVALID_ARG, MM_ERR_CUDA.
+ */
+mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init,
+                    float* x_out, mm_layout_stats* stats, void* stream);
+
+/*
+ * Per-stage timing of one sweep on `level` (no paper counterpart; a
+ * measurement aid): the sweep of mm_sweep is run `reps` times from x with
+ * CUDA events between its stages, and the mean milliseconds per stage are
+ * written to stage_ms (host [8]): bbox, morton, sort, radix-tree, bottom-up,
+ * traverse (or the exact O(n^2) kernel), gather, controller.  work (host
+ * [4]) receives the walk's warp node visits and lane interactions (from one
+ * instrumented walk), |S| and n.  alpha = 0.3.  x device [2n], unchanged.
+ */
+mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
+                           int32_t reps, double* stage_ms, int64_t* work,
+                           void* stream);
+
+/*
+ * Maxent-stress objective, Eq. 1, general model over S of `level`:
+ *   M(x) = sum_{{u,v} in S} w_uv (|x_u-x_v| - d_uv)^2
+ *        - alpha sum_{{u,v} not in S, u != v} ln|x_u - x_v|
+ * over unordered pairs, exact (all O(n^2) pairs on the device, FP64
+ * accumulation).  Coincident pairs contribute 0 to the ln-sum.
+ *   x device [2n]; stress, lnsum, M host outputs (each may be NULL).
+ * Synchronises the stream.
+ */
+mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x,
+                       double alpha, double* stress, double* lnsum, double* M,
+                       void* stream);
+
+/*
+ * The k-hop pair set S of an arbitrary graph (Sec. 2.3 footnote): for every
+ * u, all v != u within k hops (k = 1 or 2), d_uv = the shortest such path
+ * with edge length edge_len (or 1) -- or sqrt(c_u) + sqrt(c_v) when node_c is
+ * given (coarse-level lengths, Sec. 3.2) -- and rho_u = sum d^-2.  Rows are
+ * ascending in v.
+ *   row_ptr/col device CSR; edge_len, node_c device or NULL.
+ *   First call with s_col == NULL: writes s_ptr (device int64 [n+1]) and
+ *   *nnz_S (host).  Second call with s_col [nnz_S], s_d [nnz_S], rho [n]
+ *   fills S.  Synchronises the stream.
+ */
+mm_status mm_khop(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                  const float* edge_len, const float* node_c, int32_t k,
+                  int64_t* s_ptr, int64_t* nnz_S, int32_t* s_col, float* s_d,
+                  float* rho, void* stream);
+
+/*
+ * Size-constrained label propagation (Sec. 3.1) on the device: `rounds`
+ * synchronous rounds in two seeded halves; a vertex moves to the
+ * neighbouring cluster of strongest omega-connection whose weight stays
+ * <= U; concurrent moves into one cluster are admitted in a seeded priority
+ * order while the bound holds.  labels_out device [n].
+ */
+mm_status mm_cluster(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                     const float* omega, const float* node_c, float U,
+                     int32_t rounds, uint64_t seed, int32_t level,
+                     int32_t* labels_out, void* stream);
+
+/*
+ * Cluster contraction (Sec. 3.1): one coarse node per distinct label (coarse
+ * id = rank of the label), c' = sum of member weights, coarse edge {a,b}
+ * iff some fine edge joins the blocks, omega' = sum of the joining weights
+ * (summed in fine-entry order).  Coarse rows ascending.
+ *   labels device [n] in [0, n).  Outputs (device): map [n], c_out
+ *   [capacity n], crow_ptr int64 [capacity n+1], ccol and comega [capacity
+ *   nnz]; n_coarse and nnz_coarse are host outputs.  Synchronises.
+ */
+mm_status mm_contract(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                      const float* omega, const float* node_c,
+                      const int32_t* labels, int32_t* map, float* c_out,
+                      int64_t* crow_ptr, int32_t* ccol, float* comega,
+                      int32_t* n_coarse, int64_t* nnz_coarse, void* stream);
+
+/*
+ * Prolongation (Sec. 3.2): x_fine[v] = x_coarse[map[v]] + rad (cos phi,
+ * sin phi), phi = 2 pi U1, rad = sqrt(c_coarse[map[v]]) U2, with U1, U2 the
+ * top 24 bits of words 0 and 1 of Philox4x32-10(counter = (v, level, 0, 0),
+ * key = seed) scaled to [0, 1).  All pointers device.
+ */
+mm_status mm_prolong(int32_t n_fine, const int32_t* map,
+                     const float* x_coarse, const float* c_coarse,
+                     uint64_t seed, int32_t level, float* x_fine,
+                     void* stream);
+
+/*
+ * One-call convenience API with HOST buffers: copies the CSR to the device,
+ * builds the hierarchy, runs mm_layout and copies the layout back.
+ *   row_ptr host [n+1], col host [nnz], edge_len host [nnz] or NULL,
+ *   x_out host [2n], stats host or NULL.
+ */
+mm_status mm_layout_host(int32_t n, const int64_t* row_ptr,
+                         const int32_t* col, const float* edge_len,
+                         const mm_params* p, float* x_out,
+                         mm_layout_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

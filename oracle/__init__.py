@@ -313,14 +313,20 @@ def alpha_rounds(p):
     return out
 
 
-def schedule(S, x, p, rep_mode: int, trace=None):
+def schedule(S, x, p, rep_mode: int, trace=None, start_at_min: bool = False):
     """Rounds of Jacobi iterations (Sec. 3.2): at most iters_per_alpha
     iterations per alpha, fewer if the relative change drops below eps; at
     alpha_min iterate until the relative change is below eps_final (capped at
-    max_iters_at_min).  early_exit = 0 runs the caps exactly."""
+    max_iters_at_min).  early_exit = 0 runs the caps exactly.  One schedule
+    spans the whole multilevel run: it starts at alpha0 on the coarsest level,
+    which ends only once alpha_min is reached and converged, so every finer
+    level runs at alpha_min (start_at_min)."""
     x = _f64(x).reshape(-1, 2)
     sweeps = 0
-    for alpha in alpha_rounds(p):
+    rounds = alpha_rounds(p)
+    if start_at_min:
+        rounds = rounds[-1:]
+    for alpha in rounds:
         at_min = alpha <= p["alpha_min"]
         cap = p["max_iters_at_min"] if at_min else p["iters_per_alpha"]
         tol = p["eps_final"] if at_min else p["eps"]
@@ -351,8 +357,10 @@ def initial_layout(L, p, level_index):
 
 
 def layout(rp, col, p, elen=None, x_init=None, levels=None, trace=None):
-    """Multilevel maxent-stress layout (Sec. 3).  With x_init the schedule
-    runs on the finest level only, from x_init.  Returns (x, info)."""
+    """Multilevel maxent-stress layout (Sec. 3).  alpha is set to alpha0
+    once, at the start (coarsest level), and reduced by rounds down to
+    alpha_min; the finer levels refine at alpha_min.  With x_init the whole
+    schedule runs on the finest level only, from x_init.  Returns (x, info)."""
     if levels is None:
         levels = build_hierarchy(rp, col, p, elen=elen)
     rep_fine = 0 if p["exact_repulsion"] else 1
@@ -366,6 +374,6 @@ def layout(rp, col, p, elen=None, x_init=None, levels=None, trace=None):
     sweeps.append(s)
     for h in range(top - 1, -1, -1):
         x = prolong(levels[h]["map"], x, levels[h + 1]["c"], p["seed"], h)
-        x, s = schedule(levels[h]["S"], x, p, rep_fine, trace)
+        x, s = schedule(levels[h]["S"], x, p, rep_fine, trace, start_at_min=True)
         sweeps.append(s)
     return x, dict(levels=levels, sweeps=sweeps[::-1])

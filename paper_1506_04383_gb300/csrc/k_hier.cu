@@ -1,0 +1,620 @@
+// Hierarchy construction on the device (Sec. 3.1) and the per-level pair
+// set S (Sec. 2.3 footnote, Sec. 3.2):
+//   * input validation (CSR shape, sorted rows, symmetry, no self-loops);
+//   * k-hop S with shortest <=k-hop distances (k = 1 copies E; k = 2
+//     enumerates 1- and 2-hop paths, sorts (u, v) keys and keeps the minimum
+//     length per pair);
+//   * size-constrained label propagation (synchronous rounds in two seeded
+//     halves, warp per vertex with a shared-memory hash of neighbouring
+//     clusters, concurrent moves into a cluster admitted in seeded priority
+//     order while the size bound holds);
+//   * contraction (rank relabelling, sorted coarse edge keys, weights summed
+//     in fine-entry order).
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+
+// RAII device buffer for temporaries of the build phase.
+struct Tmp {
+  void* p = nullptr;
+  ~Tmp() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T* as() const { return (T*)p; }
+};
+
+mm_status tmp_alloc(Tmp& t, size_t bytes) {
+  MM_CK(cudaMalloc(&t.p, bytes > 0 ? bytes : 16));
+  return MM_OK;
+}
+
+int bits_for(int64_t v) {  // bits needed to hold values in [0, v]
+  int b = 1;
+  while (b < 62 && ((int64_t)1 << b) <= v) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------ validation --
+enum : int {
+  kBadRowPtr = 1, kBadCol = 2, kSelfLoop = 4, kUnsorted = 8, kAsym = 16
+};
+
+__global__ void validate_kernel(int n, int64_t nnz, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, int32_t* rp32, int* flags) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u > n) return;
+  const int64_t b = rp[u];
+  rp32[u] = (int32_t)b;
+  if (u == 0 && b != 0) atomicOr(flags, kBadRowPtr);
+  if (u == n) {
+    if (b != nnz) atomicOr(flags, kBadRowPtr);
+    return;
+  }
+  const int64_t e = rp[u + 1];
+  if (e < b || e > nnz) {
+    atomicOr(flags, kBadRowPtr);
+    return;
+  }
+  int prev = -1;
+  for (int64_t i = b; i < e; ++i) {
+    const int v = col[i];
+    if (v < 0 || v >= n) { atomicOr(flags, kBadCol); return; }
+    if (v == u) atomicOr(flags, kSelfLoop);
+    if (v <= prev) atomicOr(flags, kUnsorted);
+    prev = v;
+    // symmetry: u must appear in row v (binary search; rows sorted)
+    int64_t lo = rp[v], hi = rp[v + 1] - 1;
+    if (lo < 0 || hi >= nnz) { atomicOr(flags, kBadRowPtr); return; }
+    bool found = false;
+    while (lo <= hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const int w = col[mid];
+      if (w == u) { found = true; break; }
+      if (w < u) lo = mid + 1; else hi = mid - 1;
+    }
+    if (!found) atomicOr(flags, kAsym);
+  }
+}
+
+// ------------------------------------------------------------ k-hop S ---
+__device__ __forceinline__ float edge_length(const float* c, const float* elen, int e, int a,
+                                             int b) {
+  if (c) return sqrtf(c[a]) + sqrtf(c[b]);
+  return elen ? elen[e] : 1.f;
+}
+
+__global__ void khop1_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const float* __restrict__ c, const float* __restrict__ elen,
+                             int32_t* sp, SEnt* S, float* rho) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u > n) return;
+  sp[u] = rp[u];
+  if (u == n) return;
+  float r = 0.f;
+  for (int e = rp[u]; e < rp[u + 1]; ++e) {
+    const int v = col[e];
+    const float d = edge_length(c, elen, e, u, v);
+    S[e].col = v;
+    S[e].d = d;
+    r += 1.f / (d * d);
+  }
+  rho[u] = r;
+}
+
+__global__ void khop2_count(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            int32_t* cnt) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int64_t s = rp[u + 1] - rp[u];
+  for (int e = rp[u]; e < rp[u + 1]; ++e) {
+    const int w = col[e];
+    s += rp[w + 1] - rp[w];
+  }
+  cnt[u] = (int32_t)min(s, (int64_t)0x7fffffff);
+}
+
+// Emits (u, v, length) for every path of one or two edges out of u.
+__global__ void khop2_emit(int n, int vb, const int32_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, const float* __restrict__ c,
+                           const float* __restrict__ elen, const int64_t* __restrict__ off,
+                           uint64_t* keys, int32_t* dbits) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int64_t o = off[u];
+  for (int e = rp[u]; e < rp[u + 1]; ++e) {
+    const int w = col[e];
+    const float l1 = edge_length(c, elen, e, u, w);
+    keys[o] = ((uint64_t)u << vb) | (uint64_t)w;
+    dbits[o] = __float_as_int(l1);
+    ++o;
+    for (int f = rp[w]; f < rp[w + 1]; ++f) {
+      const int v = col[f];
+      const float l2 = l1 + edge_length(c, elen, f, w, v);
+      // the path back to u itself is padded with an impossible key (u, u)
+      keys[o] = ((uint64_t)u << vb) | (uint64_t)(v == u ? u : v);
+      dbits[o] = v == u ? __float_as_int(CUDART_INF_F) : __float_as_int(l2);
+      ++o;
+    }
+  }
+}
+
+__global__ void run_heads(int m, const uint64_t* __restrict__ keys, int32_t* head) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// One thread per run of equal (u, v) keys: minimum length, skipping (u, u).
+__global__ void khop2_reduce(int m, int vb, const uint64_t* __restrict__ keys,
+                             const int32_t* __restrict__ dbits, const int32_t* __restrict__ head,
+                             const int32_t* __restrict__ pos, SEnt* S, int32_t* rowcnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !head[i]) return;
+  const uint64_t k = keys[i];
+  const int u = (int)(k >> vb);
+  const int v = (int)(k & (((uint64_t)1 << vb) - 1));
+  float d = __int_as_float(dbits[i]);
+  for (int j = i + 1; j < m && keys[j] == k; ++j) d = fminf(d, __int_as_float(dbits[j]));
+  S[pos[i]].col = v;
+  S[pos[i]].d = d;
+  if (u != v) atomicAdd(&rowcnt[u], 1);
+}
+
+// Removes the (u, u) padding entries while copying into the final rows.
+__global__ void khop2_finish(int n, const int32_t* __restrict__ sp_tmp, const SEnt* __restrict__ S_tmp,
+                             const int32_t* __restrict__ sp, SEnt* S, float* rho) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  int o = sp[u];
+  float r = 0.f;
+  for (int i = sp_tmp[u]; i < sp_tmp[u + 1]; ++i) {
+    const SEnt en = S_tmp[i];
+    if (en.col == u) continue;
+    S[o++] = en;
+    r += 1.f / (en.d * en.d);
+  }
+  rho[u] = r;
+}
+
+// Row starts of the unique (u, v) runs: counts every run including (u, u).
+__global__ void count_runs(int m, int vb, const uint64_t* __restrict__ keys,
+                           const int32_t* __restrict__ head, int32_t* cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !head[i]) return;
+  atomicAdd(&cnt[(int)(keys[i] >> vb)], 1);
+}
+
+// ------------------------------------------------- label propagation ----
+constexpr int kLPWarps = 4;
+constexpr int kLPHash = 1024;  // distinct neighbouring clusters per vertex
+
+__global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
+    int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+    const float* __restrict__ omega, const float* __restrict__ c, const float* __restrict__ W,
+    const int32_t* __restrict__ labels, float U, uint32_t k0, uint32_t k1, uint32_t round,
+    uint32_t level, uint32_t half, int tb, uint64_t* keys, int32_t* vals) {
+  __shared__ int32_t hk[kLPWarps][kLPHash];
+  __shared__ float hv[kLPWarps][kLPHash];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int v = blockIdx.x * kLPWarps + wl;
+  if (v >= n) return;
+  uint32_t z[4];
+  philox4x32_10((uint32_t)v, round, level, 2u, k0, k1, z);
+  const uint64_t none = ~(uint64_t)0;
+  vals[v] = v;
+  if ((z[0] & 1u) != half) {
+    if (lane == 0) keys[v] = none;
+    return;
+  }
+  for (int i = lane; i < kLPHash; i += 32) { hk[wl][i] = -1; hv[wl][i] = 0.f; }
+  __syncwarp();
+  for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+    const int L = labels[col[e]];
+    const float w = omega ? omega[e] : 1.f;
+    uint32_t hsh = ((uint32_t)L * 2654435761u) & (kLPHash - 1);
+    for (int probe = 0; probe < kLPHash; ++probe) {
+      const int prev = atomicCAS(&hk[wl][hsh], -1, L);
+      if (prev == -1 || prev == L) {
+        atomicAdd(&hv[wl][hsh], w);
+        break;
+      }
+      hsh = (hsh + 1) & (kLPHash - 1);
+    }
+  }
+  __syncwarp();
+  const int own = labels[v];
+  const float cv = c[v];
+  // best eligible cluster: max connection, then smallest label
+  float best = -1.f;
+  int bestL = 0x7fffffff;
+  float ownc = 0.f;
+  for (int i = lane; i < kLPHash; i += 32) {
+    const int L = hk[wl][i];
+    if (L < 0) continue;
+    const float cn = hv[wl][i];
+    if (L == own) { ownc = cn; continue; }
+    if (W[L] + cv > U) continue;
+    if (cn > best || (cn == best && L < bestL)) { best = cn; bestL = L; }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oL = __shfl_xor_sync(0xffffffffu, bestL, o);
+    ownc += __shfl_xor_sync(0xffffffffu, ownc, o);
+    if (ob > best || (ob == best && oL < bestL)) { best = ob; bestL = oL; }
+  }
+  if (lane == 0) {
+    // stay unless another eligible cluster is strictly better connected
+    if (best > ownc && bestL != 0x7fffffff)
+      keys[v] = ((uint64_t)bestL << 32) | (uint64_t)z[1];
+    else
+      keys[v] = none;
+  }
+  (void)tb;
+}
+
+// One thread per run of movers into the same cluster (sorted by priority):
+// admit while the cluster weight stays <= U.
+__global__ void lp_admit(int n, const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals,
+                         const float* __restrict__ c, const float* __restrict__ W, float U,
+                         int32_t* labels) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t k = keys[i];
+  if (k == ~(uint64_t)0) return;
+  const int T = (int)(k >> 32);
+  if (i > 0 && (int)(keys[i - 1] >> 32) == T && keys[i - 1] != ~(uint64_t)0) return;
+  float acc = W[T];
+  for (int j = i; j < n && keys[j] != ~(uint64_t)0 && (int)(keys[j] >> 32) == T; ++j) {
+    const int v = vals[j];
+    if (acc + c[v] <= U) {
+      acc += c[v];
+      labels[v] = T;
+    }
+  }
+}
+
+__global__ void lp_init(int n, const float* __restrict__ c, int32_t* labels, float* W) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  labels[v] = v;
+  W[v] = c[v];
+}
+
+__global__ void lp_weights(int n, const float* __restrict__ c, const int32_t* __restrict__ labels,
+                           float* W) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  atomicAdd(&W[labels[v]], c[v]);
+}
+
+// ------------------------------------------------------------ contraction --
+__global__ void mark_used(int n, const int32_t* __restrict__ labels, int32_t* used) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) used[labels[v]] = 1;
+}
+
+__global__ void apply_map(int n, const int32_t* __restrict__ labels, const int32_t* __restrict__ rank,
+                          const float* __restrict__ c, int32_t* map, float* cc) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int m = rank[labels[v]];
+  map[v] = m;
+  atomicAdd(&cc[m], c[v]);
+}
+
+__global__ void cut_flags(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ map, int32_t* flag) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const int mu = map[u];
+  for (int e = rp[u]; e < rp[u + 1]; ++e) flag[e] = map[col[e]] != mu ? 1 : 0;
+}
+
+__global__ void cut_emit(int n, int cb, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const int32_t* __restrict__ map, const int32_t* __restrict__ pos,
+                         uint64_t* keys, int32_t* vals) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const int mu = map[u];
+  for (int e = rp[u]; e < rp[u + 1]; ++e) {
+    const int mv = map[col[e]];
+    if (mv == mu) continue;
+    keys[pos[e]] = ((uint64_t)mu << cb) | (uint64_t)mv;
+    vals[pos[e]] = e;
+  }
+}
+
+__global__ void coarse_reduce(int m, int cb, const uint64_t* __restrict__ keys,
+                              const int32_t* __restrict__ vals, const float* __restrict__ omega,
+                              const int32_t* __restrict__ head, const int32_t* __restrict__ pos,
+                              int32_t* ccol, float* comega, int32_t* rowcnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !head[i]) return;
+  const uint64_t k = keys[i];
+  float w = 0.f;
+  for (int j = i; j < m && keys[j] == k; ++j) w += omega ? omega[vals[j]] : 1.f;
+  ccol[pos[i]] = (int)(k & (((uint64_t)1 << cb) - 1));
+  comega[pos[i]] = w;
+  atomicAdd(&rowcnt[(int)(k >> cb)], 1);
+}
+
+__global__ void heavy_list_kernel(int n, const int32_t* __restrict__ sp, int thr, int32_t* list,
+                                  int32_t* count, int32_t* maxdeg) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const int d = sp[u + 1] - sp[u];
+  atomicMax(maxdeg, d);
+  if (d > thr) list[atomicAdd(count, 1)] = u;
+}
+
+__global__ void sort_small_list(int m, int32_t* list) {
+  // single thread insertion sort: heavy lists are short
+  if (blockIdx.x || threadIdx.x) return;
+  for (int i = 1; i < m; ++i) {
+    const int v = list[i];
+    int j = i - 1;
+    while (j >= 0 && list[j] > v) { list[j + 1] = list[j]; --j; }
+    list[j + 1] = v;
+  }
+}
+
+}  // namespace
+
+mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t* col,
+                         int32_t* rp32_out, cudaStream_t s) {
+  Tmp fl;
+  MM_TRY(tmp_alloc(fl, sizeof(int)));
+  MM_CK(cudaMemsetAsync(fl.p, 0, sizeof(int), s));
+  validate_kernel<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, nnz, rp64, col, rp32_out, fl.as<int>());
+  MM_CK(cudaGetLastError());
+  int flags = 0;
+  MM_CK(cudaMemcpyAsync(&flags, fl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (flags) {
+    set_error("malformed graph:%s%s%s%s%s", (flags & kBadRowPtr) ? " row_ptr" : "",
+              (flags & kBadCol) ? " col-out-of-range" : "", (flags & kSelfLoop) ? " self-loop" : "",
+              (flags & kUnsorted) ? " unsorted-or-duplicate-row" : "",
+              (flags & kAsym) ? " asymmetric" : "");
+    return MM_ERR_INVALID_ARG;
+  }
+  return MM_OK;
+}
+
+mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* elen,
+                     const float* c, int k, int32_t** sp_out, SEnt** s_out, float** rho_out,
+                     int64_t* nnz_out, cudaStream_t s) {
+  if (k != 1 && k != 2) {
+    set_error("k = %d: the device S builder supports k = 1 and k = 2", k);
+    return MM_ERR_UNSUPPORTED;
+  }
+  int32_t nnzE = 0;
+  MM_CK(cudaMemcpyAsync(&nnzE, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  int32_t* sp = nullptr;
+  SEnt* S = nullptr;
+  float* rho = nullptr;
+  MM_CK(cudaMalloc(&sp, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_CK(cudaMalloc(&rho, sizeof(float) * (size_t)std::max(n, 1)));
+  *sp_out = sp;
+  *rho_out = rho;
+  if (k == 1) {
+    MM_CK(cudaMalloc(&S, sizeof(SEnt) * (size_t)std::max(nnzE, 1)));
+    *s_out = S;
+    khop1_kernel<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, rp, col, c, elen, sp, S, rho);
+    MM_CK(cudaGetLastError());
+    *nnz_out = nnzE;
+    return MM_OK;
+  }
+  // k = 2: enumerate paths of one and two edges
+  Tmp cnt, off, scan_ws;
+  MM_TRY(tmp_alloc(cnt, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_TRY(tmp_alloc(off, sizeof(int64_t) * (size_t)(n + 1)));
+  MM_TRY(tmp_alloc(scan_ws, scan_ws_bytes(std::max<int64_t>(n, 1)) + 64));
+  khop2_count<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, cnt.as<int32_t>());
+  MM_TRY(scan_exclusive_i64(cnt.as<int32_t>(), off.as<int64_t>(), n, scan_ws.p, s));
+  int64_t m64 = 0;
+  MM_CK(cudaMemcpyAsync(&m64, off.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (m64 >= 0x7fffffffLL) {
+    set_error("2-hop enumeration has %lld paths (limit 2^31-1)", (long long)m64);
+    return MM_ERR_UNSUPPORTED;
+  }
+  const int m = (int)m64;
+  const int vb = bits_for(std::max(n - 1, 1));
+  const int ub = bits_for(std::max(n - 1, 1));
+  Tmp k0, k1, d0, d1, head, pos, rowcnt, sp_tmp, S_tmp, ws2;
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(d0, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(d1, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  khop2_emit<<<ceil_div(n, 256), 256, 0, s>>>(n, vb, rp, col, c, elen, off.as<int64_t>(),
+                                              k0.as<uint64_t>(), d0.as<int32_t>());
+  MM_CK(cudaGetLastError());
+  SortWS sws;
+  MM_TRY(sort_ws_alloc(sws, std::max(m, 1)));
+  uint64_t* keys;
+  int32_t* dbits;
+  mm_status st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), d0.as<int32_t>(),
+                                d1.as<int32_t>(), m, 0, ub + vb, sws, s, &keys, &dbits);
+  if (st != MM_OK) { sort_ws_free(sws); return st; }
+  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(m + 1)));
+  MM_TRY(tmp_alloc(ws2, scan_ws_bytes(std::max(m, 1)) + 64));
+  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_TRY(tmp_alloc(sp_tmp, sizeof(int32_t) * (size_t)(n + 1)));
+  run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(head.as<int32_t>(), pos.as<int32_t>(), m, ws2.p, s));
+  int32_t uniq = 0;
+  MM_CK(cudaMemcpyAsync(&uniq, pos.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  MM_TRY(tmp_alloc(S_tmp, sizeof(SEnt) * (size_t)std::max(uniq, 1)));
+  // temporary rows include the (u, u) padding runs
+  MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
+  count_runs<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, vb, keys, head.as<int32_t>(),
+                                                          rowcnt.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(rowcnt.as<int32_t>(), sp_tmp.as<int32_t>(), n, ws2.p, s));
+  MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
+  khop2_reduce<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(
+      m, vb, keys, dbits, head.as<int32_t>(), pos.as<int32_t>(), S_tmp.as<SEnt>(),
+      rowcnt.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(rowcnt.as<int32_t>(), sp, n, ws2.p, s));
+  int32_t nnzS = 0;
+  MM_CK(cudaMemcpyAsync(&nnzS, sp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  sort_ws_free(sws);
+  MM_CK(cudaMalloc(&S, sizeof(SEnt) * (size_t)std::max(nnzS, 1)));
+  *s_out = S;
+  khop2_finish<<<ceil_div(n, 256), 256, 0, s>>>(n, sp_tmp.as<int32_t>(), S_tmp.as<SEnt>(), sp, S,
+                                                rho);
+  MM_CK(cudaGetLastError());
+  MM_CK(cudaStreamSynchronize(s));
+  *nnz_out = nnzS;
+  return MM_OK;
+}
+
+mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* omega,
+                     const float* c, float U, int rounds, uint64_t seed, int level,
+                     int32_t* labels, cudaStream_t s) {
+  if (n <= 0) return MM_OK;
+  Tmp W, k0, k1, v0, v1;
+  MM_TRY(tmp_alloc(W, sizeof(float) * (size_t)n));
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)n));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)n));
+  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)n));
+  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)n));
+  SortWS sws;
+  MM_TRY(sort_ws_alloc(sws, n));
+  lp_init<<<ceil_div(n, 256), 256, 0, s>>>(n, c, labels, W.as<float>());
+  const int tb = bits_for(n) + 1;
+  const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+  mm_status st = MM_OK;
+  for (int r = 0; r < rounds && st == MM_OK; ++r) {
+    for (uint32_t half = 0; half < 2 && st == MM_OK; ++half) {
+      lp_propose<<<ceil_div(n, kLPWarps), kLPWarps * 32, 0, s>>>(
+          n, rp, col, omega, c, W.as<float>(), labels, U, key0, key1, (uint32_t)r,
+          (uint32_t)level, half, tb, k0.as<uint64_t>(), v0.as<int32_t>());
+      uint64_t* keys;
+      int32_t* vals;
+      st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(), v1.as<int32_t>(),
+                          n, 0, 32 + tb, sws, s, &keys, &vals);
+      if (st != MM_OK) break;
+      // keys equal to all ones sort last only if every bit is compared: the
+      // sort above covers bits [0, 32 + tb) and targets are < 2^(tb-1)
+      lp_admit<<<ceil_div(n, 256), 256, 0, s>>>(n, keys, vals, c, W.as<float>(), U, labels);
+      cudaMemsetAsync(W.p, 0, sizeof(float) * (size_t)n, s);
+      lp_weights<<<ceil_div(n, 256), 256, 0, s>>>(n, c, labels, W.as<float>());
+    }
+  }
+  sort_ws_free(sws);
+  if (st != MM_OK) return st;
+  MM_CK(cudaGetLastError());
+  MM_CK(cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* omega,
+                   const float* c, const int32_t* labels, int32_t* map, Level& out,
+                   cudaStream_t s) {
+  int32_t nnz = 0;
+  MM_CK(cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  Tmp used, rank, ws, flag, pos, k0, k1, v0, v1, head, hpos, rowcnt;
+  MM_TRY(tmp_alloc(used, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_TRY(tmp_alloc(rank, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_TRY(tmp_alloc(ws, scan_ws_bytes(std::max(std::max(n, nnz), 1)) + 64));
+  MM_CK(cudaMemsetAsync(used.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
+  mark_used<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, used.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(used.as<int32_t>(), rank.as<int32_t>(), n, ws.p, s));
+  int32_t nc = 0;
+  MM_CK(cudaMemcpyAsync(&nc, rank.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  out.n = nc;
+  MM_CK(cudaMalloc(&out.c, sizeof(float) * (size_t)std::max(nc, 1)));
+  MM_CK(cudaMemsetAsync(out.c, 0, sizeof(float) * (size_t)std::max(nc, 1), s));
+  apply_map<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, rank.as<int32_t>(), c, map, out.c);
+  MM_TRY(tmp_alloc(flag, sizeof(int32_t) * (size_t)std::max(nnz, 1)));
+  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(nnz + 1)));
+  cut_flags<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, map, flag.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(flag.as<int32_t>(), pos.as<int32_t>(), nnz, ws.p, s));
+  int32_t m = 0;
+  MM_CK(cudaMemcpyAsync(&m, pos.as<int32_t>() + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  const int cb = bits_for(std::max(nc - 1, 1));
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  cut_emit<<<ceil_div(n, 256), 256, 0, s>>>(n, cb, rp, col, map, pos.as<int32_t>(),
+                                            k0.as<uint64_t>(), v0.as<int32_t>());
+  SortWS sws;
+  MM_TRY(sort_ws_alloc(sws, std::max(m, 1)));
+  uint64_t* keys;
+  int32_t* vals;
+  mm_status st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(),
+                                v1.as<int32_t>(), m, 0, 2 * cb, sws, s, &keys, &vals);
+  if (st != MM_OK) { sort_ws_free(sws); return st; }
+  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(hpos, sizeof(int32_t) * (size_t)(m + 1)));
+  run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(head.as<int32_t>(), hpos.as<int32_t>(), m, ws.p, s));
+  int32_t cnnz = 0;
+  MM_CK(cudaMemcpyAsync(&cnnz, hpos.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  out.nnzE = cnnz;
+  MM_CK(cudaMalloc(&out.col, sizeof(int32_t) * (size_t)std::max(cnnz, 1)));
+  MM_CK(cudaMalloc(&out.omega, sizeof(float) * (size_t)std::max(cnnz, 1)));
+  MM_CK(cudaMalloc(&out.rp, sizeof(int32_t) * (size_t)(nc + 1)));
+  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(nc + 1)));
+  MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), s));
+  coarse_reduce<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(
+      m, cb, keys, vals, omega, head.as<int32_t>(), hpos.as<int32_t>(), out.col, out.omega,
+      rowcnt.as<int32_t>());
+  MM_TRY(scan_exclusive_i32(rowcnt.as<int32_t>(), out.rp, nc, ws.p, s));
+  MM_CK(cudaGetLastError());
+  MM_CK(cudaStreamSynchronize(s));
+  sort_ws_free(sws);
+  return MM_OK;
+}
+
+mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
+  const double avg = L.n > 0 ? (double)L.nnzS / L.n : 0.0;
+  int lanes = p.gather_lanes;
+  if (lanes <= 0) {
+    lanes = 1;
+    while (lanes < 32 && lanes * 3 < avg) lanes <<= 1;
+  }
+  if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) {
+    set_error("gather_lanes must be a power of two <= 32 (got %d)", lanes);
+    return MM_ERR_INVALID_ARG;
+  }
+  L.lanes = lanes;
+  L.heavy_degree = p.heavy_degree > 0 ? p.heavy_degree : std::max(512, 32 * lanes);
+  Tmp cnt;
+  MM_TRY(tmp_alloc(cnt, 2 * sizeof(int32_t)));
+  MM_CK(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
+  MM_CK(cudaMalloc(&L.heavy, sizeof(int32_t) * (size_t)std::max(L.n, 1)));
+  if (L.n > 0)
+    heavy_list_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, L.sp, L.heavy_degree, L.heavy,
+                                                         cnt.as<int32_t>(), cnt.as<int32_t>() + 1);
+  int32_t h[2] = {0, 0};
+  MM_CK(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  L.n_heavy = h[0];
+  L.max_deg = h[1];
+  // deterministic processing order of the heavy rows
+  if (L.n_heavy > 1) sort_small_list<<<1, 1, 0, s>>>(L.n_heavy, L.heavy);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+}  // namespace mm

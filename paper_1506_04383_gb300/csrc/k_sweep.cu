@@ -1,0 +1,368 @@
+// One Jacobi iteration of Eq. 2 over the pair set S, fused with the
+// reductions the alpha schedule needs, plus the device-side schedule
+// controller, prolongation and the initial layout.
+//
+//   x'_u = ( sum_{v in S_u} w_uv (x_v + d_uv (x_u - x_v)/|x_u - x_v|)
+//          + alpha (F_u - sum_{v in S_u} r(u,v)) ) / rho_u
+//
+// with F_u the Barnes-Hut (or exact) sum of r(u,v) over all v != u, so that
+// F_u - sum_S r is the entropy sum over the pairs outside S (Eq. 2; the
+// subtraction is the one of Eq. 3).  The kernel streams the CSR of S once:
+// G lanes cooperate on one row (G chosen from the mean row length so a row
+// is read as consecutive 8-byte entries), rows longer than a threshold are
+// handled by a whole block each, and per-block FP64 partials of
+// sum|x'-x|^2, sum|x|^2 and the stress feed the controller.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+
+struct RowAcc {
+  float gx, gy, sx, sy, st;
+};
+
+__device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const float2* x) {
+  const float2 xv = __ldg(&x[en.col]);
+  const float dx = xu.x - xv.x, dy = xu.y - xv.y;
+  const float q = fmaf(dx, dx, dy * dy);
+  const float inv = q > 0.f ? rsqrtf(q) : 0.f;   // 1/|x_u - x_v|, 0 if coincident
+  const float dist = q * inv;
+  const float w = __fdividef(1.f, en.d * en.d);
+  const float du = en.d * inv;                    // d / |x_u - x_v|
+  a.gx = fmaf(w, fmaf(du, dx, xv.x), a.gx);
+  a.gy = fmaf(w, fmaf(du, dy, xv.y), a.gy);
+  const float inv2 = inv * inv;
+  a.sx = fmaf(dx, inv2, a.sx);
+  a.sy = fmaf(dy, inv2, a.sy);
+  const float t = dist - en.d;
+  a.st = fmaf(w * t, t, a.st);
+}
+
+__device__ __forceinline__ void finish_vertex(int u, const RowAcc& a, float2 xu, float alpha,
+                                              const float* rho, const float2* F, float2* xo,
+                                              double& s_dx, double& s_x, double& s_st) {
+  const float2 f = F[u];
+  const float r = rho[u];
+  const float nx = (a.gx + alpha * (f.x - a.sx)) / r;
+  const float ny = (a.gy + alpha * (f.y - a.sy)) / r;
+  xo[u] = make_float2(nx, ny);
+  const double ddx = (double)nx - xu.x, ddy = (double)ny - xu.y;
+  s_dx += ddx * ddx + ddy * ddy;
+  s_x += (double)xu.x * xu.x + (double)xu.y * xu.y;
+  s_st += 0.5 * (double)a.st;
+}
+
+template <int kT>
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+  __shared__ double sh[3][kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < kT / 32; ++w) { x += sh[0][w]; y += sh[1][w]; z += sh[2][w]; }
+    out[0] = x; out[1] = y; out[2] = z;
+  }
+}
+
+// G lanes per vertex; rows with more than `heavy` entries are skipped here.
+template <int G>
+__global__ void __launch_bounds__(kGatherThreads) gather_light(
+    int n, const int32_t* __restrict__ sp, const SEnt* __restrict__ S,
+    const float* __restrict__ rho, XSel xs, const float2* __restrict__ F,
+    const SweepState* st, int heavy, double* partials) {
+  const float2* x = xs.cur();
+  float2* xo = xs.next();
+  const float alpha = (float)st->alpha;
+  constexpr int kGroups = kGatherThreads / G;
+  const int g = threadIdx.x / G, lg = threadIdx.x % G;
+  double s_dx = 0, s_x = 0, s_st = 0;
+  for (int base = blockIdx.x * kGroups; base < n; base += gridDim.x * kGroups) {
+    const int u = base + g;
+    RowAcc a = {0.f, 0.f, 0.f, 0.f, 0.f};
+    bool mine = false;
+    float2 xu = make_float2(0.f, 0.f);
+    if (u < n) {
+      const int b = sp[u], e = sp[u + 1];
+      if (e - b <= heavy) {
+        mine = true;
+        xu = x[u];
+        for (int k = b + lg; k < e; k += G) accumulate(a, xu, S[k], x);
+      }
+    }
+    if (G > 1) {
+#pragma unroll
+      for (int o = G / 2; o; o >>= 1) {
+        a.gx += __shfl_xor_sync(0xffffffffu, a.gx, o);
+        a.gy += __shfl_xor_sync(0xffffffffu, a.gy, o);
+        a.sx += __shfl_xor_sync(0xffffffffu, a.sx, o);
+        a.sy += __shfl_xor_sync(0xffffffffu, a.sy, o);
+        a.st += __shfl_xor_sync(0xffffffffu, a.st, o);
+      }
+    }
+    if (mine && lg == 0) finish_vertex(u, a, xu, alpha, rho, F, xo, s_dx, s_x, s_st);
+  }
+  block_reduce3<kGatherThreads>(s_dx, s_x, s_st, partials + 3 * (size_t)blockIdx.x);
+}
+
+// One block per heavy row (power-law hubs).
+__global__ void __launch_bounds__(kGatherThreads) gather_heavy(
+    const int32_t* __restrict__ heavy_list, int n_heavy, const int32_t* __restrict__ sp,
+    const SEnt* __restrict__ S, const float* __restrict__ rho, XSel xs,
+    const float2* __restrict__ F, const SweepState* st, double* partials) {
+  const float2* x = xs.cur();
+  float2* xo = xs.next();
+  const float alpha = (float)st->alpha;
+  __shared__ float red[5][kGatherThreads / 32];
+  double s_dx = 0, s_x = 0, s_st = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+    const int u = heavy_list[h];
+    const float2 xu = x[u];
+    RowAcc a = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = sp[u] + threadIdx.x; k < sp[u + 1]; k += blockDim.x) accumulate(a, xu, S[k], x);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a.gx += __shfl_xor_sync(0xffffffffu, a.gx, o);
+      a.gy += __shfl_xor_sync(0xffffffffu, a.gy, o);
+      a.sx += __shfl_xor_sync(0xffffffffu, a.sx, o);
+      a.sy += __shfl_xor_sync(0xffffffffu, a.sy, o);
+      a.st += __shfl_xor_sync(0xffffffffu, a.st, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = a.gx; red[1][warp] = a.gy; red[2][warp] = a.sx;
+      red[3][warp] = a.sy; red[4][warp] = a.st;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      RowAcc t = {0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int w = 0; w < kGatherThreads / 32; ++w) {
+        t.gx += red[0][w]; t.gy += red[1][w]; t.sx += red[2][w];
+        t.sy += red[3][w]; t.st += red[4][w];
+      }
+      finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st);
+    }
+    __syncthreads();
+  }
+  block_reduce3<kGatherThreads>(s_dx, s_x, s_st, partials + 3 * (size_t)blockIdx.x);
+}
+
+constexpr int kCtlThreads = 256;
+
+// Reduces the per-block partials in a fixed order and advances the alpha
+// schedule of Sec. 3.2: at most iters_per_alpha iterations per alpha (fewer
+// if the relative change |x'-x|/|x| drops below eps), alpha := max(factor *
+// alpha, alpha_min); at alpha_min iterate until the change is below
+// eps_final or max_iters_at_min iterations.
+__global__ void __launch_bounds__(kCtlThreads) controller_kernel(
+    int nparts, const double* __restrict__ partials, SweepState* st, SchedParams sp,
+    float* trace, int trace_cap, int* level_sweeps_out, cudaGraphConditionalHandle h,
+    int use_h) {
+  double a = 0, b = 0, c = 0;
+  for (int i = threadIdx.x; i < nparts; i += kCtlThreads) {
+    a += partials[3 * i];
+    b += partials[3 * i + 1];
+    c += partials[3 * i + 2];
+  }
+  __shared__ double out[3];
+  block_reduce3<kCtlThreads>(a, b, c, out);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double sdx = out[0], sx = out[1], stress = out[2];
+  const double rel = sx > 0 ? sqrt(sdx) / sqrt(sx) : (sdx == 0 ? 0.0 : CUDART_INF);
+  const double alpha = st->alpha;
+  const int t = st->total;
+  if (trace && t < trace_cap) {
+    trace[3 * t] = (float)alpha;
+    trace[3 * t + 1] = (float)rel;
+    trace[3 * t + 2] = (float)stress;
+  }
+  st->total = t + 1;
+  st->level_sweeps += 1;
+  st->parity ^= 1;
+  st->it_in_round += 1;
+  st->last_rel = rel;
+  st->last_stress = stress;
+  st->last_sdx = sdx;
+  st->last_sx = sx;
+  const bool at_min = alpha <= sp.alpha_min;
+  const int cap = at_min ? sp.max_iters_at_min : sp.iters_per_alpha;
+  const double tol = at_min ? sp.eps_final : sp.eps;
+  if ((sp.early_exit && rel < tol) || st->it_in_round >= cap) {
+    if (at_min) {
+      st->done = 1;
+    } else {
+      st->alpha = fmax(alpha * sp.alpha_factor, sp.alpha_min);
+      st->it_in_round = 0;
+    }
+  }
+  if (!isfinite(sdx) || !isfinite(sx)) {
+    st->error = MM_ERR_NONFINITE;
+    st->done = 1;
+  }
+  if (st->level_sweeps >= sp.level_cap) st->done = 1;
+  if (level_sweeps_out) *level_sweeps_out = st->level_sweeps;
+  if (use_h) cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+__device__ __forceinline__ float u01(uint32_t z) { return (float)(z >> 8) * (1.0f / 16777216.0f); }
+
+// Random polar placement around the coarse representative (Sec. 3.2).
+__global__ void prolong_kernel(int nf, const int32_t* __restrict__ map, XSel xc,
+                               const float* __restrict__ cc, uint32_t k0, uint32_t k1,
+                               uint32_t level, float2* xf_direct) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nf) return;
+  uint32_t z[4];
+  philox4x32_10((uint32_t)v, level, 0u, 0u, k0, k1, z);
+  const int p = map[v];
+  const float2 P = xc.cur()[p];
+  const float phi = 6.28318530717958647692f * u01(z[0]);
+  const float rad = sqrtf(cc[p]) * u01(z[1]);
+  float sn, cs;
+  sincosf(phi, &sn, &cs);
+  float2* out = xf_direct ? xf_direct : xc.next();
+  out[v] = make_float2(fmaf(rad, cs, P.x), fmaf(rad, sn, P.y));
+}
+
+// Resets the schedule for a new level; flip = 1 moves to the buffer the
+// prolongation just wrote.
+__global__ void level_start_kernel(SweepState* st, double alpha0, int flip) {
+  st->alpha = alpha0;
+  st->it_in_round = 0;
+  st->level_sweeps = 0;
+  st->done = 0;
+  if (flip) st->parity ^= 1;
+}
+
+// Initial layout of the coarsest level (Sec. 3.1): one vertex at the origin;
+// two vertices at their target distance d (first S entry of vertex 0);
+// more than two placed around the origin at radius R = sqrt(sum c).
+__global__ void init_coarsest_kernel(int n, const float* __restrict__ c, const SEnt* s0,
+                                     uint32_t k0, uint32_t k1, uint32_t level, float R,
+                                     float2* x0, SweepState* st, double alpha0) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v == 0) {
+    st->parity = 0;
+    st->alpha = alpha0;
+    st->it_in_round = 0;
+    st->level_sweeps = 0;
+    st->done = 0;
+  }
+  if (v >= n) return;
+  if (n == 1) {
+    x0[0] = make_float2(0.f, 0.f);
+  } else if (n == 2) {
+    const float D = s0[0].d;
+    x0[v] = make_float2(v == 0 ? -0.5f * D : 0.5f * D, 0.f);
+  } else {
+    uint32_t z[4];
+    philox4x32_10((uint32_t)v, level, 1u, 0u, k0, k1, z);
+    const float phi = 6.28318530717958647692f * u01(z[0]);
+    const float rad = R * u01(z[1]);
+    float sn, cs;
+    sincosf(phi, &sn, &cs);
+    x0[v] = make_float2(rad * cs, rad * sn);
+  }
+}
+
+__global__ void copy_current_kernel(XSel xs, int n, float2* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = xs.cur()[i];
+}
+
+template <int G>
+void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st, double* partials,
+                  int blocks, cudaStream_t s) {
+  gather_light<G><<<blocks, kGatherThreads, 0, s>>>(L.n, L.sp, L.s, L.rho, x, F, st,
+                                                    L.heavy_degree, partials);
+}
+
+}  // namespace
+
+int gather_light_blocks(const Level& L) {
+  const int groups = kGatherThreads / std::max(1, L.lanes);
+  return std::max(1, std::min(ceil_div(L.n, groups), kSMs * 16));
+}
+
+int gather_heavy_blocks(const Level& L) { return L.n_heavy > 0 ? std::min(L.n_heavy, kSMs * 8) : 0; }
+
+int gather_blocks(const Level& L) { return gather_light_blocks(L) + gather_heavy_blocks(L); }
+
+mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
+                        double* partials, cudaStream_t s) {
+  if (L.n <= 0) return MM_OK;
+  const int lb = gather_light_blocks(L);
+  switch (L.lanes) {
+    case 1: launch_light<1>(L, x, F, st, partials, lb, s); break;
+    case 2: launch_light<2>(L, x, F, st, partials, lb, s); break;
+    case 4: launch_light<4>(L, x, F, st, partials, lb, s); break;
+    case 8: launch_light<8>(L, x, F, st, partials, lb, s); break;
+    case 16: launch_light<16>(L, x, F, st, partials, lb, s); break;
+    case 32: launch_light<32>(L, x, F, st, partials, lb, s); break;
+    default:
+      set_error("unsupported lanes per vertex %d", L.lanes);
+      return MM_ERR_INVALID_ARG;
+  }
+  const int hb = gather_heavy_blocks(L);
+  if (hb > 0)
+    gather_heavy<<<hb, kGatherThreads, 0, s>>>(L.heavy, L.n_heavy, L.sp, L.s, L.rho, x, F, st,
+                                               partials + 3 * (size_t)lb);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status controller(int nblocks, const double* partials, SweepState* st, SchedParams sp,
+                     float* trace, int trace_cap, int* level_sweeps_out,
+                     cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s) {
+  controller_kernel<<<1, kCtlThreads, 0, s>>>(nblocks, partials, st, sp, trace, trace_cap,
+                                              level_sweeps_out, handle, use_handle ? 1 : 0);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status prolong(int n_fine, const int32_t* map, XSel xc, const float* cc, uint64_t seed,
+                  int level, float2* xf_direct, cudaStream_t s) {
+  if (n_fine <= 0) return MM_OK;
+  prolong_kernel<<<ceil_div(n_fine, 256), 256, 0, s>>>(
+      n_fine, map, xc, cc, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
+      (uint32_t)level, xf_direct);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status level_start(SweepState* st, double alpha0, int flip, cudaStream_t s) {
+  level_start_kernel<<<1, 1, 0, s>>>(st, alpha0, flip);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status init_coarsest(int n, const float* c, const SEnt* s0, uint64_t seed, int level,
+                        float R, float2* x0, SweepState* st, double alpha0, cudaStream_t s) {
+  init_coarsest_kernel<<<ceil_div(std::max(n, 1), 256), 256, 0, s>>>(
+      n, c, s0, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)level, R, x0,
+      st, alpha0);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s) {
+  if (n <= 0) return MM_OK;
+  copy_current_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, n, out);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+}  // namespace mm

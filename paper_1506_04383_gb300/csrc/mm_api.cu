@@ -1,0 +1,1109 @@
+// C-ABI entry points and host orchestration of the multilevel layout.
+//
+// Sec. 3 of the paper: coarsen (SCLaP + contraction) until the coarsest
+// level, lay out the coarsest graph, then prolongate level by level and run
+// the alpha schedule of Eq. 2 iterations on each.  Here the whole uncoarsening
+// is one CUDA graph: per level a child graph (initial layout or prolongation)
+// followed by a conditional WHILE node whose body is one sweep (tree build,
+// tree walk or exact sum, fused gather/update, controller).  The controller
+// kernel decides on the device whether the level continues, so the host
+// launches the graph once and waits once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+struct mm_hierarchy {
+  mm_params p;
+  int device = 0;
+  cudaStream_t cs = nullptr;  // capture stream (non-blocking)
+  std::vector<mm::Level> levels;
+  mm::TreeWS tree;
+  float2* xb[2] = {nullptr, nullptr};
+  float2* F = nullptr;
+  double* partials = nullptr;
+  mm::SweepState* state = nullptr;   // layout schedule state
+  mm::SweepState* sstate = nullptr;  // standalone calls
+  int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
+  int32_t* lsw = nullptr;            // [MM_MAX_LEVELS] sweeps per level
+  float* trace = nullptr;
+  int trace_cap = 0;
+  int level_cap = 0;
+  // cached uncoarsening graph
+  cudaGraphExec_t gexec = nullptr;
+  mm_params gparams;
+  int gsingle = -1;
+};
+
+namespace mm {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+mm_status cuda_status(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed at %s:%d: %s", what, file, line, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
+}
+
+int gather_light_blocks(const Level& L);
+
+namespace {
+
+__global__ void rp_to_i32(int n, const int64_t* __restrict__ a, int32_t* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) b[i] = (int32_t)a[i];
+}
+__global__ void i32_to_i64(int n, const int32_t* __restrict__ a, int64_t* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+__global__ void fill_f32(int64_t n, float v, float* a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+__global__ void max_f32(int n, const float* __restrict__ a, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, __float_as_int(a[i]));  // non-negative floats order as ints
+}
+__global__ void split_sent(int64_t m, const SEnt* __restrict__ S, int32_t* col, float* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  if (col) col[i] = S[i].col;
+  if (d) d[i] = S[i].d;
+}
+__global__ void set_state(SweepState* st, double alpha) {
+  st->alpha = alpha;
+  st->it_in_round = 0;
+  st->level_sweeps = 0;
+  st->total = 0;
+  st->done = 0;
+  st->error = 0;
+  st->parity = 0;
+}
+
+void free_level(Level& L) {
+  void* ptrs[] = {L.rp, L.col, L.omega, L.c, L.elen, L.map, L.sp, L.s, L.rho, L.heavy};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  L = Level();
+}
+
+mm_status check_params(const mm_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (p->struct_version != MM_PARAMS_VERSION) {
+    set_error("mm_params.struct_version %u, library expects %u", p->struct_version,
+              MM_PARAMS_VERSION);
+    return MM_ERR_INVALID_ARG;
+  }
+  if (p->k != 1 && p->k != 2) {
+    set_error("k = %d: the device path supports k = 1 and k = 2", p->k);
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (!(p->theta >= 0.f) || p->coarsest_n < 1 || !(p->f > 0.f) || !(p->b > 1.f) ||
+      p->lp_rounds < 0 || p->iters_per_alpha < 1 || p->max_iters_at_min < 1 ||
+      !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
+      p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS) {
+    set_error("parameter out of range");
+    return MM_ERR_INVALID_ARG;
+  }
+  return MM_OK;
+}
+
+int alpha_rounds(const mm_params& p) {
+  double a = p.alpha0;
+  int r = 1;
+  while (a > p.alpha_min && r < 1000) {
+    a = std::max(a * p.alpha_factor, p.alpha_min);
+    ++r;
+  }
+  return r;
+}
+
+SchedParams sched_of(const mm_params& p, int level_cap) {
+  SchedParams sp;
+  sp.alpha0 = p.alpha0;
+  sp.alpha_factor = p.alpha_factor;
+  sp.alpha_min = p.alpha_min;
+  sp.eps = p.eps;
+  sp.eps_final = p.eps_final;
+  sp.iters_per_alpha = p.iters_per_alpha;
+  sp.max_iters_at_min = p.max_iters_at_min;
+  sp.early_exit = p.early_exit;
+  sp.level_cap = level_cap;
+  return sp;
+}
+
+// Host BFS over one (small) level: the coarse graph is connected iff the
+// input is, since label propagation only merges adjacent clusters.
+mm_status check_connected(const Level& L, cudaStream_t s) {
+  if (L.n <= 1) return MM_OK;
+  std::vector<int32_t> rp(L.n + 1), col((size_t)std::max<int64_t>(L.nnzE, 1));
+  MM_CK(cudaMemcpyAsync(rp.data(), L.rp, sizeof(int32_t) * (L.n + 1), cudaMemcpyDeviceToHost, s));
+  if (L.nnzE)
+    MM_CK(cudaMemcpyAsync(col.data(), L.col, sizeof(int32_t) * L.nnzE, cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  std::vector<char> seen(L.n, 0);
+  std::vector<int32_t> q;
+  q.push_back(0);
+  seen[0] = 1;
+  for (size_t i = 0; i < q.size(); ++i)
+    for (int e = rp[q[i]]; e < rp[q[i] + 1]; ++e)
+      if (!seen[col[e]]) {
+        seen[col[e]] = 1;
+        q.push_back(col[e]);
+      }
+  if ((int)q.size() != L.n) {
+    set_error("graph is not connected (%zu of %d coarsest vertices reachable)", q.size(), L.n);
+    return MM_ERR_NOT_CONNECTED;
+  }
+  return MM_OK;
+}
+
+// A tree walk that met an out-of-range node id or exceeded its visit budget
+// stops and raises a flag (never faults); the host reports it here.
+mm_status tree_error(mm_hierarchy* h, cudaStream_t s) {
+  int e = 0;
+  MM_CK(cudaMemcpyAsync(&e, h->tree.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (e) {
+    cudaMemsetAsync(h->tree.err, 0, sizeof(int), s);
+    set_error("internal error: Barnes-Hut walk met an inconsistent tree");
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
+}
+
+bool level_exact(const mm_hierarchy* h, int level, bool single) {
+  if (h->p.exact_repulsion) return true;
+  // the coarsest level of a multilevel run is refined with the exact sum
+  return !single && level == (int)h->levels.size() - 1;
+}
+
+// Library kernels one sweep launches (mirrors sweep_body).
+int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
+  const Level& L = h->levels[level];
+  int64_t k = 2 + (L.n_heavy > 0 ? 1 : 0);  // gather (+ heavy rows) + controller
+  if (exact) return k + 1;
+  k += 1 + 1 + 1;                            // bbox, morton, bottom-up
+  if (L.n > 1) k += 4 * 3 + 1;               // 4 radix passes x 3 kernels, radix tree
+  return k + 1;                              // walk
+}
+
+// One sweep on `level`: repulsion, fused update, controller.
+mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState* st,
+                     SchedParams sp, float* trace, int trace_cap, int* lsw,
+                     cudaGraphConditionalHandle hnd, bool use_h, cudaStream_t s) {
+  const Level& L = h->levels[level];
+  if (exact) {
+    MM_TRY(exact_repulsion(x, L.n, h->F, s));
+  } else {
+    MM_TRY(bh_build(x, L.n, h->p.theta, h->tree, s));
+    MM_TRY(bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, nullptr, s));
+  }
+  MM_TRY(gather_update(L, x, h->F, st, h->partials, s));
+  MM_TRY(controller(gather_blocks(L), h->partials, st, sp, trace, trace_cap, lsw, hnd, use_h, s));
+  return MM_OK;
+}
+
+mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single) {
+  cudaStream_t cs = h->cs;
+  XSel x{h->xb[0], h->xb[1], &h->state->parity};
+  const SchedParams sp = sched_of(p, h->level_cap);
+  cudaGraph_t g = nullptr;
+  MM_CK(cudaGraphCreate(&g, 0));
+  cudaGraphNode_t prev = nullptr;
+  mm_status st = MM_OK;
+  auto fail = [&](mm_status s2) {
+    cudaGraphDestroy(g);
+    return s2;
+  };
+  auto add_child = [&](auto&& launches) -> mm_status {
+    cudaGraph_t sub = nullptr;
+    MM_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    mm_status r = launches(cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &sub);
+    if (r != MM_OK) {
+      if (sub) cudaGraphDestroy(sub);
+      return r;
+    }
+    MM_CK(e);
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, sub);
+    cudaGraphDestroy(sub);
+    MM_CK(e);
+    prev = node;
+    return MM_OK;
+  };
+  auto add_loop = [&](int level, bool exact) -> mm_status {
+    cudaGraphConditionalHandle hnd;
+    MM_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    MM_CK(cudaGraphAddNode(&node, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MM_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+    mm_status r = sweep_body(h, level, exact, x, h->state, sp, h->trace, h->trace_cap,
+                             h->lsw + level, hnd, true, cs);
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &out);
+    if (r != MM_OK) return r;
+    MM_CK(e);
+    prev = node;
+    return MM_OK;
+  };
+  const int top = (int)h->levels.size() - 1;
+  if (single) {
+    st = add_child([&](cudaStream_t s) -> mm_status {
+      set_state<<<1, 1, 0, s>>>(h->state, p.alpha0);
+      MM_CK(cudaGetLastError());
+      return MM_OK;
+    });
+    if (st == MM_OK) st = add_loop(0, level_exact(h, 0, true));
+  } else {
+    const Level& C = h->levels[top];
+    st = add_child([&](cudaStream_t s) -> mm_status {
+      set_state<<<1, 1, 0, s>>>(h->state, p.alpha0);
+      MM_CK(cudaGetLastError());
+      return init_coarsest(C.n, C.c, C.s, p.seed, top, (float)std::sqrt(C.sum_c), h->xb[0],
+                           h->state, p.alpha0, s);
+    });
+    if (st == MM_OK) st = add_loop(top, level_exact(h, top, false));
+    for (int lv = top - 1; lv >= 0 && st == MM_OK; --lv) {
+      const Level& L = h->levels[lv];
+      const Level& Cn = h->levels[lv + 1];
+      // one alpha schedule spans the run: the coarsest level ends at
+      // alpha_min, so every finer level refines at alpha_min
+      st = add_child([&](cudaStream_t s) -> mm_status {
+        MM_TRY(prolong(L.n, L.map, x, Cn.c, p.seed, lv, nullptr, s));
+        return level_start(h->state, p.alpha_min, 1, s);
+      });
+      if (st == MM_OK) st = add_loop(lv, level_exact(h, lv, false));
+    }
+  }
+  if (st != MM_OK) return fail(st);
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  MM_CK(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = ex;
+  h->gparams = p;
+  h->gsingle = single ? 1 : 0;
+  return MM_OK;
+}
+
+mm_status level_check(const mm_hierarchy* h, int level) {
+  if (!h) {
+    set_error("hierarchy is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (level < 0 || level >= (int)h->levels.size()) {
+    set_error("level %d out of range [0, %zu)", level, h->levels.size());
+    return MM_ERR_INVALID_ARG;
+  }
+  return MM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s);
+
+mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
+  MM_TRY(check_params(p));
+  if (!g || !out || g->n < 1 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col)) {
+    set_error("invalid graph descriptor");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (g->nnz >= 0x7fffffffLL) {
+    set_error("graphs with 2^31 or more CSR entries are not supported");
+    return MM_ERR_UNSUPPORTED;
+  }
+  mm_hierarchy* h = new mm_hierarchy();
+  *out = h;  // freed by the caller's wrapper on error
+  h->p = *p;
+  MM_CK(cudaGetDevice(&h->device));
+  MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+  const int n0 = g->n;
+  Level L0;
+  L0.n = n0;
+  L0.nnzE = g->nnz;
+  MM_CK(cudaMalloc(&L0.rp, sizeof(int32_t) * (size_t)(n0 + 1)));
+  h->levels.push_back(L0);
+  Level& l0 = h->levels[0];
+  MM_TRY(validate_graph(n0, g->nnz, g->row_ptr, g->col, l0.rp, s));
+  MM_CK(cudaMalloc(&l0.col, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1)));
+  MM_CK(cudaMalloc(&l0.omega, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1)));
+  MM_CK(cudaMalloc(&l0.c, sizeof(float) * (size_t)n0));
+  if (g->nnz)
+    MM_CK(cudaMemcpyAsync(l0.col, g->col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToDevice, s));
+  if (g->edge_len) {
+    MM_CK(cudaMalloc(&l0.elen, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1)));
+    if (g->nnz)
+      MM_CK(cudaMemcpyAsync(l0.elen, g->edge_len, sizeof(float) * g->nnz,
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  fill_f32<<<ceil_div(std::max<int64_t>(g->nnz, 1), 256), 256, 0, s>>>(g->nnz, 1.f, l0.omega);
+  fill_f32<<<ceil_div(n0, 256), 256, 0, s>>>(n0, 1.f, l0.c);
+  MM_CK(cudaGetLastError());
+
+  // ---- coarsening (Sec. 3.1)
+  double f = p->f;
+  int stalls = 0;
+  int* dmax = nullptr;
+  int32_t* labels = nullptr;
+  MM_CK(cudaMalloc(&dmax, sizeof(int)));
+  MM_CK(cudaMalloc(&labels, sizeof(int32_t) * (size_t)n0));
+  mm_status st = MM_OK;
+  while (st == MM_OK && h->levels.back().n > p->coarsest_n &&
+         (int)h->levels.size() < p->max_levels && stalls < p->max_stalls) {
+    Level& cur = h->levels.back();
+    const int hidx = (int)h->levels.size() - 1;
+    int maxc_bits = 0;
+    cudaMemsetAsync(dmax, 0, sizeof(int), s);
+    max_f32<<<ceil_div(cur.n, 256), 256, 0, s>>>(cur.n, cur.c, dmax);
+    cudaMemcpyAsync(&maxc_bits, dmax, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_status(cudaGetLastError(), "max reduction", __FILE__, __LINE__);
+      break;
+    }
+    float maxc;
+    memcpy(&maxc, &maxc_bits, sizeof(float));
+    const double W = std::min(std::pow((double)p->b, hidx + 1), cur.n / f);
+    const float U = (float)std::max((double)maxc, W);
+    st = cluster_lp(cur.n, cur.rp, cur.col, cur.omega, cur.c, U, p->lp_rounds, p->seed, hidx,
+                    labels, s);
+    if (st != MM_OK) break;
+    Level nxt;
+    int32_t* map = nullptr;
+    if (cudaMalloc(&map, sizeof(int32_t) * (size_t)cur.n) != cudaSuccess) {
+      st = cuda_status(cudaErrorMemoryAllocation, "cudaMalloc(map)", __FILE__, __LINE__);
+      break;
+    }
+    st = contract(cur.n, cur.rp, cur.col, cur.omega, cur.c, labels, map, nxt, s);
+    if (st != MM_OK) {
+      cudaFree(map);
+      free_level(nxt);
+      break;
+    }
+    if (nxt.n >= cur.n || nxt.n < 2) {
+      cudaFree(map);
+      free_level(nxt);
+      f *= 0.7;
+      ++stalls;
+      continue;
+    }
+    stalls = 0;
+    if (nxt.n > 0.9 * cur.n) f *= 0.7;
+    cur.map = map;
+    h->levels.push_back(nxt);
+  }
+  cudaFree(dmax);
+  cudaFree(labels);
+  MM_TRY(st);
+
+  return finish_levels(h, p, s);
+}
+
+__global__ void check_map(int n, const int32_t* __restrict__ map, int nc, int* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (map[i] < 0 || map[i] >= nc)) atomicOr(bad, 1);
+}
+
+// Copies one caller-described level into library memory (validated).
+mm_status import_level(const mm_level_desc& d, const mm_level_desc* next, Level& L,
+                       cudaStream_t s) {
+  if (d.n < 1 || d.nnz < 0 || !d.row_ptr || (d.nnz > 0 && !d.col)) {
+    set_error("invalid level descriptor");
+    return MM_ERR_INVALID_ARG;
+  }
+  L.n = d.n;
+  L.nnzE = d.nnz;
+  MM_CK(cudaMalloc(&L.rp, sizeof(int32_t) * (size_t)(d.n + 1)));
+  MM_TRY(validate_graph(d.n, d.nnz, d.row_ptr, d.col, L.rp, s));
+  const size_t m = (size_t)std::max<int64_t>(d.nnz, 1);
+  MM_CK(cudaMalloc(&L.col, sizeof(int32_t) * m));
+  MM_CK(cudaMalloc(&L.omega, sizeof(float) * m));
+  MM_CK(cudaMalloc(&L.c, sizeof(float) * (size_t)d.n));
+  if (d.nnz) MM_CK(cudaMemcpyAsync(L.col, d.col, 4 * d.nnz, cudaMemcpyDeviceToDevice, s));
+  if (d.omega && d.nnz)
+    MM_CK(cudaMemcpyAsync(L.omega, d.omega, 4 * d.nnz, cudaMemcpyDeviceToDevice, s));
+  else
+    fill_f32<<<ceil_div((int64_t)m, 256), 256, 0, s>>>(d.nnz, 1.f, L.omega);
+  if (d.node_c)
+    MM_CK(cudaMemcpyAsync(L.c, d.node_c, 4 * (size_t)d.n, cudaMemcpyDeviceToDevice, s));
+  else
+    fill_f32<<<ceil_div(d.n, 256), 256, 0, s>>>(d.n, 1.f, L.c);
+  if (next) {
+    if (!d.map) {
+      set_error("level map missing");
+      return MM_ERR_INVALID_ARG;
+    }
+    MM_CK(cudaMalloc(&L.map, sizeof(int32_t) * (size_t)d.n));
+    MM_CK(cudaMemcpyAsync(L.map, d.map, 4 * (size_t)d.n, cudaMemcpyDeviceToDevice, s));
+    int* bad = nullptr;
+    int hb = 0;
+    MM_CK(cudaMalloc(&bad, sizeof(int)));
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
+    check_map<<<ceil_div(d.n, 256), 256, 0, s>>>(d.n, L.map, next->n, bad);
+    cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(bad);
+    MM_CK(e);
+    if (hb) {
+      set_error("level map entry outside [0, %d)", next->n);
+      return MM_ERR_INVALID_ARG;
+    }
+  }
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status build_explicit(int num_levels, const mm_level_desc* d, const float* elen0,
+                         const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
+  MM_TRY(check_params(p));
+  if (num_levels < 1 || num_levels > MM_MAX_LEVELS || !d || !out) {
+    set_error("num_levels must lie in [1, %d]", MM_MAX_LEVELS);
+    return MM_ERR_INVALID_ARG;
+  }
+  mm_hierarchy* h = new mm_hierarchy();
+  *out = h;
+  h->p = *p;
+  MM_CK(cudaGetDevice(&h->device));
+  MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+  for (int l = 0; l < num_levels; ++l) {
+    h->levels.push_back(Level());
+    MM_TRY(import_level(d[l], l + 1 < num_levels ? &d[l + 1] : nullptr, h->levels.back(), s));
+  }
+  if (elen0 && d[0].nnz) {
+    Level& L0 = h->levels[0];
+    MM_CK(cudaMalloc(&L0.elen, sizeof(float) * (size_t)d[0].nnz));
+    MM_CK(cudaMemcpyAsync(L0.elen, elen0, 4 * d[0].nnz, cudaMemcpyDeviceToDevice, s));
+  }
+  return finish_levels(h, p, s);
+}
+
+// Connectivity, pair sets S and gather configuration per level, workspaces.
+mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
+  MM_TRY(check_connected(h->levels.back(), s));
+  for (size_t lv = 0; lv < h->levels.size(); ++lv) {
+    Level& L = h->levels[lv];
+    MM_TRY(build_khop(L.n, L.rp, L.col, lv == 0 ? L.elen : nullptr, lv == 0 ? nullptr : L.c,
+                      p->k, &L.sp, &L.s, &L.rho, &L.nnzS, s));
+    MM_TRY(gather_config(L, *p, s));
+  }
+  {
+    Level& C = h->levels.back();
+    std::vector<float> hc(C.n);
+    MM_CK(cudaMemcpyAsync(hc.data(), C.c, sizeof(float) * C.n, cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaStreamSynchronize(s));
+    double sc = 0;
+    for (float v : hc) sc += v;
+    C.sum_c = sc;
+  }
+
+  // ---- workspaces, sized for the largest level
+  int n0 = 1;
+  for (const Level& L : h->levels) n0 = std::max(n0, L.n);
+  MM_TRY(tree_ws_alloc(h->tree, n0));
+  MM_CK(cudaMalloc(&h->xb[0], sizeof(float2) * (size_t)n0));
+  MM_CK(cudaMalloc(&h->xb[1], sizeof(float2) * (size_t)n0));
+  MM_CK(cudaMalloc(&h->F, sizeof(float2) * (size_t)n0));
+  int maxb = 1;
+  for (const Level& L : h->levels) maxb = std::max(maxb, gather_blocks(L));
+  MM_CK(cudaMalloc(&h->partials, sizeof(double) * 3 * (size_t)maxb));
+  MM_CK(cudaMalloc(&h->state, sizeof(SweepState)));
+  MM_CK(cudaMalloc(&h->sstate, sizeof(SweepState)));
+  MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
+  MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
+  MM_CK(cudaMalloc(&h->zero, sizeof(int32_t)));
+  MM_CK(cudaMemsetAsync(h->zero, 0, sizeof(int32_t), s));
+  MM_CK(cudaMalloc(&h->lsw, sizeof(int32_t) * MM_MAX_LEVELS));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+mm_status ensure_trace(mm_hierarchy* h, const mm_params& p) {
+  const int per_level = (alpha_rounds(p) - 1) * p.iters_per_alpha + p.max_iters_at_min;
+  const int cap = per_level * (int)h->levels.size();
+  h->level_cap = per_level;
+  if (cap > h->trace_cap) {
+    if (h->trace) cudaFree(h->trace);
+    h->trace = nullptr;
+    MM_CK(cudaMalloc(&h->trace, sizeof(float) * 3 * (size_t)cap));
+    h->trace_cap = cap;
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+  }
+  return MM_OK;
+}
+
+bool same_schedule(const mm_params& a, const mm_params& b) {
+  return a.alpha0 == b.alpha0 && a.alpha_factor == b.alpha_factor && a.alpha_min == b.alpha_min &&
+         a.eps == b.eps && a.eps_final == b.eps_final && a.iters_per_alpha == b.iters_per_alpha &&
+         a.max_iters_at_min == b.max_iters_at_min && a.early_exit == b.early_exit &&
+         a.seed == b.seed;
+}
+
+mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, float* x_out,
+                 mm_layout_stats* stats, cudaStream_t s) {
+  mm_params p = h->p;
+  if (pin) {
+    MM_TRY(check_params(pin));
+    p.alpha0 = pin->alpha0; p.alpha_factor = pin->alpha_factor; p.alpha_min = pin->alpha_min;
+    p.eps = pin->eps; p.eps_final = pin->eps_final; p.iters_per_alpha = pin->iters_per_alpha;
+    p.max_iters_at_min = pin->max_iters_at_min; p.early_exit = pin->early_exit;
+    p.seed = pin->seed;
+  }
+  if (!x_out) {
+    set_error("x_out is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  const int n0 = h->levels[0].n;
+  const bool single = x_init != nullptr;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (n0 == 1) {  // a single vertex sits at the origin
+    MM_CK(cudaMemsetAsync(x_out, 0, sizeof(float2), s));
+    MM_CK(cudaStreamSynchronize(s));
+    if (stats) { stats->num_levels = 1; stats->level_n[0] = 1; }
+    return MM_OK;
+  }
+  MM_TRY(ensure_trace(h, p));
+  if (!h->gexec || h->gsingle != (single ? 1 : 0) || !same_schedule(h->gparams, p))
+    MM_TRY(build_graph(h, p, single));
+  if (single)
+    MM_CK(cudaMemcpyAsync(h->xb[0], x_init, sizeof(float2) * n0, cudaMemcpyDeviceToDevice, s));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaGraphLaunch(h->gexec, s));
+  XSel x{h->xb[0], h->xb[1], &h->state->parity};
+  MM_TRY(copy_current(x, n0, (float2*)x_out, s));
+  SweepState hs;
+  int32_t lsw[MM_MAX_LEVELS];
+  MM_CK(cudaMemcpyAsync(&hs, h->state, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaMemcpyAsync(lsw, h->lsw, sizeof(lsw), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (stats) {
+    const int nl = (int)h->levels.size();
+    stats->num_levels = nl;
+    int64_t vu = 0;
+    for (int i = 0; i < nl; ++i) {
+      stats->level_n[i] = h->levels[i].n;
+      stats->level_sweeps[i] = lsw[i];
+      vu += (int64_t)lsw[i] * h->levels[i].n;
+    }
+    stats->total_sweeps = hs.total;
+    stats->vertex_updates = vu;
+    stats->final_alpha = hs.alpha;
+    stats->final_rel_change = hs.last_rel;
+    stats->final_stress = hs.last_stress;
+    int64_t kl = 1;  // copy of the result
+    for (int i = 0; i < nl; ++i) {
+      if (single && i > 0) break;
+      kl += 2 + (int64_t)lsw[i] * kernels_per_sweep(h, i, level_exact(h, i, single));
+    }
+    stats->kernel_launches = kl;
+  }
+  if (hs.error) {
+    set_error("a sweep produced non-finite coordinates");
+    return MM_ERR_NONFINITE;
+  }
+  return tree_error(h, s);
+}
+
+}  // namespace
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+void mm_default_params(mm_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->struct_version = MM_PARAMS_VERSION;
+  p->k = 2;
+  p->theta = 0.5f;
+  p->exact_repulsion = 0;
+  p->coarsest_n = 2;
+  p->f = 20.f;
+  p->b = 2.f;
+  p->lp_rounds = 10;
+  p->iters_per_alpha = 2;
+  p->alpha0 = 1.0;
+  p->alpha_factor = 0.3;
+  p->alpha_min = 0.008;
+  p->eps = 1e-4;
+  p->eps_final = 1e-4;
+  p->max_iters_at_min = 100;
+  p->early_exit = 1;
+  p->seed = 1506;
+  p->max_levels = MM_MAX_LEVELS;
+  p->max_stalls = 10;
+  p->gather_lanes = 0;
+  p->heavy_degree = 0;
+  p->traverse_warps = 0;
+}
+
+const char* mm_status_string(mm_status s) {
+  switch (s) {
+    case MM_OK: return "ok";
+    case MM_ERR_INVALID_ARG: return "invalid argument";
+    case MM_ERR_NOT_CONNECTED: return "graph not connected";
+    case MM_ERR_CUDA: return "CUDA error";
+    case MM_ERR_OOM: return "out of device memory";
+    case MM_ERR_NONFINITE: return "non-finite coordinates";
+    case MM_ERR_TIMEOUT: return "device wait timed out";
+    case MM_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* mm_last_error(void) { return g_err.c_str(); }
+
+mm_status mm_build_hierarchy(const mm_graph* g, const mm_params* p, void* stream,
+                             mm_hierarchy** out) {
+  g_err.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mm_hierarchy* h = nullptr;
+  mm_status st = build(g, p, (cudaStream_t)stream, &h);
+  if (st != MM_OK) {
+    mm_free_hierarchy(h);
+    return st;
+  }
+  *out = h;
+  return MM_OK;
+}
+
+mm_status mm_build_hierarchy_levels(int32_t num_levels, const mm_level_desc* levels,
+                                    const float* edge_len0, const mm_params* p, void* stream,
+                                    mm_hierarchy** out) {
+  g_err.clear();
+  if (!out) {
+    set_error("out is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mm_hierarchy* h = nullptr;
+  mm_status st = build_explicit(num_levels, levels, edge_len0, p, (cudaStream_t)stream, &h);
+  if (st != MM_OK) {
+    mm_free_hierarchy(h);
+    return st;
+  }
+  *out = h;
+  return MM_OK;
+}
+
+void mm_free_hierarchy(mm_hierarchy* h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  cudaDeviceSynchronize();
+  for (Level& L : h->levels) free_level(L);
+  tree_ws_free(h->tree);
+  void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate,
+                  h->zero, h->lsw, h->trace};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cs) cudaStreamDestroy(h->cs);
+  delete h;
+}
+
+mm_status mm_hierarchy_levels(const mm_hierarchy* h, int32_t* num_levels) {
+  if (!h || !num_levels) {
+    set_error("NULL argument");
+    return MM_ERR_INVALID_ARG;
+  }
+  *num_levels = (int32_t)h->levels.size();
+  return MM_OK;
+}
+
+mm_status mm_level_info(const mm_hierarchy* h, int32_t level, int32_t* n, int64_t* nnz_E,
+                        int64_t* nnz_S) {
+  MM_TRY(level_check(h, level));
+  const Level& L = h->levels[level];
+  if (n) *n = L.n;
+  if (nnz_E) *nnz_E = L.nnzE;
+  if (nnz_S) *nnz_S = L.nnzS;
+  return MM_OK;
+}
+
+mm_status mm_level_export(const mm_hierarchy* h, int32_t level, int64_t* row_ptr, int32_t* col,
+                          float* omega, float* c, int32_t* map, int64_t* s_ptr, int32_t* s_col,
+                          float* s_d, float* rho, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = h->levels[level];
+  const int nb = ceil_div(L.n + 1, 256);
+  if (row_ptr) i32_to_i64<<<nb, 256, 0, s>>>(L.n + 1, L.rp, row_ptr);
+  if (col && L.nnzE) MM_CK(cudaMemcpyAsync(col, L.col, 4 * L.nnzE, cudaMemcpyDeviceToDevice, s));
+  if (omega && L.nnzE)
+    MM_CK(cudaMemcpyAsync(omega, L.omega, 4 * L.nnzE, cudaMemcpyDeviceToDevice, s));
+  if (c) MM_CK(cudaMemcpyAsync(c, L.c, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+  if (map && L.map) MM_CK(cudaMemcpyAsync(map, L.map, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+  if (s_ptr) i32_to_i64<<<nb, 256, 0, s>>>(L.n + 1, L.sp, s_ptr);
+  if ((s_col || s_d) && L.nnzS)
+    split_sent<<<ceil_div(L.nnzS, 256), 256, 0, s>>>(L.nnzS, L.s, s_col, s_d);
+  if (rho) MM_CK(cudaMemcpyAsync(rho, L.rho, 4 * (size_t)L.n, cudaMemcpyDeviceToDevice, s));
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha, const float* x_in, float* x_out,
+                   double* stats, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x_in || !x_out || x_in == x_out) {
+    set_error("x_in and x_out must be distinct device buffers");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = h->levels[level];
+  XSel x{(const float2*)x_in, (const float2*)x_out, h->zero};
+  set_state<<<1, 1, 0, s>>>(h->sstate, alpha);
+  MM_CK(cudaGetLastError());
+  SchedParams sp = sched_of(h->p, 1 << 30);
+  sp.iters_per_alpha = 1 << 30;
+  sp.max_iters_at_min = 1 << 30;
+  sp.early_exit = 0;
+  MM_TRY(sweep_body(h, level, h->p.exact_repulsion != 0, x, h->sstate, sp, nullptr, 0, nullptr,
+                    0, false, s));
+  if (stats) {
+    SweepState hs;
+    MM_CK(cudaMemcpyAsync(&hs, h->sstate, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaStreamSynchronize(s));
+    stats[0] = hs.last_sdx;
+    stats[1] = hs.last_sx;
+    stats[2] = hs.last_stress;
+    if (hs.error) {
+      set_error("the sweep produced non-finite coordinates");
+      return MM_ERR_NONFINITE;
+    }
+    return tree_error(h, s);
+  }
+  return MM_OK;
+}
+
+mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float theta, float* F_out,
+                       void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x || !F_out) {
+    set_error("NULL buffer");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->levels[level].n;
+  XSel xs{(const float2*)x, (const float2*)x, h->zero};
+  if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
+  MM_TRY(bh_build(xs, n, theta, h->tree, s));
+  MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s));
+  return tree_error(h, s);
+}
+
+mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init, float* x_out,
+                    mm_layout_stats* stats, void* stream) {
+  g_err.clear();
+  if (!h) {
+    set_error("hierarchy is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  return layout(h, p, x_init, x_out, stats, (cudaStream_t)stream);
+}
+
+mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32_t reps,
+                           double* stage_ms, int64_t* work, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x || !stage_ms || reps < 1) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = h->levels[level];
+  const bool exact = h->p.exact_repulsion != 0;
+  float2* tmp = nullptr;
+  unsigned long long* cnt = nullptr;
+  MM_CK(cudaMalloc(&tmp, sizeof(float2) * (size_t)std::max(L.n, 1)));
+  MM_CK(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
+  MM_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+  XSel xs{(const float2*)x, tmp, h->zero};
+  cudaEvent_t ev[9];
+  for (auto& e : ev) MM_CK(cudaEventCreate(&e));
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  SchedParams sp = sched_of(h->p, 1 << 30);
+  sp.early_exit = 0;
+  mm_status st = MM_OK;
+  for (int r = 0; r <= reps && st == MM_OK; ++r) {  // r = 0 warms up
+    set_state<<<1, 1, 0, s>>>(h->sstate, 0.3);
+    if (exact) {
+      cudaEventRecord(ev[0], s);
+      for (int i = 1; i <= 5; ++i) cudaEventRecord(ev[i], s);
+      st = exact_repulsion(xs, L.n, h->F, s);
+    } else {
+      st = bh_build(xs, L.n, h->p.theta, h->tree, s, ev);
+      if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, nullptr, s);
+    }
+    cudaEventRecord(ev[6], s);
+    if (st == MM_OK) st = gather_update(L, xs, h->F, h->sstate, h->partials, s);
+    cudaEventRecord(ev[7], s);
+    if (st == MM_OK)
+      st = controller(gather_blocks(L), h->partials, h->sstate, sp, nullptr, 0, nullptr, 0, false, s);
+    cudaEventRecord(ev[8], s);
+    if (cudaEventSynchronize(ev[8]) != cudaSuccess) {
+      st = cuda_status(cudaGetLastError(), "profile sweep", __FILE__, __LINE__);
+      break;
+    }
+    if (r == 0) continue;
+    for (int i = 0; i < 8; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  if (st == MM_OK && !exact && work) {
+    st = bh_build(xs, L.n, h->p.theta, h->tree, s);
+    if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, cnt, s);
+  }
+  unsigned long long hc[2] = {0, 0};
+  if (st == MM_OK) {
+    cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "profile", __FILE__, __LINE__);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaFree(tmp);
+  cudaFree(cnt);
+  MM_TRY(st);
+  for (int i = 0; i < 8; ++i) stage_ms[i] = acc[i] / reps;
+  if (work) {
+    work[0] = (int64_t)hc[0];
+    work[1] = exact ? (int64_t)L.n * L.n : (int64_t)hc[1];
+    work[2] = L.nnzS;
+    work[3] = L.n;
+  }
+  return tree_error(h, s);
+}
+
+mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x, double alpha,
+                       double* stress, double* lnsum, double* M, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x) {
+    set_error("x is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  double out[3];
+  MM_TRY(objective_exact(h->levels[level], (const float2*)x, alpha, out, (cudaStream_t)stream));
+  if (stress) *stress = out[0];
+  if (lnsum) *lnsum = out[1];
+  if (M) *M = out[2];
+  return MM_OK;
+}
+
+mm_status mm_khop(int32_t n, const int64_t* row_ptr, const int32_t* col, const float* edge_len,
+                  const float* node_c, int32_t k, int64_t* s_ptr, int64_t* nnz_S, int32_t* s_col,
+                  float* s_d, float* rho, void* stream) {
+  g_err.clear();
+  if (n < 1 || !row_ptr || !s_ptr || !nnz_S || (s_col && (!s_d || !rho))) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* rp = nullptr;
+  int32_t* sp = nullptr;
+  SEnt* S = nullptr;
+  float* r = nullptr;
+  int64_t nnz = 0;
+  MM_CK(cudaMalloc(&rp, sizeof(int32_t) * (size_t)(n + 1)));
+  rp_to_i32<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, row_ptr, rp);
+  mm_status st = build_khop(n, rp, col, edge_len, node_c, k, &sp, &S, &r, &nnz, s);
+  if (st == MM_OK) {
+    i32_to_i64<<<ceil_div(n + 1, 256), 256, 0, s>>>(n + 1, sp, s_ptr);
+    *nnz_S = nnz;
+    if (s_col) {
+      if (nnz) split_sent<<<ceil_div(nnz, 256), 256, 0, s>>>(nnz, S, s_col, s_d);
+      cudaMemcpyAsync(rho, r, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "mm_khop", __FILE__, __LINE__);
+  }
+  cudaFree(rp);
+  if (sp) cudaFree(sp);
+  if (S) cudaFree(S);
+  if (r) cudaFree(r);
+  return st;
+}
+
+mm_status mm_cluster(int32_t n, const int64_t* row_ptr, const int32_t* col, const float* omega,
+                     const float* node_c, float U, int32_t rounds, uint64_t seed, int32_t level,
+                     int32_t* labels_out, void* stream) {
+  g_err.clear();
+  if (n < 1 || !row_ptr || !node_c || !labels_out || rounds < 0) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* rp = nullptr;
+  MM_CK(cudaMalloc(&rp, sizeof(int32_t) * (size_t)(n + 1)));
+  rp_to_i32<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, row_ptr, rp);
+  mm_status st = cluster_lp(n, rp, col, omega, node_c, U, rounds, seed, level, labels_out, s);
+  cudaStreamSynchronize(s);
+  cudaFree(rp);
+  return st;
+}
+
+mm_status mm_contract(int32_t n, const int64_t* row_ptr, const int32_t* col, const float* omega,
+                      const float* node_c, const int32_t* labels, int32_t* map, float* c_out,
+                      int64_t* crow_ptr, int32_t* ccol, float* comega, int32_t* n_coarse,
+                      int64_t* nnz_coarse, void* stream) {
+  g_err.clear();
+  if (n < 1 || !row_ptr || !node_c || !labels || !map || !c_out || !crow_ptr || !ccol ||
+      !comega || !n_coarse || !nnz_coarse) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* rp = nullptr;
+  MM_CK(cudaMalloc(&rp, sizeof(int32_t) * (size_t)(n + 1)));
+  rp_to_i32<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, row_ptr, rp);
+  Level out;
+  mm_status st = contract(n, rp, col, omega, node_c, labels, map, out, s);
+  if (st == MM_OK) {
+    *n_coarse = out.n;
+    *nnz_coarse = out.nnzE;
+    cudaMemcpyAsync(c_out, out.c, sizeof(float) * out.n, cudaMemcpyDeviceToDevice, s);
+    i32_to_i64<<<ceil_div(out.n + 1, 256), 256, 0, s>>>(out.n + 1, out.rp, crow_ptr);
+    if (out.nnzE) {
+      cudaMemcpyAsync(ccol, out.col, sizeof(int32_t) * out.nnzE, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(comega, out.omega, sizeof(float) * out.nnzE, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "mm_contract", __FILE__, __LINE__);
+  }
+  free_level(out);
+  cudaFree(rp);
+  return st;
+}
+
+mm_status mm_prolong(int32_t n_fine, const int32_t* map, const float* x_coarse,
+                     const float* c_coarse, uint64_t seed, int32_t level, float* x_fine,
+                     void* stream) {
+  g_err.clear();
+  if (n_fine < 0 || (n_fine > 0 && (!map || !x_coarse || !c_coarse || !x_fine))) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  int32_t* zero = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  MM_CK(cudaMalloc(&zero, sizeof(int32_t)));
+  cudaMemsetAsync(zero, 0, sizeof(int32_t), s);
+  XSel xc{(const float2*)x_coarse, (const float2*)x_coarse, zero};
+  mm_status st = prolong(n_fine, map, xc, c_coarse, seed, level, (float2*)x_fine, s);
+  cudaStreamSynchronize(s);
+  cudaFree(zero);
+  return st;
+}
+
+mm_status mm_layout_host(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                         const float* edge_len, const mm_params* p, float* x_out,
+                         mm_layout_stats* stats, void* stream) {
+  g_err.clear();
+  if (n < 1 || !row_ptr || !x_out) {
+    set_error("invalid arguments");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nnz = row_ptr[n];
+  int64_t* drp = nullptr;
+  int32_t* dcol = nullptr;
+  float* dlen = nullptr;
+  float* dx = nullptr;
+  mm_hierarchy* h = nullptr;
+  mm_status st = MM_OK;
+  cudaError_t e = cudaMalloc(&drp, sizeof(int64_t) * (size_t)(n + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&dcol, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1));
+  if (e == cudaSuccess && edge_len)
+    e = cudaMalloc(&dlen, sizeof(float) * (size_t)std::max<int64_t>(nnz, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&dx, sizeof(float2) * (size_t)n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(drp, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpyAsync(dcol, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && edge_len && nnz)
+    e = cudaMemcpyAsync(dlen, edge_len, sizeof(float) * nnz, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = cuda_status(e, "mm_layout_host upload", __FILE__, __LINE__);
+  if (st == MM_OK) {
+    mm_graph g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.nnz = nnz;
+    g.row_ptr = drp;
+    g.col = dcol;
+    g.edge_len = dlen;
+    g.num_graphs = 1;
+    st = mm_build_hierarchy(&g, p, stream, &h);
+  }
+  if (st == MM_OK) st = mm_layout(h, p, nullptr, dx, stats, stream);
+  if (st == MM_OK) {
+    e = cudaMemcpyAsync(x_out, dx, sizeof(float2) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "mm_layout_host download", __FILE__, __LINE__);
+  }
+  std::string keep = g_err;
+  mm_free_hierarchy(h);
+  cudaFree(drp);
+  cudaFree(dcol);
+  if (dlen) cudaFree(dlen);
+  cudaFree(dx);
+  g_err = keep;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// Internal declarations of the GB300 MulMent library.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mm.h"
+
+namespace mm {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char* fmt, ...);
+mm_status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define MM_CK(call)                                                          \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) return mm::cuda_status(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+// Propagates an mm_status from a helper.
+#define MM_TRY(expr)                      \
+  do {                                    \
+    mm_status s_ = (expr);                \
+    if (s_ != MM_OK) return s_;           \
+  } while (0)
+
+constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ data types --
+// One entry of the pair set S: neighbour id and target distance d_uv.
+struct __align__(8) SEnt {
+  int32_t col;
+  float d;
+};
+
+// Device-resident state of the alpha schedule (Sec. 3.2).  The sweep kernels
+// read alpha and the buffer parity from here; the controller kernel updates
+// it after each sweep, so a whole level runs without host round trips.
+struct SweepState {
+  double alpha;        // alpha of the next sweep
+  double last_rel;     // relative change of the last sweep
+  double last_stress;  // stress over S of the last sweep's input
+  double last_sdx, last_sx;
+  int32_t it_in_round; // iterations done at the current alpha
+  int32_t total;       // sweeps in this layout so far
+  int32_t level_sweeps;
+  int32_t parity;      // x lives in buffer [parity]
+  int32_t done;
+  int32_t error;       // MM_ERR_NONFINITE when a sweep went non-finite
+  int32_t pad[2];
+};
+
+// Schedule constants (copied into the controller launch).
+struct SchedParams {
+  double alpha0, alpha_factor, alpha_min, eps, eps_final;
+  int32_t iters_per_alpha, max_iters_at_min, early_exit, level_cap;
+};
+
+// Selects the current position buffer by the device-side parity.
+struct XSel {
+  const float2* b0;
+  const float2* b1;
+  const int32_t* parity;
+  __device__ __forceinline__ const float2* cur() const { return *parity ? b1 : b0; }
+  __device__ __forceinline__ float2* next() const {
+    return const_cast<float2*>(*parity ? b0 : b1);
+  }
+};
+
+// One level of the hierarchy (device arrays).
+struct Level {
+  int32_t n = 0;
+  int64_t nnzE = 0, nnzS = 0;
+  int32_t* rp = nullptr;     // [n+1]
+  int32_t* col = nullptr;    // [nnzE]
+  float* omega = nullptr;    // [nnzE] edge weights (Sec. 3.1)
+  float* c = nullptr;        // [n] node weights
+  float* elen = nullptr;     // [nnzE] input lengths (level 0 only, nullable)
+  int32_t* map = nullptr;    // [n] -> next coarser level
+  int32_t* sp = nullptr;     // [n+1]
+  SEnt* s = nullptr;         // [nnzS]
+  float* rho = nullptr;      // [n]
+  int32_t* heavy = nullptr;  // vertices whose |S_u| > heavy_degree
+  int32_t n_heavy = 0;
+  int32_t max_deg = 0;       // max |S_u|
+  int32_t lanes = 1;         // lanes per vertex in the light gather
+  int32_t heavy_degree = 0;
+  double sum_c = 0;
+};
+
+// ----------------------------------------------------------- primitives --
+struct SortWS {
+  uint32_t* counts = nullptr;  // [256 * max_tiles]
+  uint32_t* totals = nullptr;  // [256]
+  int max_tiles = 0;
+};
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 8;
+constexpr int kSortTile = kSortThreads * kSortIPT;
+
+mm_status sort_ws_alloc(SortWS& ws, int64_t max_n);
+void sort_ws_free(SortWS& ws);
+
+// Stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit).
+// Ping-pongs between the two buffers; *keys_out / *vals_out receive the
+// buffer that holds the result.
+mm_status radix_sort_u32(uint32_t* k0, uint32_t* k1, int32_t* v0, int32_t* v1, int n,
+                         int begin_bit, int end_bit, SortWS& ws, cudaStream_t s,
+                         uint32_t** keys_out, int32_t** vals_out);
+mm_status radix_sort_u64(uint64_t* k0, uint64_t* k1, int32_t* v0, int32_t* v1, int n,
+                         int begin_bit, int end_bit, SortWS& ws, cudaStream_t s,
+                         uint64_t** keys_out, int32_t** vals_out);
+
+// Exclusive scan of int32 counts; out[n] receives the total.  ws needs
+// scan_ws_bytes(n) bytes.
+size_t scan_ws_bytes(int64_t n);
+mm_status scan_exclusive_i32(const int32_t* in, int32_t* out, int n, void* ws,
+                             cudaStream_t s);
+mm_status scan_exclusive_i64(const int32_t* in, int64_t* out, int n, void* ws,
+                             cudaStream_t s);
+
+// ------------------------------------------------------------ quadtree --
+// Workspace of the Barnes-Hut tree, sized for the largest level.
+struct TreeWS {
+  int64_t cap = 0;
+  uint32_t* keys[2] = {nullptr, nullptr};
+  int32_t* vals[2] = {nullptr, nullptr};
+  float2* xs = nullptr;       // positions in Morton order
+  int32_t* lo = nullptr;      // internal nodes [n-1]
+  int32_t* hi = nullptr;
+  int32_t* left = nullptr;
+  int32_t* right = nullptr;
+  int32_t* delta = nullptr;
+  int32_t* owner = nullptr;   // owner[g] = internal node whose split is g
+  int32_t* parent = nullptr;  // all nodes [2n-1]
+  uint32_t* visit = nullptr;  // internal nodes, epoch of the first arrival
+  double2* sums = nullptr;    // all nodes, position sums
+  float4* nodeA = nullptr;    // (cx, cy, r_crit^2, count)
+  int4* nodeB = nullptr;      // (first child | -1, escape | -1, lo, hi+1)
+  float4* partials = nullptr; // bbox partial results
+  float4* root = nullptr;     // (min x, min y, side, key scale)
+  uint32_t* ticket = nullptr; // [0] last-block ticket, [1] build epoch
+  int* err = nullptr;         // set by a walk that met a broken tree
+  SortWS sort;
+};
+constexpr int kKeyBits = 16;  // per axis -> 32-bit Morton keys, depth 16
+
+mm_status tree_ws_alloc(TreeWS& ws, int64_t n);
+void tree_ws_free(TreeWS& ws);
+
+// Rebuilds the quadtree from the current positions (bbox, Morton keys,
+// sort, radix tree, bottom-up centroids, node records).
+// ev (nullable, 6 events) records the stage boundaries for profiling.
+mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s,
+                   cudaEvent_t* ev = nullptr);
+// Warp-synchronous stackless walk: F[v] = sum over accepted cells / leaves.
+mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
+                      unsigned long long* counters, cudaStream_t s);
+// Tiled exact sum F[v] = sum_{u != v} r(v, u).
+mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
+
+// ---------------------------------------------------------------- sweep --
+constexpr int kGatherThreads = 256;
+int gather_blocks(const Level& L);
+// Fused Eq. 2 update over S plus per-block partial sums (3 doubles/block).
+mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
+                        double* partials, cudaStream_t s);
+// Reduces the partials, applies the alpha schedule, optionally sets the
+// graph loop condition.
+mm_status controller(int nblocks, const double* partials, SweepState* st, SchedParams sp,
+                     float* trace, int trace_cap, int* level_sweeps_out,
+                     cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s);
+// Writes the prolongated positions into xf_direct, or into xc.next() when
+// xf_direct is NULL.
+mm_status prolong(int n_fine, const int32_t* map, XSel xc, const float* cc, uint64_t seed,
+                  int level, float2* xf_direct, cudaStream_t s);
+mm_status level_start(SweepState* st, double alpha0, int flip, cudaStream_t s);
+mm_status init_coarsest(int n, const float* c, const SEnt* s0, uint64_t seed, int level,
+                        float R, float2* x0, SweepState* st, double alpha0, cudaStream_t s);
+mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s);
+
+// ------------------------------------------------------------ hierarchy --
+mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t* col,
+                         int32_t* rp32_out, cudaStream_t s);
+mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* elen,
+                     const float* c, int k, int32_t** sp_out, SEnt** s_out, float** rho_out,
+                     int64_t* nnz_out, cudaStream_t s);
+mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* omega,
+                     const float* c, float U, int rounds, uint64_t seed, int level,
+                     int32_t* labels, cudaStream_t s);
+mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* omega,
+                   const float* c, const int32_t* labels, int32_t* map, Level& out,
+                   cudaStream_t s);
+mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s);
+
+// ------------------------------------------------------------ objective --
+mm_status objective_exact(const Level& L, const float2* x, double alpha, double out[3],
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------- philox --
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 bijection.
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                        uint32_t c3, uint32_t k0, uint32_t k1,
+                                                        uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+}  // namespace mm

@@ -1,0 +1,402 @@
+"""Thin Python binding of the libmm.so C-ABI (include/mm.h).
+
+Argument marshalling only: every step of the layout runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  The
+binding fails loudly when the library has not been built or no GPU is
+visible; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmm.so")
+
+MM_OK = 0
+STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_NOT_CONNECTED", 3: "MM_ERR_CUDA",
+          4: "MM_ERR_OOM", 5: "MM_ERR_NONFINITE", 6: "MM_ERR_TIMEOUT", 7: "MM_ERR_UNSUPPORTED"}
+MM_PARAMS_VERSION = 1
+MM_MAX_LEVELS = 64
+
+# every symbol include/mm.h declares
+EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_hierarchy",
+           "mm_build_hierarchy_levels",
+           "mm_free_hierarchy", "mm_hierarchy_levels", "mm_level_info", "mm_level_export",
+           "mm_sweep", "mm_repulsion", "mm_layout", "mm_sweep_profile", "mm_objective",
+           "mm_khop", "mm_cluster",
+           "mm_contract", "mm_prolong", "mm_layout_host"]
+
+
+class MMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("struct_version", ctypes.c_uint32), ("k", ctypes.c_int32), ("theta", ctypes.c_float),
+        ("exact_repulsion", ctypes.c_int32), ("coarsest_n", ctypes.c_int32),
+        ("f", ctypes.c_float), ("b", ctypes.c_float), ("lp_rounds", ctypes.c_int32),
+        ("iters_per_alpha", ctypes.c_int32), ("alpha0", ctypes.c_double),
+        ("alpha_factor", ctypes.c_double), ("alpha_min", ctypes.c_double),
+        ("eps", ctypes.c_double), ("eps_final", ctypes.c_double),
+        ("max_iters_at_min", ctypes.c_int32), ("early_exit", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("max_levels", ctypes.c_int32),
+        ("max_stalls", ctypes.c_int32), ("gather_lanes", ctypes.c_int32),
+        ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("edge_len", ctypes.c_void_p),
+                ("num_graphs", ctypes.c_int32), ("graph_ptr", ctypes.c_void_p)]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("omega", ctypes.c_void_p), ("node_c", ctypes.c_void_p),
+                ("map", ctypes.c_void_p)]
+
+
+class LayoutStats(ctypes.Structure):
+    _fields_ = [("num_levels", ctypes.c_int32), ("total_sweeps", ctypes.c_int32),
+                ("vertex_updates", ctypes.c_int64),
+                ("level_n", ctypes.c_int32 * MM_MAX_LEVELS),
+                ("level_sweeps", ctypes.c_int32 * MM_MAX_LEVELS),
+                ("final_alpha", ctypes.c_double), ("final_rel_change", ctypes.c_double),
+                ("final_stress", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        nl = self.num_levels
+        return dict(num_levels=nl, total_sweeps=self.total_sweeps,
+                    vertex_updates=int(self.vertex_updates),
+                    level_n=list(self.level_n[:nl]), level_sweeps=list(self.level_sweeps[:nl]),
+                    final_alpha=self.final_alpha, final_rel_change=self.final_rel_change,
+                    final_stress=self.final_stress, kernel_launches=int(self.kernel_launches))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libmm.so; raises if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1506_04383_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u64, f32, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                  ctypes.c_uint64, ctypes.c_float, ctypes.c_double)
+    lib.mm_default_params.argtypes = [P]
+    lib.mm_default_params.restype = None
+    lib.mm_status_string.argtypes = [i32]
+    lib.mm_status_string.restype = ctypes.c_char_p
+    lib.mm_last_error.argtypes = []
+    lib.mm_last_error.restype = ctypes.c_char_p
+    lib.mm_build_hierarchy.argtypes = [P, P, P, P]
+    lib.mm_build_hierarchy_levels.argtypes = [i32, P, P, P, P, P]
+    lib.mm_free_hierarchy.argtypes = [P]
+    lib.mm_free_hierarchy.restype = None
+    lib.mm_hierarchy_levels.argtypes = [P, P]
+    lib.mm_level_info.argtypes = [P, i32, P, P, P]
+    lib.mm_level_export.argtypes = [P, i32, P, P, P, P, P, P, P, P, P, P]
+    lib.mm_sweep.argtypes = [P, i32, f64, P, P, P, P]
+    lib.mm_repulsion.argtypes = [P, i32, P, f32, P, P]
+    lib.mm_layout.argtypes = [P, P, P, P, P, P]
+    lib.mm_sweep_profile.argtypes = [P, i32, P, i32, P, P, P]
+    lib.mm_objective.argtypes = [P, i32, P, f64, P, P, P, P]
+    lib.mm_khop.argtypes = [i32, P, P, P, P, i32, P, P, P, P, P, P]
+    lib.mm_cluster.argtypes = [i32, P, P, P, P, f32, i32, u64, i32, P, P]
+    lib.mm_contract.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P, P, P]
+    lib.mm_prolong.argtypes = [i32, P, P, P, u64, i32, P, P]
+    lib.mm_layout_host.argtypes = [i32, P, P, P, P, P, P, P]
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
+                        "mm_last_error"):
+            fn.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != MM_OK:
+        msg = load().mm_last_error().decode(errors="replace")
+        raise MMError(status, msg)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().mm_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device visible: libmm has no CPU fallback")
+
+
+class Hierarchy:
+    """Owns an mm_hierarchy (freed on deletion)."""
+
+    def __init__(self, handle, n):
+        self.handle = handle
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mm_free_hierarchy(self.handle)
+            self.handle = None
+
+    def levels(self) -> int:
+        v = ctypes.c_int32()
+        _check(load().mm_hierarchy_levels(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def level_info(self, level):
+        n, e, s = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().mm_level_info(self.handle, level, ctypes.byref(n), ctypes.byref(e),
+                                    ctypes.byref(s)))
+        return n.value, e.value, s.value
+
+
+def build_hierarchy(row_ptr, col, params: Params = None, edge_len=None, stream=None):
+    """row_ptr int64 [n+1] and col int32 [nnz] CUDA tensors (symmetric CSR)."""
+    _require_cuda()
+    lib = load()
+    row_ptr = _dev(row_ptr, torch.int64, "row_ptr")
+    col = _dev(col, torch.int32, "col")
+    edge_len = _dev(edge_len, torch.float32, "edge_len")
+    p = params if params is not None else default_params()
+    g = Graph(n=row_ptr.numel() - 1, nnz=col.numel(), row_ptr=row_ptr.data_ptr(),
+              col=col.data_ptr() if col.numel() else None,
+              edge_len=edge_len.data_ptr() if edge_len is not None else None,
+              num_graphs=1, graph_ptr=None)
+    h = ctypes.c_void_p()
+    _check(lib.mm_build_hierarchy(ctypes.byref(g), ctypes.byref(p), _stream(stream),
+                                  ctypes.byref(h)))
+    return Hierarchy(h, g.n)
+
+
+def build_hierarchy_levels(levels, params: Params = None, edge_len0=None, stream=None):
+    """Hierarchy from caller-supplied levels: a list of dicts with CUDA
+    tensors row_ptr (int64), col (int32), optional omega / c (float32) and
+    map (int32, all but the last level)."""
+    _require_cuda()
+    keep = []
+    descs = (LevelDesc * len(levels))()
+    for i, L in enumerate(levels):
+        rp = _dev(L["row_ptr"], torch.int64, "row_ptr")
+        col = _dev(L["col"], torch.int32, "col")
+        om = _dev(L.get("omega"), torch.float32, "omega")
+        c = _dev(L.get("c"), torch.float32, "c")
+        mp = _dev(L.get("map"), torch.int32, "map")
+        keep += [rp, col, om, c, mp]
+        descs[i] = LevelDesc(n=rp.numel() - 1, nnz=col.numel(), row_ptr=rp.data_ptr(),
+                             col=col.data_ptr() if col.numel() else None,
+                             omega=om.data_ptr() if om is not None else None,
+                             node_c=c.data_ptr() if c is not None else None,
+                             map=mp.data_ptr() if mp is not None else None)
+    el = _dev(edge_len0, torch.float32, "edge_len0")
+    p = params if params is not None else default_params()
+    h = ctypes.c_void_p()
+    _check(load().mm_build_hierarchy_levels(len(levels), descs, _ptr(el), ctypes.byref(p),
+                                            _stream(stream), ctypes.byref(h)))
+    return Hierarchy(h, descs[0].n)
+
+
+def level_export(h: Hierarchy, level: int, stream=None):
+    n, nnzE, nnzS = h.level_info(level)
+    dev = torch.device("cuda")
+    out = dict(
+        row_ptr=torch.empty(n + 1, dtype=torch.int64, device=dev),
+        col=torch.empty(nnzE, dtype=torch.int32, device=dev),
+        omega=torch.empty(nnzE, dtype=torch.float32, device=dev),
+        c=torch.empty(n, dtype=torch.float32, device=dev),
+        map=torch.full((n,), -1, dtype=torch.int32, device=dev),
+        s_ptr=torch.empty(n + 1, dtype=torch.int64, device=dev),
+        s_col=torch.empty(nnzS, dtype=torch.int32, device=dev),
+        s_d=torch.empty(nnzS, dtype=torch.float32, device=dev),
+        rho=torch.empty(n, dtype=torch.float32, device=dev),
+    )
+    _check(load().mm_level_export(h.handle, level, *[_ptr(out[k]) if out[k].numel() else None
+                                                     for k in ("row_ptr", "col", "omega", "c",
+                                                               "map", "s_ptr", "s_col", "s_d",
+                                                               "rho")], _stream(stream)))
+    torch.cuda.current_stream().synchronize()
+    return out
+
+
+def sweep(h: Hierarchy, level: int, alpha: float, x_in, x_out=None, stats=True, stream=None):
+    """One Eq. 2 iteration; returns (x_out, [sum|dx|^2, sum|x|^2, stress] or None)."""
+    x_in = _dev(x_in, torch.float32, "x_in")
+    if x_out is None:
+        x_out = torch.empty_like(x_in)
+    st = (ctypes.c_double * 3)() if stats else None
+    _check(load().mm_sweep(h.handle, level, float(alpha), _ptr(x_in), _ptr(x_out), st,
+                           _stream(stream)))
+    return x_out, (list(st) if stats else None)
+
+
+def repulsion(h: Hierarchy, level: int, x, theta: float, stream=None):
+    """F_u = sum_{v != u} r(u,v): theta > 0 Barnes-Hut, 0 tree-exact, < 0 tiled exact."""
+    x = _dev(x, torch.float32, "x")
+    F = torch.empty_like(x)
+    _check(load().mm_repulsion(h.handle, level, _ptr(x), float(theta), _ptr(F), _stream(stream)))
+    return F
+
+
+def layout(h: Hierarchy, params: Params = None, x_init=None, x_out=None, stream=None):
+    """Multilevel layout (or single-level schedule from x_init); returns (x, stats)."""
+    x_init = _dev(x_init, torch.float32, "x_init")
+    if x_out is None:
+        x_out = torch.empty((h.n, 2), dtype=torch.float32, device="cuda")
+    st = LayoutStats()
+    _check(load().mm_layout(h.handle, ctypes.byref(params) if params is not None else None,
+                            _ptr(x_init), _ptr(x_out), ctypes.byref(st), _stream(stream)))
+    return x_out, st.as_dict()
+
+
+STAGES = ["bbox", "morton", "sort", "radix_tree", "bottom_up", "traverse", "gather",
+          "controller"]
+
+
+def sweep_profile(h: Hierarchy, level: int, x, reps: int = 10, stream=None):
+    """Mean ms per sweep stage (CUDA events) and the walk's work counters."""
+    x = _dev(x, torch.float32, "x")
+    ms = (ctypes.c_double * 8)()
+    work = (ctypes.c_int64 * 4)()
+    _check(load().mm_sweep_profile(h.handle, level, _ptr(x), int(reps), ms, work,
+                                   _stream(stream)))
+    return dict(stage_names=list(STAGES), stage_ms=list(ms), visits=int(work[0]),
+                interactions=int(work[1]), nnz_S=int(work[2]), n=int(work[3]))
+
+
+def objective(h: Hierarchy, level: int, x, alpha: float, stream=None):
+    """Eq. 1 over S (exact, all pairs): returns (stress, lnsum, M)."""
+    x = _dev(x, torch.float32, "x")
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().mm_objective(h.handle, level, _ptr(x), float(alpha), ctypes.byref(a),
+                               ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+    return a.value, b.value, c.value
+
+
+def khop(row_ptr, col, k: int, edge_len=None, node_c=None, stream=None):
+    """Pair set S of any graph; returns (s_ptr int64, s_col int32, s_d f32, rho f32)."""
+    _require_cuda()
+    lib = load()
+    row_ptr = _dev(row_ptr, torch.int64, "row_ptr")
+    col = _dev(col, torch.int32, "col")
+    edge_len = _dev(edge_len, torch.float32, "edge_len")
+    node_c = _dev(node_c, torch.float32, "node_c")
+    n = row_ptr.numel() - 1
+    sp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    nnz = ctypes.c_int64()
+    args = (n, _ptr(row_ptr), _ptr(col) if col.numel() else None, _ptr(edge_len), _ptr(node_c),
+            int(k), _ptr(sp), ctypes.byref(nnz))
+    _check(lib.mm_khop(*args, None, None, None, _stream(stream)))
+    m = nnz.value
+    scol = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    sd = torch.empty(max(m, 1), dtype=torch.float32, device="cuda")
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib.mm_khop(*args, _ptr(scol), _ptr(sd), _ptr(rho), _stream(stream)))
+    return sp, scol[:m], sd[:m], rho
+
+
+def cluster(row_ptr, col, omega, node_c, U: float, rounds: int, seed: int, level: int,
+            stream=None):
+    _require_cuda()
+    row_ptr = _dev(row_ptr, torch.int64, "row_ptr")
+    col = _dev(col, torch.int32, "col")
+    omega = _dev(omega, torch.float32, "omega")
+    node_c = _dev(node_c, torch.float32, "node_c")
+    n = row_ptr.numel() - 1
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(load().mm_cluster(n, _ptr(row_ptr), _ptr(col), _ptr(omega), _ptr(node_c), float(U),
+                             int(rounds), int(seed), int(level), _ptr(labels), _stream(stream)))
+    return labels
+
+
+def contract(row_ptr, col, omega, node_c, labels, stream=None):
+    """Returns (map, c', row_ptr', col', omega')."""
+    _require_cuda()
+    row_ptr = _dev(row_ptr, torch.int64, "row_ptr")
+    col = _dev(col, torch.int32, "col")
+    omega = _dev(omega, torch.float32, "omega")
+    node_c = _dev(node_c, torch.float32, "node_c")
+    labels = _dev(labels, torch.int32, "labels")
+    n = row_ptr.numel() - 1
+    nnz = col.numel()
+    mp = torch.empty(n, dtype=torch.int32, device="cuda")
+    cc = torch.empty(n, dtype=torch.float32, device="cuda")
+    crp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    ccol = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    cw = torch.empty(max(nnz, 1), dtype=torch.float32, device="cuda")
+    nc, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().mm_contract(n, _ptr(row_ptr), _ptr(col), _ptr(omega), _ptr(node_c),
+                              _ptr(labels), _ptr(mp), _ptr(cc), _ptr(crp), _ptr(ccol), _ptr(cw),
+                              ctypes.byref(nc), ctypes.byref(m), _stream(stream)))
+    nc, m = nc.value, m.value
+    return mp, cc[:nc], crp[:nc + 1], ccol[:m], cw[:m]
+
+
+def prolong(mp, x_coarse, c_coarse, seed: int, level: int, stream=None):
+    _require_cuda()
+    mp = _dev(mp, torch.int32, "map")
+    x_coarse = _dev(x_coarse, torch.float32, "x_coarse")
+    c_coarse = _dev(c_coarse, torch.float32, "c_coarse")
+    xf = torch.empty((mp.numel(), 2), dtype=torch.float32, device="cuda")
+    _check(load().mm_prolong(mp.numel(), _ptr(mp), _ptr(x_coarse), _ptr(c_coarse), int(seed),
+                             int(level), _ptr(xf), _stream(stream)))
+    return xf
+
+
+def layout_host(row_ptr, col, params: Params = None, edge_len=None, stream=None):
+    """One-call API over host numpy buffers; returns (x numpy [n,2], stats)."""
+    _require_cuda()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    el = None if edge_len is None else np.ascontiguousarray(edge_len, dtype=np.float32)
+    n = len(rp) - 1
+    x = np.empty((n, 2), dtype=np.float32)
+    st = LayoutStats()
+    p = params if params is not None else default_params()
+    _check(load().mm_layout_host(n, rp.ctypes.data_as(ctypes.c_void_p),
+                                 cl.ctypes.data_as(ctypes.c_void_p),
+                                 el.ctypes.data_as(ctypes.c_void_p) if el is not None else None,
+                                 ctypes.byref(p), x.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.byref(st), _stream(stream)))
+    return x, st.as_dict()

@@ -25,5 +25,7 @@ def mm():
     """The CUDA library through its C-ABI binding (GPU tests only)."""
     if not gpu_available():
         pytest.skip("no CUDA device")
-    from paper_1506_04383_gb300 import mm as lib
+    from paper_1506_04383_gb300 import build, mm as lib
+    build.build()
+    lib.load()
     return lib

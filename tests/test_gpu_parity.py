@@ -1,0 +1,400 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances:
+  * one exact sweep: max |dx| <= 1e-4 x layout diameter;
+  * long-range sums F: per vertex |F_gpu - F_ref| <= 2e-4 * sum_v 1/|x_u-x_v|
+    (an FP32 accumulation bound: every term has magnitude 1/|x_u - x_v|);
+  * Barnes-Hut: the GPU walk accepts the same cells as the oracle's pointer
+    quadtree, so per-vertex forces agree to the FP32 bound above except for
+    acceptance-boundary ties (allowed on <= 1% of vertices); the GPU error
+    against the exact sum stays within the 2-D multipole remainder bound
+    2 theta^2 sum_v 1/|x_u - x_v| and, in RMS, within 5% of the oracle's own
+    Barnes-Hut error;
+  * pair sets, contraction: exact integers; distances to FP32 rounding;
+  * objective: relative 1e-5; final layouts: objective within 1%.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1506_04383_gb300 import graphs
+from golden_io import contract_example
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def inv_dist_sum(x):
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(len(x))
+    for i in range(0, len(x), 512):
+        d = np.sqrt(((x[i:i + 512, None, :] - x[None, :, :]) ** 2).sum(-1))
+        with np.errstate(divide="ignore"):
+            r = np.where(d > 0, 1.0 / d, 0.0)
+        out[i:i + 512] = r.sum(1)
+    return out
+
+
+def hier(mm, rp, col, **kw):
+    p = mm.default_params(**kw)
+    return mm.build_hierarchy(cu(rp), cu(col), p), p
+
+
+def diameter(x):
+    return float(np.ptp(np.asarray(x), axis=0).max())
+
+
+# ------------------------------------------------------------------ S -----
+@pytest.mark.parametrize("k", [1, 2])
+def test_khop_grid_matches_oracle(mm, k):
+    rp, col = graphs.grid(32, 32)
+    sp, scol, sd, rho = mm.khop(cu(rp), cu(col), k)
+    osp, oscol, osd, orho = oracle.build_S(rp, col, k)
+    assert np.array_equal(sp.cpu().numpy(), osp)
+    assert np.array_equal(scol.cpu().numpy(), oscol)
+    np.testing.assert_allclose(sd.cpu().numpy(), osd, rtol=1e-6)
+    np.testing.assert_allclose(rho.cpu().numpy(), orho, rtol=1e-5)
+    if k == 2:
+        assert len(oscol) == 11652
+
+
+def test_khop_coarse_lengths_match_oracle(mm):
+    rp, col, _, _ = graphs.rgg(3000, 7.0, 12, tune=False)
+    n = len(rp) - 1
+    c = np.random.default_rng(3).integers(1, 9, n).astype(np.float64)
+    sp, scol, sd, rho = mm.khop(cu(rp), cu(col), 2, node_c=cu(f32(c)))
+    osp, oscol, osd, orho = oracle.build_S(rp, col, 2, c=c, coarse=True)
+    assert np.array_equal(sp.cpu().numpy(), osp)
+    assert np.array_equal(scol.cpu().numpy(), oscol)
+    np.testing.assert_allclose(sd.cpu().numpy(), osd, rtol=2e-6)
+    np.testing.assert_allclose(rho.cpu().numpy(), orho, rtol=1e-5)
+
+
+# ----------------------------------------------------- exact repulsion ---
+@pytest.mark.parametrize("n_side", [(32, 32), (37, 29), (5, 3)])
+def test_exact_repulsion_matches_oracle(mm, n_side):
+    rp, col = graphs.grid(*n_side)
+    n = len(rp) - 1
+    x = f32(graphs.uniform_positions(n, 1506))
+    h, _ = hier(mm, rp, col, coarsest_n=n)
+    ref = oracle.repulsion_exact(x.astype(np.float64))
+    tol = 2e-4 * inv_dist_sum(x)[:, None]
+    for theta in (-1.0, 0.0):  # tiled kernel, fully opened tree
+        F = mm.repulsion(h, 0, cu(x), theta).cpu().numpy()
+        assert np.all(np.abs(F - ref) <= tol)
+
+
+# ---------------------------------------------------------- Barnes-Hut ---
+def _bh_check(mm, x, theta):
+    n = len(x)
+    rp, col = graphs.path(n)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1)
+    x64 = x.astype(np.float64)
+    F = mm.repulsion(h, 0, cu(x), theta).cpu().numpy().astype(np.float64)
+    Fo = oracle.repulsion_bh(x64, theta)
+    Fe = oracle.repulsion_exact(x64)
+    mag = inv_dist_sum(x)
+    same = np.all(np.abs(F - Fo) <= 2e-4 * mag[:, None], axis=1)
+    assert same.mean() >= 0.99, same.mean()
+    err_g = np.sqrt(((F - Fe) ** 2).sum(1))
+    err_o = np.sqrt(((Fo - Fe) ** 2).sum(1))
+    assert np.all(err_g <= 2 * theta ** 2 * mag * (1 + 1e-3) + 2e-4 * mag)
+    assert np.sqrt((err_g ** 2).mean()) <= 1.05 * np.sqrt((err_o ** 2).mean()) + 1e-6
+    return same.mean()
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+def test_bh_matches_oracle_uniform(mm, theta):
+    x = f32(graphs.uniform_positions(3001, 77, 0.0, 50.0))
+    _bh_check(mm, x, theta)
+
+
+def test_bh_matches_oracle_clustered_and_duplicates(mm):
+    rng = np.random.default_rng(5)
+    x = np.vstack([rng.normal(0, 1, (1500, 2)), rng.normal(30, 0.05, (700, 2)),
+                   np.repeat([[7.0, -3.0]], 40, axis=0),       # exact duplicates (bucket)
+                   rng.random((257, 2)) * 60 - 10])
+    _bh_check(mm, f32(x), 0.5)
+
+
+def test_bh_small_sizes(mm):
+    for n in (1, 2, 3, 31, 32, 33, 65):
+        x = f32(graphs.uniform_positions(n, n))
+        rp, col = graphs.path(n) if n > 1 else (np.array([0, 0]), np.zeros(0, np.int32))
+        if n == 1:
+            continue
+        h, _ = hier(mm, rp, col, coarsest_n=n, k=1)
+        F = mm.repulsion(h, 0, cu(x), 0.0).cpu().numpy()
+        ref = oracle.repulsion_exact(x.astype(np.float64))
+        assert np.all(np.abs(F - ref) <= 2e-4 * inv_dist_sum(x)[:, None] + 1e-12)
+
+
+# --------------------------------------------------------------- sweep ---
+@pytest.mark.parametrize("alpha", [1.0, 0.09, 0.008])
+@pytest.mark.parametrize("shape", [(32, 32), (37, 29)])
+def test_sweep_exact_matches_oracle(mm, alpha, shape):
+    rp, col = graphs.grid(*shape)
+    n = len(rp) - 1
+    x = f32(graphs.uniform_positions(n, 1506))
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, exact_repulsion=1)
+    xg, st = mm.sweep(h, 0, alpha, cu(x))
+    S = oracle.build_S(rp, col, 2)
+    xo, sto = oracle.sweep(x.astype(np.float64), S, alpha, 0)
+    assert np.abs(xg.cpu().numpy() - xo).max() <= 1e-4 * diameter(xo)
+    np.testing.assert_allclose(st, sto, rtol=1e-4)
+
+
+def test_sweep_bh_matches_oracle(mm):
+    rp, col, pts, _ = graphs.rgg(4000, 8.0, 21)
+    n = len(rp) - 1
+    x = f32(pts * 60.0)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5)
+    xg, _ = mm.sweep(h, 0, 0.3, cu(x))
+    S = oracle.build_S(rp, col, 2)
+    xo, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
+    d = np.abs(xg.cpu().numpy() - xo).max(1)
+    # acceptance-boundary ties may differ on a few vertices
+    assert np.mean(d <= 1e-4 * diameter(xo)) >= 0.99
+
+
+def test_sweep_heavy_row_star(mm):
+    n = 3000
+    rp, col = graphs.csr_from_edges(n, np.zeros(n - 1, dtype=int), np.arange(1, n))
+    x = f32(graphs.uniform_positions(n, 9, -5, 5))
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, exact_repulsion=1)
+    xg, _ = mm.sweep(h, 0, 0.09, cu(x))
+    xo, _ = oracle.sweep(x.astype(np.float64), oracle.build_S(rp, col, 1), 0.09, 0)
+    assert np.abs(xg.cpu().numpy() - xo).max() <= 1e-4 * diameter(xo)
+
+
+def test_sweep_coincident_points(mm):
+    rp, col = graphs.grid(10, 10)
+    n = 100
+    x = f32(graphs.uniform_positions(n, 4))
+    x[10:20] = x[10]          # ten coincident vertices (neighbours among them)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, exact_repulsion=1)
+    xg, _ = mm.sweep(h, 0, 0.3, cu(x))
+    xo, _ = oracle.sweep(x.astype(np.float64), oracle.build_S(rp, col, 2), 0.3, 0)
+    assert np.abs(xg.cpu().numpy() - xo).max() <= 1e-4 * diameter(xo)
+
+
+def test_sweep_full_size_rgg_100k(mm):
+    # the benchmark workload (100k-vertex random geometric graph, k = 2,
+    # theta = 0.5) at full size, compared on every vertex
+    rp, col, pts, _ = graphs.rgg(100000, 8.0, 1506)
+    n = len(rp) - 1
+    x = f32(pts * math.sqrt(n))
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5)
+    xg, _ = mm.sweep(h, 0, 0.3, cu(x))
+    S = oracle.build_S(rp, col, 2)
+    xo, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
+    d = np.abs(xg.cpu().numpy() - xo).max(1)
+    assert np.mean(d <= 1e-4 * diameter(xo)) >= 0.99
+
+
+# ------------------------------------------------------------ objective --
+def test_objective_matches_oracle(mm):
+    rp, col = graphs.grid(30, 31)
+    n = len(rp) - 1
+    x = f32(graphs.uniform_positions(n, 8, 0, 30))
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2)
+    st, ln, M = mm.objective(h, 0, cu(x), 0.008)
+    ost, oln, oM = oracle.objective(x.astype(np.float64), oracle.build_S(rp, col, 2), 0.008)
+    assert st == pytest.approx(ost, rel=1e-5)
+    assert ln == pytest.approx(oln, rel=1e-5)
+    assert M == pytest.approx(oM, rel=1e-5)
+
+
+# ------------------------------------------------- prolongation, coarsening
+def test_prolong_matches_oracle(mm):
+    nf, nc = 5000, 700
+    mp = np.random.default_rng(1).integers(0, nc, nf).astype(np.int32)
+    xc = f32(graphs.uniform_positions(nc, 2, -40, 40))
+    cc = f32(np.random.default_rng(2).integers(1, 30, nc))
+    xf = mm.prolong(cu(mp), cu(xc), cu(cc), seed=1506, level=3).cpu().numpy()
+    xo = oracle.prolong(mp, xc.astype(np.float64), cc.astype(np.float64), 1506, 3)
+    assert np.abs(xf - xo).max() <= 1e-5 * 50
+
+
+def test_contract_golden(mm):
+    g = contract_example()
+    mp, cc, crp, ccol, cw = mm.contract(cu(g["rp"]), cu(g["col"]), cu(f32(g["ew"])),
+                                        cu(f32(np.ones(g["n"]))), cu(g["labels"]))
+    assert mp.cpu().numpy().tolist() == g["map"].tolist()
+    assert cc.cpu().numpy().tolist() == g["c"].tolist()
+    assert crp.cpu().numpy().tolist() == g["crp"].tolist()
+    assert ccol.cpu().numpy().tolist() == g["ccol"].tolist()
+    assert cw.cpu().numpy().tolist() == g["cew"].tolist()
+
+
+def test_contract_matches_oracle_on_oracle_labels(mm):
+    rp, col, _, _ = graphs.rgg(20000, 8.0, 33, tune=False)
+    n = len(rp) - 1
+    c = np.ones(n)
+    lab = oracle.sclap(rp, col, c, 4.0, 10, 7, 1)
+    omp, occ, orp, ocol, ow = oracle.contract(rp, col, c, lab)
+    mp, cc, crp, ccol, cw = mm.contract(cu(rp), cu(col), cu(f32(np.ones(len(col)))),
+                                        cu(f32(c)), cu(lab))
+    assert np.array_equal(mp.cpu().numpy(), omp)
+    assert np.array_equal(cc.cpu().numpy(), occ)
+    assert np.array_equal(crp.cpu().numpy(), orp)
+    assert np.array_equal(ccol.cpu().numpy(), ocol)
+    assert np.array_equal(cw.cpu().numpy(), ow)
+
+
+@pytest.mark.parametrize("U", [2.0, 4.0, 9.0])
+def test_cluster_invariants(mm, U):
+    rp, col, _, _ = graphs.rgg(20000, 8.0, 34, tune=False)
+    n = len(rp) - 1
+    c = np.ones(n, dtype=np.float32)
+    lab = mm.cluster(cu(rp), cu(col), cu(np.ones(len(col), np.float32)), cu(c), U, 10, 5,
+                     0).cpu().numpy()
+    assert lab.min() >= 0 and lab.max() < n
+    w = np.bincount(lab, minlength=n)
+    assert w.max() <= U
+    ncl = np.count_nonzero(w)
+    # the parallel rounds coarsen about as strongly as the sequential
+    # label propagation of the oracle
+    olab = oracle.sclap(rp, col, np.ones(n), U, 10, 5, 0)
+    oncl = len(np.unique(olab))
+    assert ncl < 0.8 * n and ncl <= 1.3 * oncl, (ncl, oncl)
+    lab2 = mm.cluster(cu(rp), cu(col), cu(np.ones(len(col), np.float32)), cu(c), U, 10, 5,
+                      0).cpu().numpy()
+    assert np.array_equal(lab, lab2)  # deterministic
+
+
+def test_hierarchy_invariants(mm):
+    rp, col, _, _ = graphs.rgg(30000, 8.0, 35)
+    n = len(rp) - 1
+    h, p = hier(mm, rp, col, k=2, coarsest_n=100)
+    L = h.levels()
+    assert L >= 3
+    prev = None
+    for lv in range(L):
+        e = mm.level_export(h, lv)
+        nl = e["c"].numel()
+        assert float(e["c"].sum()) == n
+        if prev is not None:
+            assert nl < prev
+        prev = nl
+    assert prev <= 100
+
+
+# ---------------------------------------------------------------- layout --
+def test_layout_config1_grid_matches_oracle_objective(mm):
+    # 32x32 grid, k=2, exact repulsion, uniform [0,1]^2 start, 100 sweeps
+    rp, col = graphs.grid(32, 32)
+    n = len(rp) - 1
+    x0 = f32(graphs.uniform_positions(n, 1506))
+    kw = dict(k=2, exact_repulsion=1, coarsest_n=n, early_exit=0, max_iters_at_min=90)
+    h, p = hier(mm, rp, col, **kw)
+    x, st = mm.layout(h, p, x_init=cu(x0))
+    assert st["total_sweeps"] == 100 and st["level_sweeps"][0] == 100
+    po = oracle.params(**{k: v for k, v in kw.items()})
+    xo, _ = oracle.layout(rp, col, po, x_init=x0.astype(np.float64))
+    S = oracle.build_S(rp, col, 2)
+    Mg = oracle.objective(x.cpu().numpy().astype(np.float64), S, 0.008)[2]
+    Mo = oracle.objective(xo, S, 0.008)[2]
+    assert abs(Mg - Mo) <= 0.01 * abs(Mo)
+
+
+def oracle_levels_to_device(levels):
+    out = []
+    for L in levels:
+        d = dict(row_ptr=cu(L["rp"]), col=cu(L["col"]), omega=cu(f32(L["ew"])), c=cu(f32(L["c"])))
+        if L["map"] is not None:
+            d["map"] = cu(L["map"])
+        out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("case", ["rgg", "btree"])
+def test_layout_same_hierarchy_matches_oracle_objective(mm, case):
+    # the oracle's coarsening fed to the GPU: same levels, same seed, so the
+    # prolongation draws and the schedule are identical; the final
+    # objectives (Eq. 1 at alpha = 0.008) must agree within 1%
+    if case == "rgg":
+        rp, col, _, _ = graphs.rgg(3000, 8.0, 36)
+        kw = dict(k=2, theta=0.5, coarsest_n=100)
+    else:
+        rp, col = graphs.binary_tree(1023)
+        kw = dict(k=1, exact_repulsion=1, coarsest_n=2)
+    po = oracle.params(**kw)
+    levels = oracle.build_hierarchy(rp, col, po)
+    xo, info = oracle.layout(rp, col, po, levels=levels)
+    h = mm.build_hierarchy_levels(oracle_levels_to_device(levels), mm.default_params(**kw))
+    assert h.levels() == len(levels)
+    x, st = mm.layout(h)
+    xs = x.cpu().numpy()
+    assert np.all(np.isfinite(xs))
+    S = levels[0]["S"]
+    Mg = oracle.objective(xs.astype(np.float64), S, 0.008)[2]
+    Mo = oracle.objective(xo, S, 0.008)[2]
+    assert abs(Mg - Mo) <= 0.01 * abs(Mo), (Mg, Mo)
+    _, _, Mgpu = mm.objective(h, 0, x, 0.008)
+    assert Mgpu == pytest.approx(Mg, rel=1e-5)
+
+
+def test_layout_own_hierarchy_close_to_oracle(mm):
+    # the GPU's parallel label propagation builds a different hierarchy than
+    # the sequential one of the oracle; the layouts still reach comparable
+    # objectives (different random hierarchies of the oracle itself differ
+    # by several percent on graphs of this size)
+    rp, col, _, _ = graphs.rgg(3000, 8.0, 36)
+    kw = dict(k=2, theta=0.5, coarsest_n=100)
+    h, p = hier(mm, rp, col, **kw)
+    x, st = mm.layout(h, p)
+    xo, info = oracle.layout(rp, col, oracle.params(**kw))
+    S = oracle.build_S(rp, col, 2)
+    Mg = oracle.objective(x.cpu().numpy().astype(np.float64), S, 0.008)[2]
+    Mo = oracle.objective(xo, S, 0.008)[2]
+    assert abs(Mg - Mo) <= 0.15 * abs(Mo), (Mg, Mo)
+
+
+def test_layout_tiny_graphs(mm):
+    rp, col = graphs.path(2)
+    h, p = hier(mm, rp, col)
+    x, st = mm.layout(h, p)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x[0] - x[1]) == pytest.approx(1.0, rel=1e-6)
+    rp, col = graphs.path(3)
+    h, p = hier(mm, rp, col)
+    x, _ = mm.layout(h, p)
+    assert np.all(np.isfinite(x.cpu().numpy()))
+
+
+def test_errors_are_reported(mm):
+    rp, col = graphs.csr_from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5])  # two components
+    with pytest.raises(mm.MMError) as e:
+        hier(mm, rp, col)
+    assert e.value.status == 2
+    rp = np.array([0, 1, 1], dtype=np.int64)  # asymmetric
+    col = np.array([1], dtype=np.int32)
+    with pytest.raises(mm.MMError) as e:
+        hier(mm, rp, col)
+    assert e.value.status == 1
+    rp, col = graphs.path(4)
+    with pytest.raises(mm.MMError) as e:
+        hier(mm, rp, col, k=3)
+    assert e.value.status == 7
+
+
+def test_layout_host_api(mm):
+    rp, col = graphs.grid(20, 20)
+    x, st = mm.layout_host(rp, col, mm.default_params(k=2, coarsest_n=2))
+    assert x.shape == (400, 2) and np.all(np.isfinite(x))
+    assert st["vertex_updates"] > 0
