@@ -242,6 +242,27 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
                            void* stream);
 
 /*
+ * Allocation-free Barnes-Hut long-range sum (the paper has no counterpart;
+ * this is a deployment variant of the quadtree build and walk behind
+ * mm_repulsion).  For callers that cannot call cudaMalloc/cudaFree on their
+ * path -- a custom or pool allocator that forbids outside allocations, a
+ * real-time loop that cannot take the device synchronisation of cudaFree, a
+ * fixed device-memory budget: the caller passes inputs and outputs and the
+ * tree workspace lives in one fixed static device array of the library
+ * (under 8 MiB, held on every GPU that loads libmm.so until exit).
+ *   n      number of points, 1 <= n <= 32768 (larger n: MM_ERR_INVALID_ARG)
+ *   x      device [2n] positions; F_out device [2n] receives
+ *          F_u ~ sum_{v != u} r(u,v) with opening parameter theta >= 0
+ *          (theta = 0: exact through the tree)
+ * The first call on a device (with that device current) resolves the
+ * array's address; make it before any stream capture.  All calls share the
+ * array: calls whose GPU work overlaps race and must be serialised by the
+ * caller.  Synchronises the stream (to report a broken walk).
+ */
+mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta,
+                               float* F_out, void* stream);
+
+/*
  * Maxent-stress objective, Eq. 1, general model over S of `level`:
  *   M(x) = sum_{{u,v} in S} w_uv (|x_u-x_v| - d_uv)^2
  *        - alpha sum_{{u,v} not in S, u != v} ln|x_u - x_v|

@@ -1,0 +1,174 @@
+// mm_repulsion_noalloc: the Barnes-Hut long-range sum with every byte of its
+// scratch in one fixed, file-scope device array, so the call itself never
+// allocates.
+//
+// Who needs it: callers that must not call cudaMalloc/cudaFree on their hot
+// path -- code running under a custom or pool allocator that forbids other
+// allocations, real-time loops that cannot afford the implicit device
+// synchronisation cudaFree brings, and hosts that hand the library a fixed
+// device-memory budget up front.  They pass their own input and output
+// buffers; the tree workspace (sort buffers, radix tree, node records) comes
+// from the static array below.
+//
+// Cost of the array: kScratchBytes of device memory on every GPU that loads
+// this library, held until the process exits.
+//
+// Set-up: the first call on a device, with that device current, resolves the
+// array's device address with cudaGetSymbolAddress (a host-side name of a
+// __device__ array is only a host stand-in, not a usable device pointer).
+// Make that first call before any stream capture.
+//
+// Sharing: every call uses the same array and it keeps the previous call's
+// contents; the walk's error flag is cleared at the start of each call.
+// Calls whose GPU work overlaps (different streams, different host threads)
+// race on the array and must be serialised by the caller.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+
+constexpr int kNoAllocMaxN = 32768;   // largest point set accepted
+constexpr size_t kAlign = 256;
+
+constexpr size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+// Byte offsets of the workspace pieces inside the array.
+struct Carve {
+  size_t keys0, keys1, vals0, vals1, xs, lo, hi, left, right, delta, owner, parent, visit, sums,
+      nodeA, nodeB, partials, root, ticket, err, zero, counts, totals, total;
+};
+
+constexpr Carve carve() {
+  constexpr size_t N = kNoAllocMaxN;
+  constexpr size_t tiles = (N + kSortTile - 1) / kSortTile;
+  Carve c{};
+  size_t o = 0;
+  c.keys0 = o; o += up(4 * N);
+  c.keys1 = o; o += up(4 * N);
+  c.vals0 = o; o += up(4 * N);
+  c.vals1 = o; o += up(4 * N);
+  c.xs = o; o += up(8 * N);
+  c.lo = o; o += up(4 * N);
+  c.hi = o; o += up(4 * N);
+  c.left = o; o += up(4 * N);
+  c.right = o; o += up(4 * N);
+  c.delta = o; o += up(4 * N);
+  c.owner = o; o += up(4 * N);
+  c.parent = o; o += up(4 * 2 * N);
+  c.visit = o; o += up(4 * N);
+  c.sums = o; o += up(16 * 2 * N);
+  c.nodeA = o; o += up(16 * 2 * N);
+  c.nodeB = o; o += up(16 * 2 * N);
+  c.partials = o; o += up(16 * 2 * kSMs);
+  c.root = o; o += up(16);
+  c.ticket = o; o += up(8);
+  c.err = o; o += up(4);
+  c.zero = o; o += up(4);
+  c.counts = o; o += up(4 * 256 * tiles);
+  c.totals = o; o += up(4 * 256);
+  c.total = o;
+  return c;
+}
+
+constexpr Carve kCarve = carve();
+constexpr size_t kScratchBytes = kCarve.total;
+static_assert(kScratchBytes < (8u << 20), "no-allocation scratch stays under 8 MiB");
+
+// The scratch array (zero at module load).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_addr[64] = {nullptr};
+
+// Device address of g_scratch for the current device (resolved once).
+mm_status scratch_address(void** out) {
+  int dev = 0;
+  MM_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return MM_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s",
+                cudaGetErrorString(e));
+      return MM_ERR_CUDA;
+    }
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return MM_OK;
+}
+
+}  // namespace
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta, float* F_out,
+                                          void* stream) {
+  if (n < 1 || !x || !F_out || !(theta >= 0.f)) {
+    set_error("mm_repulsion_noalloc: need n >= 1, device x and F_out, theta >= 0");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (n > kNoAllocMaxN) {
+    set_error("mm_repulsion_noalloc: n = %d exceeds the fixed scratch limit of %d points", n,
+              kNoAllocMaxN);
+    return MM_ERR_INVALID_ARG;
+  }
+  void* base = nullptr;
+  MM_TRY(scratch_address(&base));
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* b = (unsigned char*)base;
+  const Carve& c = kCarve;
+  TreeWS ws;
+  ws.cap = kNoAllocMaxN;
+  ws.keys[0] = (uint32_t*)(b + c.keys0);
+  ws.keys[1] = (uint32_t*)(b + c.keys1);
+  ws.vals[0] = (int32_t*)(b + c.vals0);
+  ws.vals[1] = (int32_t*)(b + c.vals1);
+  ws.xs = (float2*)(b + c.xs);
+  ws.lo = (int32_t*)(b + c.lo);
+  ws.hi = (int32_t*)(b + c.hi);
+  ws.left = (int32_t*)(b + c.left);
+  ws.right = (int32_t*)(b + c.right);
+  ws.delta = (int32_t*)(b + c.delta);
+  ws.owner = (int32_t*)(b + c.owner);
+  ws.parent = (int32_t*)(b + c.parent);
+  ws.visit = (uint32_t*)(b + c.visit);
+  ws.sums = (double2*)(b + c.sums);
+  ws.nodeA = (float4*)(b + c.nodeA);
+  ws.nodeB = (int4*)(b + c.nodeB);
+  ws.partials = (float4*)(b + c.partials);
+  ws.root = (float4*)(b + c.root);
+  ws.ticket = (uint32_t*)(b + c.ticket);
+  ws.err = (int*)(b + c.err);
+  ws.sort.counts = (uint32_t*)(b + c.counts);
+  ws.sort.totals = (uint32_t*)(b + c.totals);
+  ws.sort.max_tiles = ceil_div(kNoAllocMaxN, kSortTile);
+  // the walk's error flag and the bounding-box ticket must start at zero;
+  // the build epoch (ticket[1]) must persist, since the visit flags compare
+  // against it
+  MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
+  MM_CK(cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), s));
+  XSel xs{(const float2*)x, (const float2*)x, (const int32_t*)(b + c.zero)};
+  MM_TRY(bh_build(xs, n, theta, ws, s));
+  MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s));
+  int err = 0;
+  MM_CK(cudaMemcpyAsync(&err, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("internal error: Barnes-Hut walk met an inconsistent tree");
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
+}

@@ -28,7 +28,7 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_free_hierarchy", "mm_hierarchy_levels", "mm_level_info", "mm_level_export",
            "mm_sweep", "mm_repulsion", "mm_layout", "mm_sweep_profile", "mm_objective",
            "mm_khop", "mm_cluster",
-           "mm_contract", "mm_prolong", "mm_layout_host"]
+           "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc"]
 
 
 class MMError(RuntimeError):
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
     lib.mm_contract.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P, P, P]
     lib.mm_prolong.argtypes = [i32, P, P, P, u64, i32, P, P]
     lib.mm_layout_host.argtypes = [i32, P, P, P, P, P, P, P]
+    lib.mm_repulsion_noalloc.argtypes = [i32, P, f32, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -277,6 +278,20 @@ def repulsion(h: Hierarchy, level: int, x, theta: float, stream=None):
     F = torch.empty_like(x)
     _check(load().mm_repulsion(h.handle, level, _ptr(x), float(theta), _ptr(F), _stream(stream)))
     return F
+
+
+def repulsion_noalloc(x, theta: float, F_out=None, stream=None):
+    """Barnes-Hut F for up to 32768 points with the library's fixed static
+    scratch (the call allocates no device memory itself; the output buffer
+    is the caller's).  Calls that overlap on the GPU race on the shared
+    scratch."""
+    _require_cuda()
+    x = _dev(x, torch.float32, "x")
+    if F_out is None:
+        F_out = torch.empty_like(x)
+    _check(load().mm_repulsion_noalloc(x.shape[0], _ptr(x), float(theta), _ptr(F_out),
+                                       _stream(stream)))
+    return F_out
 
 
 def layout(h: Hierarchy, params: Params = None, x_init=None, x_out=None, stream=None):
