@@ -341,8 +341,7 @@ def roofline(prof, peaks, src, clk, n):
     lanes x 2 (FMA) x SM clock.  gather: HBM bound; algorithmic bytes per
     vertex = 4 (row_ptr) + 8 (x_u) + 8 (x'_u) + 8 (F_u) + 4 (rho_u) + 8 per S
     entry (col, d); neighbour positions are L2 hits and not counted.
-    sort: HBM bound; 4 passes x (4 B key read in the histogram pass + 8 B
-    read + 8 B write in the scatter pass) per element.
+    sort: HBM bound; 4 look-back passes x (8 B read + 8 B write) per element.
     """
     st = prof["stage_ms"]
     names = prof["stage_names"]
@@ -362,7 +361,7 @@ def roofline(prof, peaks, src, clk, n):
     kern["gather"] = {"bound": "hbm", "achieved": gbytes / t_g / 1e9, "peak": hbm, "unit": "GB/s",
                       "traffic": None}
     t_s = st[names.index("sort")] / 1e3
-    sbytes = 4 * (4.0 + 16.0) * n
+    sbytes = 4 * 16.0 * n
     kern["sort"] = {"bound": "hbm", "achieved": sbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "traffic": None}
     for v in kern.values():

@@ -76,7 +76,9 @@ typedef struct mm_params {
   int32_t gather_lanes;     /* lanes per vertex in the S gather; 0 = auto     */
   int32_t heavy_degree;     /* rows above this use a block each; 0 = auto     */
   int32_t traverse_warps;   /* warps per block in the tree walk; 0 = auto     */
-  int32_t reserved[7];
+  int32_t fused_max_n;      /* levels with n <= this run in one single-CTA    */
+                            /* kernel; 0 = auto (2048, the maximum), -1 = off */
+  int32_t reserved[6];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */
@@ -232,8 +234,9 @@ mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init,
  * Per-stage timing of one sweep on `level` (no paper counterpart; a
  * measurement aid): the sweep of mm_sweep is run `reps` times from x with
  * CUDA events between its stages, and the mean milliseconds per stage are
- * written to stage_ms (host [8]): bbox, morton, sort, radix-tree, bottom-up,
- * traverse (or the exact O(n^2) kernel), gather, controller.  work (host
+ * written to stage_ms (host [8]): bbox, Morton keys + digit histograms, sort
+ * passes, radix tree + prefix sums, node records, traverse (or the exact
+ * O(n^2) kernel), gather, controller.  work (host
  * [4]) receives the walk's warp node visits and lane interactions (from one
  * instrumented walk), |S| and n.  alpha = 0.3.  x device [2n], unchanged.
  */

@@ -1,0 +1,482 @@
+// Fused level kernel for small levels: one CTA of 1024 threads runs a whole
+// level schedule (Sec. 3.2) -- every Eq. 2 iteration and every alpha round --
+// without leaving the kernel.
+//
+// On the coarse levels of a hierarchy (a few dozen to a few thousand
+// vertices) a sweep is a chain of tiny dependent steps; issued as separate
+// launches each costs a launch and an L2 round trip per node visit.  Here
+// every per-sweep structure lives in shared memory:
+//   bounding square -> Morton keys (16 bits per axis, the same cells as the
+//   multi-kernel path) -> bitonic sort of (key, index) -> Karras radix tree
+//   -> centroids from FP64 prefix sums of the sorted positions -> 32-byte
+//   node records -> warp-synchronous stackless walk (per-lane acceptance,
+//   as in the multi-kernel walk) -> Eq. 2 update over S (rows read from
+//   global memory) -> FP64 block reductions -> the schedule step.
+// With exact repulsion (the coarsest level) the walk is replaced by the
+// all-pairs sum over the staged positions.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+
+constexpr int kT = kSmallThreads;
+constexpr int kN = kSmallMaxN;
+constexpr int kNodes = 2 * kN - 1;
+constexpr int kNone = -2;
+
+struct __align__(16) SmallSmem {
+  // about 216 KB: fits the 227 KB a CTA may opt into
+  float4 nodeA[kNodes];       // (cx, cy, (w/theta)^2, count)
+  short4 nodeB[kNodes];       // (first child, escape, lo, hi+1)
+  union {                         // three phases, three uses:
+    unsigned long long keys[kN];  //   sort keys (sort, radix tree)
+    float4 P[kN + 1];             //   float-float prefix sums (x_hi, y_hi, x_lo, y_lo)
+    float2 F[kN];                 //   long-range sums by vertex id (walk, update)
+  };
+  float2 xs[kN];              // sorted positions (tree build, walk)
+  float2 xv[kN];              // positions by vertex id, staged once per sweep
+  int32_t sp[kN + 1];         // S row pointers of the level (staged once)
+  float rho[kN];              // rho of the level (staged once)
+  int16_t lo[kN], hi[kN], left[kN], right[kN], owner[kN];
+  int16_t parent[kNodes + 1];
+  int16_t vals[kN];
+  int8_t delta[kN];
+};
+
+// Error-free float-float addition (Knuth's two-sum, then renormalise): the
+// prefix sums keep ~44 significant bits using only FP32 arithmetic.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float v = s - a.x;
+  float e = (a.x - (s - v)) + (b.x - v);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+__device__ __forceinline__ uint32_t spread16(uint32_t v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+__device__ __forceinline__ int plen(const SmallSmem& s, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = (uint32_t)(s.keys[i] >> 32), b = (uint32_t)(s.keys[j] >> 32);
+  if (a != b) return __clz(a ^ b);
+  return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+__device__ __forceinline__ int s_resolve(const SmallSmem& s, int n, int x) {
+  if (x >= n - 1 || x == 0) return x;
+  const int dx = s.delta[x];
+  if (dx >= 32) return x;
+  const int dp = s.delta[s.parent[x]];
+  return (dp >> 1) == (dx >> 1) ? s.left[x] : x;
+}
+
+__device__ __forceinline__ int s_escape(const SmallSmem& s, int n, int h) {
+  if (h >= n - 1) return -1;
+  return s_resolve(s, n, s.right[s.owner[h]]);
+}
+
+// Block-wide sums of three per-thread partials: warp shuffles in FP32, the 32
+// warp totals summed in FP64 by thread 0 only (FP64 issue rate on this part
+// is a small fraction of FP32).  Result valid in thread 0.
+__device__ __forceinline__ void bsum3(float a, float b, float c, double* red, double out[3]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  __syncthreads();
+  if (lane == 0) { red[warp] = a; red[32 + warp] = b; red[64 + warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < kT / 32; ++w) { x += red[w]; y += red[32 + w]; z += red[64 + w]; }
+    out[0] = x; out[1] = y; out[2] = z;
+  }
+}
+
+#define MM_STAMP(i)                                          \
+  do {                                                       \
+    if (prof && threadIdx.x == 0) prof[i] = clock64();       \
+  } while (0)
+
+__device__ void build_tree(SmallSmem& s, int n, float theta, float4* root_sh, double* red,
+                           long long* prof) {
+  const float2* x = s.xv;
+  const int tid = threadIdx.x;
+  // bounding square
+  float mnx = CUDART_INF_F, mny = CUDART_INF_F, mxx = -CUDART_INF_F, mxy = -CUDART_INF_F;
+  for (int i = tid; i < n; i += kT) {
+    const float2 p = x[i];
+    mnx = fminf(mnx, p.x); mny = fminf(mny, p.y);
+    mxx = fmaxf(mxx, p.x); mxy = fmaxf(mxy, p.y);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+    mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+    mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+    mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+  }
+  float* fr = reinterpret_cast<float*>(red);
+  const int lane = tid & 31, warp = tid >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    fr[4 * warp] = mnx; fr[4 * warp + 1] = mny; fr[4 * warp + 2] = mxx; fr[4 * warp + 3] = mxy;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float4 r = make_float4(fr[0], fr[1], fr[2], fr[3]);
+    for (int w = 1; w < kT / 32; ++w) {
+      r.x = fminf(r.x, fr[4 * w]); r.y = fminf(r.y, fr[4 * w + 1]);
+      r.z = fmaxf(r.z, fr[4 * w + 2]); r.w = fmaxf(r.w, fr[4 * w + 3]);
+    }
+    const float side = fmaxf(r.z - r.x, r.w - r.y);
+    *root_sh = make_float4(r.x, r.y, side, side > 0.f ? 65536.0f / side : 0.f);
+  }
+  __syncthreads();
+  MM_STAMP(2);
+  const float4 root = *root_sh;
+  // Morton keys with the index in the low word: a total order that equals
+  // the stable order of the multi-kernel radix sort
+  int np = 2;
+  while (np < n) np <<= 1;
+  for (int i = tid; i < np; i += kT) {
+    unsigned long long k = ~0ull;
+    if (i < n) {
+      const float2 p = x[i];
+      const float fx = (p.x - root.x) * root.w, fy = (p.y - root.y) * root.w;
+      const uint32_t ix = (uint32_t)fminf(fmaxf(fx, 0.f), 65535.f);
+      const uint32_t iy = (uint32_t)fminf(fmaxf(fy, 0.f), 65535.f);
+      k = ((unsigned long long)((spread16(ix) << 1) | spread16(iy)) << 32) | (uint32_t)i;
+    }
+    s.keys[i] = k;
+  }
+  __syncthreads();
+  // bitonic sort of np keys
+  for (int k = 2; k <= np; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < np; i += kT) {
+        const int ij = i ^ j;
+        if (ij > i) {
+          const unsigned long long a = s.keys[i], b = s.keys[ij];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { s.keys[i] = b; s.keys[ij] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  MM_STAMP(3);
+  for (int i = tid; i < n; i += kT) {
+    const int v = (int)(uint32_t)s.keys[i];
+    s.vals[i] = (int16_t)v;
+    s.xs[i] = x[v];
+  }
+  __syncthreads();
+  // Karras radix tree over the sorted keys
+  for (int i = tid; i < n - 1; i += kT) {
+    const int dr = plen(s, n, i, i + 1), dl = plen(s, n, i, i - 1);
+    const int d = dr > dl ? 1 : -1;
+    const int dmin = d > 0 ? dl : dr;
+    int lmax = 2;
+    while (plen(s, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (plen(s, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = plen(s, n, i, j);
+    int sp = 0, t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (plen(s, n, i, i + (sp + t) * d) > dnode) sp += t;
+    } while (t > 1);
+    const int g = i + sp * d + (d < 0 ? -1 : 0);
+    const int a = min(i, j), b = max(i, j);
+    const int L = (a == g) ? (n - 1 + g) : g;
+    const int R = (b == g + 1) ? (n - 1 + g + 1) : g + 1;
+    s.lo[i] = (int16_t)a; s.hi[i] = (int16_t)b; s.left[i] = (int16_t)L;
+    s.right[i] = (int16_t)R; s.delta[i] = (int8_t)dnode; s.owner[g] = (int16_t)i;
+    s.parent[L] = (int16_t)i; s.parent[R] = (int16_t)i;
+  }
+  if (tid == 0) s.parent[0] = -1;
+  __syncthreads();
+  MM_STAMP(4);
+  // float-float prefix sums of the sorted positions: P[i] = sum_{j < i} xs[j]
+  {
+    const int i0 = 2 * tid;
+    const float2 a = i0 < n ? s.xs[i0] : make_float2(0.f, 0.f);
+    const float2 b2 = i0 + 1 < n ? s.xs[i0 + 1] : make_float2(0.f, 0.f);
+    // pair sums (hi, lo) per coordinate
+    float2 px = ff_add(make_float2(a.x, 0.f), make_float2(b2.x, 0.f));
+    float2 py = ff_add(make_float2(a.y, 0.f), make_float2(b2.y, 0.f));
+    float2 ix = px, iy = py;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float2 tx = make_float2(__shfl_up_sync(0xffffffffu, ix.x, o),
+                                    __shfl_up_sync(0xffffffffu, ix.y, o));
+      const float2 ty = make_float2(__shfl_up_sync(0xffffffffu, iy.x, o),
+                                    __shfl_up_sync(0xffffffffu, iy.y, o));
+      if (lane >= o) { ix = ff_add(ix, tx); iy = ff_add(iy, ty); }
+    }
+    float4* wsum = reinterpret_cast<float4*>(red);  // 32 warp totals (red holds 96 doubles)
+    __syncthreads();
+    if (lane == 31) wsum[warp] = make_float4(ix.x, ix.y, iy.x, iy.y);
+    __syncthreads();
+    float2 wx = make_float2(0.f, 0.f), wy = make_float2(0.f, 0.f);
+    for (int w = 0; w < warp; ++w) {
+      const float4 t = wsum[w];
+      wx = ff_add(wx, make_float2(t.x, t.y));
+      wy = ff_add(wy, make_float2(t.z, t.w));
+    }
+    // exclusive prefix of this pair = warp offset + inclusive - own pair
+    const float2 ex = ff_add(wx, ff_add(ix, make_float2(-px.x, -px.y)));
+    const float2 ey = ff_add(wy, ff_add(iy, make_float2(-py.x, -py.y)));
+    const float2 ax = ff_add(ex, make_float2(a.x, 0.f)), ay = ff_add(ey, make_float2(a.y, 0.f));
+    if (i0 < n) s.P[i0] = make_float4(ex.x, ey.x, ex.y, ey.y);
+    if (i0 + 1 < n) s.P[i0 + 1] = make_float4(ax.x, ay.x, ax.y, ay.y);
+    // the owner of the last element writes the total
+    if (i0 == n - 1) s.P[n] = make_float4(ax.x, ay.x, ax.y, ay.y);
+    if (i0 + 1 == n - 1) {
+      const float2 tx = ff_add(ex, px), ty = ff_add(ey, py);
+      s.P[n] = make_float4(tx.x, ty.x, tx.y, ty.y);
+    }
+  }
+  __syncthreads();
+  MM_STAMP(5);
+  // node records
+  for (int id = tid; id < 2 * n - 1; id += kT) {
+    if (id >= n - 1) {
+      const int j = id - (n - 1);
+      if (n > 1 && s.delta[s.parent[id]] >= 32) continue;  // inside a bucket
+      const float2 p = s.xs[j];
+      s.nodeA[id] = make_float4(p.x, p.y, 0.f, 1.f);
+      s.nodeB[id] = make_short4(-1, (short)s_escape(s, n, j), (short)j, (short)(j + 1));
+      continue;
+    }
+    const int dd = s.delta[id];
+    const int dp = id == 0 ? -1 : s.delta[s.parent[id]];
+    int depth, first;
+    if (dd >= 32) {
+      if (dp >= 32) continue;
+      depth = kKeyBits;
+      first = -1;
+    } else {
+      if (dp >= 0 && (dp >> 1) == (dd >> 1)) continue;
+      depth = dd >> 1;
+      first = s_resolve(s, n, s.left[id]);
+    }
+    const int a = s.lo[id], b = s.hi[id];
+    const float cnt = (float)(b - a + 1);
+    const float4 pa = s.P[a], pb = s.P[b + 1];
+    const float2 dx = ff_add(make_float2(pb.x, pb.z), make_float2(-pa.x, -pa.z));
+    const float2 dy = ff_add(make_float2(pb.y, pb.w), make_float2(-pa.y, -pa.w));
+    const float w = ldexpf(root.z, -depth);
+    const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
+    s.nodeA[id] = make_float4((dx.x + dx.y) / cnt, (dy.x + dy.y) / cnt, rc, cnt);
+    s.nodeB[id] = make_short4((short)first, (short)s_escape(s, n, b), (short)a, (short)(b + 1));
+  }
+  __syncthreads();
+}
+
+// The walk of the multi-kernel path over the shared-memory records.
+__device__ void walk(const SmallSmem& s, int n, float2* F, int* err) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int task = warp; task * 32 < n; task += kT / 32) {
+    const int pos = task * 32 + lane;
+    const bool valid = pos < n;
+    const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
+    int wait = valid ? kNone : -1;
+    int cur = n > 1 ? 0 : -1;
+    int budget = 2 * n + 2;
+    float fx = 0.f, fy = 0.f;
+    while (cur >= 0) {
+      if (cur >= 2 * n - 1 || --budget < 0) {
+        if (lane == 0) atomicOr(err, 1);
+        break;
+      }
+      const float4 A = s.nodeA[cur];
+      const short4 B = s.nodeB[cur];
+      if (wait == cur) wait = kNone;
+      bool desc = false;
+      if (wait == kNone) {
+        const float dx = xu.x - A.x, dy = xu.y - A.y;
+        const float q = fmaf(dx, dx, dy * dy);
+        const bool inside = pos >= B.z && pos < B.w;
+        if (!inside && q > A.z) {
+          const float sc = __fdividef(A.w, q);
+          fx = fmaf(sc, dx, fx);
+          fy = fmaf(sc, dy, fy);
+          wait = B.y;
+        } else if (B.x < 0) {
+          const int pb = max((int)B.z, 0), pe = min((int)B.w, n);
+          for (int p = pb; p < pe; ++p) {
+            if (p == pos) continue;
+            const float2 xv = s.xs[p];
+            const float ex = xu.x - xv.x, ey = xu.y - xv.y;
+            const float eq = fmaf(ex, ex, ey * ey);
+            if (eq > 0.f) {
+              const float inv = __fdividef(1.f, eq);
+              fx = fmaf(inv, ex, fx);
+              fy = fmaf(inv, ey, fy);
+            }
+          }
+          wait = B.y;
+        } else {
+          desc = true;
+        }
+      }
+      cur = __any_sync(0xffffffffu, desc) ? B.x : B.y;
+    }
+    if (valid) F[s.vals[pos]] = make_float2(fx, fy);
+  }
+}
+
+__global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallSmem& s = *reinterpret_cast<SmallSmem*>(smem_raw);
+  __shared__ double red[96];
+  __shared__ float4 root;
+  __shared__ int sh_parity, sh_done;
+  __shared__ float sh_alpha;
+  const int n = a.n, tid = threadIdx.x;
+  float2* F = s.F;
+  for (int i = tid; i <= n; i += kT) s.sp[i] = a.sp[i];
+  for (int i = tid; i < n; i += kT) s.rho[i] = a.rho[i];
+  for (int sweep = 0;; ++sweep) {
+    if (tid == 0) {
+      sh_parity = a.st->parity;
+      sh_alpha = (float)a.st->alpha;
+      if (sweep == 0 && a.prof) a.prof[0] = clock64();
+    }
+    __syncthreads();
+    const float2* xg = sh_parity ? a.b1 : a.b0;
+    float2* xo = sh_parity ? a.b0 : a.b1;
+    const float alpha = sh_alpha;
+    for (int i = tid; i < n; i += kT) s.xv[i] = xg[i];
+    __syncthreads();
+    const float2* x = s.xv;
+    long long* prof = sweep == 0 ? a.prof : nullptr;
+    MM_STAMP(1);
+    if (a.exact) {
+      for (int u = tid; u < n; u += kT) {
+        const float2 xu = x[u];
+        float fx = 0.f, fy = 0.f;
+        for (int k = 0; k < n; ++k) {
+          const float dx = xu.x - x[k].x, dy = xu.y - x[k].y;
+          const float q = fmaf(dx, dx, dy * dy);
+          const float inv = q > 0.f ? __fdividef(1.f, q) : 0.f;
+          fx = fmaf(inv, dx, fx);
+          fy = fmaf(inv, dy, fy);
+        }
+        F[u] = make_float2(fx, fy);
+      }
+    } else {
+      build_tree(s, n, a.theta, &root, red, prof);
+      MM_STAMP(6);
+      walk(s, n, F, a.err);
+    }
+    __syncthreads();
+    MM_STAMP(7);
+    // Eq. 2 over S: G lanes per row (G = a.lanes, a power of two <= 32),
+    // positions, row pointers and rho from shared memory; FP32 partials
+    float psdx = 0.f, psx = 0.f, psst = 0.f;
+    {
+      const int G = a.lanes;
+      const int lg = tid & (G - 1);
+      for (int base = 0; base < n; base += kT / G) {
+        const int u = base + tid / G;
+        float gx = 0.f, gy = 0.f, rx = 0.f, ry = 0.f, st = 0.f;
+        float2 xu = make_float2(0.f, 0.f);
+        if (u < n) {
+          xu = x[u];
+          const int e1 = s.sp[u + 1];
+#pragma unroll 4
+          for (int e = s.sp[u] + lg; e < e1; e += G) {
+            const SEnt en = a.S[e];
+            const float2 xw = x[en.col];
+            const float dx = xu.x - xw.x, dy = xu.y - xw.y;
+            const float q = fmaf(dx, dx, dy * dy);
+            const float inv = q > 0.f ? rsqrtf(q) : 0.f;
+            const float dist = q * inv;
+            const float w = __fdividef(1.f, en.d * en.d);
+            const float du = en.d * inv;
+            gx = fmaf(w, fmaf(du, dx, xw.x), gx);
+            gy = fmaf(w, fmaf(du, dy, xw.y), gy);
+            const float inv2 = inv * inv;
+            rx = fmaf(dx, inv2, rx);
+            ry = fmaf(dy, inv2, ry);
+            const float t = dist - en.d;
+            st = fmaf(w * t, t, st);
+          }
+        }
+        for (int o = G >> 1; o; o >>= 1) {
+          gx += __shfl_xor_sync(0xffffffffu, gx, o);
+          gy += __shfl_xor_sync(0xffffffffu, gy, o);
+          rx += __shfl_xor_sync(0xffffffffu, rx, o);
+          ry += __shfl_xor_sync(0xffffffffu, ry, o);
+          st += __shfl_xor_sync(0xffffffffu, st, o);
+        }
+        if (u < n && lg == 0) {
+          const float2 f = F[u];
+          const float r = s.rho[u];
+          const float nx = (gx + alpha * (f.x - rx)) / r;
+          const float ny = (gy + alpha * (f.y - ry)) / r;
+          xo[u] = make_float2(nx, ny);
+          const float ddx = nx - xu.x, ddy = ny - xu.y;
+          psdx = fmaf(ddx, ddx, fmaf(ddy, ddy, psdx));
+          psx = fmaf(xu.x, xu.x, fmaf(xu.y, xu.y, psx));
+          psst = fmaf(0.5f, st, psst);
+        }
+      }
+    }
+    double tot[3];
+    bsum3(psdx, psx, psst, red, tot);
+    MM_STAMP(8);
+    if (tid == 0) {
+      const bool done =
+          schedule_step(a.st, a.sched, tot[0], tot[1], tot[2], a.trace, a.trace_cap, a.lsw);
+      sh_done = (done || sweep + 1 >= a.max_sweeps) ? 1 : 0;
+    }
+    __syncthreads();
+    MM_STAMP(9);
+    if (sh_done) break;
+  }
+}
+
+}  // namespace
+
+static_assert(sizeof(SmallSmem) + 1024 <= 227 * 1024, "fused level kernel exceeds shared memory");
+
+size_t small_level_smem() { return sizeof(SmallSmem); }
+
+mm_status small_level_setup() {
+  MM_CK(cudaFuncSetAttribute(small_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmallSmem)));
+  return MM_OK;
+}
+
+mm_status small_level(const SmallArgs& a, cudaStream_t s) {
+  if (a.n < 1 || a.n > kSmallMaxN) {
+    set_error("fused level kernel takes 1..%d vertices, got %d", kSmallMaxN, a.n);
+    return MM_ERR_INVALID_ARG;
+  }
+  small_level_kernel<<<1, kT, sizeof(SmallSmem), s>>>(a);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+}  // namespace mm

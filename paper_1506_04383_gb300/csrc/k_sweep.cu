@@ -46,20 +46,42 @@ __device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const 
 
 __device__ __forceinline__ void finish_vertex(int u, const RowAcc& a, float2 xu, float alpha,
                                               const float* rho, const float2* F, float2* xo,
-                                              double& s_dx, double& s_x, double& s_st) {
+                                              float& s_dx, float& s_x, float& s_st) {
   const float2 f = F[u];
   const float r = rho[u];
   const float nx = (a.gx + alpha * (f.x - a.sx)) / r;
   const float ny = (a.gy + alpha * (f.y - a.sy)) / r;
   xo[u] = make_float2(nx, ny);
-  const double ddx = (double)nx - xu.x, ddy = (double)ny - xu.y;
-  s_dx += ddx * ddx + ddy * ddy;
-  s_x += (double)xu.x * xu.x + (double)xu.y * xu.y;
-  s_st += 0.5 * (double)a.st;
+  const float ddx = nx - xu.x, ddy = ny - xu.y;
+  s_dx = fmaf(ddx, ddx, fmaf(ddy, ddy, s_dx));
+  s_x = fmaf(xu.x, xu.x, fmaf(xu.y, xu.y, s_x));
+  s_st = fmaf(0.5f, a.st, s_st);
 }
 
+// Per-thread FP32 partials -> warp totals (FP32 shuffles) -> FP64 block sums
+// by thread 0 (FP64 issue rate on this part is a small fraction of FP32).
 template <int kT>
-__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+__device__ __forceinline__ void block_reduce3(float a, float b, float c, double* out) {
+  __shared__ float sh[3][kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < kT / 32; ++w) { x += sh[0][w]; y += sh[1][w]; z += sh[2][w]; }
+    out[0] = x; out[1] = y; out[2] = z;
+  }
+}
+
+// FP64 variant for the controller (reduces per-block FP64 partials).
+template <int kT>
+__device__ __forceinline__ void block_reduce3d(double a, double b, double c, double* out) {
   __shared__ double sh[3][kT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -88,7 +110,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
   const float alpha = (float)st->alpha;
   constexpr int kGroups = kGatherThreads / G;
   const int g = threadIdx.x / G, lg = threadIdx.x % G;
-  double s_dx = 0, s_x = 0, s_st = 0;
+  float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
   for (int base = blockIdx.x * kGroups; base < n; base += gridDim.x * kGroups) {
     const int u = base + g;
     RowAcc a = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -126,7 +148,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
   float2* xo = xs.next();
   const float alpha = (float)st->alpha;
   __shared__ float red[5][kGatherThreads / 32];
-  double s_dx = 0, s_x = 0, s_st = 0;
+  float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const int u = heavy_list[h];
@@ -177,44 +199,12 @@ __global__ void __launch_bounds__(kCtlThreads) controller_kernel(
     c += partials[3 * i + 2];
   }
   __shared__ double out[3];
-  block_reduce3<kCtlThreads>(a, b, c, out);
+  block_reduce3d<kCtlThreads>(a, b, c, out);
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double sdx = out[0], sx = out[1], stress = out[2];
-  const double rel = sx > 0 ? sqrt(sdx) / sqrt(sx) : (sdx == 0 ? 0.0 : CUDART_INF);
-  const double alpha = st->alpha;
-  const int t = st->total;
-  if (trace && t < trace_cap) {
-    trace[3 * t] = (float)alpha;
-    trace[3 * t + 1] = (float)rel;
-    trace[3 * t + 2] = (float)stress;
-  }
-  st->total = t + 1;
-  st->level_sweeps += 1;
-  st->parity ^= 1;
-  st->it_in_round += 1;
-  st->last_rel = rel;
-  st->last_stress = stress;
-  st->last_sdx = sdx;
-  st->last_sx = sx;
-  const bool at_min = alpha <= sp.alpha_min;
-  const int cap = at_min ? sp.max_iters_at_min : sp.iters_per_alpha;
-  const double tol = at_min ? sp.eps_final : sp.eps;
-  if ((sp.early_exit && rel < tol) || st->it_in_round >= cap) {
-    if (at_min) {
-      st->done = 1;
-    } else {
-      st->alpha = fmax(alpha * sp.alpha_factor, sp.alpha_min);
-      st->it_in_round = 0;
-    }
-  }
-  if (!isfinite(sdx) || !isfinite(sx)) {
-    st->error = MM_ERR_NONFINITE;
-    st->done = 1;
-  }
-  if (st->level_sweeps >= sp.level_cap) st->done = 1;
-  if (level_sweeps_out) *level_sweeps_out = st->level_sweeps;
-  if (use_h) cudaGraphSetConditional(h, st->done ? 0u : 1u);
+  const bool done = schedule_step(st, sp, out[0], out[1], out[2], trace, trace_cap,
+                                  level_sweeps_out);
+  if (use_h) cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
 __device__ __forceinline__ float u01(uint32_t z) { return (float)(z >> 8) * (1.0f / 16777216.0f); }

@@ -59,11 +59,12 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // Bounding square of the layout.  The last block to finish reduces the
-// per-block partials (fixed order) and writes root = (min x, min y, side,
-// 2^16 / side); it also bumps the epoch (ticket[1]) used by the bottom-up
-// pass.
+// per-block partials and writes root = (min x, min y, side, 2^16 / side);
+// it also bumps the build epoch (ticket[1]) that tags the sort's look-back
+// status words, and zeroes the sort histograms and tile counters.
 __global__ void __launch_bounds__(kBBoxThreads) bbox_kernel(XSel xs, int n, float4* partials,
-                                                            unsigned* ticket, float4* root) {
+                                                            unsigned* ticket, float4* root,
+                                                            uint32_t* hist, uint32_t* counters) {
   const float2* x = xs.cur();
   float mnx = CUDART_INF_F, mny = CUDART_INF_F, mxx = -CUDART_INF_F, mxy = -CUDART_INF_F;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -89,12 +90,24 @@ __global__ void __launch_bounds__(kBBoxThreads) bbox_kernel(XSel xs, int n, floa
   }
   __syncthreads();
   if (!last) return;
+  // last block: reduce the partials in parallel, reset the sort state
+  float4 r = make_float4(CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const float4 q = __ldcg(&partials[b]);
+    r.x = fminf(r.x, q.x); r.y = fminf(r.y, q.y);
+    r.z = fmaxf(r.z, q.z); r.w = fmaxf(r.w, q.w);
+  }
+  r.x = warp_min(r.x); r.y = warp_min(r.y); r.z = warp_max(r.z); r.w = warp_max(r.w);
+  __syncthreads();
+  if (lane == 0) sh[warp] = r;
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) hist[i] = 0u;
+  if (threadIdx.x < 4) counters[threadIdx.x] = 0u;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    float4 r = __ldcg(&partials[0]);
-    for (int b = 1; b < (int)gridDim.x; ++b) {
-      const float4 q = __ldcg(&partials[b]);
-      r.x = fminf(r.x, q.x); r.y = fminf(r.y, q.y);
-      r.z = fmaxf(r.z, q.z); r.w = fmaxf(r.w, q.w);
+    r = sh[0];
+    for (int w = 1; w < kBBoxThreads / 32; ++w) {
+      r.x = fminf(r.x, sh[w].x); r.y = fminf(r.y, sh[w].y);
+      r.z = fmaxf(r.z, sh[w].z); r.w = fmaxf(r.w, sh[w].w);
     }
     const float side = fmaxf(r.z - r.x, r.w - r.y);
     const float scale = side > 0.f ? 65536.0f / side : 0.f;
@@ -104,18 +117,161 @@ __global__ void __launch_bounds__(kBBoxThreads) bbox_kernel(XSel xs, int n, floa
   }
 }
 
-__global__ void morton_kernel(XSel xs, int n, const float4* __restrict__ root,
-                              uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float2 p = xs.cur()[i];
+// Morton keys (16 bits per axis) and the four 8-bit digit histograms of the
+// radix sort, in one pass over the positions.
+__global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
+    XSel xs, int n, const float4* __restrict__ root, uint32_t* __restrict__ keys,
+    int32_t* __restrict__ vals, uint32_t* hist) {
+  __shared__ uint32_t h[4][256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
+  __syncthreads();
+  const float2* x = xs.cur();
   const float4 r = *root;
-  const float fx = (p.x - r.x) * r.w, fy = (p.y - r.y) * r.w;
-  // clamp in float first: the conversion of out-of-range values is undefined
-  const uint32_t ix = (uint32_t)fminf(fmaxf(fx, 0.f), 65535.f);
-  const uint32_t iy = (uint32_t)fminf(fmaxf(fy, 0.f), 65535.f);
-  keys[i] = (spread16(ix) << 1) | spread16(iy);
-  vals[i] = i;
+  const int base = blockIdx.x * kSortTile;
+  for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
+    const int i = base + j;
+    if (i >= n) break;
+    const float2 p = x[i];
+    const float fx = (p.x - r.x) * r.w, fy = (p.y - r.y) * r.w;
+    // clamp in float first: the conversion of out-of-range values is undefined
+    const uint32_t ix = (uint32_t)fminf(fmaxf(fx, 0.f), 65535.f);
+    const uint32_t iy = (uint32_t)fminf(fmaxf(fy, 0.f), 65535.f);
+    const uint32_t k = (spread16(ix) << 1) | spread16(iy);
+    keys[i] = k;
+    vals[i] = i;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+// One stable counting pass of the sort (8-bit digit at `shift`) with
+// decoupled look-back: a block takes the next tile in order, publishes its
+// per-digit counts, accumulates the counts of the preceding tiles from their
+// status words (epoch | flag | value; flag 1 = tile count, 2 = inclusive
+// prefix) and scatters.  Waits are bounded: after kSpinLimit polls the block
+// raises err[0] |= 2 and treats the missing tile as empty, so the kernel
+// always finishes.
+constexpr int kSpinLimit = 1 << 22;
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_pass(
+    const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    int32_t* __restrict__ vout, int n, int pass, const uint32_t* __restrict__ hist,
+    uint32_t* counters, unsigned long long* status, const unsigned* ticket, int* err) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t whist[kWarps][256];
+  __shared__ uint32_t dbase[256];
+  __shared__ int tile_sh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int shift = 8 * pass;
+  const int tiles = (n + kSortTile - 1) / kSortTile;
+  if (threadIdx.x == 0) tile_sh = (int)atomicAdd(&counters[pass], 1u);
+  for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&whist[0][0])[i] = 0u;
+  if (threadIdx.x < 32) {
+    // exclusive scan of the 256 global digit counts of this pass
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = hist[pass * 256 + lane * 8 + j];
+      sum += v[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      dbase[lane * 8 + j] = run;
+      run += v[j];
+    }
+  }
+  __syncthreads();
+  const int tile = tile_sh;
+  const int64_t base = (int64_t)tile * kSortTile + warp * (32 * kSortIPT);
+  uint32_t key[kSortIPT];
+  int32_t val[kSortIPT];
+  uint32_t dig[kSortIPT];
+  unsigned peers[kSortIPT];
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    const int64_t idx = base + j * 32 + lane;
+    const unsigned valid = __ballot_sync(0xffffffffu, idx < n);
+    peers[j] = 0;
+    if (idx < n) {
+      key[j] = kin[idx];
+      val[j] = vin[idx];
+      dig[j] = (key[j] >> shift) & 255u;
+      peers[j] = __match_any_sync(valid, dig[j]);
+      if (lane == __ffs(peers[j]) - 1) whist[warp][dig[j]] += __popc(peers[j]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    const int d = threadIdx.x;  // one thread per digit (256 threads)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) cnt += whist[w][d];
+    const unsigned long long ep = (unsigned long long)ticket[1] << 32;
+    unsigned long long* st = status + ((size_t)pass * tiles) * 256;
+    volatile unsigned long long* vst = st;
+    if (tile == 0) {
+      vst[d] = ep | (2ull << 30) | cnt;
+    } else {
+      vst[(size_t)tile * 256 + d] = ep | (1ull << 30) | cnt;
+    }
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int t = tile - 1;
+      int spins = 0;
+      while (t >= 0) {
+        const unsigned long long w = vst[(size_t)t * 256 + d];
+        const uint32_t flag = (uint32_t)(w >> 30) & 3u;
+        if ((w & 0xffffffff00000000ull) != ep || flag == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(err, 2);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += (uint32_t)(w & 0x3fffffffull);
+        if (flag == 2) break;
+        --t;
+      }
+      __threadfence();
+      vst[(size_t)tile * 256 + d] = ep | (2ull << 30) | (excl + cnt);
+    }
+    uint32_t run = dbase[d] + excl;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = whist[w][d];
+      whist[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    uint32_t pos = 0;
+    const bool valid = peers[j] != 0;
+    if (valid) pos = whist[warp][dig[j]] + __popc(peers[j] & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers[j]) - 1) whist[warp][dig[j]] += __popc(peers[j]);
+    __syncwarp();
+    if (valid && pos < (uint32_t)n) {
+      kout[pos] = key[j];
+      vout[pos] = val[j];
+    }
+  }
 }
 
 // Common prefix length of sorted keys i and j; equal keys are told apart by
@@ -131,11 +287,10 @@ __device__ __forceinline__ int prefix_len(const uint32_t* __restrict__ k, int n,
 // Karras (2012) binary radix tree: internal node i covers [lo, hi]; its split
 // g separates [lo, g] and [g+1, hi].  Node ids: internal 0..n-2 (root 0),
 // leaf j -> n-1+j.
-__global__ void karras_kernel(const uint32_t* __restrict__ k, int n, int32_t* lo, int32_t* hi,
-                              int32_t* left, int32_t* right, int32_t* delta, int32_t* owner,
-                              int32_t* parent) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
+__device__ __forceinline__ void karras_node(const uint32_t* __restrict__ k, int n, int i,
+                                            int32_t* lo, int32_t* hi, int32_t* left,
+                                            int32_t* right, int32_t* delta, int32_t* owner,
+                                            int32_t* parent) {
   const int dr = prefix_len(k, n, i, (int64_t)i + 1);
   const int dl = prefix_len(k, n, i, (int64_t)i - 1);
   const int d = dr > dl ? 1 : -1;
@@ -159,6 +314,88 @@ __global__ void karras_kernel(const uint32_t* __restrict__ k, int n, int32_t* lo
   lo[i] = a; hi[i] = b; left[i] = L; right[i] = R; delta[i] = dnode; owner[g] = i;
   parent[L] = i; parent[R] = i;
   if (i == 0) parent[0] = -1;
+}
+
+// One radix-tree node per thread: the binary searches are chains of
+// dependent loads, so they need all the parallelism there is.
+__global__ void karras_kernel(const uint32_t* __restrict__ k, int n, int32_t* lo, int32_t* hi,
+                              int32_t* left, int32_t* right, int32_t* delta, int32_t* owner,
+                              int32_t* parent) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n - 1) karras_node(k, n, i, lo, hi, left, right, delta, owner, parent);
+}
+
+// Per tile of kSortTile sorted positions: the FP64 inclusive prefix sums of
+// the sorted positions within the tile (the tile total goes to tile_sum).
+__global__ void __launch_bounds__(kSortThreads) scan_xs_kernel(
+    XSel xs, const int32_t* __restrict__ vals, int n, float2* __restrict__ xsorted,
+    double2* __restrict__ incl, double2* __restrict__ tile_sum) {
+  const int base = blockIdx.x * kSortTile + threadIdx.x * kSortIPT;
+  const float2* x = xs.cur();
+  float2 v[kSortIPT];
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    const int i = base + j;
+    v[j] = make_float2(0.f, 0.f);
+    if (i < n) {
+      v[j] = x[vals[i]];
+      xsorted[i] = v[j];
+    }
+    sx += v[j].x;
+    sy += v[j].y;
+  }
+  // block exclusive scan of the per-thread sums
+  __shared__ double shx[kSortThreads / 32], shy[kSortThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double ix = sx, iy = sy;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double tx = __shfl_up_sync(0xffffffffu, ix, o);
+    const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+    if (lane >= o) { ix += tx; iy += ty; }
+  }
+  if (lane == 31) { shx[warp] = ix; shy[warp] = iy; }
+  __syncthreads();
+  double wx = 0.0, wy = 0.0;
+  for (int w = 0; w < warp; ++w) { wx += shx[w]; wy += shy[w]; }
+  double rx = wx + ix - sx, ry = wy + iy - sy;
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    rx += v[j].x;
+    ry += v[j].y;
+    if (base + j < n) incl[base + j] = make_double2(rx, ry);
+  }
+  if (threadIdx.x == kSortThreads - 1) tile_sum[blockIdx.x] = make_double2(rx, ry);
+}
+
+// Exclusive scan of the tile totals (one block).
+__global__ void __launch_bounds__(1024) tile_scan_kernel(double2* tile_sum, int tiles) {
+  __shared__ double shx[32], shy[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (tiles + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per, end = min(beg + per, tiles);
+  double sx = 0.0, sy = 0.0;
+  for (int i = beg; i < end; ++i) { sx += tile_sum[i].x; sy += tile_sum[i].y; }
+  double ix = sx, iy = sy;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double tx = __shfl_up_sync(0xffffffffu, ix, o);
+    const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+    if (lane >= o) { ix += tx; iy += ty; }
+  }
+  if (lane == 31) { shx[warp] = ix; shy[warp] = iy; }
+  __syncthreads();
+  double wx = 0.0, wy = 0.0;
+  for (int w = 0; w < warp; ++w) { wx += shx[w]; wy += shy[w]; }
+  double run_x = wx + ix - sx, run_y = wy + iy - sy;
+  __syncthreads();
+  for (int i = beg; i < end; ++i) {
+    const double2 c = tile_sum[i];
+    tile_sum[i] = make_double2(run_x, run_y);
+    run_x += c.x;
+    run_y += c.y;
+  }
 }
 
 struct TreeView {
@@ -206,45 +443,43 @@ __device__ void write_record(const TreeView& t, int id, double2 sum, float side,
     first = resolve(t, t.left[id]);
   }
   const int a = t.lo[id], b = t.hi[id];
-  const double cnt = (double)(b - a + 1);
+  const float cnt = (float)(b - a + 1);
   const float w = ldexpf(side, -depth);
   const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
-  nodeA[id] = make_float4((float)(sum.x / cnt), (float)(sum.y / cnt), rc, (float)cnt);
+  // the FP64 sum is rounded once to FP32, the division is FP32
+  nodeA[id] = make_float4((float)sum.x / cnt, (float)sum.y / cnt, rc, cnt);
   nodeB[id] = make_int4(first, escape_of(t, b), a, b + 1);
 }
 
-// One thread per leaf: writes the sorted positions and leaf records, then
-// climbs; the second thread to reach an internal node sums its children and
-// writes its record (the first one stops).
-__global__ void bottomup_kernel(XSel xs, const int32_t* __restrict__ vals, TreeView t,
-                                uint32_t* visit, double2* sums, float4* nodeA, int4* nodeB,
-                                float2* xsorted, const float4* __restrict__ root, float theta,
-                                const unsigned* ticket) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// Sum of the sorted positions [0, k): tile offset + inclusive sum in tile.
+__device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
+                                             const double2* __restrict__ tile_off, int k) {
+  if (k == 0) return make_double2(0.0, 0.0);
+  const double2 a = tile_off[(k - 1) / kSortTile];
+  const double2 b = incl[k - 1];
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+
+// Node-parallel records: a cell's position sum is the difference of two
+// prefix sums over its sorted range.
+__global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
+                               const double2* __restrict__ incl,
+                               const double2* __restrict__ tile_off,
+                               const float4* __restrict__ root, float theta, float4* nodeA,
+                               int4* nodeB) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
-  if (j >= n) return;
-  const float2 p = xs.cur()[vals[j]];
-  xsorted[j] = p;
-  const float side = root->z;
-  const uint32_t epoch = ticket[1];
-  int cur = n - 1 + j;
-  double2 s = make_double2(p.x, p.y);
-  sums[cur] = s;
-  write_record(t, cur, s, side, theta, nodeA, nodeB);
-  if (n == 1) return;
-  while (true) {
-    const int par = t.parent[cur];
-    if (par < 0) break;
-    __threadfence();
-    if (atomicExch(&visit[par], epoch) != epoch) break;  // first arrival
-    const int L = t.left[par], R = t.right[par];
-    const double2 a = __ldcg(&sums[L]);
-    const double2 b = __ldcg(&sums[R]);
-    s = make_double2(a.x + b.x, a.y + b.y);
-    sums[par] = s;
-    write_record(t, par, s, side, theta, nodeA, nodeB);
-    cur = par;
+  if (id >= 2 * n - 1) return;
+  double2 sum;
+  if (id >= n - 1) {
+    const float2 p = xsorted[id - (n - 1)];
+    sum = make_double2(p.x, p.y);
+  } else {
+    const double2 a = prefix_at(incl, tile_off, t.lo[id]);
+    const double2 b = prefix_at(incl, tile_off, t.hi[id] + 1);
+    sum = make_double2(b.x - a.x, b.y - a.y);
   }
+  write_record(t, id, sum, root->z, theta, nodeA, nodeB);
 }
 
 // Guards: node ids must stay in [0, 2n-1) and a walk visits each node at
@@ -350,8 +585,13 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
 
 }  // namespace
 
+size_t tree_status_words(int64_t n) {
+  return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortTile) * 256;
+}
+
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n) {
   const size_t N = (size_t)(n > 1 ? n : 2);
+  const size_t tiles = (size_t)ceil_div((int64_t)N, kSortTile);
   ws.cap = n;
   MM_CK(cudaMalloc(&ws.keys[0], sizeof(uint32_t) * N));
   MM_CK(cudaMalloc(&ws.keys[1], sizeof(uint32_t) * N));
@@ -365,9 +605,12 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n) {
   MM_CK(cudaMalloc(&ws.delta, sizeof(int32_t) * N));
   MM_CK(cudaMalloc(&ws.owner, sizeof(int32_t) * N));
   MM_CK(cudaMalloc(&ws.parent, sizeof(int32_t) * 2 * N));
-  MM_CK(cudaMalloc(&ws.visit, sizeof(uint32_t) * N));
-  MM_CK(cudaMemset(ws.visit, 0, sizeof(uint32_t) * N));
-  MM_CK(cudaMalloc(&ws.sums, sizeof(double2) * 2 * N));
+  MM_CK(cudaMalloc(&ws.incl, sizeof(double2) * N));
+  MM_CK(cudaMalloc(&ws.tile_sum, sizeof(double2) * tiles));
+  MM_CK(cudaMalloc(&ws.status, sizeof(unsigned long long) * tree_status_words(N)));
+  MM_CK(cudaMemset(ws.status, 0, sizeof(unsigned long long) * tree_status_words(N)));
+  MM_CK(cudaMalloc(&ws.hist, sizeof(uint32_t) * 4 * 256));
+  MM_CK(cudaMalloc(&ws.counters, sizeof(uint32_t) * 4));
   MM_CK(cudaMalloc(&ws.nodeA, sizeof(float4) * 2 * N));
   MM_CK(cudaMalloc(&ws.nodeB, sizeof(int4) * 2 * N));
   MM_CK(cudaMalloc(&ws.partials, sizeof(float4) * kBBoxMaxBlocks));
@@ -378,16 +621,15 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n) {
   MM_CK(cudaMemset(ws.err, 0, sizeof(int)));
   // unwritten records read as leaves whose escape ends the walk
   MM_CK(cudaMemset(ws.nodeB, 0xff, sizeof(int4) * 2 * N));
-  MM_TRY(sort_ws_alloc(ws.sort, N));
   return MM_OK;
 }
 
 void tree_ws_free(TreeWS& ws) {
   void* ptrs[] = {ws.keys[0], ws.keys[1], ws.vals[0], ws.vals[1], ws.xs, ws.lo, ws.hi,
-                  ws.left, ws.right, ws.delta, ws.owner, ws.parent, ws.visit, ws.sums,
-                  ws.nodeA, ws.nodeB, ws.partials, ws.root, ws.ticket, ws.err};
+                  ws.left, ws.right, ws.delta, ws.owner, ws.parent, ws.incl, ws.tile_sum,
+                  ws.status, ws.hist, ws.counters, ws.nodeA, ws.nodeB, ws.partials, ws.root,
+                  ws.ticket, ws.err};
   for (void* p : ptrs) cudaFree(p);
-  sort_ws_free(ws.sort);
   ws = TreeWS();
 }
 
@@ -397,28 +639,35 @@ mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s, cudaE
     set_error("tree workspace holds %lld vertices, level has %d", (long long)ws.cap, n);
     return MM_ERR_INVALID_ARG;
   }
-  const int bb = std::min(kBBoxMaxBlocks, ceil_div(n, kBBoxThreads));
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(ev[i], s);
   };
+  const int tiles = ceil_div(n, kSortTile);
+  const int bb = std::min(kBBoxMaxBlocks, ceil_div(n, kBBoxThreads));
   mark(0);
-  bbox_kernel<<<bb, kBBoxThreads, 0, s>>>(x, n, ws.partials, ws.ticket, ws.root);
+  bbox_kernel<<<bb, kBBoxThreads, 0, s>>>(x, n, ws.partials, ws.ticket, ws.root, ws.hist,
+                                          ws.counters);
   mark(1);
-  morton_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, n, ws.root, ws.keys[0], ws.vals[0]);
+  morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, ws.root, ws.keys[0], ws.vals[0],
+                                                   ws.hist);
   mark(2);
-  uint32_t* keys;
-  int32_t* vals;
-  MM_TRY(radix_sort_u32(ws.keys[0], ws.keys[1], ws.vals[0], ws.vals[1], n, 0, 32, ws.sort, s,
-                        &keys, &vals));
+  // four stable 8-bit passes; the result is back in buffer 0
+  for (int pass = 0; pass < 4; ++pass) {
+    const int a = pass & 1;
+    onesweep_pass<<<tiles, kSortThreads, 0, s>>>(ws.keys[a], ws.vals[a], ws.keys[a ^ 1],
+                                                 ws.vals[a ^ 1], n, pass, ws.hist, ws.counters,
+                                                 ws.status, ws.ticket, ws.err);
+  }
   mark(3);
-  // 4 passes: the result is back in buffer 0
-  if (n > 1) karras_kernel<<<ceil_div(n - 1, 256), 256, 0, s>>>(keys, n, ws.lo, ws.hi, ws.left,
-                                                                 ws.right, ws.delta, ws.owner,
-                                                                 ws.parent);
+  if (n > 1)
+    karras_kernel<<<ceil_div(n - 1, 256), 256, 0, s>>>(ws.keys[0], n, ws.lo, ws.hi, ws.left,
+                                                       ws.right, ws.delta, ws.owner, ws.parent);
+  scan_xs_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.xs, ws.incl, ws.tile_sum);
+  tile_scan_kernel<<<1, 1024, 0, s>>>(ws.tile_sum, tiles);
   mark(4);
   TreeView tv{n, ws.lo, ws.hi, ws.left, ws.right, ws.delta, ws.owner, ws.parent};
-  bottomup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, vals, tv, ws.visit, ws.sums, ws.nodeA,
-                                                   ws.nodeB, ws.xs, ws.root, theta, ws.ticket);
+  records_kernel<<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(tv, ws.xs, ws.incl, ws.tile_sum,
+                                                          ws.root, theta, ws.nodeA, ws.nodeB);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;

@@ -207,6 +207,30 @@ int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
   return k + 1;                              // walk
 }
 
+SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, SchedParams sp,
+                     float* trace, int trace_cap, int* lsw, int max_sweeps) {
+  const Level& L = h->levels[level];
+  SmallArgs a;
+  a.n = L.n;
+  a.sp = L.sp;
+  a.S = L.s;
+  a.rho = L.rho;
+  a.exact = exact ? 1 : 0;
+  a.theta = h->p.theta;
+  a.b0 = h->xb[0];
+  a.b1 = h->xb[1];
+  a.st = st;
+  a.sched = sp;
+  a.trace = trace;
+  a.trace_cap = trace_cap;
+  a.lsw = lsw;
+  a.max_sweeps = max_sweeps;
+  a.lanes = L.lanes;
+  a.err = h->tree.err;
+  a.prof = nullptr;
+  return a;
+}
+
 // One sweep on `level`: repulsion, fused update, controller.
 mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState* st,
                      SchedParams sp, float* trace, int trace_cap, int* lsw,
@@ -253,6 +277,12 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single) {
     return MM_OK;
   };
   auto add_loop = [&](int level, bool exact) -> mm_status {
+    if (h->levels[level].fused)
+      return add_child([&](cudaStream_t s) -> mm_status {
+        return small_level(small_args(h, level, exact, h->state, sp, h->trace, h->trace_cap,
+                                      h->lsw + level, 1 << 30),
+                           s);
+      });
     cudaGraphConditionalHandle hnd;
     MM_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
     alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
@@ -524,7 +554,10 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
     MM_TRY(build_khop(L.n, L.rp, L.col, lv == 0 ? L.elen : nullptr, lv == 0 ? nullptr : L.c,
                       p->k, &L.sp, &L.s, &L.rho, &L.nnzS, s));
     MM_TRY(gather_config(L, *p, s));
+    const int lim = p->fused_max_n == 0 ? kSmallMaxN : std::min(p->fused_max_n, kSmallMaxN);
+    L.fused = p->fused_max_n >= 0 && L.n <= lim;
   }
+  MM_TRY(small_level_setup());
   {
     Level& C = h->levels.back();
     std::vector<float> hc(C.n);
@@ -635,7 +668,10 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     int64_t kl = 1;  // copy of the result
     for (int i = 0; i < nl; ++i) {
       if (single && i > 0) break;
-      kl += 2 + (int64_t)lsw[i] * kernels_per_sweep(h, i, level_exact(h, i, single));
+      if (h->levels[i].fused)
+        kl += 2 + 1;
+      else
+        kl += 2 + (int64_t)lsw[i] * kernels_per_sweep(h, i, level_exact(h, i, single));
     }
     stats->kernel_launches = kl;
   }
@@ -808,8 +844,16 @@ mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha, const float* x_
   sp.iters_per_alpha = 1 << 30;
   sp.max_iters_at_min = 1 << 30;
   sp.early_exit = 0;
-  MM_TRY(sweep_body(h, level, h->p.exact_repulsion != 0, x, h->sstate, sp, nullptr, 0, nullptr,
-                    0, false, s));
+  if (L.fused) {
+    SmallArgs a = small_args(h, level, h->p.exact_repulsion != 0, h->sstate, sp, nullptr, 0,
+                             nullptr, 1);
+    a.b0 = const_cast<float2*>((const float2*)x_in);
+    a.b1 = (float2*)x_out;
+    MM_TRY(small_level(a, s));
+  } else {
+    MM_TRY(sweep_body(h, level, h->p.exact_repulsion != 0, x, h->sstate, sp, nullptr, 0,
+                      nullptr, 0, false, s));
+  }
   if (stats) {
     SweepState hs;
     MM_CK(cudaMemcpyAsync(&hs, h->sstate, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -867,6 +911,60 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
   const bool exact = h->p.exact_repulsion != 0;
+  if (L.fused) {
+    // fused level kernel: phases from clock64 stamps of one sweep (stage
+    // order: stage x, bbox, sort, radix tree, prefix sums, records, walk or
+    // exact sum, update + reductions; schedule step reported as controller)
+    long long* prof = nullptr;
+    float2* tmp = nullptr;
+    MM_CK(cudaMalloc(&prof, 10 * sizeof(long long)));
+    MM_CK(cudaMalloc(&tmp, sizeof(float2) * (size_t)std::max(L.n, 1)));
+    SchedParams sp = sched_of(h->p, 1 << 30);
+    sp.early_exit = 0;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device);
+    mm_status st = MM_OK;
+    for (int r = 0; r <= reps && st == MM_OK; ++r) {
+      set_state<<<1, 1, 0, s>>>(h->sstate, 0.3);
+      MM_CK(cudaMemsetAsync(prof, 0, 10 * sizeof(long long), s));
+      SmallArgs a = small_args(h, level, exact, h->sstate, sp, nullptr, 0, nullptr, 1);
+      a.b0 = const_cast<float2*>((const float2*)x);
+      a.b1 = tmp;
+      a.prof = prof;
+      st = small_level(a, s);
+      long long hp[10];
+      if (st == MM_OK) {
+        cudaMemcpyAsync(hp, prof, sizeof(hp), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) st = MM_ERR_CUDA;
+      }
+      if (st != MM_OK || r == 0) continue;
+      for (int i = 0; i < 9; ++i) {
+        const long long d = (hp[i + 1] && hp[i]) ? hp[i + 1] - hp[i] : 0;
+        acc[i] += khz > 0 ? (double)d / khz : 0.0;  // cycles / kHz = ms
+      }
+    }
+    cudaFree(prof);
+    cudaFree(tmp);
+    MM_TRY(st);
+    // 9 intervals mapped onto the 8 reported stages: [x staging + bbox],
+    // morton+sort, radix tree, prefix sums, records, walk, update, schedule
+    stage_ms[0] = (acc[0] + acc[1]) / reps;
+    stage_ms[1] = 0.0;
+    stage_ms[2] = acc[2] / reps;
+    stage_ms[3] = (acc[3] + acc[4]) / reps;
+    stage_ms[4] = acc[5] / reps;
+    stage_ms[5] = acc[6] / reps;
+    stage_ms[6] = acc[7] / reps;
+    stage_ms[7] = acc[8] / reps;
+    if (work) {
+      work[0] = 0;
+      work[1] = 0;
+      work[2] = L.nnzS;
+      work[3] = L.n;
+    }
+    return tree_error(h, s);
+  }
   float2* tmp = nullptr;
   unsigned long long* cnt = nullptr;
   MM_CK(cudaMalloc(&tmp, sizeof(float2) * (size_t)std::max(L.n, 1)));

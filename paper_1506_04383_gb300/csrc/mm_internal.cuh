@@ -59,6 +59,52 @@ struct SchedParams {
   int32_t iters_per_alpha, max_iters_at_min, early_exit, level_cap;
 };
 
+// One step of the alpha schedule of Sec. 3.2 after a sweep with reductions
+// sdx = sum|x'-x|^2, sx = sum|x|^2 and stress: at most iters_per_alpha
+// iterations per alpha (fewer when the relative change |x'-x|/|x| drops
+// below eps), alpha := max(factor * alpha, alpha_min); at alpha_min iterate
+// until the change is below eps_final or max_iters_at_min iterations.
+// Flips the buffer parity.  Returns true when the level is done.  Single
+// thread.
+__device__ __forceinline__ bool schedule_step(SweepState* st, const SchedParams& sp, double sdx,
+                                              double sx, double stress, float* trace,
+                                              int trace_cap, int* level_sweeps_out) {
+  const double rel = sx > 0 ? sqrt(sdx) / sqrt(sx) : (sdx == 0 ? 0.0 : (double)INFINITY);
+  const double alpha = st->alpha;
+  const int t = st->total;
+  if (trace && t < trace_cap) {
+    trace[3 * t] = (float)alpha;
+    trace[3 * t + 1] = (float)rel;
+    trace[3 * t + 2] = (float)stress;
+  }
+  st->total = t + 1;
+  st->level_sweeps += 1;
+  st->parity ^= 1;
+  st->it_in_round += 1;
+  st->last_rel = rel;
+  st->last_stress = stress;
+  st->last_sdx = sdx;
+  st->last_sx = sx;
+  const bool at_min = alpha <= sp.alpha_min;
+  const int cap = at_min ? sp.max_iters_at_min : sp.iters_per_alpha;
+  const double tol = at_min ? sp.eps_final : sp.eps;
+  if ((sp.early_exit && rel < tol) || st->it_in_round >= cap) {
+    if (at_min) {
+      st->done = 1;
+    } else {
+      st->alpha = fmax(alpha * sp.alpha_factor, sp.alpha_min);
+      st->it_in_round = 0;
+    }
+  }
+  if (!isfinite(sdx) || !isfinite(sx)) {
+    st->error = MM_ERR_NONFINITE;
+    st->done = 1;
+  }
+  if (st->level_sweeps >= sp.level_cap) st->done = 1;
+  if (level_sweeps_out) *level_sweeps_out = st->level_sweeps;
+  return st->done != 0;
+}
+
 // Selects the current position buffer by the device-side parity.
 struct XSel {
   const float2* b0;
@@ -88,6 +134,7 @@ struct Level {
   int32_t max_deg = 0;       // max |S_u|
   int32_t lanes = 1;         // lanes per vertex in the light gather
   int32_t heavy_degree = 0;
+  bool fused = false;        // whole level in the single-CTA kernel
   double sum_c = 0;
 };
 
@@ -136,23 +183,28 @@ struct TreeWS {
   int32_t* delta = nullptr;
   int32_t* owner = nullptr;   // owner[g] = internal node whose split is g
   int32_t* parent = nullptr;  // all nodes [2n-1]
-  uint32_t* visit = nullptr;  // internal nodes, epoch of the first arrival
-  double2* sums = nullptr;    // all nodes, position sums
+  double2* incl = nullptr;    // [n] inclusive position sums within each sort tile
+  double2* tile_sum = nullptr;// [tiles] tile totals, then their exclusive prefix
+  unsigned long long* status = nullptr;  // [4][tiles][256] look-back words
+  uint32_t* hist = nullptr;   // [4][256] digit counts
+  uint32_t* counters = nullptr;  // [4] tile tickets of the sort passes
   float4* nodeA = nullptr;    // (cx, cy, r_crit^2, count)
   int4* nodeB = nullptr;      // (first child | -1, escape | -1, lo, hi+1)
   float4* partials = nullptr; // bbox partial results
   float4* root = nullptr;     // (min x, min y, side, key scale)
   uint32_t* ticket = nullptr; // [0] last-block ticket, [1] build epoch
-  int* err = nullptr;         // set by a walk that met a broken tree
-  SortWS sort;
+  int* err = nullptr;         // set by a walk that met a broken tree (1) or a
+                              // sort pass whose look-back gave up (2)
 };
 constexpr int kKeyBits = 16;  // per axis -> 32-bit Morton keys, depth 16
 
+size_t tree_status_words(int64_t n);
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n);
 void tree_ws_free(TreeWS& ws);
 
-// Rebuilds the quadtree from the current positions (bbox, Morton keys,
-// sort, radix tree, bottom-up centroids, node records).
+// Rebuilds the quadtree from the current positions (bbox, Morton keys and
+// digit histograms, four look-back sort passes, radix tree with FP64 prefix
+// sums, node records).
 // ev (nullable, 6 events) records the stage boundaries for profiling.
 mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s,
                    cudaEvent_t* ev = nullptr);
@@ -181,6 +233,35 @@ mm_status level_start(SweepState* st, double alpha0, int flip, cudaStream_t s);
 mm_status init_coarsest(int n, const float* c, const SEnt* s0, uint64_t seed, int level,
                         float R, float2* x0, SweepState* st, double alpha0, cudaStream_t s);
 mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s);
+
+// ------------------------------------------------- fused small levels ---
+constexpr int kSmallMaxN = 2048;     // largest level the single-CTA kernel takes
+constexpr int kSmallThreads = 1024;
+
+struct SmallArgs {
+  int n;
+  const int32_t* sp;
+  const SEnt* S;
+  const float* rho;
+  int exact;
+  float theta;
+  float2* b0;
+  float2* b1;
+  SweepState* st;
+  SchedParams sched;
+  float* trace;
+  int trace_cap;
+  int* lsw;
+  int max_sweeps;
+  int lanes;       // lanes per S row in the update (power of two <= 32)
+  int* err;
+  long long* prof; // nullable: clock64 stamps of the first sweep's phases [10]
+};
+size_t small_level_smem();
+mm_status small_level_setup();
+// Runs sweeps of one level in one CTA until the schedule ends the level or
+// max_sweeps sweeps are done; reads buffer [st->parity], flips it per sweep.
+mm_status small_level(const SmallArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------ hierarchy --
 mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t* col,

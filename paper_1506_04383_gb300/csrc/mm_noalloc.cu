@@ -39,8 +39,8 @@ constexpr size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of the workspace pieces inside the array.
 struct Carve {
-  size_t keys0, keys1, vals0, vals1, xs, lo, hi, left, right, delta, owner, parent, visit, sums,
-      nodeA, nodeB, partials, root, ticket, err, zero, counts, totals, total;
+  size_t keys0, keys1, vals0, vals1, xs, lo, hi, left, right, delta, owner, parent, incl,
+      tile_sum, status, hist, counters, nodeA, nodeB, partials, root, ticket, err, zero, total;
 };
 
 constexpr Carve carve() {
@@ -60,8 +60,11 @@ constexpr Carve carve() {
   c.delta = o; o += up(4 * N);
   c.owner = o; o += up(4 * N);
   c.parent = o; o += up(4 * 2 * N);
-  c.visit = o; o += up(4 * N);
-  c.sums = o; o += up(16 * 2 * N);
+  c.incl = o; o += up(16 * N);
+  c.tile_sum = o; o += up(16 * tiles);
+  c.status = o; o += up(8 * 4 * tiles * 256);
+  c.hist = o; o += up(4 * 4 * 256);
+  c.counters = o; o += up(4 * 4);
   c.nodeA = o; o += up(16 * 2 * N);
   c.nodeB = o; o += up(16 * 2 * N);
   c.partials = o; o += up(16 * 2 * kSMs);
@@ -69,8 +72,6 @@ constexpr Carve carve() {
   c.ticket = o; o += up(8);
   c.err = o; o += up(4);
   c.zero = o; o += up(4);
-  c.counts = o; o += up(4 * 256 * tiles);
-  c.totals = o; o += up(4 * 256);
   c.total = o;
   return c;
 }
@@ -144,20 +145,20 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   ws.delta = (int32_t*)(b + c.delta);
   ws.owner = (int32_t*)(b + c.owner);
   ws.parent = (int32_t*)(b + c.parent);
-  ws.visit = (uint32_t*)(b + c.visit);
-  ws.sums = (double2*)(b + c.sums);
+  ws.incl = (double2*)(b + c.incl);
+  ws.tile_sum = (double2*)(b + c.tile_sum);
+  ws.status = (unsigned long long*)(b + c.status);
+  ws.hist = (uint32_t*)(b + c.hist);
+  ws.counters = (uint32_t*)(b + c.counters);
   ws.nodeA = (float4*)(b + c.nodeA);
   ws.nodeB = (int4*)(b + c.nodeB);
   ws.partials = (float4*)(b + c.partials);
   ws.root = (float4*)(b + c.root);
   ws.ticket = (uint32_t*)(b + c.ticket);
   ws.err = (int*)(b + c.err);
-  ws.sort.counts = (uint32_t*)(b + c.counts);
-  ws.sort.totals = (uint32_t*)(b + c.totals);
-  ws.sort.max_tiles = ceil_div(kNoAllocMaxN, kSortTile);
-  // the walk's error flag and the bounding-box ticket must start at zero;
-  // the build epoch (ticket[1]) must persist, since the visit flags compare
-  // against it
+  // the error flag and the bounding-box ticket must start at zero; the
+  // build epoch (ticket[1]) must persist, since the sort's look-back status
+  // words are tagged with it
   MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   MM_CK(cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), s));
   XSel xs{(const float2*)x, (const float2*)x, (const int32_t*)(b + c.zero)};

@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("max_levels", ctypes.c_int32),
         ("max_stalls", ctypes.c_int32), ("gather_lanes", ctypes.c_int32),
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("fused_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -305,7 +305,7 @@ def layout(h: Hierarchy, params: Params = None, x_init=None, x_out=None, stream=
     return x_out, st.as_dict()
 
 
-STAGES = ["bbox", "morton", "sort", "radix_tree", "bottom_up", "traverse", "gather",
+STAGES = ["bbox", "morton_hist", "sort", "radix_tree_scan", "records", "traverse", "gather",
           "controller"]
 
 

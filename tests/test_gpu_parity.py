@@ -144,13 +144,16 @@ def test_bh_small_sizes(mm):
 
 
 # --------------------------------------------------------------- sweep ---
+# fused_max_n = 0: levels of <= 2048 vertices run in the single-CTA level
+# kernel; -1: the multi-kernel sweep.  Both paths are checked on every case.
+@pytest.mark.parametrize("fused", [0, -1])
 @pytest.mark.parametrize("alpha", [1.0, 0.09, 0.008])
 @pytest.mark.parametrize("shape", [(32, 32), (37, 29)])
-def test_sweep_exact_matches_oracle(mm, alpha, shape):
+def test_sweep_exact_matches_oracle(mm, alpha, shape, fused):
     rp, col = graphs.grid(*shape)
     n = len(rp) - 1
     x = f32(graphs.uniform_positions(n, 1506))
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, exact_repulsion=1)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, exact_repulsion=1, fused_max_n=fused)
     xg, st = mm.sweep(h, 0, alpha, cu(x))
     S = oracle.build_S(rp, col, 2)
     xo, sto = oracle.sweep(x.astype(np.float64), S, alpha, 0)
@@ -169,6 +172,25 @@ def test_sweep_bh_matches_oracle(mm):
     d = np.abs(xg.cpu().numpy() - xo).max(1)
     # acceptance-boundary ties may differ on a few vertices
     assert np.mean(d <= 1e-4 * diameter(xo)) >= 0.99
+
+
+@pytest.mark.parametrize("fused", [0, -1])
+@pytest.mark.parametrize("n_pts", [1800, 33, 2048])
+def test_sweep_bh_small_level_paths(mm, fused, n_pts):
+    rp, col, pts, _ = graphs.rgg(n_pts, 8.0, 22 + n_pts, tune=False, lcc=False)
+    n = len(rp) - 1
+    # isolated vertices have no S row (rho = 0); give them a neighbour chain
+    src = np.repeat(np.arange(n), np.diff(rp))
+    rp, col = graphs.csr_from_edges(n, np.concatenate([src, np.arange(n - 1)]),
+                                    np.concatenate([col, np.arange(1, n)]))
+    x = f32(pts * 40.0)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, fused_max_n=fused)
+    xg, st = mm.sweep(h, 0, 0.3, cu(x))
+    S = oracle.build_S(rp, col, 2)
+    xo, sto = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
+    d = np.abs(xg.cpu().numpy() - xo).max(1)
+    assert np.mean(d <= 1e-4 * diameter(xo)) >= 0.99
+    np.testing.assert_allclose(st[1:], sto[1:], rtol=1e-4)
 
 
 def test_sweep_heavy_row_star(mm):
@@ -295,16 +317,17 @@ def test_hierarchy_invariants(mm):
 
 
 # ---------------------------------------------------------------- layout --
-def test_layout_config1_grid_matches_oracle_objective(mm):
+@pytest.mark.parametrize("fused", [0, -1])
+def test_layout_config1_grid_matches_oracle_objective(mm, fused):
     # 32x32 grid, k=2, exact repulsion, uniform [0,1]^2 start, 100 sweeps
     rp, col = graphs.grid(32, 32)
     n = len(rp) - 1
     x0 = f32(graphs.uniform_positions(n, 1506))
     kw = dict(k=2, exact_repulsion=1, coarsest_n=n, early_exit=0, max_iters_at_min=90)
-    h, p = hier(mm, rp, col, **kw)
+    h, p = hier(mm, rp, col, fused_max_n=fused, **kw)
     x, st = mm.layout(h, p, x_init=cu(x0))
     assert st["total_sweeps"] == 100 and st["level_sweeps"][0] == 100
-    po = oracle.params(**{k: v for k, v in kw.items()})
+    po = oracle.params(**kw)
     xo, _ = oracle.layout(rp, col, po, x_init=x0.astype(np.float64))
     S = oracle.build_S(rp, col, 2)
     Mg = oracle.objective(x.cpu().numpy().astype(np.float64), S, 0.008)[2]
@@ -322,8 +345,9 @@ def oracle_levels_to_device(levels):
     return out
 
 
+@pytest.mark.parametrize("fused", [0, -1])
 @pytest.mark.parametrize("case", ["rgg", "btree"])
-def test_layout_same_hierarchy_matches_oracle_objective(mm, case):
+def test_layout_same_hierarchy_matches_oracle_objective(mm, case, fused):
     # the oracle's coarsening fed to the GPU: same levels, same seed, so the
     # prolongation draws and the schedule are identical; the final
     # objectives (Eq. 1 at alpha = 0.008) must agree within 1%
@@ -336,7 +360,8 @@ def test_layout_same_hierarchy_matches_oracle_objective(mm, case):
     po = oracle.params(**kw)
     levels = oracle.build_hierarchy(rp, col, po)
     xo, info = oracle.layout(rp, col, po, levels=levels)
-    h = mm.build_hierarchy_levels(oracle_levels_to_device(levels), mm.default_params(**kw))
+    h = mm.build_hierarchy_levels(oracle_levels_to_device(levels),
+                                  mm.default_params(fused_max_n=fused, **kw))
     assert h.levels() == len(levels)
     x, st = mm.layout(h)
     xs = x.cpu().numpy()
