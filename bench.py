@@ -53,6 +53,10 @@ WORKLOADS = {
                         "component, k=1, theta=0.6"),
     "del20": dict(kind="delaunay", n=1 << 20, seed=1506, k=1, theta=0.6, coarsest_n=100,
                   desc="Delaunay triangulation of 2^20 uniform points, k=1, theta=0.6"),
+    "batch512": dict(kind="batch", count=512, seed=1506, k=2, theta=0.5, coarsest_n=2,
+                     desc="512 graphs, lognormal sizes (median 3000, sigma 1) in [200, 50000], "
+                          "thirds grids / random geometric (mean degree 6-12) / random trees, "
+                          "k=2, theta=0.5, one batched layout"),
 }
 
 
@@ -64,6 +68,11 @@ def make_graph(w):
         rp, col = graphs.grid(w["nx"], w["ny"])
     elif w["kind"] == "rmat":
         rp, col = graphs.rmat(w["scale"], w["ef"], w["seed"])
+    elif w["kind"] == "batch":
+        sizes = graphs.batch_sizes(w["count"], w["seed"])
+        gs = [graphs.batch_graph(i, sz, w["seed"]) for i, sz in enumerate(sizes)]
+        rp, col, gp = graphs.concat_graphs(gs)
+        return rp, col, gp, gs
     else:
         rp, col, _ = graphs.delaunay(w["n"], w["seed"])
     return rp, col
@@ -202,6 +211,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--batch-compare", type=int, default=64,
+                    help="graphs of the batch also laid out one by one for comparison")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -225,7 +237,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    rp, col = make_graph(w)
+    made = make_graph(w)
+    rp, col = made[0], made[1]
+    gp = made[2] if len(made) > 2 else None
     n = len(rp) - 1
     kw = params_of(mm, w)
     p = mm.default_params(**kw)
@@ -238,10 +252,13 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    h = mm.build_hierarchy(drp, dcol, p)
+    h = mm.build_hierarchy(drp, dcol, p, graph_ptr=gp)
     e1.record()
     torch.cuda.synchronize()
     build_ms = e0.elapsed_time(e1)
+    tune = None
+    if args.autotune:
+        tune = mm.autotune(h, max_rel_drift=0.01)
     xbuf = torch.empty((n, 2), dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 0)):
         _, st = mm.layout(h, p, x_init=x_init, x_out=xbuf)
@@ -273,13 +290,26 @@ def main():
     launches = sum(s["kernel_launches"] for s in stats)
 
     # quality: objective of the final layout (Eq. 1 at alpha = 0.008)
-    _, _, M = mm.objective(h, 0, xbuf, 0.008)
+    M = None if gp is not None else mm.objective(h, 0, xbuf, 0.008)[2]
+    batch_cmp = None
+    if gp is not None:
+        batch_cmp = compare_batch(mm, made[3], p, args.batch_compare)
 
     # roofline of the dominant kernel on the finest level, live with events
-    prof = mm.sweep_profile(h, 0, xbuf, reps=10)
     peaks, src = measured_peaks()
     clk_sum = clk.summary()
-    roof = roofline(prof, peaks, src, clk_sum, n)
+    if gp is None:
+        prof = mm.sweep_profile(h, 0, xbuf, reps=10)
+        roof = roofline(prof, peaks, src, clk_sum, n)
+    else:
+        big = int(np.argmax(np.diff(gp)))
+        grp, gcol = made[3][big]
+        hb = mm.build_hierarchy(torch.from_numpy(grp).cuda(), torch.from_numpy(gcol).cuda(),
+                                mm.default_params(**dict(kw, seed=int(kw.get("seed", 1506)))))
+        xb, _ = mm.layout(hb)
+        prof = mm.sweep_profile(hb, 0, xb, reps=10)
+        roof = roofline(prof, peaks, src, clk_sum, len(grp) - 1)
+        roof["graph"] = f"largest graph of the batch (n={len(grp) - 1})"
 
     # end to end through the host API (pinned host buffers)
     e2e = None
@@ -290,7 +320,8 @@ def main():
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            xh, sth = mm.layout_host(prp, pcol, p)
+            xh, sth = mm.layout_host(prp, pcol, p) if gp is None else \
+                layout_host_batch(mm, prp, pcol, gp, p)
             t1 = time.perf_counter()
             if i > 0:
                 times.append(t1 - t0)
@@ -321,6 +352,8 @@ def main():
             "time_to_layout_s": (build_ms + statistics.mean(step_ms)) / 1e3,
             "hierarchy_build_ms": build_ms,
             "objective_M": M,
+            "batch_vs_plain": batch_cmp,
+            "autotune": tune,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -331,6 +364,59 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def layout_host_batch(mm, rp, col, gp, p):
+    """End to end for a batch: host CSR in, hierarchy build, batched layout,
+    host layout out (the batch needs graph_ptr, which the one-call host API
+    does not take)."""
+    import numpy as np
+    import torch
+    drp = torch.from_numpy(rp).cuda(non_blocking=True)
+    dcol = torch.from_numpy(col).cuda(non_blocking=True)
+    h = mm.build_hierarchy(drp, dcol, p, graph_ptr=gp)
+    x, st = mm.layout(h, p)
+    return x.cpu().numpy(), st
+
+
+def compare_batch(mm, gs, p, count):
+    """The first `count` graphs laid out one by one (plain per-graph
+    mm_layout, hierarchy prebuilt) against the same graphs as one batch."""
+    import numpy as np
+    import torch
+    from paper_1506_04383_gb300 import graphs
+    count = min(count, len(gs))
+    sub = gs[:count]
+    hs = []
+    for i, (rp, col) in enumerate(sub):
+        pi = mm.default_params()
+        ctypes_copy(pi, p)
+        pi.seed = p.seed + i
+        hs.append((mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(),
+                                      pi), pi))
+    rp, col, gp = graphs.concat_graphs(sub)
+    hb = mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), p,
+                            graph_ptr=gp)
+    for h, pi in hs:
+        mm.layout(h, pi)
+    xb, _ = mm.layout(hb, p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, pi in hs:
+        mm.layout(h, pi)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    xb, _ = mm.layout(hb, p)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    return {"graphs": count, "plain_sequential_ms": t_plain * 1e3,
+            "batched_ms": t_batch * 1e3, "speedup": t_plain / t_batch}
+
+
+def ctypes_copy(dst, src):
+    import ctypes
+    ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
 
 
 def roofline(prof, peaks, src, clk, n):

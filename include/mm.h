@@ -265,6 +265,34 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
 mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta,
                                float* F_out, void* stream);
 
+/* Result of mm_autotune (host struct). */
+typedef struct mm_tune_result {
+  int32_t gather_lanes[MM_MAX_LEVELS];   /* chosen lanes per S row (0: fused level) */
+  int32_t traverse_warps[MM_MAX_LEVELS]; /* chosen warps per walk block (0: fused)  */
+  float theta;                           /* chosen opening parameter               */
+  double objective_ref;                  /* M (Eq. 1, alpha = 0.008) at the old theta */
+  double objective;                      /* M at the chosen theta                  */
+  double layout_ms_before;               /* one mm_layout before tuning            */
+  double layout_ms_after;                /* one mm_layout after tuning             */
+} mm_tune_result;
+
+/*
+ * Autotuner (no paper counterpart; a deployment aid).  For every level run by
+ * the multi-kernel sweep it times the S update with 1..32 lanes per row and
+ * the tree walk with 2..16 warps per block on the level's own data and keeps
+ * the fastest; then it lays the graph out once per candidate opening
+ * parameter and keeps the fastest theta whose final objective (Eq. 1 at
+ * alpha = 0.008, summed over the graphs of a batch) stays within
+ * max_rel_drift of the objective at the hierarchy's current theta.  The
+ * choices are stored in the hierarchy (and cached per device and level
+ * shape for later hierarchies); mm_layout uses them from then on.
+ *   thetas     host [n_theta] candidates (NULL: 0.4, 0.5, 0.6, 0.7, 0.8)
+ *   out        host or NULL
+ * Synchronises the stream; allocates a layout buffer for the trials.
+ */
+mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta,
+                      double max_rel_drift, mm_tune_result* out, void* stream);
+
 /*
  * Maxent-stress objective, Eq. 1, general model over S of `level`:
  *   M(x) = sum_{{u,v} in S} w_uv (|x_u-x_v| - d_uv)^2

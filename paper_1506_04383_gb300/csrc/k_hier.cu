@@ -22,18 +22,40 @@ namespace mm {
 
 namespace {
 
-// RAII device buffer for temporaries of the build phase.
+// RAII device buffer for temporaries of the build phase, stream-ordered
+// (cudaMallocAsync / cudaFreeAsync never synchronise the device, so builds on
+// different streams -- the graphs of a batch -- overlap).
 struct Tmp {
   void* p = nullptr;
+  cudaStream_t s = nullptr;
   ~Tmp() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
   template <typename T>
   T* as() const { return (T*)p; }
 };
 
-mm_status tmp_alloc(Tmp& t, size_t bytes) {
-  MM_CK(cudaMalloc(&t.p, bytes > 0 ? bytes : 16));
+mm_status tmp_alloc(Tmp& t, size_t bytes, cudaStream_t s) {
+  t.s = s;
+  MM_CK(cudaMallocAsync(&t.p, bytes > 0 ? bytes : 16, s));
+  return MM_OK;
+}
+
+// Sort workspace on the stream's pool.
+struct TmpSort {
+  SortWS ws;
+  cudaStream_t s = nullptr;
+  ~TmpSort() {
+    if (ws.counts) cudaFreeAsync(ws.counts, s);
+    if (ws.totals) cudaFreeAsync(ws.totals, s);
+  }
+};
+
+mm_status tmp_sort(TmpSort& t, int64_t max_n, cudaStream_t s) {
+  t.s = s;
+  t.ws.max_tiles = ceil_div(max_n > 0 ? max_n : 1, kSortTile);
+  MM_CK(cudaMallocAsync(&t.ws.counts, sizeof(uint32_t) * 256 * (size_t)t.ws.max_tiles, s));
+  MM_CK(cudaMallocAsync(&t.ws.totals, sizeof(uint32_t) * 256, s));
   return MM_OK;
 }
 
@@ -266,7 +288,7 @@ __global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
 // admit while the cluster weight stays <= U.
 __global__ void lp_admit(int n, const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals,
                          const float* __restrict__ c, const float* __restrict__ W, float U,
-                         int32_t* labels) {
+                         int32_t* labels, int* moved) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t k = keys[i];
@@ -279,8 +301,144 @@ __global__ void lp_admit(int n, const uint64_t* __restrict__ keys, const int32_t
     if (acc + c[v] <= U) {
       acc += c[v];
       labels[v] = T;
+      atomicAdd(moved, 1);
     }
   }
+}
+
+// The whole label propagation of a level of at most kLPSmallN vertices in
+// one CTA, with the semantics of the multi-kernel rounds above: per round
+// two seeded halves; per half, every active vertex proposes its best
+// eligible neighbouring cluster (shared-memory hash per warp), movers are
+// ordered by (target, priority, vertex) with a bitonic sort and admitted
+// while the target's weight stays <= U, weights are recomputed.  Stops after
+// a round without moves (the labels are then a fixed point).
+constexpr int kLPSmallN = 4096;
+constexpr int kLPSmallT = 1024;
+constexpr int kLPSmallHash = 512;
+
+struct LPSmem {
+  int32_t hk[kLPSmallT / 32][kLPSmallHash];
+  float hv[kLPSmallT / 32][kLPSmallHash];
+  unsigned long long key[kLPSmallN];
+  int32_t lab[kLPSmallN];
+  float W[kLPSmallN];
+  float cv[kLPSmallN];
+};
+
+__global__ void __launch_bounds__(kLPSmallT, 1) lp_small_kernel(
+    int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+    const float* __restrict__ omega, const float* __restrict__ c, float U, int rounds,
+    uint32_t k0, uint32_t k1, uint32_t level, int32_t* labels) {
+  extern __shared__ __align__(16) unsigned char lp_raw[];
+  LPSmem& s = *reinterpret_cast<LPSmem*>(lp_raw);
+  __shared__ int moved;
+  const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+  const unsigned long long none = ~0ull;
+  for (int v = tid; v < n; v += kLPSmallT) {
+    s.lab[v] = v;
+    s.W[v] = c[v];
+    s.cv[v] = c[v];
+  }
+  int np = 2;
+  while (np < n) np <<= 1;
+  __syncthreads();
+  for (int r = 0; r < rounds; ++r) {
+    if (tid == 0) moved = 0;
+    for (uint32_t half = 0; half < 2; ++half) {
+      // proposals, one warp per vertex
+      for (int v = wl; v < np; v += kLPSmallT / 32) {
+        if (v >= n) {
+          if (lane == 0) s.key[v] = none;
+          continue;
+        }
+        uint32_t z[4];
+        philox4x32_10((uint32_t)v, (uint32_t)r, level, 2u, k0, k1, z);
+        if ((z[0] & 1u) != half) {
+          if (lane == 0) s.key[v] = none;
+          continue;
+        }
+        for (int i = lane; i < kLPSmallHash; i += 32) { s.hk[wl][i] = -1; s.hv[wl][i] = 0.f; }
+        __syncwarp();
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+          const int L = s.lab[col[e]];
+          const float w = omega ? omega[e] : 1.f;
+          uint32_t hsh = ((uint32_t)L * 2654435761u) & (kLPSmallHash - 1);
+          for (int probe = 0; probe < kLPSmallHash; ++probe) {
+            const int prev = atomicCAS(&s.hk[wl][hsh], -1, L);
+            if (prev == -1 || prev == L) {
+              atomicAdd(&s.hv[wl][hsh], w);
+              break;
+            }
+            hsh = (hsh + 1) & (kLPSmallHash - 1);
+          }
+        }
+        __syncwarp();
+        const int own = s.lab[v];
+        const float cvv = s.cv[v];
+        float best = -1.f, ownc = 0.f;
+        int bestL = 0x7fffffff;
+        for (int i = lane; i < kLPSmallHash; i += 32) {
+          const int L = s.hk[wl][i];
+          if (L < 0) continue;
+          const float cn = s.hv[wl][i];
+          if (L == own) { ownc = cn; continue; }
+          if (s.W[L] + cvv > U) continue;
+          if (cn > best || (cn == best && L < bestL)) { best = cn; bestL = L; }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oL = __shfl_xor_sync(0xffffffffu, bestL, o);
+          ownc += __shfl_xor_sync(0xffffffffu, ownc, o);
+          if (ob > best || (ob == best && oL < bestL)) { best = ob; bestL = oL; }
+        }
+        if (lane == 0)
+          s.key[v] = (best > ownc && bestL != 0x7fffffff)
+                         ? ((unsigned long long)bestL << 44) |
+                               ((unsigned long long)z[1] << 12) | (unsigned long long)v
+                         : none;
+        __syncwarp();
+      }
+      __syncthreads();
+      // order movers by (target, priority, vertex)
+      for (int k = 2; k <= np; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = tid; i < np; i += kLPSmallT) {
+            const int ij = i ^ j;
+            if (ij > i) {
+              const unsigned long long a = s.key[i], b = s.key[ij];
+              if ((a > b) == ((i & k) == 0)) { s.key[i] = b; s.key[ij] = a; }
+            }
+          }
+          __syncthreads();
+        }
+      // admission per target run
+      for (int i = tid; i < n; i += kLPSmallT) {
+        const unsigned long long k = s.key[i];
+        if (k == none) continue;
+        const int T = (int)(k >> 44);
+        if (i > 0 && s.key[i - 1] != none && (int)(s.key[i - 1] >> 44) == T) continue;
+        float acc = s.W[T];
+        for (int j = i; j < n && s.key[j] != none && (int)(s.key[j] >> 44) == T; ++j) {
+          const int v = (int)(s.key[j] & 0xfffull);
+          if (acc + s.cv[v] <= U) {
+            acc += s.cv[v];
+            s.lab[v] = T;
+            atomicAdd(&moved, 1);
+          }
+        }
+      }
+      __syncthreads();
+      for (int v = tid; v < n; v += kLPSmallT) s.W[v] = 0.f;
+      __syncthreads();
+      for (int v = tid; v < n; v += kLPSmallT) atomicAdd(&s.W[s.lab[v]], s.cv[v]);
+      __syncthreads();
+    }
+    if (moved == 0) break;
+    __syncthreads();
+  }
+  for (int v = tid; v < n; v += kLPSmallT) labels[v] = s.lab[v];
 }
 
 __global__ void lp_init(int n, const float* __restrict__ c, int32_t* labels, float* W) {
@@ -373,7 +531,7 @@ __global__ void sort_small_list(int m, int32_t* list) {
 mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t* col,
                          int32_t* rp32_out, cudaStream_t s) {
   Tmp fl;
-  MM_TRY(tmp_alloc(fl, sizeof(int)));
+  MM_TRY(tmp_alloc(fl, sizeof(int), s));
   MM_CK(cudaMemsetAsync(fl.p, 0, sizeof(int), s));
   validate_kernel<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, nnz, rp64, col, rp32_out, fl.as<int>());
   MM_CK(cudaGetLastError());
@@ -417,9 +575,9 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
   }
   // k = 2: enumerate paths of one and two edges
   Tmp cnt, off, scan_ws;
-  MM_TRY(tmp_alloc(cnt, sizeof(int32_t) * (size_t)(n + 1)));
-  MM_TRY(tmp_alloc(off, sizeof(int64_t) * (size_t)(n + 1)));
-  MM_TRY(tmp_alloc(scan_ws, scan_ws_bytes(std::max<int64_t>(n, 1)) + 64));
+  MM_TRY(tmp_alloc(cnt, sizeof(int32_t) * (size_t)(n + 1), s));
+  MM_TRY(tmp_alloc(off, sizeof(int64_t) * (size_t)(n + 1), s));
+  MM_TRY(tmp_alloc(scan_ws, scan_ws_bytes(std::max<int64_t>(n, 1)) + 64, s));
   khop2_count<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, cnt.as<int32_t>());
   MM_TRY(scan_exclusive_i64(cnt.as<int32_t>(), off.as<int64_t>(), n, scan_ws.p, s));
   int64_t m64 = 0;
@@ -433,31 +591,30 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
   const int vb = bits_for(std::max(n - 1, 1));
   const int ub = bits_for(std::max(n - 1, 1));
   Tmp k0, k1, d0, d1, head, pos, rowcnt, sp_tmp, S_tmp, ws2;
-  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(d0, sizeof(int32_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(d1, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(d0, sizeof(int32_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(d1, sizeof(int32_t) * (size_t)std::max(m, 1), s));
   khop2_emit<<<ceil_div(n, 256), 256, 0, s>>>(n, vb, rp, col, c, elen, off.as<int64_t>(),
                                               k0.as<uint64_t>(), d0.as<int32_t>());
   MM_CK(cudaGetLastError());
-  SortWS sws;
-  MM_TRY(sort_ws_alloc(sws, std::max(m, 1)));
+  TmpSort sws;
+  MM_TRY(tmp_sort(sws, std::max(m, 1), s));
   uint64_t* keys;
   int32_t* dbits;
-  mm_status st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), d0.as<int32_t>(),
-                                d1.as<int32_t>(), m, 0, ub + vb, sws, s, &keys, &dbits);
-  if (st != MM_OK) { sort_ws_free(sws); return st; }
-  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(m + 1)));
-  MM_TRY(tmp_alloc(ws2, scan_ws_bytes(std::max(m, 1)) + 64));
-  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(n + 1)));
-  MM_TRY(tmp_alloc(sp_tmp, sizeof(int32_t) * (size_t)(n + 1)));
+  MM_TRY(radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), d0.as<int32_t>(),
+                        d1.as<int32_t>(), m, 0, ub + vb, sws.ws, s, &keys, &dbits));
+  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(m + 1), s));
+  MM_TRY(tmp_alloc(ws2, scan_ws_bytes(std::max(m, 1)) + 64, s));
+  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(n + 1), s));
+  MM_TRY(tmp_alloc(sp_tmp, sizeof(int32_t) * (size_t)(n + 1), s));
   run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
   MM_TRY(scan_exclusive_i32(head.as<int32_t>(), pos.as<int32_t>(), m, ws2.p, s));
   int32_t uniq = 0;
   MM_CK(cudaMemcpyAsync(&uniq, pos.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
-  MM_TRY(tmp_alloc(S_tmp, sizeof(SEnt) * (size_t)std::max(uniq, 1)));
+  MM_TRY(tmp_alloc(S_tmp, sizeof(SEnt) * (size_t)std::max(uniq, 1), s));
   // temporary rows include the (u, u) padding runs
   MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
   count_runs<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, vb, keys, head.as<int32_t>(),
@@ -471,7 +628,6 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
   int32_t nnzS = 0;
   MM_CK(cudaMemcpyAsync(&nnzS, sp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
-  sort_ws_free(sws);
   MM_CK(cudaMalloc(&S, sizeof(SEnt) * (size_t)std::max(nnzS, 1)));
   *s_out = S;
   khop2_finish<<<ceil_div(n, 256), 256, 0, s>>>(n, sp_tmp.as<int32_t>(), S_tmp.as<SEnt>(), sp, S,
@@ -486,19 +642,31 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
                      const float* c, float U, int rounds, uint64_t seed, int level,
                      int32_t* labels, cudaStream_t s) {
   if (n <= 0) return MM_OK;
-  Tmp W, k0, k1, v0, v1;
-  MM_TRY(tmp_alloc(W, sizeof(float) * (size_t)n));
-  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)n));
-  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)n));
-  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)n));
-  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)n));
-  SortWS sws;
-  MM_TRY(sort_ws_alloc(sws, n));
+  const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+  if (n <= kLPSmallN) {
+    static_assert(sizeof(LPSmem) <= 227 * 1024, "LP kernel exceeds shared memory");
+    MM_CK(cudaFuncSetAttribute(lp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(LPSmem)));
+    lp_small_kernel<<<1, kLPSmallT, sizeof(LPSmem), s>>>(n, rp, col, omega, c, U, rounds, key0,
+                                                         key1, (uint32_t)level, labels);
+    MM_CK(cudaGetLastError());
+    MM_CK(cudaStreamSynchronize(s));
+    return MM_OK;
+  }
+  Tmp W, k0, k1, v0, v1, mv;
+  MM_TRY(tmp_alloc(mv, sizeof(int), s));
+  MM_TRY(tmp_alloc(W, sizeof(float) * (size_t)n, s));
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)n, s));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)n, s));
+  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)n, s));
+  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)n, s));
+  TmpSort sws;
+  MM_TRY(tmp_sort(sws, n, s));
   lp_init<<<ceil_div(n, 256), 256, 0, s>>>(n, c, labels, W.as<float>());
   const int tb = bits_for(n) + 1;
-  const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
   mm_status st = MM_OK;
   for (int r = 0; r < rounds && st == MM_OK; ++r) {
+    MM_CK(cudaMemsetAsync(mv.p, 0, sizeof(int), s));
     for (uint32_t half = 0; half < 2 && st == MM_OK; ++half) {
       lp_propose<<<ceil_div(n, kLPWarps), kLPWarps * 32, 0, s>>>(
           n, rp, col, omega, c, W.as<float>(), labels, U, key0, key1, (uint32_t)r,
@@ -506,16 +674,22 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
       uint64_t* keys;
       int32_t* vals;
       st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(), v1.as<int32_t>(),
-                          n, 0, 32 + tb, sws, s, &keys, &vals);
+                          n, 0, 32 + tb, sws.ws, s, &keys, &vals);
       if (st != MM_OK) break;
       // keys equal to all ones sort last only if every bit is compared: the
       // sort above covers bits [0, 32 + tb) and targets are < 2^(tb-1)
-      lp_admit<<<ceil_div(n, 256), 256, 0, s>>>(n, keys, vals, c, W.as<float>(), U, labels);
+      lp_admit<<<ceil_div(n, 256), 256, 0, s>>>(n, keys, vals, c, W.as<float>(), U, labels,
+                                                 mv.as<int>());
       cudaMemsetAsync(W.p, 0, sizeof(float) * (size_t)n, s);
       lp_weights<<<ceil_div(n, 256), 256, 0, s>>>(n, c, labels, W.as<float>());
     }
+    // a round without moves leaves a fixed point: every later round would
+    // make the same (no) choices
+    int moved = 0;
+    MM_CK(cudaMemcpyAsync(&moved, mv.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaStreamSynchronize(s));
+    if (moved == 0) break;
   }
-  sort_ws_free(sws);
   if (st != MM_OK) return st;
   MM_CK(cudaGetLastError());
   MM_CK(cudaStreamSynchronize(s));
@@ -529,9 +703,9 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   MM_CK(cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
   Tmp used, rank, ws, flag, pos, k0, k1, v0, v1, head, hpos, rowcnt;
-  MM_TRY(tmp_alloc(used, sizeof(int32_t) * (size_t)(n + 1)));
-  MM_TRY(tmp_alloc(rank, sizeof(int32_t) * (size_t)(n + 1)));
-  MM_TRY(tmp_alloc(ws, scan_ws_bytes(std::max(std::max(n, nnz), 1)) + 64));
+  MM_TRY(tmp_alloc(used, sizeof(int32_t) * (size_t)(n + 1), s));
+  MM_TRY(tmp_alloc(rank, sizeof(int32_t) * (size_t)(n + 1), s));
+  MM_TRY(tmp_alloc(ws, scan_ws_bytes(std::max(std::max(n, nnz), 1)) + 64, s));
   MM_CK(cudaMemsetAsync(used.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
   mark_used<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, used.as<int32_t>());
   MM_TRY(scan_exclusive_i32(used.as<int32_t>(), rank.as<int32_t>(), n, ws.p, s));
@@ -542,29 +716,28 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   MM_CK(cudaMalloc(&out.c, sizeof(float) * (size_t)std::max(nc, 1)));
   MM_CK(cudaMemsetAsync(out.c, 0, sizeof(float) * (size_t)std::max(nc, 1), s));
   apply_map<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, rank.as<int32_t>(), c, map, out.c);
-  MM_TRY(tmp_alloc(flag, sizeof(int32_t) * (size_t)std::max(nnz, 1)));
-  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(nnz + 1)));
+  MM_TRY(tmp_alloc(flag, sizeof(int32_t) * (size_t)std::max(nnz, 1), s));
+  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * (size_t)(nnz + 1), s));
   cut_flags<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, map, flag.as<int32_t>());
   MM_TRY(scan_exclusive_i32(flag.as<int32_t>(), pos.as<int32_t>(), nnz, ws.p, s));
   int32_t m = 0;
   MM_CK(cudaMemcpyAsync(&m, pos.as<int32_t>() + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
   const int cb = bits_for(std::max(nc - 1, 1));
-  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)std::max(m, 1)));
+  MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(k1, sizeof(uint64_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(v0, sizeof(int32_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)std::max(m, 1), s));
   cut_emit<<<ceil_div(n, 256), 256, 0, s>>>(n, cb, rp, col, map, pos.as<int32_t>(),
                                             k0.as<uint64_t>(), v0.as<int32_t>());
-  SortWS sws;
-  MM_TRY(sort_ws_alloc(sws, std::max(m, 1)));
+  TmpSort sws;
+  MM_TRY(tmp_sort(sws, std::max(m, 1), s));
   uint64_t* keys;
   int32_t* vals;
-  mm_status st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(),
-                                v1.as<int32_t>(), m, 0, 2 * cb, sws, s, &keys, &vals);
-  if (st != MM_OK) { sort_ws_free(sws); return st; }
-  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1)));
-  MM_TRY(tmp_alloc(hpos, sizeof(int32_t) * (size_t)(m + 1)));
+  MM_TRY(radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(),
+                        v1.as<int32_t>(), m, 0, 2 * cb, sws.ws, s, &keys, &vals));
+  MM_TRY(tmp_alloc(head, sizeof(int32_t) * (size_t)std::max(m, 1), s));
+  MM_TRY(tmp_alloc(hpos, sizeof(int32_t) * (size_t)(m + 1), s));
   run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
   MM_TRY(scan_exclusive_i32(head.as<int32_t>(), hpos.as<int32_t>(), m, ws.p, s));
   int32_t cnnz = 0;
@@ -574,7 +747,7 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   MM_CK(cudaMalloc(&out.col, sizeof(int32_t) * (size_t)std::max(cnnz, 1)));
   MM_CK(cudaMalloc(&out.omega, sizeof(float) * (size_t)std::max(cnnz, 1)));
   MM_CK(cudaMalloc(&out.rp, sizeof(int32_t) * (size_t)(nc + 1)));
-  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(nc + 1)));
+  MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(nc + 1), s));
   MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), s));
   coarse_reduce<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(
       m, cb, keys, vals, omega, head.as<int32_t>(), hpos.as<int32_t>(), out.col, out.omega,
@@ -582,7 +755,6 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   MM_TRY(scan_exclusive_i32(rowcnt.as<int32_t>(), out.rp, nc, ws.p, s));
   MM_CK(cudaGetLastError());
   MM_CK(cudaStreamSynchronize(s));
-  sort_ws_free(sws);
   return MM_OK;
 }
 
@@ -590,17 +762,21 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
   const double avg = L.n > 0 ? (double)L.nnzS / L.n : 0.0;
   int lanes = p.gather_lanes;
   if (lanes <= 0) {
+    // enough lanes to fill the GPU (152 SMs x 2048 threads) when n is small,
+    // never more than the mean row length
     lanes = 1;
-    while (lanes < 32 && lanes * 3 < avg) lanes <<= 1;
+    const int64_t want = (int64_t)kSMs * 2048 / std::max(L.n, 1);
+    while (lanes < 32 && 2 * lanes <= want && lanes < avg) lanes <<= 1;
   }
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) {
     set_error("gather_lanes must be a power of two <= 32 (got %d)", lanes);
     return MM_ERR_INVALID_ARG;
   }
   L.lanes = lanes;
+  L.walk_warps = p.traverse_warps > 0 ? p.traverse_warps : (L.n >= 20000 ? 16 : 8);
   L.heavy_degree = p.heavy_degree > 0 ? p.heavy_degree : std::max(512, 32 * lanes);
   Tmp cnt;
-  MM_TRY(tmp_alloc(cnt, 2 * sizeof(int32_t)));
+  MM_TRY(tmp_alloc(cnt, 2 * sizeof(int32_t), s));
   MM_CK(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
   MM_CK(cudaMalloc(&L.heavy, sizeof(int32_t) * (size_t)std::max(L.n, 1)));
   if (L.n > 0)

@@ -345,7 +345,7 @@ __device__ void walk(const SmallSmem& s, int n, float2* F, int* err) {
   }
 }
 
-__global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) {
+__device__ __forceinline__ void run_level(const SmallArgs& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& s = *reinterpret_cast<SmallSmem*>(smem_raw);
   __shared__ double red[96];
@@ -457,6 +457,14 @@ __global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) { run_level(a); }
+
+// Batched form: CTA b runs the level described by args[b] (one graph each).
+__global__ void __launch_bounds__(kT, 1) small_level_batch_kernel(const SmallArgs* args) {
+  const SmallArgs a = args[blockIdx.x];
+  run_level(a);
+}
+
 }  // namespace
 
 static_assert(sizeof(SmallSmem) + 1024 <= 227 * 1024, "fused level kernel exceeds shared memory");
@@ -466,6 +474,15 @@ size_t small_level_smem() { return sizeof(SmallSmem); }
 mm_status small_level_setup() {
   MM_CK(cudaFuncSetAttribute(small_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmallSmem)));
+  MM_CK(cudaFuncSetAttribute(small_level_batch_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmallSmem)));
+  return MM_OK;
+}
+
+mm_status small_level_batch(const SmallArgs* dev_args, int count, cudaStream_t s) {
+  if (count <= 0) return MM_OK;
+  small_level_batch_kernel<<<count, kT, sizeof(SmallSmem), s>>>(dev_args);
+  MM_CK(cudaGetLastError());
   return MM_OK;
 }
 

@@ -15,7 +15,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mm_internal.cuh"
@@ -40,6 +44,14 @@ struct mm_hierarchy {
   cudaGraphExec_t gexec = nullptr;
   mm_params gparams;
   int gsingle = -1;
+  // batch of independent graphs (mm_graph.num_graphs > 1): one hierarchy per
+  // graph, built by the single-graph path with seed + graph index; the
+  // fields above then describe none of them
+  std::vector<mm_hierarchy*> subs;
+  std::vector<int32_t> gptr;           // vertex offsets of the graphs
+  mm::SmallArgs* batch_args = nullptr; // device, fused levels of every round
+  float2* xcat = nullptr;              // concatenated result
+  int64_t batch_launches = 0;          // kernels per batched layout (fixed part)
 };
 
 namespace mm {
@@ -240,7 +252,8 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
     MM_TRY(exact_repulsion(x, L.n, h->F, s));
   } else {
     MM_TRY(bh_build(x, L.n, h->p.theta, h->tree, s));
-    MM_TRY(bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, nullptr, s));
+    MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
+                       nullptr, s));
   }
   MM_TRY(gather_update(L, x, h->F, st, h->partials, s));
   MM_TRY(controller(gather_blocks(L), h->partials, st, sp, trace, trace_cap, lsw, hnd, use_h, s));
@@ -352,6 +365,10 @@ mm_status level_check(const mm_hierarchy* h, int level) {
     set_error("hierarchy is NULL");
     return MM_ERR_INVALID_ARG;
   }
+  if (!h->subs.empty()) {
+    set_error("per-level calls take a single-graph hierarchy, not a batch");
+    return MM_ERR_UNSUPPORTED;
+  }
   if (level < 0 || level >= (int)h->levels.size()) {
     set_error("level %d out of range [0, %zu)", level, h->levels.size());
     return MM_ERR_INVALID_ARG;
@@ -371,8 +388,10 @@ struct DeviceGuard {
 };
 
 mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s);
+mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out);
 
 mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
+  if (g && g->num_graphs > 1) return build_batch(g, p, s, out);
   MM_TRY(check_params(p));
   if (!g || !out || g->n < 1 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && !g->col)) {
     set_error("invalid graph descriptor");
@@ -415,8 +434,8 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
   int stalls = 0;
   int* dmax = nullptr;
   int32_t* labels = nullptr;
-  MM_CK(cudaMalloc(&dmax, sizeof(int)));
-  MM_CK(cudaMalloc(&labels, sizeof(int32_t) * (size_t)n0));
+  MM_CK(cudaMallocAsync(&dmax, sizeof(int), s));
+  MM_CK(cudaMallocAsync(&labels, sizeof(int32_t) * (size_t)n0, s));
   mm_status st = MM_OK;
   while (st == MM_OK && h->levels.back().n > p->coarsest_n &&
          (int)h->levels.size() < p->max_levels && stalls < p->max_stalls) {
@@ -461,8 +480,8 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
     cur.map = map;
     h->levels.push_back(nxt);
   }
-  cudaFree(dmax);
-  cudaFree(labels);
+  cudaFreeAsync(dmax, s);
+  cudaFreeAsync(labels, s);
   MM_TRY(st);
 
   return finish_levels(h, p, s);
@@ -575,9 +594,8 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMalloc(&h->xb[0], sizeof(float2) * (size_t)n0));
   MM_CK(cudaMalloc(&h->xb[1], sizeof(float2) * (size_t)n0));
   MM_CK(cudaMalloc(&h->F, sizeof(float2) * (size_t)n0));
-  int maxb = 1;
-  for (const Level& L : h->levels) maxb = std::max(maxb, gather_blocks(L));
-  MM_CK(cudaMalloc(&h->partials, sizeof(double) * 3 * (size_t)maxb));
+  // partials for the largest grid any lanes setting (autotuner) can launch
+  MM_CK(cudaMalloc(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks));
   MM_CK(cudaMalloc(&h->state, sizeof(SweepState)));
   MM_CK(cudaMalloc(&h->sstate, sizeof(SweepState)));
   MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
@@ -587,6 +605,134 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMalloc(&h->lsw, sizeof(int32_t) * MM_MAX_LEVELS));
   MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
   MM_CK(cudaStreamSynchronize(s));
+  return MM_OK;
+}
+
+__global__ void slice_csr(int n, int64_t e0, int a, const int64_t* __restrict__ rp,
+                          const int32_t* __restrict__ col, int64_t m, int64_t* srp,
+                          int32_t* scol) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) srp[i] = rp[a + i] - e0;
+  if (i < m) scol[i] = col[e0 + i] - a;
+}
+
+// One hierarchy per graph of a block-diagonal batch.  Graph i is built
+// exactly as mm_build_hierarchy would build it alone, with seed + i, so its
+// batched layout equals its own unbatched layout.
+mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
+  MM_TRY(check_params(p));
+  if (!g->graph_ptr || g->n < 1 || !g->row_ptr) {
+    set_error("a batch needs graph_ptr (host) and a CSR");
+    return MM_ERR_INVALID_ARG;
+  }
+  const int G = g->num_graphs;
+  std::vector<int32_t> gp(g->graph_ptr, g->graph_ptr + G + 1);
+  if (gp[0] != 0 || gp[G] != g->n) {
+    set_error("graph_ptr must start at 0 and end at n");
+    return MM_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < G; ++i)
+    if (gp[i + 1] <= gp[i]) {
+      set_error("graph %d of the batch is empty or graph_ptr is not increasing", i);
+      return MM_ERR_INVALID_ARG;
+    }
+  mm_hierarchy* h = new mm_hierarchy();
+  *out = h;
+  h->p = *p;
+  h->gptr = gp;
+  MM_CK(cudaGetDevice(&h->device));
+  MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+  std::vector<int64_t> rp(g->n + 1);
+  MM_CK(cudaMemcpyAsync(rp.data(), g->row_ptr, sizeof(int64_t) * (g->n + 1),
+                        cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (rp[g->n] != g->nnz) {
+    set_error("row_ptr[n] != nnz");
+    return MM_ERR_INVALID_ARG;
+  }
+  // the graphs are built by a pool of host threads, each on its own
+  // non-blocking stream; temporaries are stream-ordered, so the builds overlap
+  h->subs.assign(G, nullptr);
+  std::atomic<int> next(0);
+  std::atomic<int> failed(-1);
+  std::string fail_msg;
+  mm_status fail_st = MM_OK;
+  std::mutex fail_mu;
+  auto worker = [&]() {
+    cudaSetDevice(h->device);
+    cudaStream_t ts = nullptr;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+      std::lock_guard<std::mutex> lock(fail_mu);
+      if (fail_st == MM_OK) { fail_st = MM_ERR_CUDA; fail_msg = "stream creation failed"; }
+      return;
+    }
+    while (true) {
+      const int i = next.fetch_add(1);
+      if (i >= G || failed.load() >= 0) break;
+      const int a = gp[i], ni = gp[i + 1] - gp[i];
+      const int64_t e0 = rp[a], m = rp[gp[i + 1]] - e0;
+      int64_t* srp = nullptr;
+      int32_t* scol = nullptr;
+      float* slen = nullptr;
+      mm_status st = MM_OK;
+      if (cudaMallocAsync(&srp, sizeof(int64_t) * (size_t)(ni + 1), ts) != cudaSuccess ||
+          cudaMallocAsync(&scol, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), ts) !=
+              cudaSuccess ||
+          (g->edge_len &&
+           cudaMallocAsync(&slen, sizeof(float) * (size_t)std::max<int64_t>(m, 1), ts) !=
+               cudaSuccess)) {
+        st = MM_ERR_OOM;
+        set_error("allocation of a graph slice failed");
+      }
+      if (st == MM_OK) {
+        slice_csr<<<ceil_div(std::max<int64_t>(ni + 1, m), 256), 256, 0, ts>>>(
+            ni, e0, a, g->row_ptr, g->col, m, srp, scol);
+        if (slen && m)
+          cudaMemcpyAsync(slen, g->edge_len + e0, sizeof(float) * m, cudaMemcpyDeviceToDevice,
+                          ts);
+        mm_graph sg;
+        memset(&sg, 0, sizeof(sg));
+        sg.n = ni;
+        sg.nnz = m;
+        sg.row_ptr = srp;
+        sg.col = scol;
+        sg.edge_len = slen;
+        sg.num_graphs = 1;
+        mm_params pi = *p;
+        pi.seed = p->seed + (uint64_t)i;
+        mm_hierarchy* sub = nullptr;
+        st = build(&sg, &pi, ts, &sub);
+        h->subs[i] = sub;
+      }
+      if (srp) cudaFreeAsync(srp, ts);
+      if (scol) cudaFreeAsync(scol, ts);
+      if (slen) cudaFreeAsync(slen, ts);
+      cudaStreamSynchronize(ts);
+      if (st != MM_OK) {
+        std::lock_guard<std::mutex> lock(fail_mu);
+        if (fail_st == MM_OK) {
+          fail_st = st;
+          fail_msg = "graph " + std::to_string(i) + " of the batch: " + g_err;
+          failed.store(i);
+        }
+      }
+    }
+    cudaStreamDestroy(ts);
+  };
+  const int T = std::max(1, std::min(G, 16));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < T; ++t) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  // drop empty slots (a failed build) so the hierarchy frees cleanly
+  std::vector<mm_hierarchy*> built;
+  for (mm_hierarchy* sub : h->subs)
+    if (sub) built.push_back(sub);
+  if (fail_st != MM_OK) {
+    h->subs = built;
+    set_error("%s", fail_msg.c_str());
+    return fail_st;
+  }
+  MM_CK(cudaMalloc(&h->xcat, sizeof(float2) * (size_t)g->n));
   return MM_OK;
 }
 
@@ -614,6 +760,228 @@ bool same_schedule(const mm_params& a, const mm_params& b) {
          a.seed == b.seed;
 }
 
+// Adds a child graph captured from `launches` after `deps`.
+template <typename Fn>
+mm_status graph_child(cudaGraph_t g, cudaStream_t cs, const std::vector<cudaGraphNode_t>& deps,
+                      Fn&& launches, cudaGraphNode_t* out) {
+  cudaGraph_t sub = nullptr;
+  MM_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  mm_status r = launches(cs);
+  cudaError_t e = cudaStreamEndCapture(cs, &sub);
+  if (r != MM_OK) {
+    if (sub) cudaGraphDestroy(sub);
+    return r;
+  }
+  MM_CK(e);
+  e = cudaGraphAddChildGraphNode(out, g, deps.empty() ? nullptr : deps.data(), deps.size(), sub);
+  cudaGraphDestroy(sub);
+  MM_CK(e);
+  return MM_OK;
+}
+
+// Adds a WHILE node after `deps` whose body is one sweep of `level` of h.
+mm_status graph_loop(cudaGraph_t g, cudaStream_t cs, const std::vector<cudaGraphNode_t>& deps,
+                     mm_hierarchy* h, int level, bool exact, SchedParams sp,
+                     cudaGraphNode_t* out) {
+  cudaGraphConditionalHandle hnd;
+  MM_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  MM_CK(cudaGraphAddNode(out, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  MM_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+  XSel x{h->xb[0], h->xb[1], &h->state->parity};
+  mm_status r = sweep_body(h, level, exact, x, h->state, sp, h->trace, h->trace_cap,
+                           h->lsw + level, hnd, true, cs);
+  cudaGraph_t o = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &o);
+  MM_TRY(r);
+  MM_CK(e);
+  return MM_OK;
+}
+
+// The batched uncoarsening: rounds aligned at each graph's coarsest level.
+// Round r runs level L_g - 1 - r of every graph g that has it: the
+// initial layout or prolongation kernels of all graphs, then one launch of
+// the fused level kernel with a CTA per small graph-level (each CTA runs
+// that level's whole schedule), and a WHILE loop per larger level, all
+// larger levels of a round in parallel graph branches.
+mm_status build_graph_batch(mm_hierarchy* h, const mm_params& p) {
+  cudaStream_t cs = h->cs;
+  const int G = (int)h->subs.size();
+  int rounds = 0;
+  for (mm_hierarchy* sub : h->subs) rounds = std::max(rounds, (int)sub->levels.size());
+  const SchedParams sp = sched_of(p, h->subs.empty() ? 1 : h->subs[0]->level_cap);
+  std::vector<SmallArgs> args;
+  std::vector<int> off(rounds + 1, 0);
+  for (int r = 0; r < rounds; ++r) {
+    off[r] = (int)args.size();
+    for (int i = 0; i < G; ++i) {
+      mm_hierarchy* sub = h->subs[i];
+      const int lev = (int)sub->levels.size() - 1 - r;
+      if (lev < 0 || sub->levels[0].n < 2 || !sub->levels[lev].fused) continue;
+      args.push_back(small_args(sub, lev, level_exact(sub, lev, false), sub->state, sp, nullptr,
+                                0, sub->lsw + lev, 1 << 30));
+    }
+  }
+  off[rounds] = (int)args.size();
+  if (h->batch_args) cudaFree(h->batch_args);
+  h->batch_args = nullptr;
+  MM_CK(cudaMalloc(&h->batch_args, sizeof(SmallArgs) * std::max<size_t>(args.size(), 1)));
+  if (!args.empty())
+    MM_CK(cudaMemcpy(h->batch_args, args.data(), sizeof(SmallArgs) * args.size(),
+                     cudaMemcpyHostToDevice));
+  cudaGraph_t g = nullptr;
+  MM_CK(cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphNode_t> join;
+  mm_status st = MM_OK;
+  int64_t launches = 0;
+  for (int r = 0; r < rounds && st == MM_OK; ++r) {
+    cudaGraphNode_t pre;
+    st = graph_child(g, cs, join, [&](cudaStream_t s) -> mm_status {
+      for (int i = 0; i < G; ++i) {
+        mm_hierarchy* sub = h->subs[i];
+        const int L = (int)sub->levels.size();
+        const int lev = L - 1 - r;
+        if (lev < 0 || sub->levels[0].n < 2) continue;
+        const uint64_t seed = p.seed + (uint64_t)i;
+        if (lev == L - 1) {
+          const Level& C = sub->levels[lev];
+          set_state<<<1, 1, 0, s>>>(sub->state, p.alpha0);
+          MM_TRY(init_coarsest(C.n, C.c, C.s, seed, lev, (float)std::sqrt(C.sum_c), sub->xb[0],
+                               sub->state, p.alpha0, s));
+        } else {
+          XSel x{sub->xb[0], sub->xb[1], &sub->state->parity};
+          MM_TRY(prolong(sub->levels[lev].n, sub->levels[lev].map, x, sub->levels[lev + 1].c,
+                         seed, lev, nullptr, s));
+          MM_TRY(level_start(sub->state, p.alpha_min, 1, s));
+        }
+        launches += 2;
+      }
+      return MM_OK;
+    }, &pre);
+    if (st != MM_OK) break;
+    join.clear();
+    if (off[r + 1] > off[r]) {
+      cudaGraphNode_t fused;
+      st = graph_child(g, cs, {pre}, [&](cudaStream_t s) -> mm_status {
+        return small_level_batch(h->batch_args + off[r], off[r + 1] - off[r], s);
+      }, &fused);
+      join.push_back(fused);
+      launches += 1;
+    }
+    for (int i = 0; i < G && st == MM_OK; ++i) {
+      mm_hierarchy* sub = h->subs[i];
+      const int lev = (int)sub->levels.size() - 1 - r;
+      if (lev < 0 || sub->levels[0].n < 2 || sub->levels[lev].fused) continue;
+      cudaGraphNode_t loop;
+      st = graph_loop(g, cs, {pre}, sub, lev, level_exact(sub, lev, false), sp, &loop);
+      join.push_back(loop);
+    }
+    if (join.empty()) join.push_back(pre);
+  }
+  if (st == MM_OK) {
+    cudaGraphNode_t fin;
+    st = graph_child(g, cs, join, [&](cudaStream_t s) -> mm_status {
+      for (int i = 0; i < G; ++i) {
+        mm_hierarchy* sub = h->subs[i];
+        const int n = sub->levels[0].n;
+        if (n < 2) {
+          MM_CK(cudaMemsetAsync(h->xcat + h->gptr[i], 0, sizeof(float2) * n, s));
+          continue;
+        }
+        XSel x{sub->xb[0], sub->xb[1], &sub->state->parity};
+        MM_TRY(copy_current(x, n, h->xcat + h->gptr[i], s));
+        launches += 1;
+      }
+      return MM_OK;
+    }, &fin);
+  }
+  if (st != MM_OK) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  MM_CK(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = ex;
+  h->gparams = p;
+  h->gsingle = 0;
+  h->batch_launches = launches;
+  return MM_OK;
+}
+
+mm_status layout_batch(mm_hierarchy* h, const mm_params& p, const float* x_init, float* x_out,
+                       mm_layout_stats* stats, cudaStream_t s) {
+  if (x_init) {
+    set_error("a batched hierarchy lays out from scratch only (x_init must be NULL)");
+    return MM_ERR_UNSUPPORTED;
+  }
+  for (mm_hierarchy* sub : h->subs) MM_TRY(ensure_trace(sub, p));
+  if (!h->gexec || !same_schedule(h->gparams, p)) MM_TRY(build_graph_batch(h, p));
+  for (mm_hierarchy* sub : h->subs)
+    MM_CK(cudaMemsetAsync(sub->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaGraphLaunch(h->gexec, s));
+  const int64_t n = h->gptr.back();
+  MM_CK(cudaMemcpyAsync(x_out, h->xcat, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+  const int G = (int)h->subs.size();
+  std::vector<SweepState> hs(G);
+  std::vector<int32_t> lsw((size_t)G * MM_MAX_LEVELS);
+  for (int i = 0; i < G; ++i) {
+    MM_CK(cudaMemcpyAsync(&hs[i], h->subs[i]->state, sizeof(SweepState), cudaMemcpyDeviceToHost,
+                          s));
+    MM_CK(cudaMemcpyAsync(&lsw[(size_t)i * MM_MAX_LEVELS], h->subs[i]->lsw,
+                          sizeof(int32_t) * MM_MAX_LEVELS, cudaMemcpyDeviceToHost, s));
+  }
+  MM_CK(cudaStreamSynchronize(s));
+  int64_t vu = 0, kl = h->batch_launches;
+  int tot = 0, err = 0, maxl = 0;
+  for (int i = 0; i < G; ++i) {
+    mm_hierarchy* sub = h->subs[i];
+    const int nl = (int)sub->levels.size();
+    maxl = std::max(maxl, nl);
+    for (int l = 0; l < nl; ++l) {
+      const int32_t sw = lsw[(size_t)i * MM_MAX_LEVELS + l];
+      vu += (int64_t)sw * sub->levels[l].n;
+      tot += sw;
+      if (!sub->levels[l].fused) kl += (int64_t)sw * kernels_per_sweep(sub, l, level_exact(sub, l, false));
+    }
+    if (hs[i].error) err = 1;
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->num_levels = maxl;
+    stats->total_sweeps = tot;
+    stats->vertex_updates = vu;
+    stats->kernel_launches = kl + 1;
+    // per round: vertices and sweeps summed over the graphs
+    for (int i = 0; i < G; ++i) {
+      mm_hierarchy* sub = h->subs[i];
+      const int nl = (int)sub->levels.size();
+      for (int l = 0; l < nl; ++l) {
+        const int r = nl - 1 - l;
+        const int slot = maxl - 1 - r;
+        stats->level_n[slot] += sub->levels[l].n;
+        stats->level_sweeps[slot] += lsw[(size_t)i * MM_MAX_LEVELS + l];
+      }
+    }
+  }
+  if (err) {
+    set_error("a sweep produced non-finite coordinates");
+    return MM_ERR_NONFINITE;
+  }
+  for (mm_hierarchy* sub : h->subs) MM_TRY(tree_error(sub, s));
+  return MM_OK;
+}
+
 mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, float* x_out,
                  mm_layout_stats* stats, cudaStream_t s) {
   mm_params p = h->p;
@@ -628,6 +996,7 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     set_error("x_out is NULL");
     return MM_ERR_INVALID_ARG;
   }
+  if (!h->subs.empty()) return layout_batch(h, p, x_init, x_out, stats, s);
   const int n0 = h->levels[0].n;
   const bool single = x_init != nullptr;
   if (stats) memset(stats, 0, sizeof(*stats));
@@ -680,6 +1049,200 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     return MM_ERR_NONFINITE;
   }
   return tree_error(h, s);
+}
+
+// ---------------------------------------------------------------- autotune
+struct TuneKey {
+  int device, n, lanes_hint;
+  int64_t nnzS;
+  bool operator<(const TuneKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (n != o.n) return n < o.n;
+    if (nnzS != o.nnzS) return nnzS < o.nnzS;
+    return lanes_hint < o.lanes_hint;
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mu;
+
+// Mean milliseconds of `reps` launches of fn (after one warm-up).
+template <typename Fn>
+mm_status time_ms(cudaStream_t s, int reps, Fn&& fn, double* ms) {
+  cudaEvent_t a, b;
+  MM_CK(cudaEventCreate(&a));
+  MM_CK(cudaEventCreate(&b));
+  mm_status st = fn();
+  cudaEventRecord(a, s);
+  for (int r = 0; r < reps && st == MM_OK; ++r) st = fn();
+  cudaEventRecord(b, s);
+  cudaError_t e = cudaEventSynchronize(b);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  MM_TRY(st);
+  MM_CK(e);
+  *ms = t / reps;
+  return MM_OK;
+}
+
+__global__ void fill_uniform(int n, float side, uint32_t k0, float2* x) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint32_t z[4];
+  philox4x32_10((uint32_t)v, 0u, 7u, 0u, k0, 0u, z);
+  x[v] = make_float2(side * (float)(z[0] >> 8) * (1.f / 16777216.f),
+                     side * (float)(z[1] >> 8) * (1.f / 16777216.f));
+}
+
+// Lanes per row and walk block shape of every multi-kernel level of h.
+mm_status tune_levels(mm_hierarchy* h, cudaStream_t s) {
+  for (size_t lv = 0; lv < h->levels.size(); ++lv) {
+    Level& L = h->levels[lv];
+    if (L.fused || L.n < 2) continue;
+    const TuneKey key{h->device, L.n, 0, L.nnzS};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        L.lanes = it->second.first;
+        L.walk_warps = it->second.second;
+        continue;
+      }
+    }
+    // random positions on the level's scale, F from one real walk
+    fill_uniform<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, sqrtf((float)L.n), 12345u, h->xb[0]);
+    XSel x{h->xb[0], h->xb[1], h->zero};
+    set_state<<<1, 1, 0, s>>>(h->sstate, 0.008);
+    MM_TRY(bh_build(x, L.n, h->p.theta, h->tree, s));
+    double best = 1e30;
+    int best_lanes = L.lanes;
+    const int keep = L.lanes;
+    for (int lanes = 1; lanes <= 32; lanes <<= 1) {
+      L.lanes = lanes;
+      double ms = 0;
+      MM_TRY(time_ms(s, 5, [&]() { return gather_update(L, x, h->F, h->sstate, h->partials, s); },
+                     &ms));
+      if (ms < best) { best = ms; best_lanes = lanes; }
+    }
+    L.lanes = best_lanes;
+    (void)keep;
+    best = 1e30;
+    int best_w = 4;
+    for (int w = 2; w <= 16; w <<= 1) {
+      double ms = 0;
+      MM_TRY(time_ms(s, 5, [&]() { return bh_traverse(L.n, h->tree, h->F, w, nullptr, s); }, &ms));
+      if (ms < best) { best = ms; best_w = w; }
+    }
+    L.walk_warps = best_w;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {L.lanes, L.walk_warps};
+  }
+  MM_TRY(tree_error(h, s));
+  return MM_OK;
+}
+
+// Objective of the finest level (summed over a batch) of layout x.
+mm_status layout_objective(mm_hierarchy* h, const float2* x, double* M, cudaStream_t s) {
+  double out[3];
+  if (h->subs.empty()) {
+    MM_TRY(objective_exact(h->levels[0], x, 0.008, out, s));
+    *M = out[2];
+    return MM_OK;
+  }
+  double tot = 0;
+  for (size_t i = 0; i < h->subs.size(); ++i) {
+    MM_TRY(objective_exact(h->subs[i]->levels[0], x + h->gptr[i], 0.008, out, s));
+    tot += out[2];
+  }
+  *M = tot;
+  return MM_OK;
+}
+
+void set_theta(mm_hierarchy* h, float theta) {
+  h->p.theta = theta;
+  for (mm_hierarchy* sub : h->subs) sub->p.theta = theta;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  for (mm_hierarchy* sub : h->subs)
+    if (sub->gexec) {
+      cudaGraphExecDestroy(sub->gexec);
+      sub->gexec = nullptr;
+    }
+}
+
+mm_status autotune(mm_hierarchy* h, const float* thetas, int n_theta, double drift,
+                   mm_tune_result* out, cudaStream_t s) {
+  static const float kDefault[] = {0.4f, 0.5f, 0.6f, 0.7f, 0.8f};
+  if (!thetas) {
+    thetas = kDefault;
+    n_theta = 5;
+  }
+  if (n_theta < 1 || !(drift >= 0)) {
+    set_error("need at least one theta and a non-negative drift bound");
+    return MM_ERR_INVALID_ARG;
+  }
+  const int64_t n = h->subs.empty() ? h->levels[0].n : h->gptr.back();
+  float2* x = nullptr;
+  MM_CK(cudaMalloc(&x, sizeof(float2) * (size_t)std::max<int64_t>(n, 1)));
+  auto run = [&](double* ms, double* M) -> mm_status {
+    MM_TRY(layout(h, nullptr, nullptr, (float*)x, nullptr, s));  // builds the graph
+    MM_TRY(time_ms(s, 1, [&]() { return layout(h, nullptr, nullptr, (float*)x, nullptr, s); }, ms));
+    return layout_objective(h, x, M, s);
+  };
+  mm_status st = MM_OK;
+  double ms0 = 0, M0 = 0;
+  const float theta0 = h->p.theta;
+  st = run(&ms0, &M0);
+  // 1. per-level kernel shapes
+  if (st == MM_OK) {
+    if (h->subs.empty()) {
+      st = tune_levels(h, s);
+    } else {
+      for (mm_hierarchy* sub : h->subs)
+        if (st == MM_OK) st = tune_levels(sub, s);
+    }
+    set_theta(h, theta0);  // rebuild the graphs with the new shapes
+  }
+  // 2. theta: fastest candidate within the objective drift bound
+  double best_ms = 1e30, best_M = M0;
+  float best_theta = theta0;
+  for (int i = 0; i < n_theta && st == MM_OK; ++i) {
+    set_theta(h, thetas[i]);
+    double ms = 0, M = 0;
+    st = run(&ms, &M);
+    if (st != MM_OK) break;
+    const bool ok = std::fabs(M - M0) <= drift * std::fabs(M0);
+    if (ok && ms < best_ms) {
+      best_ms = ms;
+      best_theta = thetas[i];
+      best_M = M;
+    }
+  }
+  if (st == MM_OK) {
+    set_theta(h, best_theta);
+    double ms1 = 0, M1 = 0;
+    st = run(&ms1, &M1);
+    if (st == MM_OK && out) {
+      memset(out, 0, sizeof(*out));
+      const Level* lv = h->subs.empty() ? h->levels.data() : h->subs[0]->levels.data();
+      const size_t nl = h->subs.empty() ? h->levels.size() : h->subs[0]->levels.size();
+      for (size_t i = 0; i < nl && i < MM_MAX_LEVELS; ++i) {
+        out->gather_lanes[i] = lv[i].fused ? 0 : lv[i].lanes;
+        out->traverse_warps[i] = lv[i].fused ? 0 : (lv[i].walk_warps ? lv[i].walk_warps : 4);
+      }
+      out->theta = best_theta;
+      out->objective_ref = M0;
+      out->objective = M1;
+      out->layout_ms_before = ms0;
+      out->layout_ms_after = ms1;
+    }
+    (void)best_M;
+  }
+  cudaFree(x);
+  return st;
 }
 
 }  // namespace
@@ -781,6 +1344,9 @@ void mm_free_hierarchy(mm_hierarchy* h) {
     if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cs) cudaStreamDestroy(h->cs);
+  for (mm_hierarchy* sub : h->subs) mm_free_hierarchy(sub);
+  if (h->batch_args) cudaFree(h->batch_args);
+  if (h->xcat) cudaFree(h->xcat);
   delete h;
 }
 
@@ -789,7 +1355,9 @@ mm_status mm_hierarchy_levels(const mm_hierarchy* h, int32_t* num_levels) {
     set_error("NULL argument");
     return MM_ERR_INVALID_ARG;
   }
-  *num_levels = (int32_t)h->levels.size();
+  int32_t nl = (int32_t)h->levels.size();
+  for (const mm_hierarchy* sub : h->subs) nl = std::max(nl, (int32_t)sub->levels.size());
+  *num_levels = nl;
   return MM_OK;
 }
 
@@ -1026,6 +1594,17 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     work[3] = L.n;
   }
   return tree_error(h, s);
+}
+
+mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta, double max_rel_drift,
+                      mm_tune_result* out, void* stream) {
+  g_err.clear();
+  if (!h) {
+    set_error("hierarchy is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  return autotune(h, thetas, n_theta, max_rel_drift, out, (cudaStream_t)stream);
 }
 
 mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x, double alpha,

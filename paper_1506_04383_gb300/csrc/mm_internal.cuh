@@ -134,6 +134,7 @@ struct Level {
   int32_t max_deg = 0;       // max |S_u|
   int32_t lanes = 1;         // lanes per vertex in the light gather
   int32_t heavy_degree = 0;
+  int32_t walk_warps = 0;    // warps per block in the tree walk (0 = default)
   bool fused = false;        // whole level in the single-CTA kernel
   double sum_c = 0;
 };
@@ -216,6 +217,10 @@ mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
 
 // ---------------------------------------------------------------- sweep --
 constexpr int kGatherThreads = 256;
+constexpr int kMaxLightBlocks = kSMs * 16;
+constexpr int kMaxHeavyBlocks = kSMs * 8;
+// Upper bound of gather_blocks() for any lanes setting (partials sizing).
+constexpr int kMaxGatherBlocks = kMaxLightBlocks + kMaxHeavyBlocks;
 int gather_blocks(const Level& L);
 // Fused Eq. 2 update over S plus per-block partial sums (3 doubles/block).
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
@@ -262,6 +267,8 @@ mm_status small_level_setup();
 // Runs sweeps of one level in one CTA until the schedule ends the level or
 // max_sweeps sweeps are done; reads buffer [st->parity], flips it per sweep.
 mm_status small_level(const SmallArgs& a, cudaStream_t s);
+// One CTA per entry of dev_args (device array of `count` levels).
+mm_status small_level_batch(const SmallArgs* dev_args, int count, cudaStream_t s);
 
 // ------------------------------------------------------------ hierarchy --
 mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t* col,

@@ -28,7 +28,8 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_free_hierarchy", "mm_hierarchy_levels", "mm_level_info", "mm_level_export",
            "mm_sweep", "mm_repulsion", "mm_layout", "mm_sweep_profile", "mm_objective",
            "mm_khop", "mm_cluster",
-           "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc"]
+           "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc",
+           "mm_autotune"]
 
 
 class MMError(RuntimeError):
@@ -63,6 +64,14 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("omega", ctypes.c_void_p), ("node_c", ctypes.c_void_p),
                 ("map", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("gather_lanes", ctypes.c_int32 * MM_MAX_LEVELS),
+                ("traverse_warps", ctypes.c_int32 * MM_MAX_LEVELS),
+                ("theta", ctypes.c_float), ("objective_ref", ctypes.c_double),
+                ("objective", ctypes.c_double), ("layout_ms_before", ctypes.c_double),
+                ("layout_ms_after", ctypes.c_double)]
 
 
 class LayoutStats(ctypes.Structure):
@@ -119,6 +128,7 @@ def load(path: str = LIB_PATH):
     lib.mm_prolong.argtypes = [i32, P, P, P, u64, i32, P, P]
     lib.mm_layout_host.argtypes = [i32, P, P, P, P, P, P, P]
     lib.mm_repulsion_noalloc.argtypes = [i32, P, f32, P, P]
+    lib.mm_autotune.argtypes = [P, P, i32, f64, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -194,18 +204,26 @@ class Hierarchy:
         return n.value, e.value, s.value
 
 
-def build_hierarchy(row_ptr, col, params: Params = None, edge_len=None, stream=None):
-    """row_ptr int64 [n+1] and col int32 [nnz] CUDA tensors (symmetric CSR)."""
+def build_hierarchy(row_ptr, col, params: Params = None, edge_len=None, graph_ptr=None,
+                    stream=None):
+    """row_ptr int64 [n+1] and col int32 [nnz] CUDA tensors (symmetric CSR).
+
+    graph_ptr (host int32 [G+1] vertex offsets) lays out a block-diagonal
+    batch of G independent graphs; graph i uses seed + i."""
     _require_cuda()
     lib = load()
     row_ptr = _dev(row_ptr, torch.int64, "row_ptr")
     col = _dev(col, torch.int32, "col")
     edge_len = _dev(edge_len, torch.float32, "edge_len")
     p = params if params is not None else default_params()
+    gp = None
+    if graph_ptr is not None:
+        gp = np.ascontiguousarray(graph_ptr, dtype=np.int32)
     g = Graph(n=row_ptr.numel() - 1, nnz=col.numel(), row_ptr=row_ptr.data_ptr(),
               col=col.data_ptr() if col.numel() else None,
               edge_len=edge_len.data_ptr() if edge_len is not None else None,
-              num_graphs=1, graph_ptr=None)
+              num_graphs=1 if gp is None else len(gp) - 1,
+              graph_ptr=gp.ctypes.data if gp is not None else None)
     h = ctypes.c_void_p()
     _check(lib.mm_build_hierarchy(ctypes.byref(g), ctypes.byref(p), _stream(stream),
                                   ctypes.byref(h)))
@@ -318,6 +336,22 @@ def sweep_profile(h: Hierarchy, level: int, x, reps: int = 10, stream=None):
                                    _stream(stream)))
     return dict(stage_names=list(STAGES), stage_ms=list(ms), visits=int(work[0]),
                 interactions=int(work[1]), nnz_S=int(work[2]), n=int(work[3]))
+
+
+def autotune(h: Hierarchy, thetas=None, max_rel_drift: float = 0.01, stream=None):
+    """Tunes lanes per S row and walk block shape per level, then theta under
+    an objective drift bound; returns the choices and before/after times."""
+    r = TuneResult()
+    th = None
+    if thetas is not None:
+        th = np.ascontiguousarray(thetas, dtype=np.float32)
+    _check(load().mm_autotune(h.handle, th.ctypes.data if th is not None else None,
+                              0 if th is None else len(th), float(max_rel_drift),
+                              ctypes.byref(r), _stream(stream)))
+    nl = h.levels()
+    return dict(gather_lanes=list(r.gather_lanes[:nl]), traverse_warps=list(r.traverse_warps[:nl]),
+                theta=r.theta, objective_ref=r.objective_ref, objective=r.objective,
+                layout_ms_before=r.layout_ms_before, layout_ms_after=r.layout_ms_after)
 
 
 def objective(h: Hierarchy, level: int, x, alpha: float, stream=None):

@@ -278,9 +278,11 @@ def test_contract_matches_oracle_on_oracle_labels(mm):
     assert np.array_equal(cw.cpu().numpy(), ow)
 
 
+# 20000 vertices: multi-kernel rounds; 3000: the single-CTA kernel
+@pytest.mark.parametrize("n_pts", [20000, 3000])
 @pytest.mark.parametrize("U", [2.0, 4.0, 9.0])
-def test_cluster_invariants(mm, U):
-    rp, col, _, _ = graphs.rgg(20000, 8.0, 34, tune=False)
+def test_cluster_invariants(mm, U, n_pts):
+    rp, col, _, _ = graphs.rgg(n_pts, 8.0, 34, tune=False)
     n = len(rp) - 1
     c = np.ones(n, dtype=np.float32)
     lab = mm.cluster(cu(rp), cu(col), cu(np.ones(len(col), np.float32)), cu(c), U, 10, 5,
