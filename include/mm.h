@@ -78,7 +78,9 @@ typedef struct mm_params {
   int32_t traverse_warps;   /* warps per block in the tree walk; 0 = auto     */
   int32_t fused_max_n;      /* levels with n <= this run in one single-CTA    */
                             /* kernel; 0 = auto (2048, the maximum), -1 = off */
-  int32_t reserved[6];
+  int32_t learned_prolong;  /* 1: prolongate with the network attached by     */
+                            /* mm_hierarchy_set_net (single-graph layouts)    */
+  int32_t reserved[5];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */
@@ -292,6 +294,77 @@ typedef struct mm_tune_result {
  */
 mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta,
                       double max_rel_drift, mm_tune_result* out, void* stream);
+
+/*
+ * The tensor-core GEMM of the learned prolongation's dense layers, exposed
+ * for testing (no paper counterpart): C = A * B^T on the tcgen05 tensor
+ * cores with BF16 inputs and FP32 accumulation, optional bias[N] and ReLU.
+ *   A device BF16 [M x K] row-major, B device BF16 [N x K] row-major,
+ *   K a multiple of 16 in [16, 128], N = 64 or 128, both 16-byte aligned;
+ *   out_f32 (device FP32 [M x N]) and/or out_bf16 (device BF16 [M x N]).
+ * Synchronises the stream (reports a tensor-core wait that gave up as
+ * MM_ERR_TIMEOUT).
+ */
+mm_status mm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A,
+                       const void* B, const float* bias, int32_t relu,
+                       float* out_f32, void* out_bf16, void* stream);
+
+/*
+ * Learned prolongation (no paper counterpart; an extension of the
+ * prolongation of Sec. 3.2).  A fine vertex v of the coarse vertex p is
+ * placed at x'_p + r_v + o_v: r_v is the paper's random polar offset (the
+ * same Philox draws as mm_prolong) and o_v = beta_0 a_v + beta_1 b_v +
+ * beta_2 r_v a drift predicted by a 3-layer message-passing network (hidden
+ * 64, mean aggregation over the fine graph, BF16 tensor-core layers with FP32
+ * accumulation) from 8 invariant features; a_v is the mean direction from
+ * x'_p to the coarse positions of v's neighbours in other clusters, b_v the
+ * mean direction from x'_p to p's coarse neighbours.  Trained on the
+ * device (Adam) to reproduce the drift that the plain layout's refinement
+ * applies: loss = mean_v |o_v - t_v|^2 / c(p), t_v = x*_v - x'_p - r_v with
+ * x* the converged positions of the level.
+ */
+typedef struct mm_prolong_net mm_prolong_net;
+#define MM_NET_PARAMS 17795 /* FP32 parameters: W0[16x64] b0 W1[128x64] b1
+                               W2[128x64] b2 Wo[64x3] bo, row-major */
+
+/* One prolongation step's inputs (device pointers). */
+typedef struct mm_prolong_sample {
+  int32_t n;                 /* fine vertices                                 */
+  const int64_t* row_ptr;    /* fine CSR [n+1]                                */
+  const int32_t* col;
+  const int32_t* map;        /* [n] fine -> coarse                            */
+  int32_t n_coarse;
+  const int64_t* crow_ptr;   /* coarse CSR [n_coarse+1]                       */
+  const int32_t* ccol;
+  const float* c_coarse;     /* [n_coarse] node weights c                     */
+  const float* x_coarse;     /* [2 n_coarse] coarse layout                    */
+  uint64_t seed;             /* Philox key of the polar offsets               */
+  int32_t level;             /* level index of the fine graph (Philox counter)*/
+  const float* x_target;     /* [2 n] converged fine layout, or NULL          */
+} mm_prolong_sample;
+
+/* Creates a network with the given parameters (host [MM_NET_PARAMS]). */
+mm_status mm_net_create(const float* params, mm_prolong_net** out);
+void mm_net_free(mm_prolong_net* net);
+/* Copies the parameters out (get, host) and/or in (set, host); NULL skips. */
+mm_status mm_net_params(mm_prolong_net* net, float* get, const float* set);
+/* Prolongation: x_fine (device [2n]); with a target, the loss (host). */
+mm_status mm_net_forward(mm_prolong_net* net, const mm_prolong_sample* smp,
+                         float* x_fine, double* loss, void* stream);
+/* Loss and its gradient with respect to every parameter (host outputs). */
+mm_status mm_net_gradients(mm_prolong_net* net, const mm_prolong_sample* smp,
+                           float* grads, double* loss, void* stream);
+/* One Adam step (learning rate lr) on one sample; loss before the step. */
+mm_status mm_net_train_step(mm_prolong_net* net, const mm_prolong_sample* smp,
+                            float lr, double* loss, void* stream);
+/* Attaches (NULL detaches) a network used by mm_layout when
+ * params->learned_prolong = 1.  The network must outlive its use. */
+mm_status mm_hierarchy_set_net(mm_hierarchy* h, mm_prolong_net* net);
+/* mm_layout that also copies every level's final layout into level_x[l]
+ * (host array of num_levels device pointers, entries may be NULL): the
+ * coarse-to-converged pairs the network is trained on. */
+mm_status mm_layout_levels(mm_hierarchy* h, const mm_params* p,
+                           float* const* level_x, void* stream);
 
 /*
  * Maxent-stress objective, Eq. 1, general model over S of `level`:

@@ -25,9 +25,18 @@ so o is equivariant by construction.  Loss: mean over v of
 |o_v - t_v|^2 / c(p) with target t_v = x*_v - x'_p - r_v (x* = the level's
 converged layout).
 
+The method fixes BF16 operands with FP32 accumulation for the dense layers.
+With ``quant=bf16_round`` the forward and backward passes round to BF16 at
+exactly the points where those operands are formed -- the features, both
+halves of every [H | A H], every W_l, every ReLU output H_l, and, in the
+backward pass, dZ_l and W_l before dZ_l W_l^T -- and stay FP64 elsewhere.
+Without it (the default) everything is FP64.
+
 Pins (tests/test_oracle_mpnn.py): analytic gradients against central finite
 differences; equivariance of o under rotation and translation of the coarse
-layout; the mean aggregation and its transpose against a dense adjacency.
+layout; the mean aggregation and its transpose against a dense adjacency;
+bf16_round against an independent library conversion, including ties and
+the extremes of the range.
 """
 from __future__ import annotations
 
@@ -41,6 +50,20 @@ F_IN = 8
 HIDDEN = 64
 N_OUT = 3
 LAYERS = 3
+
+
+def bf16_round(x):
+    """Nearest BF16 value of every FP32-rounded element (ties to even), as an
+    FP64 array.  BF16 keeps the sign, the 8 exponent bits and the top 7
+    mantissa bits of an IEEE binary32 value: add half of the dropped 16-bit
+    field (minus one, plus the kept low bit, for ties to even) and clear it."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(x):
+    return x
 
 
 def layer_shapes():
@@ -119,15 +142,16 @@ def features(rp, col, mp, xc, crp, ccol, cc, r):
     return f, a, b, r
 
 
-def forward(P, rp, col, f, a, b, r):
+def forward(P, rp, col, f, a, b, r, quant=None):
     """Returns (o [n,2], cache for backward)."""
-    H = f
+    q = quant or _ident
+    H = q(f)
     cache = []
     for l in range(LAYERS):
-        Hc = np.concatenate([H, mean_agg(rp, col, H)], axis=1)
-        Z = Hc @ P[f"W{l}"] + P[f"b{l}"]
+        Hc = np.concatenate([H, q(mean_agg(rp, col, H))], axis=1)
+        Z = Hc @ q(P[f"W{l}"]) + P[f"b{l}"]
         cache.append((Hc, Z))
-        H = np.maximum(Z, 0.0)
+        H = q(np.maximum(Z, 0.0))
     beta = H @ P[f"W{LAYERS}"] + P[f"b{LAYERS}"]
     o = beta[:, 0:1] * a + beta[:, 1:2] * b + beta[:, 2:3] * r
     return o, dict(layers=cache, H=H, beta=beta)
@@ -139,8 +163,9 @@ def loss(o, t, cp):
     return float(((d * d).sum(1) / cp).mean())
 
 
-def backward(P, rp, col, cache, a, b, r, o, t, cp):
+def backward(P, rp, col, cache, a, b, r, o, t, cp, quant=None):
     """Analytic gradients of the loss with respect to every W_l and b_l."""
+    q = quant or _ident
     n = len(o)
     do = 2.0 * (o - t) / (n * cp)[:, None]
     dbeta = np.stack([(do * a).sum(1), (do * b).sum(1), (do * r).sum(1)], axis=1)
@@ -154,7 +179,7 @@ def backward(P, rp, col, cache, a, b, r, o, t, cp):
         dZ = dH * (Z > 0)
         G[f"W{l}"] = Hc.T @ dZ
         G[f"b{l}"] = dZ.sum(0)
-        dHc = dZ @ P[f"W{l}"].T
+        dHc = q(dZ) @ q(P[f"W{l}"]).T
         d = Hc.shape[1] // 2
         dH = dHc[:, :d] + mean_agg_T(rp, col, dHc[:, d:])
     return G

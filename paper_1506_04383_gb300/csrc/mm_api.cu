@@ -24,8 +24,15 @@
 
 #include "mm_internal.cuh"
 
+struct mm_prolong_net {
+  int device = 0;
+  mm::Net net;
+  int32_t* zero = nullptr;  // device int 0 (parity of caller-given positions)
+};
+
 struct mm_hierarchy {
   mm_params p;
+  mm_prolong_net* net = nullptr;  // learned prolongation (not owned)
   int device = 0;
   cudaStream_t cs = nullptr;  // capture stream (non-blocking)
   std::vector<mm::Level> levels;
@@ -260,7 +267,8 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   return MM_OK;
 }
 
-mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single) {
+mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
+                      float* const* level_out = nullptr) {
   cudaStream_t cs = h->cs;
   XSel x{h->xb[0], h->xb[1], &h->state->parity};
   const SchedParams sp = sched_of(p, h->level_cap);
@@ -336,16 +344,39 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single) {
                            h->state, p.alpha0, s);
     });
     if (st == MM_OK) st = add_loop(top, level_exact(h, top, false));
+    if (st == MM_OK && level_out && level_out[top])
+      st = add_child([&](cudaStream_t s) -> mm_status {
+        return copy_current(x, C.n, (float2*)level_out[top], s);
+      });
     for (int lv = top - 1; lv >= 0 && st == MM_OK; --lv) {
       const Level& L = h->levels[lv];
       const Level& Cn = h->levels[lv + 1];
       // one alpha schedule spans the run: the coarsest level ends at
       // alpha_min, so every finer level refines at alpha_min
       st = add_child([&](cudaStream_t s) -> mm_status {
-        MM_TRY(prolong(L.n, L.map, x, Cn.c, p.seed, lv, nullptr, s));
+        if (p.learned_prolong && h->net) {
+          NetSample smp;
+          smp.n = L.n;
+          smp.rp = L.rp;
+          smp.col = L.col;
+          smp.map = L.map;
+          smp.xc = x;
+          smp.crp = Cn.rp;
+          smp.ccol = Cn.col;
+          smp.cc = Cn.c;
+          smp.seed = p.seed;
+          smp.level = lv;
+          MM_TRY(net_forward(h->net->net, smp, nullptr, nullptr, s));
+        } else {
+          MM_TRY(prolong(L.n, L.map, x, Cn.c, p.seed, lv, nullptr, s));
+        }
         return level_start(h->state, p.alpha_min, 1, s);
       });
       if (st == MM_OK) st = add_loop(lv, level_exact(h, lv, false));
+      if (st == MM_OK && level_out && level_out[lv])
+        st = add_child([&](cudaStream_t s) -> mm_status {
+          return copy_current(x, L.n, (float2*)level_out[lv], s);
+        });
     }
   }
   if (st != MM_OK) return fail(st);
@@ -757,7 +788,7 @@ bool same_schedule(const mm_params& a, const mm_params& b) {
   return a.alpha0 == b.alpha0 && a.alpha_factor == b.alpha_factor && a.alpha_min == b.alpha_min &&
          a.eps == b.eps && a.eps_final == b.eps_final && a.iters_per_alpha == b.iters_per_alpha &&
          a.max_iters_at_min == b.max_iters_at_min && a.early_exit == b.early_exit &&
-         a.seed == b.seed;
+         a.seed == b.seed && a.learned_prolong == b.learned_prolong;
 }
 
 // Adds a child graph captured from `launches` after `deps`.
@@ -991,6 +1022,11 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     p.eps = pin->eps; p.eps_final = pin->eps_final; p.iters_per_alpha = pin->iters_per_alpha;
     p.max_iters_at_min = pin->max_iters_at_min; p.early_exit = pin->early_exit;
     p.seed = pin->seed;
+    p.learned_prolong = pin->learned_prolong;
+  }
+  if (p.learned_prolong && !h->net) {
+    set_error("learned_prolong = 1 but no network is attached (mm_hierarchy_set_net)");
+    return MM_ERR_INVALID_ARG;
   }
   if (!x_out) {
     set_error("x_out is NULL");
@@ -1594,6 +1630,249 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     work[3] = L.n;
   }
   return tree_error(h, s);
+}
+
+namespace mm {
+namespace {
+
+__global__ void rp_to_i32_k(int n, const int64_t* __restrict__ a, int32_t* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) b[i] = (int32_t)a[i];
+}
+
+// ABI sample -> internal sample (int32 row pointers in stream-ordered temps).
+struct SampleTmp {
+  int32_t* rp = nullptr;
+  int32_t* crp = nullptr;
+  cudaStream_t s = nullptr;
+  ~SampleTmp() {
+    if (rp) cudaFreeAsync(rp, s);
+    if (crp) cudaFreeAsync(crp, s);
+  }
+};
+
+mm_status make_sample(mm_prolong_net* net, const mm_prolong_sample* a, NetSample& smp,
+                      SampleTmp& tmp, cudaStream_t s) {
+  if (!net || !a || a->n < 1 || a->n_coarse < 1 || !a->row_ptr || !a->map || !a->crow_ptr ||
+      !a->c_coarse || !a->x_coarse) {
+    set_error("invalid prolongation sample");
+    return MM_ERR_INVALID_ARG;
+  }
+  tmp.s = s;
+  MM_CK(cudaMallocAsync(&tmp.rp, sizeof(int32_t) * (size_t)(a->n + 1), s));
+  MM_CK(cudaMallocAsync(&tmp.crp, sizeof(int32_t) * (size_t)(a->n_coarse + 1), s));
+  rp_to_i32_k<<<ceil_div(a->n + 1, 256), 256, 0, s>>>(a->n, a->row_ptr, tmp.rp);
+  rp_to_i32_k<<<ceil_div(a->n_coarse + 1, 256), 256, 0, s>>>(a->n_coarse, a->crow_ptr, tmp.crp);
+  MM_CK(cudaGetLastError());
+  smp.n = a->n;
+  smp.rp = tmp.rp;
+  smp.col = a->col;
+  smp.map = a->map;
+  smp.xc = XSel{(const float2*)a->x_coarse, (const float2*)a->x_coarse, net->zero};
+  smp.crp = tmp.crp;
+  smp.ccol = a->ccol;
+  smp.cc = a->c_coarse;
+  smp.seed = a->seed;
+  smp.level = a->level;
+  MM_TRY(net_alloc(net->net, a->n));
+  return MM_OK;
+}
+
+mm_status read_loss(Net& net, int n, double* loss, cudaStream_t s) {
+  const int parts = ceil_div(n, 256);
+  std::vector<double> h((size_t)parts);
+  MM_CK(cudaMemcpyAsync(h.data(), net.loss_part, sizeof(double) * parts, cudaMemcpyDeviceToHost,
+                        s));
+  int err = 0;
+  MM_CK(cudaMemcpyAsync(&err, net.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  if (err) {
+    cudaMemsetAsync(net.err, 0, sizeof(int), s);
+    set_error("tensor-core wait gave up");
+    return MM_ERR_TIMEOUT;
+  }
+  double t = 0;
+  for (double v : h) t += v;
+  if (loss) *loss = t;
+  return MM_OK;
+}
+
+}  // namespace
+}  // namespace mm
+
+
+
+mm_status mm_net_create(const float* params, mm_prolong_net** out) {
+  g_err.clear();
+  if (!params || !out) {
+    set_error("params and out are required");
+    return MM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mm_prolong_net* net = new mm_prolong_net();
+  cudaGetDevice(&net->device);
+  mm_status st = gemm_setup();
+  if (st == MM_OK) st = net_alloc(net->net, 1);
+  if (st == MM_OK && cudaMalloc(&net->zero, sizeof(int32_t)) != cudaSuccess)
+    st = cuda_status(cudaErrorMemoryAllocation, "cudaMalloc", __FILE__, __LINE__);
+  if (st == MM_OK) cudaMemset(net->zero, 0, sizeof(int32_t));
+  if (st == MM_OK) st = mm_net_params(net, nullptr, params);
+  if (st != MM_OK) {
+    mm_net_free(net);
+    return st;
+  }
+  *out = net;
+  return MM_OK;
+}
+
+void mm_net_free(mm_prolong_net* net) {
+  if (!net) return;
+  DeviceGuard dg(net->device);
+  cudaDeviceSynchronize();
+  net_free(net->net);
+  if (net->zero) cudaFree(net->zero);
+  delete net;
+}
+
+mm_status mm_net_params(mm_prolong_net* net, float* get, const float* set) {
+  if (!net) {
+    set_error("net is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(net->device);
+  if (get) MM_CK(cudaMemcpy(get, net->net.P, sizeof(float) * MM_NET_PARAMS, cudaMemcpyDeviceToHost));
+  if (set) {
+    MM_CK(cudaMemcpy(net->net.P, set, sizeof(float) * MM_NET_PARAMS, cudaMemcpyHostToDevice));
+    MM_CK(cudaMemset(net->net.M1, 0, sizeof(float) * MM_NET_PARAMS));
+    MM_CK(cudaMemset(net->net.M2, 0, sizeof(float) * MM_NET_PARAMS));
+    net->net.step = 0;
+    MM_TRY(net_sync_weights(net->net, 0));
+    MM_CK(cudaDeviceSynchronize());
+  }
+  return MM_OK;
+}
+
+mm_status mm_net_forward(mm_prolong_net* net, const mm_prolong_sample* smp, float* x_fine,
+                         double* loss, void* stream) {
+  g_err.clear();
+  if (!net) {
+    set_error("net is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(net->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  NetSample ns;
+  SampleTmp tmp;
+  MM_TRY(make_sample(net, smp, ns, tmp, s));
+  MM_TRY(net_forward(net->net, ns, (float2*)x_fine, (const float2*)smp->x_target, s));
+  return read_loss(net->net, ns.n, smp->x_target ? loss : nullptr, s);
+}
+
+mm_status mm_net_gradients(mm_prolong_net* net, const mm_prolong_sample* smp, float* grads,
+                           double* loss, void* stream) {
+  g_err.clear();
+  if (!net || !smp || !smp->x_target) {
+    set_error("gradients need a network and a sample with x_target");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(net->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  NetSample ns;
+  SampleTmp tmp;
+  MM_TRY(make_sample(net, smp, ns, tmp, s));
+  MM_TRY(net_forward(net->net, ns, nullptr, (const float2*)smp->x_target, s));
+  MM_TRY(net_backward(net->net, ns, s));
+  MM_TRY(read_loss(net->net, ns.n, loss, s));
+  if (grads)
+    MM_CK(cudaMemcpy(grads, net->net.G, sizeof(float) * MM_NET_PARAMS, cudaMemcpyDeviceToHost));
+  return MM_OK;
+}
+
+mm_status mm_net_train_step(mm_prolong_net* net, const mm_prolong_sample* smp, float lr,
+                            double* loss, void* stream) {
+  g_err.clear();
+  if (!net || !smp || !smp->x_target || !(lr > 0.f)) {
+    set_error("a training step needs a network, a sample with x_target and lr > 0");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(net->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  NetSample ns;
+  SampleTmp tmp;
+  MM_TRY(make_sample(net, smp, ns, tmp, s));
+  MM_TRY(net_forward(net->net, ns, nullptr, (const float2*)smp->x_target, s));
+  MM_TRY(net_backward(net->net, ns, s));
+  MM_TRY(net_adam_step(net->net, lr, s));
+  return read_loss(net->net, ns.n, loss, s);
+}
+
+mm_status mm_hierarchy_set_net(mm_hierarchy* h, mm_prolong_net* net) {
+  g_err.clear();
+  if (!h) {
+    set_error("hierarchy is NULL");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (!h->subs.empty()) {
+    set_error("the learned prolongation applies to single-graph hierarchies");
+    return MM_ERR_UNSUPPORTED;
+  }
+  DeviceGuard dg(h->device);
+  if (net) MM_TRY(net_alloc(net->net, h->levels[0].n));
+  h->net = net;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return MM_OK;
+}
+
+mm_status mm_layout_levels(mm_hierarchy* h, const mm_params* p, float* const* level_x,
+                           void* stream) {
+  g_err.clear();
+  if (!h || !level_x || !h->subs.empty()) {
+    set_error("need a single-graph hierarchy and level outputs");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mm_params q = p ? *p : h->p;
+  MM_TRY(check_params(&q));
+  MM_TRY(ensure_trace(h, q));
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  MM_TRY(build_graph(h, q, false, level_x));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaGraphLaunch(h->gexec, s));
+  MM_CK(cudaStreamSynchronize(s));
+  // the recording graph is not kept: the next mm_layout builds its own
+  cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  return tree_error(h, s);
+}
+
+mm_status mm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B,
+                       const float* bias, int32_t relu, float* out_f32, void* out_bf16,
+                       void* stream) {
+  g_err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  MM_TRY(gemm_setup());
+  int* err = nullptr;
+  MM_CK(cudaMallocAsync(&err, sizeof(int), s));
+  MM_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  mm_status st = gemm_bf16(A, M, K, B, N, bias, relu, out_bf16, out_f32, err, s);
+  int he = 0;
+  cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(err, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  MM_TRY(st);
+  MM_CK(e);
+  if (he) {
+    set_error("tensor-core wait gave up");
+    return MM_ERR_TIMEOUT;
+  }
+  return MM_OK;
 }
 
 mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta, double max_rel_drift,

@@ -284,6 +284,68 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
                    cudaStream_t s);
 mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s);
 
+// --------------------------------------------------------- tensor cores ---
+// C[M x N] = A[M x K] * B[N x K]^T on tcgen05 (BF16 in, FP32 accumulate);
+// optional bias and ReLU; BF16 and/or FP32 output (row-major [M x N]).
+// K in {16, ..., 128} (multiple of 16), N in {64, 128}.  err |= 4 if the
+// bounded wait for the tensor cores gave up.
+mm_status gemm_bf16(const void* A, int M, int K, const void* B, int N, const float* bias,
+                    int relu, void* outb, float* outf, int* err, cudaStream_t s);
+
+mm_status gemm_setup();
+
+// ------------------------------------------------- learned prolongation ---
+constexpr int kNetHidden = 64;
+constexpr int kNetFeatures = 8;
+constexpr int kNetParts = 512;   // vertex chunks of the weight-gradient sums
+
+struct Net {
+  float* P = nullptr;   // FP32 parameters (flat, see net_offsets)
+  float* G = nullptr;   // gradients
+  float* M1 = nullptr;  // Adam moments
+  float* M2 = nullptr;
+  void* Wt[3] = {nullptr, nullptr, nullptr};  // BF16 W_l^T [64 x rows]
+  void* Wb[3] = {nullptr, nullptr, nullptr};  // BF16 W_l [rows x 64]
+  int* err = nullptr;
+  int cap = 0;
+  int64_t step = 0;
+  void* f = nullptr;         // BF16 features [n x 8]
+  float2* basis = nullptr;   // (a, b, r) per vertex
+  void* Hc = nullptr;        // BF16 [n x 128] concatenation
+  void* H[3] = {nullptr, nullptr, nullptr};  // BF16 layer outputs [n x 64]
+  float* dbeta = nullptr;
+  float* dH = nullptr;
+  float* dZ = nullptr;
+  void* dZb = nullptr;
+  float* dHc = nullptr;
+  float* part = nullptr;
+  double* loss_part = nullptr;
+};
+
+// One prolongation sample: fine level (CSR, map to the coarse level) and the
+// coarse level (CSR, weights, positions through an XSel).
+struct NetSample {
+  int n = 0;
+  const int32_t* rp = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* map = nullptr;
+  XSel xc;
+  const int32_t* crp = nullptr;
+  const int32_t* ccol = nullptr;
+  const float* cc = nullptr;
+  uint64_t seed = 0;
+  int level = 0;
+};
+
+void net_offsets(int off[9]);
+mm_status net_alloc(Net& net, int max_n);
+void net_free(Net& net);
+mm_status net_sync_weights(Net& net, cudaStream_t s);
+mm_status net_forward(Net& net, const NetSample& smp, float2* xout, const float2* target,
+                      cudaStream_t s);
+mm_status net_backward(Net& net, const NetSample& smp, cudaStream_t s);
+mm_status net_adam_step(Net& net, float lr, cudaStream_t s);
+
 // ------------------------------------------------------------ objective --
 mm_status objective_exact(const Level& L, const float2* x, double alpha, double out[3],
                           cudaStream_t s);

@@ -29,7 +29,10 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_sweep", "mm_repulsion", "mm_layout", "mm_sweep_profile", "mm_objective",
            "mm_khop", "mm_cluster",
            "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc",
-           "mm_autotune"]
+           "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
+           "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
+           "mm_layout_levels"]
+MM_NET_PARAMS = 17795
 
 
 class MMError(RuntimeError):
@@ -50,7 +53,8 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("max_levels", ctypes.c_int32),
         ("max_stalls", ctypes.c_int32), ("gather_lanes", ctypes.c_int32),
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
-        ("fused_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -72,6 +76,15 @@ class TuneResult(ctypes.Structure):
                 ("theta", ctypes.c_float), ("objective_ref", ctypes.c_double),
                 ("objective", ctypes.c_double), ("layout_ms_before", ctypes.c_double),
                 ("layout_ms_after", ctypes.c_double)]
+
+
+class ProlongSample(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("map", ctypes.c_void_p), ("n_coarse", ctypes.c_int32),
+                ("crow_ptr", ctypes.c_void_p), ("ccol", ctypes.c_void_p),
+                ("c_coarse", ctypes.c_void_p), ("x_coarse", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("level", ctypes.c_int32),
+                ("x_target", ctypes.c_void_p)]
 
 
 class LayoutStats(ctypes.Structure):
@@ -129,10 +142,20 @@ def load(path: str = LIB_PATH):
     lib.mm_layout_host.argtypes = [i32, P, P, P, P, P, P, P]
     lib.mm_repulsion_noalloc.argtypes = [i32, P, f32, P, P]
     lib.mm_autotune.argtypes = [P, P, i32, f64, P, P]
+    lib.mm_gemm_bf16.argtypes = [i32, i32, i32, P, P, P, i32, P, P, P]
+    lib.mm_net_create.argtypes = [P, P]
+    lib.mm_net_free.argtypes = [P]
+    lib.mm_net_free.restype = None
+    lib.mm_net_params.argtypes = [P, P, P]
+    lib.mm_net_forward.argtypes = [P, P, P, P, P]
+    lib.mm_net_gradients.argtypes = [P, P, P, P, P]
+    lib.mm_net_train_step.argtypes = [P, P, f32, P, P]
+    lib.mm_hierarchy_set_net.argtypes = [P, P]
+    lib.mm_layout_levels.argtypes = [P, P, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
-                        "mm_last_error"):
+                        "mm_last_error", "mm_net_free"):
             fn.restype = i32
     _lib = lib
     return lib
@@ -354,6 +377,23 @@ def autotune(h: Hierarchy, thetas=None, max_rel_drift: float = 0.01, stream=None
                 layout_ms_before=r.layout_ms_before, layout_ms_after=r.layout_ms_after)
 
 
+def gemm_bf16(A, B, bias=None, relu=False, out_bf16=False, stream=None):
+    """C = A @ B^T on the tcgen05 tensor cores (BF16 in, FP32 accumulate).
+
+    A [M, K] and B [N, K] bfloat16 CUDA tensors; returns FP32 [M, N] (and the
+    BF16 copy when out_bf16)."""
+    A = _dev(A, torch.bfloat16, "A")
+    B = _dev(B, torch.bfloat16, "B")
+    bias = _dev(bias, torch.float32, "bias")
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    Cb = torch.empty((M, N), dtype=torch.bfloat16, device="cuda") if out_bf16 else None
+    _check(load().mm_gemm_bf16(M, N, K, _ptr(A), _ptr(B), _ptr(bias), int(relu), _ptr(C),
+                               _ptr(Cb), _stream(stream)))
+    return (C, Cb) if out_bf16 else C
+
+
 def objective(h: Hierarchy, level: int, x, alpha: float, stream=None):
     """Eq. 1 over S (exact, all pairs): returns (stress, lnsum, M)."""
     x = _dev(x, torch.float32, "x")
@@ -449,3 +489,83 @@ def layout_host(row_ptr, col, params: Params = None, edge_len=None, stream=None)
                                  ctypes.byref(p), x.ctypes.data_as(ctypes.c_void_p),
                                  ctypes.byref(st), _stream(stream)))
     return x, st.as_dict()
+
+
+# ---------------------------------------------------------------- learned
+class Net:
+    """Learned prolongation network (owns an mm_prolong_net)."""
+
+    def __init__(self, params):
+        _require_cuda()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MM_NET_PARAMS:
+            raise ValueError(f"expected {MM_NET_PARAMS} parameters, got {p.size}")
+        h = ctypes.c_void_p()
+        _check(load().mm_net_create(p.ctypes.data, ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mm_net_free(self.handle)
+            self.handle = None
+
+    def params(self):
+        out = np.empty(MM_NET_PARAMS, dtype=np.float32)
+        _check(load().mm_net_params(self.handle, out.ctypes.data, None))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().mm_net_params(self.handle, None, p.ctypes.data))
+
+    @staticmethod
+    def sample(fine, coarse, x_coarse, seed, level, x_target=None):
+        """fine: dict row_ptr/col/map (CUDA); coarse: dict row_ptr/col/c (CUDA)."""
+        keep = [fine["row_ptr"], fine["col"], fine["map"], coarse["row_ptr"], coarse["col"],
+                coarse["c"], x_coarse, x_target]
+        smp = ProlongSample(
+            n=fine["row_ptr"].numel() - 1, row_ptr=fine["row_ptr"].data_ptr(),
+            col=fine["col"].data_ptr(), map=fine["map"].data_ptr(),
+            n_coarse=coarse["row_ptr"].numel() - 1, crow_ptr=coarse["row_ptr"].data_ptr(),
+            ccol=coarse["col"].data_ptr(), c_coarse=coarse["c"].data_ptr(),
+            x_coarse=x_coarse.data_ptr(), seed=int(seed), level=int(level),
+            x_target=x_target.data_ptr() if x_target is not None else None)
+        return smp, keep
+
+    def forward(self, smp, stream=None):
+        n = smp.n
+        x = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double(0.0)
+        _check(load().mm_net_forward(self.handle, ctypes.byref(smp), _ptr(x), ctypes.byref(loss),
+                                     _stream(stream)))
+        return x, loss.value
+
+    def gradients(self, smp, stream=None):
+        g = np.empty(MM_NET_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().mm_net_gradients(self.handle, ctypes.byref(smp), g.ctypes.data,
+                                       ctypes.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train_step(self, smp, lr, stream=None):
+        loss = ctypes.c_double(0.0)
+        _check(load().mm_net_train_step(self.handle, ctypes.byref(smp), float(lr),
+                                        ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+
+def set_net(h: Hierarchy, net):
+    _check(load().mm_hierarchy_set_net(h.handle, net.handle if net is not None else None))
+    h._net = net  # keep the network alive while attached
+
+
+def layout_levels(h: Hierarchy, params: Params = None, stream=None):
+    """mm_layout that also returns every level's final layout (list of CUDA
+    tensors, level 0 first)."""
+    L = h.levels()
+    outs = [torch.empty((h.level_info(l)[0], 2), dtype=torch.float32, device="cuda")
+            for l in range(L)]
+    arr = (ctypes.c_void_p * L)(*[o.data_ptr() for o in outs])
+    _check(load().mm_layout_levels(h.handle, ctypes.byref(params) if params is not None else None,
+                                   arr, _stream(stream)))
+    return outs

@@ -62,19 +62,28 @@ def test_struct_layout_matches_c(tmp_path):
                  sizeof(mm_graph), offsetof(mm_graph, graph_ptr));
           printf("%zu %zu %zu\\n", sizeof(mm_layout_stats),
                  offsetof(mm_layout_stats, level_sweeps), offsetof(mm_layout_stats, final_stress));
+          printf("%zu %zu %zu %zu %zu\\n", sizeof(mm_prolong_sample),
+                 offsetof(mm_prolong_sample, n_coarse), offsetof(mm_prolong_sample, seed),
+                 offsetof(mm_prolong_sample, level), offsetof(mm_prolong_sample, x_target));
+          printf("%zu\\n", offsetof(mm_params, learned_prolong));
           return 0;
         }
     """))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")[:2]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True,
+                                text=True).stdout.split("\n")[:4]
     P, G, S = mm.Params, mm.Graph, mm.LayoutStats
     assert [int(t) for t in a.split()] == [ctypes.sizeof(P), P.alpha0.offset, P.seed.offset,
                                            P.traverse_warps.offset, ctypes.sizeof(G),
                                            G.graph_ptr.offset]
     assert [int(t) for t in b.split()] == [ctypes.sizeof(S), S.level_sweeps.offset,
                                            S.final_stress.offset]
+    Q = mm.ProlongSample
+    assert [int(t) for t in c.split()] == [ctypes.sizeof(Q), Q.n_coarse.offset, Q.seed.offset,
+                                           Q.level.offset, Q.x_target.offset]
+    assert int(d) == P.learned_prolong.offset
 
 
 def test_product_path_does_not_import_oracle():

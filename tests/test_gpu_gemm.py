@@ -1,0 +1,34 @@
+"""The tcgen05 BF16 GEMM of the learned prolongation against an FP64 matmul of
+the same BF16-rounded inputs.  FP32 accumulation of K <= 128 products of
+BF16 values: relative error of each output ~ K * 2^-24 of the sum of |terms|.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 16), (1000, 64, 128), (257, 128, 64),
+                                   (5, 64, 32), (4096, 128, 128)])
+def test_gemm_matches_fp64(mm, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    C = mm.gemm_bf16(A.cuda(), B.cuda()).cpu().numpy()
+    a = A.double().numpy()
+    b = B.double().numpy()
+    ref = a @ b.T
+    bound = 1e-5 * (np.abs(a) @ np.abs(b).T) + 1e-6
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_gemm_bias_relu_bf16(mm):
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A = torch.randn(300, 128, generator=g).to(torch.bfloat16)
+    B = torch.randn(64, 128, generator=g).to(torch.bfloat16)
+    bias = torch.randn(64, generator=g)
+    C, Cb = mm.gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), relu=True, out_bf16=True)
+    ref = np.maximum(A.double().numpy() @ B.double().numpy().T + bias.double().numpy(), 0)
+    np.testing.assert_allclose(C.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(Cb.float().cpu().numpy(), ref, rtol=1e-2, atol=1e-2)

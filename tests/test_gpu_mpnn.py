@@ -1,0 +1,166 @@
+"""The learned prolongation on the GPU against the oracle (oracle/mpnn.py).
+
+The network's dense layers take BF16 operands with FP32 accumulation.  The
+oracle's quantised mode rounds to BF16 at the same points and computes the
+rest in FP64, so the device agrees with it up to FP32 accumulation order and
+the odd element that lands on the other side of a BF16 rounding boundary
+(one BF16 step is 2^-8 relative): 1% on drifts and losses, 2% norm-wise on
+gradients.  Against the plain FP64 oracle the BF16 rounding of the inputs
+itself shows (gradients here are differences of large terms, up to ~10%
+apart), so that comparison checks direction: cosine similarity >= 0.98.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mpnn
+from paper_1506_04383_gb300 import graphs
+
+pytestmark = pytest.mark.gpu
+
+
+def flat(P):
+    return np.concatenate([P[k].reshape(-1) for k in
+                           ["W0", "b0", "W1", "b1", "W2", "b2", "W3", "b3"]]).astype(np.float32)
+
+
+def unflat(v):
+    out, o = {}, 0
+    for i, (r, c) in enumerate(mpnn.layer_shapes()):
+        out[f"W{i}"] = v[o:o + r * c].reshape(r, c).astype(np.float64)
+        o += r * c
+        out[f"b{i}"] = v[o:o + c].astype(np.float64)
+        o += c
+    return out
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def sample(n_pts=4000, seed=3, level=2):
+    rp, col, _, _ = graphs.rgg(n_pts, 7.0, seed)
+    n = len(rp) - 1
+    lab = oracle.sclap(rp, col, np.ones(n), 3.0, 10, seed, 0)
+    mp, cc, crp, ccol, _ = oracle.contract(rp, col, np.ones(n), lab)
+    rng = np.random.default_rng(seed)
+    xc = (rng.random((len(cc), 2)) * 40.0).astype(np.float32)
+    r = mpnn.polar_offsets(n, mp, cc, 1506, level)
+    # a learnable target: a fixed mix of the three basis vectors plus noise
+    _, a, b, _ = mpnn.features(rp, col, mp, xc.astype(np.float64), crp, ccol, cc, r)
+    t = (xc[mp] + r + 0.3 * a + 0.2 * b - 0.5 * r + rng.normal(0, 0.05, (n, 2))).astype(np.float32)
+    return dict(rp=rp, col=col, mp=mp, cc=cc.astype(np.float32), crp=crp, ccol=ccol, xc=xc, t=t,
+                level=level)
+
+
+def device_sample(mm, s):
+    fine = dict(row_ptr=cu(s["rp"]), col=cu(s["col"]), map=cu(s["mp"].astype(np.int32)))
+    coarse = dict(row_ptr=cu(s["crp"]), col=cu(s["ccol"]), c=cu(s["cc"]))
+    return mm.Net.sample(fine, coarse, cu(s["xc"]), 1506, s["level"], cu(s["t"]))
+
+
+def oracle_run(P, s, quant=None):
+    r = mpnn.polar_offsets(len(s["rp"]) - 1, s["mp"], s["cc"].astype(np.float64), 1506,
+                           s["level"])
+    f, a, b, r = mpnn.features(s["rp"], s["col"], s["mp"], s["xc"].astype(np.float64), s["crp"],
+                               s["ccol"], s["cc"].astype(np.float64), r)
+    o, cache = mpnn.forward(P, s["rp"], s["col"], f, a, b, r, quant=quant)
+    xc = s["xc"].astype(np.float64)
+    tt = s["t"].astype(np.float64) - xc[s["mp"]] - r
+    cp = s["cc"].astype(np.float64)[s["mp"]]
+    L = mpnn.loss(o, tt, cp)
+    G = mpnn.backward(P, s["rp"], s["col"], cache, a, b, r, o, tt, cp, quant=quant)
+    return xc[s["mp"]] + r + o, L, G, r
+
+
+def params(seed=7):
+    P = mpnn.init_params(seed)
+    rng = np.random.default_rng(seed)
+    for k in P:
+        if k.startswith("b"):
+            P[k] = rng.normal(0, 0.05, P[k].shape)
+    # round to what the device stores, so both sides start from equal values
+    return unflat(flat(P))
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30)
+
+
+def cos(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+
+
+Q = mpnn.bf16_round
+
+
+def test_forward_and_loss_match_oracle(mm):
+    s = sample()
+    P = params()
+    net = mm.Net(flat(P))
+    smp, keep = device_sample(mm, s)
+    x, L = net.forward(smp)
+    xq, Lq, _, r = oracle_run(P, s, Q)
+    xo, Lo, _, _ = oracle_run(P, s)
+    base = s["xc"][s["mp"]] + r
+    drift = x.cpu().numpy() - base
+    assert rel(drift, xq - base) < 0.01
+    assert L == pytest.approx(Lq, rel=0.01)
+    assert rel(drift, xo - base) < 0.05
+    assert L == pytest.approx(Lo, rel=0.03)
+
+
+def test_gradients_match_oracle(mm):
+    s = sample(seed=5)
+    P = params(11)
+    net = mm.Net(flat(P))
+    smp, keep = device_sample(mm, s)
+    g, L = net.gradients(smp)
+    _, Lq, Gq, _ = oracle_run(P, s, Q)
+    _, Lo, Go, _ = oracle_run(P, s)
+    G = unflat(g)
+    assert L == pytest.approx(Lq, rel=0.01)
+    for k in ["W3", "b3", "W2", "b2", "W1", "b1", "W0", "b0"]:
+        assert rel(G[k], Gq[k]) < 0.02, k
+        assert cos(G[k], Go[k]) > 0.98, k
+
+
+def test_training_reduces_loss_like_the_oracle(mm):
+    s = sample(seed=8)
+    P = params(13)
+    net = mm.Net(flat(P))
+    smp, keep = device_sample(mm, s)
+    losses = [net.train_step(smp, 1e-2) for _ in range(60)]
+    _, L_end = net.forward(smp)
+    assert L_end < 0.5 * losses[0]
+    # the oracle's Adam from the same start reaches a comparable loss
+    Po = {k: v.copy() for k, v in P.items()}
+    state = {}
+    for _ in range(60):
+        _, Lo, Go, _ = oracle_run(Po, s, Q)
+        Po = mpnn.adam_step(Po, Go, state, 1e-2)
+    _, Lo_end, _, _ = oracle_run(Po, s, Q)
+    assert L_end == pytest.approx(Lo_end, rel=0.15)
+
+
+def test_learned_prolongation_layout(mm):
+    rp, col, _, _ = graphs.rgg(6000, 8.0, 21)
+    h = mm.build_hierarchy(cu(rp), cu(col))
+    p = mm.default_params()
+    x_plain, st_plain = mm.layout(h, p)
+    levels = mm.layout_levels(h, p)
+    # the recording layout is the plain layout, bit for bit
+    assert torch.equal(levels[0], x_plain)
+    net = mm.Net(flat(params(5)))
+    mm.set_net(h, net)
+    p.learned_prolong = 1
+    x_l, st_l = mm.layout(h, p)
+    assert torch.isfinite(x_l).all()
+    # the final objective stays within 2% of the plain layout's (the sweeps
+    # repair what an untrained drift gets wrong)
+    _, _, M_plain = mm.objective(h, 0, x_plain, 0.008)
+    _, _, M_l = mm.objective(h, 0, x_l, 0.008)
+    assert abs(M_l - M_plain) <= 0.02 * abs(M_plain)
+    mm.set_net(h, None)

@@ -89,3 +89,39 @@ def test_adam_matches_closed_form_first_step():
     P2 = mpnn.adam_step({k: v.copy() for k, v in P.items()}, G, {}, lr=0.01)
     np.testing.assert_allclose(P2["W0"], P["W0"] - 0.01 * np.sign(G["W0"]), atol=1e-7)
     np.testing.assert_allclose(P2["b0"], P["b0"] - 0.01 * np.sign(G["b0"]), atol=1e-7)
+
+
+def test_bf16_round_against_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                        [0.0, -0.0, 1.0, 3.4e38, -3.4e38, 1e-40, 1.00390625, 1.01171875,
+                         1.0 + 2.0 ** -8 + 2.0 ** -20]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got = mpnn.bf16_round(x)
+    np.testing.assert_array_equal(got, want)
+    # ties go to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert mpnn.bf16_round(np.float32(1.0 + 2.0 ** -8)) == 1.0
+    assert mpnn.bf16_round(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
+
+
+def test_quantised_gradients_match_finite_differences_of_quantised_loss():
+    # with BF16 operands the loss is piecewise smooth in the non-quantised
+    # parameters (biases and the head); its gradient there is still exact
+    rp, col, mp, xc, crp, ccol, cc, r, t = _sample()
+    f, a, b, r = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
+    P = mpnn.init_params(7)
+    cp = cc[mp]
+    q = mpnn.bf16_round
+    o, cache = mpnn.forward(P, rp, col, f, a, b, r, quant=q)
+    G = mpnn.backward(P, rp, col, cache, a, b, r, o, t, cp, quant=q)
+    h = 1e-7
+    for k, i in [("W3", 5), ("W3", 100), ("b3", 0), ("b3", 2)]:
+        flat = P[k].reshape(-1)
+        old = flat[i]
+        flat[i] = old + h
+        lp = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, quant=q)[0], t, cp)
+        flat[i] = old - h
+        lm = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, quant=q)[0], t, cp)
+        flat[i] = old
+        assert G[k].reshape(-1)[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
