@@ -314,18 +314,20 @@ mm_status mm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A,
  * prolongation of Sec. 3.2).  A fine vertex v of the coarse vertex p is
  * placed at x'_p + r_v + o_v: r_v is the paper's random polar offset (the
  * same Philox draws as mm_prolong) and o_v = beta_0 a_v + beta_1 b_v +
- * beta_2 r_v a drift predicted by a 3-layer message-passing network (hidden
- * 64, mean aggregation over the fine graph, BF16 tensor-core layers with FP32
- * accumulation) from 8 invariant features; a_v is the mean direction from
- * x'_p to the coarse positions of v's neighbours in other clusters, b_v the
- * mean direction from x'_p to p's coarse neighbours.  Trained on the
+ * beta_2 r_v + beta_3 g_v a drift predicted by a 3-layer message-passing
+ * network (hidden 64, mean aggregation over the fine graph, BF16 tensor-core
+ * layers with FP32 accumulation) from 8 invariant features; a_v is the mean
+ * direction from x'_p to the coarse positions of v's neighbours in other
+ * clusters, b_v the mean direction from x'_p to p's coarse neighbours and
+ * g_v = x'_p - (mean of the coarse layout), which expresses the growth of
+ * the layout about its centre while a level refines.  Trained on the
  * device (Adam) to reproduce the drift that the plain layout's refinement
  * applies: loss = mean_v |o_v - t_v|^2 / c(p), t_v = x*_v - x'_p - r_v with
  * x* the converged positions of the level.
  */
 typedef struct mm_prolong_net mm_prolong_net;
-#define MM_NET_PARAMS 17795 /* FP32 parameters: W0[16x64] b0 W1[128x64] b1
-                               W2[128x64] b2 Wo[64x3] bo, row-major */
+#define MM_NET_PARAMS 17860 /* FP32 parameters: W0[16x64] b0 W1[128x64] b1
+                               W2[128x64] b2 Wo[64x4] bo, row-major */
 
 /* One prolongation step's inputs (device pointers). */
 typedef struct mm_prolong_sample {

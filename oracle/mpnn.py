@@ -8,19 +8,22 @@ message-passing network from the coarse layout and the local structure:
 
     x_v = x'_p + r_v + o_v,      p = M(v).
 
-Inputs per fine vertex (all rotation/translation invariant except the
-three basis vectors, which rotate with the layout):
+Inputs per fine vertex (all rotation/translation/scale invariant except the
+four basis vectors, which rotate and scale with the layout):
     a_v = mean over fine neighbours w with M(w) != p of (x'_{M(w)} - x'_p)
     b_v = mean over coarse neighbours q of p of (x'_q - x'_p)
     r_v = the polar offset of the paper's prolongation (Philox draws)
-    scalars f (8): 1, ln c(p), ln(1 + deg v), fraction of v's neighbours
-        outside its cluster, |a|/R, |b|/R, cos(a, b), (a . r)/(|a| R),
-        R = sqrt(c(p)).
+    g_v = x'_p - m, m = mean of the coarse layout (unweighted): the layout
+        grows by a few percent about its centre while a level refines, and
+        o = beta_3 g expresses that growth (beta_3 = factor - 1)
+    scalars f (8): |g|/S with S the RMS distance of the coarse vertices from
+        m, ln c(p), ln(1 + deg v), fraction of v's neighbours outside its
+        cluster, |a|/R, |b|/R, cos(a, b), (a . r)/(|a| R), R = sqrt(c(p)).
 Network (3 message-passing layers, hidden 64, mean aggregation over the
 fine graph):
     H0 = f;  H_l = ReLU([H_{l-1} | A H_{l-1}] W_l + b_l),  l = 1..3
-    beta = H_3 W_o + b_o  (3 coefficients)
-    o_v = beta_0 a_v + beta_1 b_v + beta_2 r_v
+    beta = H_3 W_o + b_o  (4 coefficients)
+    o_v = beta_0 a_v + beta_1 b_v + beta_2 r_v + beta_3 g_v
 so o is equivariant by construction.  Loss: mean over v of
 |o_v - t_v|^2 / c(p) with target t_v = x*_v - x'_p - r_v (x* = the level's
 converged layout).
@@ -48,7 +51,7 @@ import oracle
 
 F_IN = 8
 HIDDEN = 64
-N_OUT = 3
+N_OUT = 4
 LAYERS = 3
 
 
@@ -109,7 +112,7 @@ def mean_agg_T(rp, col, G):
 
 
 def features(rp, col, mp, xc, crp, ccol, cc, r):
-    """Scalar features f [n, 8] and basis vectors a, b, r [n, 2] each."""
+    """Scalar features f [n, 8] and basis vectors a, b, r, g [n, 2] each."""
     n = len(rp) - 1
     deg = np.diff(rp)
     src = np.repeat(np.arange(n), deg)
@@ -130,8 +133,11 @@ def features(rp, col, mp, xc, crp, ccol, cc, r):
     R = np.sqrt(cc[p])
     na = np.linalg.norm(a, axis=1)
     nb = np.linalg.norm(b, axis=1)
+    m = xc.mean(axis=0)
+    S = math.sqrt(((xc - m) ** 2).sum(1).mean())
+    g = xc[p] - m
     f = np.zeros((n, F_IN))
-    f[:, 0] = 1.0
+    f[:, 0] = np.linalg.norm(g, axis=1) / max(S, 1e-30)
     f[:, 1] = np.log(cc[p])
     f[:, 2] = np.log1p(deg)
     f[:, 3] = cnt / np.maximum(deg, 1)
@@ -139,10 +145,10 @@ def features(rp, col, mp, xc, crp, ccol, cc, r):
     f[:, 5] = nb / R
     f[:, 6] = (a * b).sum(1) / (na * nb + 1e-12)
     f[:, 7] = (a * r).sum(1) / (na * R + 1e-12)
-    return f, a, b, r
+    return f, a, b, r, g
 
 
-def forward(P, rp, col, f, a, b, r, quant=None):
+def forward(P, rp, col, f, a, b, r, g, quant=None):
     """Returns (o [n,2], cache for backward)."""
     q = quant or _ident
     H = q(f)
@@ -153,7 +159,7 @@ def forward(P, rp, col, f, a, b, r, quant=None):
         cache.append((Hc, Z))
         H = q(np.maximum(Z, 0.0))
     beta = H @ P[f"W{LAYERS}"] + P[f"b{LAYERS}"]
-    o = beta[:, 0:1] * a + beta[:, 1:2] * b + beta[:, 2:3] * r
+    o = beta[:, 0:1] * a + beta[:, 1:2] * b + beta[:, 2:3] * r + beta[:, 3:4] * g
     return o, dict(layers=cache, H=H, beta=beta)
 
 
@@ -163,12 +169,13 @@ def loss(o, t, cp):
     return float(((d * d).sum(1) / cp).mean())
 
 
-def backward(P, rp, col, cache, a, b, r, o, t, cp, quant=None):
+def backward(P, rp, col, cache, a, b, r, g, o, t, cp, quant=None):
     """Analytic gradients of the loss with respect to every W_l and b_l."""
     q = quant or _ident
     n = len(o)
     do = 2.0 * (o - t) / (n * cp)[:, None]
-    dbeta = np.stack([(do * a).sum(1), (do * b).sum(1), (do * r).sum(1)], axis=1)
+    dbeta = np.stack([(do * a).sum(1), (do * b).sum(1), (do * r).sum(1), (do * g).sum(1)],
+                     axis=1)
     G = {}
     H = cache["H"]
     G[f"W{LAYERS}"] = H.T @ dbeta

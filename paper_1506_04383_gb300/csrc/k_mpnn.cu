@@ -5,8 +5,10 @@
 //   beta = head(H_3),  H_l = ReLU([H_{l-1} | mean_N H_{l-1}] W_l + b_l),
 // with a_v the mean direction from x'_p to the coarse positions of v's
 // neighbours in other clusters, b_v the mean direction from x'_p to p's
-// coarse neighbours and r_v the polar offset itself; the 8 input scalars are
-// rotation/translation/scale invariant, so o is equivariant.
+// coarse neighbours, r_v the polar offset itself and g_v = x'_p - m (m the
+// mean of the coarse layout; beta_3 g is a growth about the centre); the 8
+// input scalars are rotation/translation/scale invariant, so o is
+// equivariant.
 //
 // Forward and backward run on the device: the dense layers are tcgen05 BF16
 // GEMMs with FP32 accumulation (k_gemm.cu), aggregation / head / loss / ReLU
@@ -27,6 +29,62 @@ namespace {
 
 constexpr int kH = kNetHidden;   // 64
 constexpr int kF = kNetFeatures; // 8
+constexpr int kO = kNetOut;      // 4
+constexpr int kStatThreads = 1024;
+
+// Mean m and RMS radius S of the coarse layout (one block): FP32 sums per
+// thread, FP64 across the block.  stat = (m.x, m.y, S).
+__global__ void __launch_bounds__(kStatThreads) net_stat(int nc, XSel xc, float* stat) {
+  __shared__ double red[2][kStatThreads / 32];
+  __shared__ double mean[2];
+  const float2* X = xc.cur();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float sx = 0.f, sy = 0.f;
+  for (int i = tid; i < nc; i += kStatThreads) {
+    const float2 p = X[i];
+    sx += p.x;
+    sy += p.y;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (lane == 0) {
+    red[0][w] = sx;
+    red[1][w] = sy;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int i = 0; i < kStatThreads / 32; ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    mean[0] = a / nc;
+    mean[1] = b / nc;
+  }
+  __syncthreads();
+  const float mx = (float)mean[0], my = (float)mean[1];
+  float ss = 0.f;
+  for (int i = tid; i < nc; i += kStatThreads) {
+    const float2 p = X[i];
+    const float dx = p.x - mx, dy = p.y - my;
+    ss = fmaf(dx, dx, fmaf(dy, dy, ss));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  __syncthreads();
+  if (lane == 0) red[0][w] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0;
+    for (int i = 0; i < kStatThreads / 32; ++i) a += red[0][i];
+    stat[0] = mx;
+    stat[1] = my;
+    stat[2] = (float)sqrt(a / nc);
+  }
+}
 
 // ---------------------------------------------------------------- features
 __device__ __forceinline__ float u01f(uint32_t z) { return (float)(z >> 8) * (1.0f / 16777216.0f); }
@@ -34,9 +92,9 @@ __device__ __forceinline__ float u01f(uint32_t z) { return (float)(z >> 8) * (1.
 __global__ void net_features(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                              const int32_t* __restrict__ map, XSel xc,
                              const int32_t* __restrict__ crp, const int32_t* __restrict__ ccol,
-                             const float* __restrict__ cc, uint32_t k0, uint32_t k1,
-                             uint32_t level, __nv_bfloat16* __restrict__ f,
-                             float2* __restrict__ basis) {
+                             const float* __restrict__ cc, const float* __restrict__ stat,
+                             uint32_t k0, uint32_t k1, uint32_t level,
+                             __nv_bfloat16* __restrict__ f, float2* __restrict__ basis) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const float2* X = xc.cur();
@@ -71,8 +129,9 @@ __global__ void net_features(int n, const int32_t* __restrict__ rp, const int32_
   sincosf(phi, &sn, &cs);
   const float rx = rad * cs, ry = rad * sn;
   const float na = sqrtf(ax * ax + ay * ay), nb = sqrtf(bx * bx + by * by);
+  const float gx = xp.x - stat[0], gy = xp.y - stat[1];
   float g[kF];
-  g[0] = 1.f;
+  g[0] = sqrtf(gx * gx + gy * gy) / fmaxf(stat[2], 1e-30f);
   g[1] = logf(cc[p]);
   g[2] = log1pf((float)deg);
   g[3] = (float)cnt / (float)max(deg, 1);
@@ -82,9 +141,10 @@ __global__ void net_features(int n, const int32_t* __restrict__ rp, const int32_
   g[7] = (ax * rx + ay * ry) / (na * R + 1e-12f);
 #pragma unroll
   for (int j = 0; j < kF; ++j) f[(size_t)v * kF + j] = __float2bfloat16_rn(g[j]);
-  basis[3 * (size_t)v] = make_float2(ax, ay);
-  basis[3 * (size_t)v + 1] = make_float2(bx, by);
-  basis[3 * (size_t)v + 2] = make_float2(rx, ry);
+  basis[kO * (size_t)v] = make_float2(ax, ay);
+  basis[kO * (size_t)v + 1] = make_float2(bx, by);
+  basis[kO * (size_t)v + 2] = make_float2(rx, ry);
+  basis[kO * (size_t)v + 3] = make_float2(gx, gy);
 }
 
 // Hcat[v] = [H[v] | mean over neighbours of H] (BF16, width 2D), one warp
@@ -119,32 +179,39 @@ __global__ void net_aggregate(int n, const int32_t* __restrict__ rp, const int32
   }
 }
 
-// Head: beta = H3 Wo + bo, o = beta0 a + beta1 b + beta2 r.  Inference
-// writes x_v = x'_p + r_v + o_v; training also forms the loss terms and
-// dbeta = d loss / d beta.
+// Head: beta = H3 Wo + bo, o = beta0 a + beta1 b + beta2 r + beta3 g.
+// Inference writes x_v = x'_p + r_v + o_v; training also forms the loss
+// terms and dbeta = d loss / d beta.
 __global__ void net_head(int n, const __nv_bfloat16* __restrict__ H3, const float* __restrict__ Wo,
                          const float* __restrict__ bo, const float2* __restrict__ basis,
                          const int32_t* __restrict__ map, XSel xc, const float* __restrict__ cc,
                          float2* xout, const float2* __restrict__ target, float* dbeta,
                          double* loss_part) {
-  __shared__ float w[kH * 3 + 3];
-  for (int i = threadIdx.x; i < kH * 3 + 3; i += blockDim.x)
-    w[i] = i < kH * 3 ? Wo[i] : bo[i - kH * 3];
+  __shared__ float w[kH * kO + kO];
+  for (int i = threadIdx.x; i < kH * kO + kO; i += blockDim.x)
+    w[i] = i < kH * kO ? Wo[i] : bo[i - kH * kO];
   __syncthreads();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.f;
   if (v < n) {
-    float b0 = w[kH * 3], b1 = w[kH * 3 + 1], b2 = w[kH * 3 + 2];
+    float beta[kO];
+#pragma unroll
+    for (int j = 0; j < kO; ++j) beta[j] = w[kH * kO + j];
     for (int d = 0; d < kH; ++d) {
       const float h = __bfloat162float(H3[(size_t)v * kH + d]);
-      b0 = fmaf(h, w[d * 3], b0);
-      b1 = fmaf(h, w[d * 3 + 1], b1);
-      b2 = fmaf(h, w[d * 3 + 2], b2);
+#pragma unroll
+      for (int j = 0; j < kO; ++j) beta[j] = fmaf(h, w[d * kO + j], beta[j]);
     }
-    const float2 a = basis[3 * (size_t)v], bb = basis[3 * (size_t)v + 1],
-                 r = basis[3 * (size_t)v + 2];
-    const float ox = b0 * a.x + b1 * bb.x + b2 * r.x;
-    const float oy = b0 * a.y + b1 * bb.y + b2 * r.y;
+    float2 e[kO];
+#pragma unroll
+    for (int j = 0; j < kO; ++j) e[j] = basis[kO * (size_t)v + j];
+    float ox = 0.f, oy = 0.f;
+#pragma unroll
+    for (int j = 0; j < kO; ++j) {
+      ox = fmaf(beta[j], e[j].x, ox);
+      oy = fmaf(beta[j], e[j].y, oy);
+    }
+    const float2 r = e[2];
     const int p = map[v];
     // prolongation: into xout, or (no output, no target) into xc.next()
     float2* dst = xout ? xout : (target ? nullptr : xc.next());
@@ -160,9 +227,8 @@ __global__ void net_head(int n, const __nv_bfloat16* __restrict__ H3, const floa
       const float cp = cc[p];
       l = (dx * dx + dy * dy) / cp;
       const float g = 2.f / ((float)n * cp);
-      dbeta[3 * (size_t)v] = g * (dx * a.x + dy * a.y);
-      dbeta[3 * (size_t)v + 1] = g * (dx * bb.x + dy * bb.y);
-      dbeta[3 * (size_t)v + 2] = g * (dx * r.x + dy * r.y);
+#pragma unroll
+      for (int j = 0; j < kO; ++j) dbeta[kO * (size_t)v + j] = g * (dx * e[j].x + dy * e[j].y);
     }
   }
   if (loss_part) {
@@ -187,8 +253,11 @@ __global__ void net_head_back(int n, const float* __restrict__ dbeta, const floa
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * kH) return;
   const int v = i / kH, d = i % kH;
-  const float* g = dbeta + 3 * (size_t)v;
-  dH[i] = g[0] * Wo[d * 3] + g[1] * Wo[d * 3 + 1] + g[2] * Wo[d * 3 + 2];
+  const float* g = dbeta + kO * (size_t)v;
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kO; ++j) s = fmaf(g[j], Wo[d * kO + j], s);
+  dH[i] = s;
 }
 
 // dZ = dH * (H > 0) in BF16 (the backward GEMM's A operand) and FP32 (the
@@ -283,7 +352,7 @@ __global__ void net_cast_w(int rows, const float* __restrict__ W, __nv_bfloat16*
 
 // ----------------------------------------------------------------- host side
 // Parameter offsets in the flat FP32 array: W0 [16x64], b0, W1 [128x64], b1,
-// W2 [128x64], b2, Wo [64x3], bo.
+// W2 [128x64], b2, Wo [64x4], bo.
 void net_offsets(int off[9]) {
   int o = 0;
   const int rows[3] = {2 * kF, 2 * kH, 2 * kH};
@@ -294,9 +363,9 @@ void net_offsets(int off[9]) {
     o += kH;
   }
   off[6] = o;
-  o += kH * 3;
+  o += kH * kO;
   off[7] = o;
-  o += 3;
+  o += kO;
   off[8] = o;
 }
 
@@ -318,6 +387,7 @@ mm_status net_alloc(Net& net, int max_n) {
     }
     MM_CK(cudaMalloc(&net.err, sizeof(int)));
     MM_CK(cudaMemset(net.err, 0, sizeof(int)));
+    MM_CK(cudaMalloc(&net.stat, sizeof(float) * 4));
   }
   if (max_n > net.cap) {
     void* bufs[] = {net.f, net.basis, net.Hc, net.H[0], net.H[1], net.H[2], net.dbeta, net.dH,
@@ -326,10 +396,10 @@ mm_status net_alloc(Net& net, int max_n) {
       if (b) cudaFree(b);
     const size_t N = (size_t)max_n;
     MM_CK(cudaMalloc(&net.f, sizeof(__nv_bfloat16) * N * kF));
-    MM_CK(cudaMalloc(&net.basis, sizeof(float2) * N * 3));
+    MM_CK(cudaMalloc(&net.basis, sizeof(float2) * N * kO));
     MM_CK(cudaMalloc(&net.Hc, sizeof(__nv_bfloat16) * N * 2 * kH));
     for (int l = 0; l < 3; ++l) MM_CK(cudaMalloc(&net.H[l], sizeof(__nv_bfloat16) * N * kH));
-    MM_CK(cudaMalloc(&net.dbeta, sizeof(float) * N * 3));
+    MM_CK(cudaMalloc(&net.dbeta, sizeof(float) * N * kO));
     MM_CK(cudaMalloc(&net.dH, sizeof(float) * N * kH));
     MM_CK(cudaMalloc(&net.dZ, sizeof(float) * N * kH));
     MM_CK(cudaMalloc(&net.dZb, sizeof(__nv_bfloat16) * N * kH));
@@ -343,7 +413,7 @@ mm_status net_alloc(Net& net, int max_n) {
 
 void net_free(Net& net) {
   void* bufs[] = {net.P, net.G, net.M1, net.M2, net.Wt[0], net.Wt[1], net.Wt[2], net.Wb[0],
-                  net.Wb[1], net.Wb[2], net.err, net.f, net.basis, net.Hc, net.H[0], net.H[1],
+                  net.Wb[1], net.Wb[2], net.err, net.stat, net.f, net.basis, net.Hc, net.H[0], net.H[1],
                   net.H[2], net.dbeta, net.dH, net.dZ, net.dZb, net.dHc, net.part,
                   net.loss_part};
   for (void* b : bufs)
@@ -374,10 +444,15 @@ mm_status net_forward(Net& net, const NetSample& smp, float2* xout, const float2
     set_error("network workspace holds %d vertices, sample has %d", net.cap, n);
     return MM_ERR_INVALID_ARG;
   }
+  if (smp.nc < 1) {
+    set_error("prolongation sample without coarse vertices");
+    return MM_ERR_INVALID_ARG;
+  }
   int off[9];
   net_offsets(off);
+  net_stat<<<1, kStatThreads, 0, s>>>(smp.nc, smp.xc, net.stat);
   net_features<<<ceil_div(n, 256), 256, 0, s>>>(
-      n, smp.rp, smp.col, smp.map, smp.xc, smp.crp, smp.ccol, smp.cc,
+      n, smp.rp, smp.col, smp.map, smp.xc, smp.crp, smp.ccol, smp.cc, net.stat,
       (uint32_t)(smp.seed & 0xffffffffu), (uint32_t)(smp.seed >> 32), (uint32_t)smp.level,
       (__nv_bfloat16*)net.f, net.basis);
   const __nv_bfloat16* Hin = (const __nv_bfloat16*)net.f;
@@ -410,11 +485,11 @@ mm_status net_backward(Net& net, const NetSample& smp, cudaStream_t s) {
   const int parts = std::min(kNetParts, ceil_div(n, 64));
   const int chunk = ceil_div(n, parts);
   // head: dWo = H3^T dbeta, dbo = sum dbeta, dH3 = dbeta Wo^T
-  net_outer_part<<<dim3(parts, 1), 256, 0, s>>>(n, kH, 3, (const __nv_bfloat16*)net.H[2],
+  net_outer_part<<<dim3(parts, 1), 256, 0, s>>>(n, kH, kO, (const __nv_bfloat16*)net.H[2],
                                                 net.dbeta, chunk, net.part);
-  net_reduce_parts<<<1, 256, 0, s>>>(parts, kH * 3, net.part, net.G + off[6]);
-  net_colsum_part<<<parts, 32, 0, s>>>(n, 3, net.dbeta, chunk, net.part);
-  net_reduce_parts<<<1, 32, 0, s>>>(parts, 3, net.part, net.G + off[7]);
+  net_reduce_parts<<<1, 256, 0, s>>>(parts, kH * kO, net.part, net.G + off[6]);
+  net_colsum_part<<<parts, 32, 0, s>>>(n, kO, net.dbeta, chunk, net.part);
+  net_reduce_parts<<<1, 32, 0, s>>>(parts, kO, net.part, net.G + off[7]);
   net_head_back<<<ceil_div((int64_t)n * kH, 256), 256, 0, s>>>(n, net.dbeta, net.P + off[6],
                                                                net.dH);
   for (int l = 2; l >= 0; --l) {

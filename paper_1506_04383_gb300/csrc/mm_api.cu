@@ -364,6 +364,7 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
           smp.crp = Cn.rp;
           smp.ccol = Cn.col;
           smp.cc = Cn.c;
+          smp.nc = Cn.n;
           smp.seed = p.seed;
           smp.level = lv;
           MM_TRY(net_forward(h->net->net, smp, nullptr, nullptr, s));
@@ -1672,6 +1673,7 @@ mm_status make_sample(mm_prolong_net* net, const mm_prolong_sample* a, NetSample
   smp.crp = tmp.crp;
   smp.ccol = a->ccol;
   smp.cc = a->c_coarse;
+  smp.nc = a->n_coarse;
   smp.seed = a->seed;
   smp.level = a->level;
   MM_TRY(net_alloc(net->net, a->n));

@@ -297,6 +297,7 @@ mm_status gemm_setup();
 // ------------------------------------------------- learned prolongation ---
 constexpr int kNetHidden = 64;
 constexpr int kNetFeatures = 8;
+constexpr int kNetOut = 4;       // drift coefficients: a, b, r, g
 constexpr int kNetParts = 512;   // vertex chunks of the weight-gradient sums
 
 struct Net {
@@ -310,7 +311,8 @@ struct Net {
   int cap = 0;
   int64_t step = 0;
   void* f = nullptr;         // BF16 features [n x 8]
-  float2* basis = nullptr;   // (a, b, r) per vertex
+  float2* basis = nullptr;   // (a, b, r, g) per vertex
+  float* stat = nullptr;     // coarse layout mean (x, y) and RMS radius
   void* Hc = nullptr;        // BF16 [n x 128] concatenation
   void* H[3] = {nullptr, nullptr, nullptr};  // BF16 layer outputs [n x 64]
   float* dbeta = nullptr;
@@ -333,6 +335,7 @@ struct NetSample {
   const int32_t* crp = nullptr;
   const int32_t* ccol = nullptr;
   const float* cc = nullptr;
+  int nc = 0;  // coarse vertices
   uint64_t seed = 0;
   int level = 0;
 };

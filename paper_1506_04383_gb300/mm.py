@@ -32,7 +32,7 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
            "mm_layout_levels"]
-MM_NET_PARAMS = 17795
+MM_NET_PARAMS = 17860
 
 
 class MMError(RuntimeError):

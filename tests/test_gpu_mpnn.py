@@ -48,8 +48,9 @@ def sample(n_pts=4000, seed=3, level=2):
     xc = (rng.random((len(cc), 2)) * 40.0).astype(np.float32)
     r = mpnn.polar_offsets(n, mp, cc, 1506, level)
     # a learnable target: a fixed mix of the three basis vectors plus noise
-    _, a, b, _ = mpnn.features(rp, col, mp, xc.astype(np.float64), crp, ccol, cc, r)
-    t = (xc[mp] + r + 0.3 * a + 0.2 * b - 0.5 * r + rng.normal(0, 0.05, (n, 2))).astype(np.float32)
+    _, a, b, _, g = mpnn.features(rp, col, mp, xc.astype(np.float64), crp, ccol, cc, r)
+    t = (xc[mp] + r + 0.3 * a + 0.2 * b - 0.5 * r + 0.05 * g
+         + rng.normal(0, 0.05, (n, 2))).astype(np.float32)
     return dict(rp=rp, col=col, mp=mp, cc=cc.astype(np.float32), crp=crp, ccol=ccol, xc=xc, t=t,
                 level=level)
 
@@ -63,14 +64,14 @@ def device_sample(mm, s):
 def oracle_run(P, s, quant=None):
     r = mpnn.polar_offsets(len(s["rp"]) - 1, s["mp"], s["cc"].astype(np.float64), 1506,
                            s["level"])
-    f, a, b, r = mpnn.features(s["rp"], s["col"], s["mp"], s["xc"].astype(np.float64), s["crp"],
-                               s["ccol"], s["cc"].astype(np.float64), r)
-    o, cache = mpnn.forward(P, s["rp"], s["col"], f, a, b, r, quant=quant)
+    f, a, b, r, g = mpnn.features(s["rp"], s["col"], s["mp"], s["xc"].astype(np.float64),
+                                  s["crp"], s["ccol"], s["cc"].astype(np.float64), r)
+    o, cache = mpnn.forward(P, s["rp"], s["col"], f, a, b, r, g, quant=quant)
     xc = s["xc"].astype(np.float64)
     tt = s["t"].astype(np.float64) - xc[s["mp"]] - r
     cp = s["cc"].astype(np.float64)[s["mp"]]
     L = mpnn.loss(o, tt, cp)
-    G = mpnn.backward(P, s["rp"], s["col"], cache, a, b, r, o, tt, cp, quant=quant)
+    G = mpnn.backward(P, s["rp"], s["col"], cache, a, b, r, g, o, tt, cp, quant=quant)
     return xc[s["mp"]] + r + o, L, G, r
 
 
@@ -158,9 +159,9 @@ def test_learned_prolongation_layout(mm):
     p.learned_prolong = 1
     x_l, st_l = mm.layout(h, p)
     assert torch.isfinite(x_l).all()
-    # the final objective stays within 2% of the plain layout's (the sweeps
-    # repair what an untrained drift gets wrong)
+    # an untrained drift costs at most 2% of the objective (lower is better):
+    # the sweeps repair what it gets wrong
     _, _, M_plain = mm.objective(h, 0, x_plain, 0.008)
     _, _, M_l = mm.objective(h, 0, x_l, 0.008)
-    assert abs(M_l - M_plain) <= 0.02 * abs(M_plain)
+    assert M_l <= M_plain + 0.02 * abs(M_plain)
     mm.set_net(h, None)

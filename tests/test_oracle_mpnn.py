@@ -41,7 +41,7 @@ def test_aggregation_against_dense_adjacency():
 
 def test_gradients_match_finite_differences():
     rp, col, mp, xc, crp, ccol, cc, r, t = _sample()
-    f, a, b, r = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
+    f, a, b, r, g = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
     P = mpnn.init_params(7)
     # move the biases off zero so ReLU kinks are not hit exactly
     rng = np.random.default_rng(1)
@@ -49,8 +49,8 @@ def test_gradients_match_finite_differences():
         if k.startswith("b"):
             P[k] = rng.normal(0, 0.05, P[k].shape)
     cp = cc[mp]
-    o, cache = mpnn.forward(P, rp, col, f, a, b, r)
-    G = mpnn.backward(P, rp, col, cache, a, b, r, o, t, cp)
+    o, cache = mpnn.forward(P, rp, col, f, a, b, r, g)
+    G = mpnn.backward(P, rp, col, cache, a, b, r, g, o, t, cp)
     h = 1e-6
     for k in ["W0", "b0", "W1", "W2", "b2", "W3", "b3"]:
         flat = P[k].reshape(-1)
@@ -58,9 +58,9 @@ def test_gradients_match_finite_differences():
         for i in idx:
             old = flat[i]
             flat[i] = old + h
-            lp = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r)[0], t, cp)
+            lp = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, g)[0], t, cp)
             flat[i] = old - h
-            lm = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r)[0], t, cp)
+            lm = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, g)[0], t, cp)
             flat[i] = old
             fd = (lp - lm) / (2 * h)
             an = G[k].reshape(-1)[i]
@@ -70,15 +70,34 @@ def test_gradients_match_finite_differences():
 def test_drift_is_equivariant():
     rp, col, mp, xc, crp, ccol, cc, r, t = _sample()
     P = mpnn.init_params(9)
-    f, a, b, r0 = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
-    o, _ = mpnn.forward(P, rp, col, f, a, b, r0)
+    f, a, b, r0, g = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
+    o, _ = mpnn.forward(P, rp, col, f, a, b, r0, g)
     ang = 0.9
     Rm = np.array([[math.cos(ang), -math.sin(ang)], [math.sin(ang), math.cos(ang)]])
     xc2 = xc @ Rm.T + np.array([5.0, -3.0])
-    f2, a2, b2, r2 = mpnn.features(rp, col, mp, xc2, crp, ccol, cc, r @ Rm.T)
-    o2, _ = mpnn.forward(P, rp, col, f2, a2, b2, r2)
+    f2, a2, b2, r2, g2 = mpnn.features(rp, col, mp, xc2, crp, ccol, cc, r @ Rm.T)
+    o2, _ = mpnn.forward(P, rp, col, f2, a2, b2, r2, g2)
     np.testing.assert_allclose(f2, f, atol=1e-9)
     np.testing.assert_allclose(o2, o @ Rm.T, atol=1e-9)
+    # the centre direction g rotates with the layout and ignores translation
+    np.testing.assert_allclose(g2, g @ Rm.T, atol=1e-9)
+
+
+def test_centre_basis_expresses_a_uniform_growth():
+    # a target that is the coarse layout scaled by s about its mean is
+    # reproduced exactly by beta = (0, 0, 0, s - 1) -- a head with zero
+    # weights and that bias -- so the loss is 0 there
+    rp, col, mp, xc, crp, ccol, cc, r, _ = _sample()
+    f, a, b, r, g = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
+    m = xc.mean(0)
+    s = 1.07
+    t_abs = m + s * (xc[mp] - m) + r
+    t = t_abs - xc[mp] - r
+    P = mpnn.init_params(3)
+    P["W3"][:] = 0.0
+    P["b3"][:] = [0.0, 0.0, 0.0, s - 1.0]
+    o, _ = mpnn.forward(P, rp, col, f, a, b, r, g)
+    assert mpnn.loss(o, t, cc[mp]) < 1e-20
 
 
 def test_adam_matches_closed_form_first_step():
@@ -109,19 +128,19 @@ def test_quantised_gradients_match_finite_differences_of_quantised_loss():
     # with BF16 operands the loss is piecewise smooth in the non-quantised
     # parameters (biases and the head); its gradient there is still exact
     rp, col, mp, xc, crp, ccol, cc, r, t = _sample()
-    f, a, b, r = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
+    f, a, b, r, g = mpnn.features(rp, col, mp, xc, crp, ccol, cc, r)
     P = mpnn.init_params(7)
     cp = cc[mp]
     q = mpnn.bf16_round
-    o, cache = mpnn.forward(P, rp, col, f, a, b, r, quant=q)
-    G = mpnn.backward(P, rp, col, cache, a, b, r, o, t, cp, quant=q)
+    o, cache = mpnn.forward(P, rp, col, f, a, b, r, g, quant=q)
+    G = mpnn.backward(P, rp, col, cache, a, b, r, g, o, t, cp, quant=q)
     h = 1e-7
-    for k, i in [("W3", 5), ("W3", 100), ("b3", 0), ("b3", 2)]:
+    for k, i in [("W3", 5), ("W3", 100), ("W3", 131), ("b3", 0), ("b3", 3)]:
         flat = P[k].reshape(-1)
         old = flat[i]
         flat[i] = old + h
-        lp = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, quant=q)[0], t, cp)
+        lp = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, g, quant=q)[0], t, cp)
         flat[i] = old - h
-        lm = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, quant=q)[0], t, cp)
+        lm = mpnn.loss(mpnn.forward(P, rp, col, f, a, b, r, g, quant=q)[0], t, cp)
         flat[i] = old
         assert G[k].reshape(-1)[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
