@@ -53,6 +53,13 @@ WORKLOADS = {
                         "component, k=1, theta=0.6"),
     "del20": dict(kind="delaunay", n=1 << 20, seed=1506, k=1, theta=0.6, coarsest_n=100,
                   desc="Delaunay triangulation of 2^20 uniform points, k=1, theta=0.6"),
+    "learned2m": dict(kind="rgg", n=2000000, deg=8.0, seed=2027, k=2, theta=0.5, coarsest_n=100,
+                      learned=True,
+                      desc="learned prolongation: network trained on coarse-to-converged pairs of "
+                           "random geometric graphs of 10k-200k vertices, evaluated on an unseen "
+                           "2M-vertex random geometric graph (mean degree 8), k=2, theta=0.5; "
+                           "timed at the smallest per-level sweep cap whose objective matches "
+                           "the plain layout's"),
     "batch512": dict(kind="batch", count=512, seed=1506, k=2, theta=0.5, coarsest_n=2,
                      desc="512 graphs, lognormal sizes (median 3000, sigma 1) in [200, 50000], "
                           "thirds grids / random geometric (mean degree 6-12) / random trees, "
@@ -76,6 +83,90 @@ def make_graph(w):
     else:
         rp, col, _ = graphs.delaunay(w["n"], w["seed"])
     return rp, col
+
+
+# training set of the learned prolongation: random geometric graphs (mean
+# degree 8) of these sizes and seeds, none of them a bench workload
+TRAIN_RGG = [(10000, 9001), (20000, 9002), (50000, 9003), (100000, 9004), (200000, 9005)]
+CAPS = [5, 10, 20, 30, 50, 100]
+
+
+def train_prolongation(mm, p, steps=2000, lr=3e-3):
+    """Trains the learned prolongation on the method's own pairs; returns
+    (net, summary)."""
+    import numpy as np
+    import torch
+    from paper_1506_04383_gb300 import graphs, learned
+    t0 = time.perf_counter()
+    pairs = []
+    for n_, sd in TRAIN_RGG:
+        rp, col, _, _ = graphs.rgg(n_, 8.0, sd)
+        hh = mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), p)
+        pairs += learned.level_pairs(hh, p)
+    t1 = time.perf_counter()
+    net = mm.Net(learned.init_params(1))
+    losses = learned.train(net, pairs, steps, lr=lr, seed=0)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return net, {"train_graphs": [n_ for n_, _ in TRAIN_RGG], "pairs": len(pairs),
+                 "steps": steps, "pairs_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
+                 "loss_first100": float(np.mean(losses[:100])),
+                 "loss_last100": float(np.mean(losses[-100:]))}
+
+
+def timed_layout(mm, h, p, reps=2):
+    """Median device time (ms) of mm_layout after one warm-up, L2 flushed."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    x, st = mm.layout(h, p)
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, st = mm.layout(h, p)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts), st, x
+
+
+def learned_vs_plain(mm, h, p, net, tol=0.01):
+    """Time to an equal objective: the plain layout at the default per-level
+    sweep cap sets the reference objective M_ref (Eq. 1 at alpha_min); both
+    the plain and the learned prolongation then take the smallest cap in
+    CAPS whose objective is within tol of M_ref (or better; the tolerance the
+    oracle parity of layouts uses).  Returns (summary, params of the
+    matching learned run)."""
+    ms_ref, st_ref, x = timed_layout(mm, h, p)
+    M_ref = mm.objective(h, 0, x, p.alpha_min)[2]
+    bound = M_ref + tol * abs(M_ref)
+    out = {"reference": {"cap": p.max_iters_at_min, "ms": round(ms_ref, 2),
+                         "sweeps": st_ref["total_sweeps"], "M": M_ref},
+           "tolerance": tol}
+    best = {}
+    for name in ("plain", "learned"):
+        rows = []
+        for cap in CAPS:
+            q = mm.default_params()
+            ctypes_copy(q, p)
+            q.max_iters_at_min = cap
+            if name == "learned":
+                q.learned_prolong = 1
+                mm.set_net(h, net)
+            ms, st, x = timed_layout(mm, h, q)
+            M = mm.objective(h, 0, x, q.alpha_min)[2]
+            mm.set_net(h, None)
+            rows.append({"cap": cap, "ms": round(ms, 2), "sweeps": st["total_sweeps"], "M": M})
+            if M <= bound:
+                best[name] = (q, rows[-1])
+                break
+        out[name] = rows
+    if len(best) == 2:
+        out["speedup_at_equal_objective"] = best["plain"][1]["ms"] / best["learned"][1]["ms"]
+        out["sweep_ratio_at_equal_objective"] = (best["plain"][1]["sweeps"] /
+                                                 best["learned"][1]["sweeps"])
+    return out, best.get("learned", (None,))[0]
 
 
 def params_of(mm, w):
@@ -212,6 +303,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--learned", type=int, default=1,
+                    help="also train the learned prolongation and compare it with the plain "
+                         "layout at equal objective (single-graph multilevel workloads)")
     ap.add_argument("--batch-compare", type=int, default=64,
                     help="graphs of the batch also laid out one by one for comparison")
     args = ap.parse_args()
@@ -259,6 +353,20 @@ def main():
     tune = None
     if args.autotune:
         tune = mm.autotune(h, max_rel_drift=0.01)
+    learned_cmp = None
+    if w.get("learned") or (args.learned and gp is None and not w.get("single")):
+        net, tr = train_prolongation(mm, p)
+        cmp_, best = learned_vs_plain(mm, h, p, net)
+        learned_cmp = {"training": tr, **cmp_}
+        if w.get("learned"):
+            if best is None:
+                best = mm.default_params()
+                ctypes_copy(best, p)
+                best.learned_prolong = 1
+            mm.set_net(h, net)
+            p = best
+        else:
+            mm.set_net(h, None)
     xbuf = torch.empty((n, 2), dtype=torch.float32, device="cuda")
     for _ in range(max(args.warmup, 0)):
         _, st = mm.layout(h, p, x_init=x_init, x_out=xbuf)
@@ -320,8 +428,12 @@ def main():
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            xh, sth = mm.layout_host(prp, pcol, p) if gp is None else \
-                layout_host_batch(mm, prp, pcol, gp, p)
+            if w.get("learned"):
+                xh, sth = layout_host_learned(mm, prp, pcol, p, h._net)
+            elif gp is None:
+                xh, sth = mm.layout_host(prp, pcol, p)
+            else:
+                xh, sth = layout_host_batch(mm, prp, pcol, gp, p)
             t1 = time.perf_counter()
             if i > 0:
                 times.append(t1 - t0)
@@ -353,6 +465,7 @@ def main():
             "hierarchy_build_ms": build_ms,
             "objective_M": M,
             "batch_vs_plain": batch_cmp,
+            "learned_vs_plain": learned_cmp,
             "autotune": tune,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -375,6 +488,18 @@ def layout_host_batch(mm, rp, col, gp, p):
     drp = torch.from_numpy(rp).cuda(non_blocking=True)
     dcol = torch.from_numpy(col).cuda(non_blocking=True)
     h = mm.build_hierarchy(drp, dcol, p, graph_ptr=gp)
+    x, st = mm.layout(h, p)
+    return x.cpu().numpy(), st
+
+
+def layout_host_learned(mm, rp, col, p, net):
+    """End to end with the learned prolongation: host CSR in, hierarchy
+    build, network attached, layout, host layout out."""
+    import torch
+    drp = torch.from_numpy(rp).cuda(non_blocking=True)
+    dcol = torch.from_numpy(col).cuda(non_blocking=True)
+    h = mm.build_hierarchy(drp, dcol, p)
+    mm.set_net(h, net)
     x, st = mm.layout(h, p)
     return x.cpu().numpy(), st
 

@@ -165,3 +165,50 @@ def test_learned_prolongation_layout(mm):
     _, _, M_l = mm.objective(h, 0, x_l, 0.008)
     assert M_l <= M_plain + 0.02 * abs(M_plain)
     mm.set_net(h, None)
+
+
+def test_trained_network_gains_over_plain_prolongation(mm):
+    """Trained on the method's own pairs of three small random geometric
+    graphs, the network must (1) cut the prolongation error on an unseen
+    graph's levels to under a third and (2) reach the reference objective --
+    the plain layout's at the default cap of 100 sweeps per level, within
+    the 1% that layout parity uses -- with at most half the sweeps the plain
+    layout needs for it (both at their smallest matching per-level cap)."""
+    from paper_1506_04383_gb300 import learned
+    pairs = []
+    for n, sd in [(5000, 40), (10000, 41), (20000, 42)]:
+        rp, col, _, _ = graphs.rgg(n, 8.0, sd)
+        pairs += learned.level_pairs(mm.build_hierarchy(cu(rp), cu(col)))
+    net = mm.Net(learned.init_params(1))
+    losses = learned.train(net, pairs, 1500, lr=3e-3, seed=0)
+    assert np.mean(losses[-100:]) < 0.2 * np.mean(losses[:100])
+    rp, col, _, _ = graphs.rgg(30000, 8.0, 77)
+    h = mm.build_hierarchy(cu(rp), cu(col))
+    val = learned.level_pairs(h)
+    z = learned.zero_net()
+    w = np.array([p["n"] for p in val], dtype=np.float64)
+    plain = np.array([learned.pair_loss(z, p) for p in val])
+    lrn = np.array([learned.pair_loss(net, p) for p in val])
+    assert (w * lrn).sum() < (w * plain).sum() / 3
+    p = mm.default_params()
+    x_ref, st_ref = mm.layout(h, p)
+    bound = mm.objective(h, 0, x_ref, p.alpha_min)[2]
+    bound += 0.01 * abs(bound)
+
+    def sweeps_to_match(with_net):
+        for cap in (5, 10, 20, 30, 50, 100):
+            q = mm.default_params()
+            q.max_iters_at_min = cap
+            if with_net:
+                mm.set_net(h, net)
+                q.learned_prolong = 1
+            x, st = mm.layout(h, q)
+            mm.set_net(h, None)
+            if mm.objective(h, 0, x, q.alpha_min)[2] <= bound:
+                return st["total_sweeps"]
+        return None
+
+    s_plain = sweeps_to_match(False)
+    s_learned = sweeps_to_match(True)
+    assert s_plain is not None and s_learned is not None
+    assert 2 * s_learned <= s_plain, (s_learned, s_plain)
