@@ -80,7 +80,10 @@ typedef struct mm_params {
                             /* kernel; 0 = auto (2048, the maximum), -1 = off */
   int32_t learned_prolong;  /* 1: prolongate with the network attached by     */
                             /* mm_hierarchy_set_net (single-graph layouts)    */
-  int32_t reserved[5];
+  int32_t leaf_size;        /* Barnes-Hut: a cell with at most this many      */
+                            /* points is a leaf; an opened leaf is summed     */
+                            /* exactly (1 = single-point leaves; 0 = 1)       */
+  int32_t reserved[4];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -113,8 +115,8 @@ __device__ __forceinline__ void bsum3(float a, float b, float c, double* red, do
     if (prof && threadIdx.x == 0) prof[i] = clock64();       \
   } while (0)
 
-__device__ void build_tree(SmallSmem& s, int n, float theta, float4* root_sh, double* red,
-                           long long* prof) {
+__device__ void build_tree(SmallSmem& s, int n, float theta, int leaf, float4* root_sh,
+                           double* red, long long* prof) {
   const float2* x = s.xv;
   const int tid = threadIdx.x;
   // bounding square
@@ -280,6 +282,8 @@ __device__ void build_tree(SmallSmem& s, int n, float theta, float4* root_sh, do
       first = s_resolve(s, n, s.left[id]);
     }
     const int a = s.lo[id], b = s.hi[id];
+    // a cell of at most `leaf` points is a leaf: opened, it is summed exactly
+    if (b - a + 1 <= leaf) first = -1;
     const float cnt = (float)(b - a + 1);
     const float4 pa = s.P[a], pb = s.P[b + 1];
     const float2 dx = ff_add(make_float2(pb.x, pb.z), make_float2(-pa.x, -pa.z));
@@ -292,10 +296,12 @@ __device__ void build_tree(SmallSmem& s, int n, float theta, float4* root_sh, do
   __syncthreads();
 }
 
-// The walk of the multi-kernel path over the shared-memory records.
-__device__ void walk(const SmallSmem& s, int n, float2* F, int* err) {
+// The walk over the shared-memory records.  Task t = the 32 sorted
+// positions [32t, 32t + 32); CTA `crank` of a cluster of `csize` takes the
+// tasks t = crank (mod csize), its warps take those round robin.
+__device__ void walk(const SmallSmem& s, int n, float2* F, int* err, int crank, int csize) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int task = warp; task * 32 < n; task += kT / 32) {
+  for (int task = crank + csize * warp; task * 32 < n; task += csize * (kT / 32)) {
     const int pos = task * 32 + lane;
     const bool valid = pos < n;
     const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
@@ -345,7 +351,25 @@ __device__ void walk(const SmallSmem& s, int n, float2* F, int* err) {
   }
 }
 
-__device__ __forceinline__ void run_level(const SmallArgs& a) {
+// Barrier over the CTAs of the cluster (a CTA barrier for a cluster of one)
+// with release/acquire semantics: global and shared memory written before it
+// by any thread of the cluster is visible to every thread after it.
+__device__ __forceinline__ void cluster_sync(int csize) {
+  if (csize == 1) {
+    __syncthreads();
+    return;
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One level's schedule on the `csize` CTAs of a cluster (csize = 1: one
+// CTA).  Every CTA stages all positions and builds the same tree; CTA crank
+// walks and updates the vertices of its tasks, writing their new positions
+// and per-vertex partial sums to global memory; CTA 0 reduces the partials
+// in vertex order (the same order for every cluster size, so the schedule's
+// decisions do not depend on it) and takes the schedule step.
+__device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csize) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& s = *reinterpret_cast<SmallSmem*>(smem_raw);
   __shared__ double red[96];
@@ -356,23 +380,29 @@ __device__ __forceinline__ void run_level(const SmallArgs& a) {
   float2* F = s.F;
   for (int i = tid; i <= n; i += kT) s.sp[i] = a.sp[i];
   for (int i = tid; i < n; i += kT) s.rho[i] = a.rho[i];
+  const int nt = (n + 31) / 32;                                // tasks
+  const int mine = crank < nt ? ((nt - 1 - crank) / csize + 1) * 32 : 0;  // my positions
   for (int sweep = 0;; ++sweep) {
     if (tid == 0) {
-      sh_parity = a.st->parity;
-      sh_alpha = (float)a.st->alpha;
-      if (sweep == 0 && a.prof) a.prof[0] = clock64();
+      // written by CTA 0 of this cluster (or an earlier kernel): read at L2
+      sh_parity = __ldcg(&a.st->parity);
+      sh_alpha = (float)__ldcg(&a.st->alpha);
+      if (sweep == 0 && a.prof && crank == 0) a.prof[0] = clock64();
     }
     __syncthreads();
     const float2* xg = sh_parity ? a.b1 : a.b0;
     float2* xo = sh_parity ? a.b0 : a.b1;
     const float alpha = sh_alpha;
-    for (int i = tid; i < n; i += kT) s.xv[i] = xg[i];
+    for (int i = tid; i < n; i += kT) s.xv[i] = __ldcg(&xg[i]);
     __syncthreads();
     const float2* x = s.xv;
-    long long* prof = sweep == 0 ? a.prof : nullptr;
+    long long* prof = (sweep == 0 && crank == 0) ? a.prof : nullptr;
     MM_STAMP(1);
     if (a.exact) {
-      for (int u = tid; u < n; u += kT) {
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int task = crank + csize * warp; task * 32 < n; task += csize * (kT / 32)) {
+        const int u = task * 32 + lane;
+        if (u >= n) continue;
         const float2 xu = x[u];
         float fx = 0.f, fy = 0.f;
         for (int k = 0; k < n; ++k) {
@@ -385,23 +415,25 @@ __device__ __forceinline__ void run_level(const SmallArgs& a) {
         F[u] = make_float2(fx, fy);
       }
     } else {
-      build_tree(s, n, a.theta, &root, red, prof);
+      build_tree(s, n, a.theta, a.leaf, &root, red, prof);
       MM_STAMP(6);
-      walk(s, n, F, a.err);
+      walk(s, n, F, a.err, crank, csize);
     }
     __syncthreads();
     MM_STAMP(7);
-    // Eq. 2 over S: G lanes per row (G = a.lanes, a power of two <= 32),
-    // positions, row pointers and rho from shared memory; FP32 partials
-    float psdx = 0.f, psx = 0.f, psst = 0.f;
+    // Eq. 2 over S for my positions: G lanes per row (G = a.lanes, a power
+    // of two <= 32), positions, row pointers and rho from shared memory
     {
       const int G = a.lanes;
       const int lg = tid & (G - 1);
-      for (int base = 0; base < n; base += kT / G) {
-        const int u = base + tid / G;
+      for (int base = 0; base < mine; base += kT / G) {
+        const int j = base + tid / G;
+        const int pos = (crank + csize * (j >> 5)) * 32 + (j & 31);
+        const bool ok = j < mine && pos < n;
+        const int u = ok ? (a.exact ? pos : (int)s.vals[pos]) : 0;
         float gx = 0.f, gy = 0.f, rx = 0.f, ry = 0.f, st = 0.f;
         float2 xu = make_float2(0.f, 0.f);
-        if (u < n) {
+        if (ok) {
           xu = x[u];
           const int e1 = s.sp[u + 1];
 #pragma unroll 4
@@ -430,40 +462,66 @@ __device__ __forceinline__ void run_level(const SmallArgs& a) {
           ry += __shfl_xor_sync(0xffffffffu, ry, o);
           st += __shfl_xor_sync(0xffffffffu, st, o);
         }
-        if (u < n && lg == 0) {
+        if (ok && lg == 0) {
           const float2 f = F[u];
           const float r = s.rho[u];
           const float nx = (gx + alpha * (f.x - rx)) / r;
           const float ny = (gy + alpha * (f.y - ry)) / r;
           xo[u] = make_float2(nx, ny);
           const float ddx = nx - xu.x, ddy = ny - xu.y;
-          psdx = fmaf(ddx, ddx, fmaf(ddy, ddy, psdx));
-          psx = fmaf(xu.x, xu.x, fmaf(xu.y, xu.y, psx));
-          psst = fmaf(0.5f, st, psst);
+          a.part[u] = make_float4(fmaf(ddx, ddx, ddy * ddy), fmaf(xu.x, xu.x, xu.y * xu.y),
+                                  0.5f * st, 0.f);
         }
       }
     }
-    double tot[3];
-    bsum3(psdx, psx, psst, red, tot);
+    cluster_sync(csize);  // every new position and partial is written
     MM_STAMP(8);
-    if (tid == 0) {
-      const bool done =
-          schedule_step(a.st, a.sched, tot[0], tot[1], tot[2], a.trace, a.trace_cap, a.lsw);
-      sh_done = (done || sweep + 1 >= a.max_sweeps) ? 1 : 0;
+    if (crank == 0) {
+      float psdx = 0.f, psx = 0.f, psst = 0.f;
+      for (int u = tid; u < n; u += kT) {
+        const float4 q = __ldcg(&a.part[u]);
+        psdx += q.x;
+        psx += q.y;
+        psst += q.z;
+      }
+      double tot[3];
+      bsum3(psdx, psx, psst, red, tot);
+      if (tid == 0)
+        schedule_step(a.st, a.sched, tot[0], tot[1], tot[2], a.trace, a.trace_cap, a.lsw);
     }
+    cluster_sync(csize);  // the schedule state is updated
+    if (tid == 0) sh_done = (__ldcg(&a.st->done) != 0 || sweep + 1 >= a.max_sweeps) ? 1 : 0;
     __syncthreads();
     MM_STAMP(9);
     if (sh_done) break;
   }
 }
 
-__global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) { run_level(a); }
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// One level on one cluster (the grid is one cluster; a plain launch is a
+// cluster of one CTA).
+__global__ void __launch_bounds__(kT, 1) small_level_kernel(SmallArgs a) {
+  run_level(a, (int)cluster_rank(), (int)cluster_size());
+}
 
 // Batched form: CTA b runs the level described by args[b] (one graph each).
 __global__ void __launch_bounds__(kT, 1) small_level_batch_kernel(const SmallArgs* args) {
   const SmallArgs a = args[blockIdx.x];
-  run_level(a);
+  run_level(a, 0, 1);
 }
+
+int g_max_cluster = 0;  // largest cluster the fused kernel can be launched with
 
 }  // namespace
 
@@ -471,11 +529,42 @@ static_assert(sizeof(SmallSmem) + 1024 <= 227 * 1024, "fused level kernel exceed
 
 size_t small_level_smem() { return sizeof(SmallSmem); }
 
+int small_level_max_cluster() { return g_max_cluster > 0 ? g_max_cluster : 1; }
+
 mm_status small_level_setup() {
   MM_CK(cudaFuncSetAttribute(small_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmallSmem)));
   MM_CK(cudaFuncSetAttribute(small_level_batch_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmallSmem)));
+  if (g_max_cluster == 0) {
+    // 16 CTAs (one per SM: the shared memory allows one) if a GPC can hold
+    // such a cluster, else the portable 8
+    int best = 1;
+    if (cudaFuncSetAttribute(small_level_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) == cudaSuccess) {
+      for (int c : {16, 8, 4, 2}) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = c;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kT);
+        cfg.dynamicSmemBytes = sizeof(SmallSmem);
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, small_level_kernel, &cfg) == cudaSuccess &&
+            clusters > 0) {
+          best = c;
+          break;
+        }
+      }
+    }
+    cudaGetLastError();  // a refused query leaves no error behind
+    g_max_cluster = best;
+  }
   return MM_OK;
 }
 
@@ -491,7 +580,24 @@ mm_status small_level(const SmallArgs& a, cudaStream_t s) {
     set_error("fused level kernel takes 1..%d vertices, got %d", kSmallMaxN, a.n);
     return MM_ERR_INVALID_ARG;
   }
-  small_level_kernel<<<1, kT, sizeof(SmallSmem), s>>>(a);
+  const int c = std::max(1, std::min(a.cluster, small_level_max_cluster()));
+  if (c == 1) {
+    small_level_kernel<<<1, kT, sizeof(SmallSmem), s>>>(a);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = c;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kT);
+    cfg.dynamicSmemBytes = sizeof(SmallSmem);
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    MM_CK(cudaLaunchKernelEx(&cfg, small_level_kernel, a));
+  }
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

@@ -421,7 +421,7 @@ __device__ __forceinline__ int escape_of(const TreeView& t, int h) {
 }
 
 __device__ void write_record(const TreeView& t, int id, double2 sum, float side, float theta,
-                             float4* nodeA, int4* nodeB) {
+                             int leaf, float4* nodeA, int4* nodeB) {
   const int n = t.n;
   if (id >= n - 1) {  // leaf j
     const int j = id - (n - 1);
@@ -443,6 +443,8 @@ __device__ void write_record(const TreeView& t, int id, double2 sum, float side,
     first = resolve(t, t.left[id]);
   }
   const int a = t.lo[id], b = t.hi[id];
+  // a cell of at most `leaf` points is a leaf: opened, it is summed exactly
+  if (b - a + 1 <= leaf) first = -1;
   const float cnt = (float)(b - a + 1);
   const float w = ldexpf(side, -depth);
   const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
@@ -465,8 +467,8 @@ __device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
 __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const double2* __restrict__ incl,
                                const double2* __restrict__ tile_off,
-                               const float4* __restrict__ root, float theta, float4* nodeA,
-                               int4* nodeB) {
+                               const float4* __restrict__ root, float theta, int leaf,
+                               float4* nodeA, int4* nodeB) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
   if (id >= 2 * n - 1) return;
@@ -479,7 +481,7 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
     const double2 b = prefix_at(incl, tile_off, t.hi[id] + 1);
     sum = make_double2(b.x - a.x, b.y - a.y);
   }
-  write_record(t, id, sum, root->z, theta, nodeA, nodeB);
+  write_record(t, id, sum, root->z, theta, leaf, nodeA, nodeB);
 }
 
 // Guards: node ids must stay in [0, 2n-1) and a walk visits each node at
@@ -633,7 +635,8 @@ void tree_ws_free(TreeWS& ws) {
   ws = TreeWS();
 }
 
-mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s, cudaEvent_t* ev) {
+mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
+                   cudaEvent_t* ev) {
   if (n <= 0) return MM_OK;
   if (n > ws.cap) {
     set_error("tree workspace holds %lld vertices, level has %d", (long long)ws.cap, n);
@@ -667,7 +670,8 @@ mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s, cudaE
   mark(4);
   TreeView tv{n, ws.lo, ws.hi, ws.left, ws.right, ws.delta, ws.owner, ws.parent};
   records_kernel<<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(tv, ws.xs, ws.incl, ws.tile_sum,
-                                                          ws.root, theta, ws.nodeA, ws.nodeB);
+                                                          ws.root, theta, leaf, ws.nodeA,
+                                                          ws.nodeB);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;

@@ -42,6 +42,7 @@ struct mm_hierarchy {
   double* partials = nullptr;
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
+  float4* spart = nullptr;           // [kSmallMaxN] fused-level partial sums
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
   int32_t* lsw = nullptr;            // [MM_MAX_LEVELS] sweeps per level
   float* trace = nullptr;
@@ -139,7 +140,8 @@ mm_status check_params(const mm_params* p) {
   if (!(p->theta >= 0.f) || p->coarsest_n < 1 || !(p->f > 0.f) || !(p->b > 1.f) ||
       p->lp_rounds < 0 || p->iters_per_alpha < 1 || p->max_iters_at_min < 1 ||
       !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
-      p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS) {
+      p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS || p->leaf_size < 0 ||
+      p->leaf_size > kMaxLeaf) {
     set_error("parameter out of range");
     return MM_ERR_INVALID_ARG;
   }
@@ -236,6 +238,7 @@ SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, Sch
   a.rho = L.rho;
   a.exact = exact ? 1 : 0;
   a.theta = h->p.theta;
+  a.leaf = leaf_of(h->p);
   a.b0 = h->xb[0];
   a.b1 = h->xb[1];
   a.st = st;
@@ -245,6 +248,10 @@ SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, Sch
   a.lsw = lsw;
   a.max_sweeps = max_sweeps;
   a.lanes = L.lanes;
+  // about 128 vertices per CTA: the walk of 4 tasks per SM hides the
+  // shared-memory latency, the tree build is repeated on every CTA
+  a.cluster = std::max(1, std::min(16, (L.n + 127) / 128));
+  a.part = h->spart;
   a.err = h->tree.err;
   a.prof = nullptr;
   return a;
@@ -258,7 +265,7 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   if (exact) {
     MM_TRY(exact_repulsion(x, L.n, h->F, s));
   } else {
-    MM_TRY(bh_build(x, L.n, h->p.theta, h->tree, s));
+    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                        nullptr, s));
   }
@@ -630,6 +637,7 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMalloc(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks));
   MM_CK(cudaMalloc(&h->state, sizeof(SweepState)));
   MM_CK(cudaMalloc(&h->sstate, sizeof(SweepState)));
+  MM_CK(cudaMalloc(&h->spart, sizeof(float4) * (size_t)kSmallMaxN));
   MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
   MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
   MM_CK(cudaMalloc(&h->zero, sizeof(int32_t)));
@@ -1151,7 +1159,7 @@ mm_status tune_levels(mm_hierarchy* h, cudaStream_t s) {
     fill_uniform<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, sqrtf((float)L.n), 12345u, h->xb[0]);
     XSel x{h->xb[0], h->xb[1], h->zero};
     set_state<<<1, 1, 0, s>>>(h->sstate, 0.008);
-    MM_TRY(bh_build(x, L.n, h->p.theta, h->tree, s));
+    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s));
     double best = 1e30;
     int best_lanes = L.lanes;
     const int keep = L.lanes;
@@ -1314,6 +1322,7 @@ void mm_default_params(mm_params* p) {
   p->gather_lanes = 0;
   p->heavy_degree = 0;
   p->traverse_warps = 0;
+  p->leaf_size = 1;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1375,7 +1384,7 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   cudaDeviceSynchronize();
   for (Level& L : h->levels) free_level(L);
   tree_ws_free(h->tree);
-  void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate,
+  void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart,
                   h->zero, h->lsw, h->trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1488,7 +1497,7 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   const int n = h->levels[level].n;
   XSel xs{(const float2*)x, (const float2*)x, h->zero};
   if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
-  MM_TRY(bh_build(xs, n, theta, h->tree, s));
+  MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s));
   MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s));
   return tree_error(h, s);
 }
@@ -1589,7 +1598,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
       for (int i = 1; i <= 5; ++i) cudaEventRecord(ev[i], s);
       st = exact_repulsion(xs, L.n, h->F, s);
     } else {
-      st = bh_build(xs, L.n, h->p.theta, h->tree, s, ev);
+      st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev);
       if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, nullptr, s);
     }
     cudaEventRecord(ev[6], s);
@@ -1610,7 +1619,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     }
   }
   if (st == MM_OK && !exact && work) {
-    st = bh_build(xs, L.n, h->p.theta, h->tree, s);
+    st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s);
     if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, cnt, s);
   }
   unsigned long long hc[2] = {0, 0};

@@ -207,7 +207,8 @@ void tree_ws_free(TreeWS& ws);
 // digit histograms, four look-back sort passes, radix tree with FP64 prefix
 // sums, node records).
 // ev (nullable, 6 events) records the stage boundaries for profiling.
-mm_status bh_build(XSel x, int n, float theta, TreeWS& ws, cudaStream_t s,
+// leaf: cells with at most `leaf` points become leaves (1..kMaxLeaf).
+mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
                    cudaEvent_t* ev = nullptr);
 // Warp-synchronous stackless walk: F[v] = sum over accepted cells / leaves.
 mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
@@ -243,8 +244,14 @@ mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s);
 constexpr int kSmallMaxN = 2048;     // largest level the single-CTA kernel takes
 constexpr int kSmallThreads = 1024;
 
+constexpr int kMaxLeaf = 64;  // largest Barnes-Hut leaf bucket
+
+// Leaf size of a parameter set (0 reads as 1).
+inline int leaf_of(const mm_params& p) { return p.leaf_size > 0 ? p.leaf_size : 1; }
+
 struct SmallArgs {
   int n;
+  int leaf;        // Barnes-Hut leaf bucket size
   const int32_t* sp;
   const SEnt* S;
   const float* rho;
@@ -259,11 +266,14 @@ struct SmallArgs {
   int* lsw;
   int max_sweeps;
   int lanes;       // lanes per S row in the update (power of two <= 32)
+  int cluster;     // CTAs that share the level (single-level launches)
+  float4* part;    // [kSmallMaxN] per-vertex partial sums (device scratch)
   int* err;
   long long* prof; // nullable: clock64 stamps of the first sweep's phases [10]
 };
 size_t small_level_smem();
 mm_status small_level_setup();
+int small_level_max_cluster();
 // Runs sweeps of one level in one CTA until the schedule ends the level or
 // max_sweeps sweeps are done; reads buffer [st->parity], flips it per sweep.
 mm_status small_level(const SmallArgs& a, cudaStream_t s);

@@ -162,7 +162,7 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   MM_CK(cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), s));
   XSel xs{(const float2*)x, (const float2*)x, (const int32_t*)(b + c.zero)};
-  MM_TRY(bh_build(xs, n, theta, ws, s));
+  MM_TRY(bh_build(xs, n, theta, 1, ws, s));
   MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s));
   int err = 0;
   MM_CK(cudaMemcpyAsync(&err, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
         ("max_stalls", ctypes.c_int32), ("gather_lanes", ctypes.c_int32),
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
         ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("leaf_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
     ]
 
 

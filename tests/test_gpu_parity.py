@@ -10,7 +10,9 @@ Tolerances:
     acceptance-boundary ties (allowed on <= 1% of vertices); the GPU error
     against the exact sum stays within the 2-D multipole remainder bound
     2 theta^2 sum_v 1/|x_u - x_v| and, in RMS, within 5% of the oracle's own
-    Barnes-Hut error;
+    Barnes-Hut error.  With leaf buckets (leaf_size > 1) an opened small
+    cell is summed exactly where the oracle would open it further, so only
+    the two error bounds apply;
   * pair sets, contraction: exact integers; distances to FP32 rounding;
   * objective: relative 1e-5; final layouts: objective within 1%.
 """
@@ -99,17 +101,18 @@ def test_exact_repulsion_matches_oracle(mm, n_side):
 
 
 # ---------------------------------------------------------- Barnes-Hut ---
-def _bh_check(mm, x, theta):
+def _bh_check(mm, x, theta, leaf=1):
     n = len(x)
     rp, col = graphs.path(n)
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=1)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf)
     x64 = x.astype(np.float64)
     F = mm.repulsion(h, 0, cu(x), theta).cpu().numpy().astype(np.float64)
     Fo = oracle.repulsion_bh(x64, theta)
     Fe = oracle.repulsion_exact(x64)
     mag = inv_dist_sum(x)
     same = np.all(np.abs(F - Fo) <= 2e-4 * mag[:, None], axis=1)
-    assert same.mean() >= 0.99, same.mean()
+    if leaf == 1:
+        assert same.mean() >= 0.99, same.mean()
     err_g = np.sqrt(((F - Fe) ** 2).sum(1))
     err_o = np.sqrt(((Fo - Fe) ** 2).sum(1))
     assert np.all(err_g <= 2 * theta ** 2 * mag * (1 + 1e-3) + 2e-4 * mag)
@@ -129,6 +132,23 @@ def test_bh_matches_oracle_clustered_and_duplicates(mm):
                    np.repeat([[7.0, -3.0]], 40, axis=0),       # exact duplicates (bucket)
                    rng.random((257, 2)) * 60 - 10])
     _bh_check(mm, f32(x), 0.5)
+
+
+@pytest.mark.parametrize("leaf", [8, 16])
+def test_bh_leaf_buckets_within_oracle_error(mm, leaf):
+    x = f32(graphs.uniform_positions(3001, 77, 0.0, 50.0))
+    _bh_check(mm, x, 0.5, leaf)
+    rng = np.random.default_rng(6)
+    xc = np.vstack([rng.normal(0, 1, (1500, 2)), np.repeat([[7.0, -3.0]], 40, axis=0),
+                    rng.random((257, 2)) * 60 - 10])
+    _bh_check(mm, f32(xc), 0.5, leaf)
+    # theta = 0 opens every cell: the exact sum
+    n = len(x)
+    rp, col = graphs.path(n)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf)
+    F = mm.repulsion(h, 0, cu(x), 0.0).cpu().numpy()
+    ref = oracle.repulsion_exact(x.astype(np.float64))
+    assert np.all(np.abs(F - ref) <= 2e-4 * inv_dist_sum(x)[:, None] + 1e-12)
 
 
 def test_bh_small_sizes(mm):
