@@ -83,7 +83,11 @@ typedef struct mm_params {
   int32_t leaf_size;        /* Barnes-Hut: a cell with at most this many      */
                             /* points is a leaf; an opened leaf is summed     */
                             /* exactly (1 = single-point leaves; 0 = 1)       */
-  int32_t reserved[4];
+  int32_t bh_group;         /* Barnes-Hut acceptance: 0 = per point (the      */
+                            /* classic test), 1 = per group of 32 Morton-     */
+                            /* consecutive points (a cell far from all of     */
+                            /* them; refines each point's per-point sum)      */
+  int32_t reserved[3];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */
@@ -261,7 +265,8 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
  *   n      number of points, 1 <= n <= 32768 (larger n: MM_ERR_INVALID_ARG)
  *   x      device [2n] positions; F_out device [2n] receives
  *          F_u ~ sum_{v != u} r(u,v) with opening parameter theta >= 0
- *          (theta = 0: exact through the tree)
+ *          (theta = 0: exact through the tree), with the walk of the
+ *          default parameters (leaf_size, bh_group of mm_default_params)
  * The first call on a device (with that device current) resolves the
  * array's address; make it before any stream capture.  All calls share the
  * array: calls whose GPU work overlaps race and must be serialised by the

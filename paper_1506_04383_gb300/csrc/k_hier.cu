@@ -773,7 +773,18 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
     return MM_ERR_INVALID_ARG;
   }
   L.lanes = lanes;
-  L.walk_warps = p.traverse_warps > 0 ? p.traverse_warps : (L.n >= 20000 ? 16 : 8);
+  if (p.traverse_warps > 0) {
+    L.walk_warps = p.traverse_warps;
+  } else if (p.bh_group) {
+    // warps sharing one task: about 24 warps per SM in all (measured: more
+    // helpers per task only add seed overhead once the SMs are full)
+    const int64_t tasks = std::max<int64_t>(1, (L.n + 31) / 32);
+    int w = 1;
+    while (w < 16 && (int64_t)w * tasks < (int64_t)24 * kSMs) w <<= 1;
+    L.walk_warps = w;
+  } else {
+    L.walk_warps = L.n >= 20000 ? 16 : 8;  // per-point walk: warps per block
+  }
   L.heavy_degree = p.heavy_degree > 0 ? p.heavy_degree : std::max(512, 32 * lanes);
   Tmp cnt;
   MM_TRY(tmp_alloc(cnt, 2 * sizeof(int32_t), s));

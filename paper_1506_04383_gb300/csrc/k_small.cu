@@ -296,7 +296,56 @@ __device__ void build_tree(SmallSmem& s, int n, float theta, int leaf, float4* r
   __syncthreads();
 }
 
-// The walk over the shared-memory records.  Task t = the 32 sorted
+// Group acceptance over the shared-memory records: the task's 32 points
+// accept a cell only when all of them pass the per-point test (the same rule
+// as the multi-kernel group walk); the walk is uniform across the warp.
+__device__ void walk_group(const SmallSmem& s, int n, float2* F, int* err, int crank,
+                           int csize) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int task = crank + csize * warp; task * 32 < n; task += csize * (kT / 32)) {
+    const int pos = task * 32 + lane;
+    const bool valid = pos < n;
+    const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
+    int cur = n > 1 ? 0 : -1;
+    int budget = 2 * n + 2;
+    float fx = 0.f, fy = 0.f;
+    while (cur >= 0) {
+      if (cur >= 2 * n - 1 || --budget < 0) {
+        if (lane == 0) atomicOr(err, 1);
+        break;
+      }
+      const float4 A = s.nodeA[cur];
+      const short4 B = s.nodeB[cur];
+      const float dx = xu.x - A.x, dy = xu.y - A.y;
+      const float q = fmaf(dx, dx, dy * dy);
+      const bool far = !valid || ((pos < B.z || pos >= B.w) && q > A.z);
+      if (__all_sync(0xffffffffu, far)) {
+        const float sc = __fdividef(A.w, q);
+        fx = fmaf(sc, dx, fx);
+        fy = fmaf(sc, dy, fy);
+        cur = B.y;
+      } else if (B.x < 0) {
+        const int pb = max((int)B.z, 0), pe = min((int)B.w, n);
+        for (int p = pb; p < pe; ++p) {
+          const float2 xv = s.xs[p];
+          const float ex = xu.x - xv.x, ey = xu.y - xv.y;
+          const float eq = fmaf(ex, ex, ey * ey);
+          if (p != pos && eq > 0.f) {
+            const float inv = __fdividef(1.f, eq);
+            fx = fmaf(inv, ex, fx);
+            fy = fmaf(inv, ey, fy);
+          }
+        }
+        cur = B.y;
+      } else {
+        cur = B.x;
+      }
+    }
+    if (valid) F[s.vals[pos]] = make_float2(fx, fy);
+  }
+}
+
+// The per-point walk over the shared-memory records.  Task t = the 32 sorted
 // positions [32t, 32t + 32); CTA `crank` of a cluster of `csize` takes the
 // tasks t = crank (mod csize), its warps take those round robin.
 __device__ void walk(const SmallSmem& s, int n, float2* F, int* err, int crank, int csize) {
@@ -417,7 +466,10 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
     } else {
       build_tree(s, n, a.theta, a.leaf, &root, red, prof);
       MM_STAMP(6);
-      walk(s, n, F, a.err, crank, csize);
+      if (a.group)
+        walk_group(s, n, F, a.err, crank, csize);
+      else
+        walk(s, n, F, a.err, crank, csize);
     }
     __syncthreads();
     MM_STAMP(7);

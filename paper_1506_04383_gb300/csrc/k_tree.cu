@@ -560,6 +560,135 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
   }
 }
 
+constexpr int kSeedPoints = 256;  // a seed subtree holds at most this many points
+
+// Group acceptance: the 32 Morton-consecutive points of a task walk
+// together and accept a cell only when every one of them passes the
+// per-point test (w / |x_u - c| < theta, u not inside).  A per-point
+// accepted cell is then either accepted too or opened into children, so each
+// point's sum refines its per-point Barnes-Hut sum and the error is at most
+// the per-point walk's.  The walk is uniform across the warp: one vote per
+// cell, no wait markers, no divergent control flow.
+//
+// W warps share one task (a block holds tpb tasks).  The task's first warp
+// walks the tree; an opened cell of at most `seed` points is not entered but
+// recorded as a seed (up to kSeedMax), and the seeds' subtrees are then
+// walked by the task's W warps, seed j by warp j mod W.  Every cell gets the
+// same decision as in a single walk; the W partial sums are added in warp
+// order, so results are reproducible.  W = 1 is the plain single-warp walk.
+constexpr int kSeedMax = 128;
+constexpr int kGroupMaxWarps = 16;  // warps per block
+
+struct GroupShared {
+  int seeds[kGroupMaxWarps][kSeedMax];  // per task slot
+  int nseeds[kGroupMaxWarps];
+  float2 part[kGroupMaxWarps][32];      // per warp
+};
+
+template <bool kCount>
+__global__ void traverse_group_kernel(int n, int W, int seed, const float2* __restrict__ xs,
+                                      const int32_t* __restrict__ vals,
+                                      const float4* __restrict__ nodeA,
+                                      const int4* __restrict__ nodeB, float2* __restrict__ F,
+                                      unsigned long long* counters, int* err) {
+  __shared__ GroupShared sh;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int slot = wb / W, w = wb % W;  // task slot in the block, warp in the task
+  const int tpb = (blockDim.x >> 5) / W;
+  const int64_t task = (int64_t)blockIdx.x * tpb + slot;
+  const bool live = task * 32 < n;  // a whole warp is live or not
+  const int pos = (int)(task * 32) + lane;
+  const bool valid = live && pos < n;
+  const float2 xu = valid ? xs[pos] : make_float2(0.f, 0.f);
+  int* seeds = sh.seeds[slot];
+  int& nseeds = sh.nseeds[slot];
+  float fx = 0.f, fy = 0.f;
+  unsigned visits = 0, inter = 0;
+  const int nodes = 2 * n - 1;
+  int budget = 2 * n + 2;
+  bool broken = false;
+  // One vote walk from `cur` until `stop`; seeds are recorded when `seeding`.
+  auto walk = [&](int cur, int stop, bool seeding) {
+    while (cur != stop && cur >= 0) {
+      if (cur >= nodes || --budget < 0) {
+        broken = true;
+        return;
+      }
+      const float4 A = __ldg(&nodeA[cur]);
+      const int4 B = __ldg(&nodeB[cur]);
+      if (kCount) ++visits;
+      const float dx = xu.x - A.x, dy = xu.y - A.y;
+      const float q = fmaf(dx, dx, dy * dy);
+      const bool far = !valid || ((pos < B.z || pos >= B.w) && q > A.z);
+      if (__all_sync(0xffffffffu, far)) {
+        const float sc = __fdividef(A.w, q);
+        fx = fmaf(sc, dx, fx);
+        fy = fmaf(sc, dy, fy);
+        if (kCount) ++inter;
+        cur = B.y;
+      } else if (B.x < 0) {
+        const int pb = max(B.z, 0), pe = min(B.w, n);
+#pragma unroll 4
+        for (int p = pb; p < pe; ++p) {
+          const float2 xv = xs[p];
+          const float ex = xu.x - xv.x, ey = xu.y - xv.y;
+          const float eq = fmaf(ex, ex, ey * ey);
+          if (p != pos && eq > 0.f) {
+            const float inv = __fdividef(1.f, eq);
+            fx = fmaf(inv, ex, fx);
+            fy = fmaf(inv, ey, fy);
+          }
+          if (kCount) ++inter;
+        }
+        cur = B.y;
+      } else if (seeding && B.w - B.z <= seed && nseeds < kSeedMax) {
+        if (lane == 0) seeds[nseeds] = cur;
+        __syncwarp();
+        if (lane == 0) ++nseeds;
+        __syncwarp();
+        cur = B.y;
+      } else {
+        cur = B.x;
+      }
+    }
+  };
+  if (w == 0 && live) {
+    if (lane == 0) nseeds = 0;
+    __syncwarp();
+    walk(n > 1 ? 0 : -1, -1, W > 1 && seed > 0);
+  }
+  if (W > 1) {
+    __syncthreads();
+    const int ns = live ? nseeds : 0;
+    for (int j = w; j < ns && !broken; j += W) {
+      const int c = seeds[j];
+      walk(c, __ldg(&nodeB[c]).y, false);
+    }
+    sh.part[wb][lane] = make_float2(fx, fy);
+    __syncthreads();
+    if (w == 0) {
+      float sx = 0.f, sy = 0.f;
+      for (int k = 0; k < W; ++k) {
+        sx += sh.part[slot * W + k][lane].x;
+        sy += sh.part[slot * W + k][lane].y;
+      }
+      fx = sx;
+      fy = sy;
+    }
+  }
+  if (broken && lane == 0) atomicOr(err, 1);
+  if (w == 0 && valid) F[vals[pos]] = make_float2(fx, fy);
+  if (kCount) {
+    unsigned tot = valid ? inter : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && live) {
+      atomicAdd(&counters[0], (unsigned long long)visits);
+      atomicAdd(&counters[1], (unsigned long long)tot);
+    }
+  }
+}
+
 constexpr int kExactThreads = 256;
 
 __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, float2* F) {
@@ -678,17 +807,31 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
 }
 
 mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
-                      unsigned long long* counters, cudaStream_t s) {
+                      unsigned long long* counters, cudaStream_t s, bool group) {
   if (n <= 0) return MM_OK;
   const int wpb = warps_per_block > 0 ? warps_per_block : 4;
   const int warps = ceil_div(n, 32);
   const int blocks = ceil_div(warps, wpb);
-  if (counters)
+  if (group) {
+    // W warps share a task of 32 points; blocks of at least 8 warps
+    const int tasks = ceil_div(n, 32);
+    const int W = std::max(1, std::min(kGroupMaxWarps, wpb));
+    const int tpb = std::max(1, 8 / W);
+    const int seed = W > 1 ? kSeedPoints : 0;
+    const int blocks2 = ceil_div(tasks, tpb);
+    if (counters)
+      traverse_group_kernel<true><<<blocks2, tpb * W * 32, 0, s>>>(
+          n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, counters, ws.err);
+    else
+      traverse_group_kernel<false><<<blocks2, tpb * W * 32, 0, s>>>(
+          n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, nullptr, ws.err);
+  } else if (counters) {
     traverse_kernel<true><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB,
                                                        F, counters, ws.err);
-  else
+  } else {
     traverse_kernel<false><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA,
                                                         ws.nodeB, F, nullptr, ws.err);
+  }
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

@@ -239,6 +239,7 @@ SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, Sch
   a.exact = exact ? 1 : 0;
   a.theta = h->p.theta;
   a.leaf = leaf_of(h->p);
+  a.group = group_of(h->p) ? 1 : 0;
   a.b0 = h->xb[0];
   a.b1 = h->xb[1];
   a.st = st;
@@ -267,7 +268,7 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   } else {
     MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
-                       nullptr, s));
+                       nullptr, s, group_of(h->p)));
   }
   MM_TRY(gather_update(L, x, h->F, st, h->partials, s));
   MM_TRY(controller(gather_blocks(L), h->partials, st, sp, trace, trace_cap, lsw, hnd, use_h, s));
@@ -1174,9 +1175,9 @@ mm_status tune_levels(mm_hierarchy* h, cudaStream_t s) {
     (void)keep;
     best = 1e30;
     int best_w = 4;
-    for (int w = 2; w <= 16; w <<= 1) {
+    for (int w = 1; w <= 16; w <<= 1) {
       double ms = 0;
-      MM_TRY(time_ms(s, 5, [&]() { return bh_traverse(L.n, h->tree, h->F, w, nullptr, s); }, &ms));
+      MM_TRY(time_ms(s, 5, [&]() { return bh_traverse(L.n, h->tree, h->F, w, nullptr, s, group_of(h->p)); }, &ms));
       if (ms < best) { best = ms; best_w = w; }
     }
     L.walk_warps = best_w;
@@ -1322,7 +1323,8 @@ void mm_default_params(mm_params* p) {
   p->gather_lanes = 0;
   p->heavy_degree = 0;
   p->traverse_warps = 0;
-  p->leaf_size = 1;
+  p->leaf_size = 16;
+  p->bh_group = 1;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1498,7 +1500,8 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   XSel xs{(const float2*)x, (const float2*)x, h->zero};
   if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
   MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s));
-  MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s));
+  MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s,
+                     group_of(h->p)));
   return tree_error(h, s);
 }
 
@@ -1599,7 +1602,9 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
       st = exact_repulsion(xs, L.n, h->F, s);
     } else {
       st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev);
-      if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, nullptr, s);
+      if (st == MM_OK)
+        st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
+                         nullptr, s, group_of(h->p));
     }
     cudaEventRecord(ev[6], s);
     if (st == MM_OK) st = gather_update(L, xs, h->F, h->sstate, h->partials, s);
@@ -1620,7 +1625,9 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
   }
   if (st == MM_OK && !exact && work) {
     st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s);
-    if (st == MM_OK) st = bh_traverse(L.n, h->tree, h->F, h->p.traverse_warps, cnt, s);
+    if (st == MM_OK)
+      st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
+                       cnt, s, group_of(h->p));
   }
   unsigned long long hc[2] = {0, 0};
   if (st == MM_OK) {

@@ -211,8 +211,16 @@ void tree_ws_free(TreeWS& ws);
 mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
                    cudaEvent_t* ev = nullptr);
 // Warp-synchronous stackless walk: F[v] = sum over accepted cells / leaves.
+// group = false: per-point acceptance (the oracle's Barnes-Hut); true: a
+// cell is accepted for a warp's 32 points together (refines every point's
+// per-point sum).
 mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
-                      unsigned long long* counters, cudaStream_t s);
+                      unsigned long long* counters, cudaStream_t s, bool group = false);
+
+constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
+
+// Group acceptance of a parameter set.
+inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
 // Tiled exact sum F[v] = sum_{u != v} r(v, u).
 mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
 
@@ -252,6 +260,7 @@ inline int leaf_of(const mm_params& p) { return p.leaf_size > 0 ? p.leaf_size : 
 struct SmallArgs {
   int n;
   int leaf;        // Barnes-Hut leaf bucket size
+  int group;       // Barnes-Hut group acceptance
   const int32_t* sp;
   const SEnt* S;
   const float* rho;

@@ -162,8 +162,12 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   MM_CK(cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), s));
   XSel xs{(const float2*)x, (const float2*)x, (const int32_t*)(b + c.zero)};
-  MM_TRY(bh_build(xs, n, theta, 1, ws, s));
-  MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s));
+  // the library's default walk (leaf buckets, group acceptance), as
+  // mm_repulsion on a hierarchy built with mm_default_params
+  mm_params d;
+  mm_default_params(&d);
+  MM_TRY(bh_build(xs, n, theta, leaf_of(d), ws, s));
+  MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s, group_of(d)));
   int err = 0;
   MM_CK(cudaMemcpyAsync(&err, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));

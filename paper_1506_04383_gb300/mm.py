@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
         ("max_stalls", ctypes.c_int32), ("gather_lanes", ctypes.c_int32),
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
         ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
-        ("leaf_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("leaf_size", ctypes.c_int32), ("bh_group", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

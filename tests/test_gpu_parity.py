@@ -56,6 +56,10 @@ def hier(mm, rp, col, **kw):
     return mm.build_hierarchy(cu(rp), cu(col), p), p
 
 
+# single-point leaves and per-point acceptance: the oracle's Barnes-Hut
+ORACLE_BH = dict(leaf_size=1, bh_group=0)
+
+
 def diameter(x):
     return float(np.ptp(np.asarray(x), axis=0).max())
 
@@ -101,17 +105,17 @@ def test_exact_repulsion_matches_oracle(mm, n_side):
 
 
 # ---------------------------------------------------------- Barnes-Hut ---
-def _bh_check(mm, x, theta, leaf=1):
+def _bh_check(mm, x, theta, leaf=1, group=0):
     n = len(x)
     rp, col = graphs.path(n)
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf, bh_group=group)
     x64 = x.astype(np.float64)
     F = mm.repulsion(h, 0, cu(x), theta).cpu().numpy().astype(np.float64)
     Fo = oracle.repulsion_bh(x64, theta)
     Fe = oracle.repulsion_exact(x64)
     mag = inv_dist_sum(x)
     same = np.all(np.abs(F - Fo) <= 2e-4 * mag[:, None], axis=1)
-    if leaf == 1:
+    if leaf == 1 and not group:
         assert same.mean() >= 0.99, same.mean()
     err_g = np.sqrt(((F - Fe) ** 2).sum(1))
     err_o = np.sqrt(((Fo - Fe) ** 2).sum(1))
@@ -145,10 +149,45 @@ def test_bh_leaf_buckets_within_oracle_error(mm, leaf):
     # theta = 0 opens every cell: the exact sum
     n = len(x)
     rp, col = graphs.path(n)
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf, bh_group=0)
     F = mm.repulsion(h, 0, cu(x), 0.0).cpu().numpy()
     ref = oracle.repulsion_exact(x.astype(np.float64))
     assert np.all(np.abs(F - ref) <= 2e-4 * inv_dist_sum(x)[:, None] + 1e-12)
+
+
+@pytest.mark.parametrize("leaf", [1, 16])
+def test_bh_group_acceptance_within_oracle_error(mm, leaf):
+    # a cell accepted for all 32 points of a warp passes every point's test:
+    # each point's sum refines its per-point Barnes-Hut sum
+    x = f32(graphs.uniform_positions(3001, 77, 0.0, 50.0))
+    _bh_check(mm, x, 0.5, leaf, group=1)
+    rng = np.random.default_rng(7)
+    xc = np.vstack([rng.normal(0, 1, (1500, 2)), rng.normal(30, 0.05, (700, 2)),
+                    np.repeat([[7.0, -3.0]], 40, axis=0), rng.random((257, 2)) * 60 - 10])
+    _bh_check(mm, f32(xc), 0.7, leaf, group=1)
+    n = len(x)
+    rp, col = graphs.path(n)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=leaf, bh_group=1)
+    F = mm.repulsion(h, 0, cu(x), 0.0).cpu().numpy()
+    ref = oracle.repulsion_exact(x.astype(np.float64))
+    assert np.all(np.abs(F - ref) <= 2e-4 * inv_dist_sum(x)[:, None] + 1e-12)
+
+
+@pytest.mark.parametrize("fused", [0, -1])
+def test_sweep_default_barnes_hut_within_oracle_error(mm, fused):
+    # default walk (leaf buckets of 16, group acceptance): one sweep is at
+    # least as close to the exact sweep as the oracle's Barnes-Hut sweep
+    rp, col, pts, _ = graphs.rgg(2000 if fused == 0 else 6000, 8.0, 31)
+    n = len(rp) - 1
+    x = f32(pts * 50.0)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, fused_max_n=fused)
+    xg, _ = mm.sweep(h, 0, 0.3, cu(x))
+    S = oracle.build_S(rp, col, 2)
+    xe, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 0)
+    xb, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
+    err_g = np.sqrt(((xg.cpu().numpy() - xe) ** 2).sum(1).mean())
+    err_o = np.sqrt(((xb - xe) ** 2).sum(1).mean())
+    assert err_g <= 1.05 * err_o + 1e-6 * diameter(xe), (err_g, err_o)
 
 
 def test_bh_small_sizes(mm):
@@ -185,7 +224,7 @@ def test_sweep_bh_matches_oracle(mm):
     rp, col, pts, _ = graphs.rgg(4000, 8.0, 21)
     n = len(rp) - 1
     x = f32(pts * 60.0)
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, **ORACLE_BH)
     xg, _ = mm.sweep(h, 0, 0.3, cu(x))
     S = oracle.build_S(rp, col, 2)
     xo, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
@@ -204,7 +243,7 @@ def test_sweep_bh_small_level_paths(mm, fused, n_pts):
     rp, col = graphs.csr_from_edges(n, np.concatenate([src, np.arange(n - 1)]),
                                     np.concatenate([col, np.arange(1, n)]))
     x = f32(pts * 40.0)
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, fused_max_n=fused)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, fused_max_n=fused, **ORACLE_BH)
     xg, st = mm.sweep(h, 0, 0.3, cu(x))
     S = oracle.build_S(rp, col, 2)
     xo, sto = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
@@ -240,7 +279,7 @@ def test_sweep_full_size_rgg_100k(mm):
     rp, col, pts, _ = graphs.rgg(100000, 8.0, 1506)
     n = len(rp) - 1
     x = f32(pts * math.sqrt(n))
-    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5)
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=2, theta=0.5, **ORACLE_BH)
     xg, _ = mm.sweep(h, 0, 0.3, cu(x))
     S = oracle.build_S(rp, col, 2)
     xo, _ = oracle.sweep(x.astype(np.float64), S, 0.3, 1, 0.5)
