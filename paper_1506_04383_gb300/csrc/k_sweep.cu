@@ -44,14 +44,24 @@ __device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const 
   a.st = fmaf(w * t, t, a.st);
 }
 
+// Bounding box accumulator (starts empty: min = +huge, max = -huge).
+struct Box {
+  float x0, y0, x1, y1;
+  __device__ Box() : x0(3.0e38f), y0(3.0e38f), x1(-3.0e38f), y1(-3.0e38f) {}
+  __device__ void add(float x, float y) {
+    x0 = fminf(x0, x); y0 = fminf(y0, y); x1 = fmaxf(x1, x); y1 = fmaxf(y1, y);
+  }
+};
+
 __device__ __forceinline__ void finish_vertex(int u, const RowAcc& a, float2 xu, float alpha,
                                               const float* rho, const float2* F, float2* xo,
-                                              float& s_dx, float& s_x, float& s_st) {
+                                              float& s_dx, float& s_x, float& s_st, Box& box) {
   const float2 f = F[u];
   const float r = rho[u];
   const float nx = (a.gx + alpha * (f.x - a.sx)) / r;
   const float ny = (a.gy + alpha * (f.y - a.sy)) / r;
   xo[u] = make_float2(nx, ny);
+  box.add(nx, ny);
   const float ddx = nx - xu.x, ddy = ny - xu.y;
   s_dx = fmaf(ddx, ddx, fmaf(ddy, ddy, s_dx));
   s_x = fmaf(xu.x, xu.x, fmaf(xu.y, xu.y, s_x));
@@ -99,18 +109,105 @@ __device__ __forceinline__ void block_reduce3d(double a, double b, double c, dou
   }
 }
 
+template <int kT>
+__device__ __forceinline__ float4 block_box(Box b) {
+  __shared__ float4 sh[kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    b.x0 = fminf(b.x0, __shfl_xor_sync(0xffffffffu, b.x0, o));
+    b.y0 = fminf(b.y0, __shfl_xor_sync(0xffffffffu, b.y0, o));
+    b.x1 = fmaxf(b.x1, __shfl_xor_sync(0xffffffffu, b.x1, o));
+    b.y1 = fmaxf(b.y1, __shfl_xor_sync(0xffffffffu, b.y1, o));
+  }
+  __syncthreads();
+  if (lane == 0) sh[warp] = make_float4(b.x0, b.y0, b.x1, b.y1);
+  __syncthreads();
+  float4 r = sh[0];
+  for (int w = 1; w < kT / 32; ++w) {
+    r.x = fminf(r.x, sh[w].x); r.y = fminf(r.y, sh[w].y);
+    r.z = fmaxf(r.z, sh[w].z); r.w = fmaxf(r.w, sh[w].w);
+  }
+  return r;
+}
+
+// End of an update launch: the block publishes its partial sums (and the
+// bounding box of the positions it wrote); with `epi` set, the last block to
+// arrive reduces all nparts partials in block order and takes the schedule
+// step (Sec. 3.2), and -- with a box buffer -- writes the next sweep's root
+// square, zeroes the sort state and starts a new look-back epoch, so the
+// next sweep needs no separate controller or bounding-box launch.
+template <int kT>
+__device__ void update_tail(float s_dx, float s_x, float s_st, const Box& box, double* parts,
+                            int part_off, int nparts, int epi, const SweepEpilogue& ep) {
+  __shared__ double tot[3];
+  __shared__ bool last;
+  block_reduce3<kT>(s_dx, s_x, s_st, tot);
+  float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ep.box) bb = block_box<kT>(box);
+  if (threadIdx.x == 0) {
+    double* p = parts + 3 * (size_t)(part_off + blockIdx.x);
+    p[0] = tot[0];
+    p[1] = tot[1];
+    p[2] = tot[2];
+    if (ep.box) ep.box[part_off + blockIdx.x] = bb;
+    if (epi) {
+      __threadfence();
+      last = atomicAdd(ep.arrive, 1u) == gridDim.x - 1;
+    }
+  }
+  if (!epi) return;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0, b = 0, c = 0;
+  float4 r = make_float4(CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
+  for (int i = threadIdx.x; i < nparts; i += kT) {
+    a += __ldcg(&parts[3 * i]);
+    b += __ldcg(&parts[3 * i + 1]);
+    c += __ldcg(&parts[3 * i + 2]);
+    if (ep.box) {
+      const float4 q = __ldcg(&ep.box[i]);
+      r.x = fminf(r.x, q.x); r.y = fminf(r.y, q.y);
+      r.z = fmaxf(r.z, q.z); r.w = fmaxf(r.w, q.w);
+    }
+  }
+  __shared__ double out[3];
+  block_reduce3d<kT>(a, b, c, out);
+  if (ep.box) {
+    Box q;
+    q.x0 = r.x; q.y0 = r.y; q.x1 = r.z; q.y1 = r.w;
+    const float4 w = block_box<kT>(q);
+    for (int i = threadIdx.x; i < 4 * 256; i += kT) ep.hist[i] = 0u;
+    if (threadIdx.x < 4) ep.counters[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+      const float side = fmaxf(w.z - w.x, w.w - w.y);
+      *ep.root = make_float4(w.x, w.y, side, side > 0.f ? 65536.0f / side : 0.f);
+      ep.tree_ticket[0] = 0u;
+      ep.tree_ticket[1] += 1u;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const bool done = schedule_step(ep.st, ep.sp, out[0], out[1], out[2], ep.trace,
+                                    ep.trace_cap, ep.lsw);
+    if (ep.use_h) cudaGraphSetConditional(ep.h, done ? 0u : 1u);
+    *ep.arrive = 0u;
+  }
+}
+
 // G lanes per vertex; rows with more than `heavy` entries are skipped here.
 template <int G>
 __global__ void __launch_bounds__(kGatherThreads) gather_light(
     int n, const int32_t* __restrict__ sp, const SEnt* __restrict__ S,
     const float* __restrict__ rho, XSel xs, const float2* __restrict__ F,
-    const SweepState* st, int heavy, double* partials) {
+    const SweepState* st, int heavy, double* partials, int nparts, int epi, SweepEpilogue ep) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
   const float alpha = (float)st->alpha;
   constexpr int kGroups = kGatherThreads / G;
   const int g = threadIdx.x / G, lg = threadIdx.x % G;
   float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
+  Box box;
   for (int base = blockIdx.x * kGroups; base < n; base += gridDim.x * kGroups) {
     const int u = base + g;
     RowAcc a = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -134,21 +231,23 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
         a.st += __shfl_xor_sync(0xffffffffu, a.st, o);
       }
     }
-    if (mine && lg == 0) finish_vertex(u, a, xu, alpha, rho, F, xo, s_dx, s_x, s_st);
+    if (mine && lg == 0) finish_vertex(u, a, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
   }
-  block_reduce3<kGatherThreads>(s_dx, s_x, s_st, partials + 3 * (size_t)blockIdx.x);
+  update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, 0, nparts, epi, ep);
 }
 
 // One block per heavy row (power-law hubs).
 __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
     const int32_t* __restrict__ heavy_list, int n_heavy, const int32_t* __restrict__ sp,
     const SEnt* __restrict__ S, const float* __restrict__ rho, XSel xs,
-    const float2* __restrict__ F, const SweepState* st, double* partials) {
+    const float2* __restrict__ F, const SweepState* st, double* partials, int part_off,
+    int nparts, int epi, SweepEpilogue ep) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
   const float alpha = (float)st->alpha;
   __shared__ float red[5][kGatherThreads / 32];
   float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
+  Box box;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const int u = heavy_list[h];
@@ -174,11 +273,11 @@ __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
         t.gx += red[0][w]; t.gy += red[1][w]; t.sx += red[2][w];
         t.sy += red[3][w]; t.st += red[4][w];
       }
-      finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st);
+      finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
     }
     __syncthreads();
   }
-  block_reduce3<kGatherThreads>(s_dx, s_x, s_st, partials + 3 * (size_t)blockIdx.x);
+  update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, part_off, nparts, epi, ep);
 }
 
 constexpr int kCtlThreads = 256;
@@ -275,9 +374,9 @@ __global__ void copy_current_kernel(XSel xs, int n, float2* out) {
 
 template <int G>
 void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st, double* partials,
-                  int blocks, cudaStream_t s) {
+                  int blocks, int nparts, int epi, const SweepEpilogue& ep, cudaStream_t s) {
   gather_light<G><<<blocks, kGatherThreads, 0, s>>>(L.n, L.sp, L.s, L.rho, x, F, st,
-                                                    L.heavy_degree, partials);
+                                                    L.heavy_degree, partials, nparts, epi, ep);
 }
 
 }  // namespace
@@ -294,24 +393,29 @@ int gather_heavy_blocks(const Level& L) {
 int gather_blocks(const Level& L) { return gather_light_blocks(L) + gather_heavy_blocks(L); }
 
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
-                        double* partials, cudaStream_t s) {
+                        double* partials, cudaStream_t s, const SweepEpilogue* epi) {
   if (L.n <= 0) return MM_OK;
   const int lb = gather_light_blocks(L);
+  const int hb = gather_heavy_blocks(L);
+  const int nparts = lb + hb;
+  SweepEpilogue ep{};
+  if (epi) ep = *epi;
+  // the epilogue runs in the last launch of the update
+  const int epi_light = epi && hb == 0 ? 1 : 0;
   switch (L.lanes) {
-    case 1: launch_light<1>(L, x, F, st, partials, lb, s); break;
-    case 2: launch_light<2>(L, x, F, st, partials, lb, s); break;
-    case 4: launch_light<4>(L, x, F, st, partials, lb, s); break;
-    case 8: launch_light<8>(L, x, F, st, partials, lb, s); break;
-    case 16: launch_light<16>(L, x, F, st, partials, lb, s); break;
-    case 32: launch_light<32>(L, x, F, st, partials, lb, s); break;
+    case 1: launch_light<1>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
+    case 2: launch_light<2>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
+    case 4: launch_light<4>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
+    case 8: launch_light<8>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
+    case 16: launch_light<16>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
+    case 32: launch_light<32>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
     default:
       set_error("unsupported lanes per vertex %d", L.lanes);
       return MM_ERR_INVALID_ARG;
   }
-  const int hb = gather_heavy_blocks(L);
   if (hb > 0)
     gather_heavy<<<hb, kGatherThreads, 0, s>>>(L.heavy, L.n_heavy, L.sp, L.s, L.rho, x, F, st,
-                                               partials + 3 * (size_t)lb);
+                                               partials, lb, nparts, epi ? 1 : 0, ep);
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

@@ -464,6 +464,11 @@ __device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
 
 // Node-parallel records: a cell's position sum is the difference of two
 // prefix sums over its sorted range.
+// kFold: tile_off holds the raw tile totals (no tile scan ran) and every
+// block scans them itself (few tiles: cheaper than one more launch).
+constexpr int kFoldTiles = 128;
+
+template <bool kFold>
 __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const double2* __restrict__ incl,
                                const double2* __restrict__ tile_off,
@@ -471,6 +476,22 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                float4* nodeA, int4* nodeB) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
+  if (kFold) {
+    // exclusive prefix of the tile totals, in tile order (one thread: at
+    // most kFoldTiles FP64 adds, the same order as the tile scan kernel)
+    __shared__ double2 off[kFoldTiles];
+    const int tiles = (n + kSortTile - 1) / kSortTile;
+    if (threadIdx.x == 0) {
+      double rx = 0.0, ry = 0.0;
+      for (int i = 0; i < tiles; ++i) {
+        off[i] = make_double2(rx, ry);
+        rx += tile_off[i].x;
+        ry += tile_off[i].y;
+      }
+    }
+    __syncthreads();
+    tile_off = off;
+  }
   if (id >= 2 * n - 1) return;
   double2 sum;
   if (id >= n - 1) {
@@ -752,6 +773,9 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n) {
   MM_CK(cudaMemset(ws.err, 0, sizeof(int)));
   // unwritten records read as leaves whose escape ends the walk
   MM_CK(cudaMemset(ws.nodeB, 0xff, sizeof(int4) * 2 * N));
+  MM_CK(cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking));
+  MM_CK(cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming));
+  MM_CK(cudaEventCreateWithFlags(&ws.join, cudaEventDisableTiming));
   return MM_OK;
 }
 
@@ -761,11 +785,23 @@ void tree_ws_free(TreeWS& ws) {
                   ws.status, ws.hist, ws.counters, ws.nodeA, ws.nodeB, ws.partials, ws.root,
                   ws.ticket, ws.err};
   for (void* p : ptrs) cudaFree(p);
+  if (ws.fork) cudaEventDestroy(ws.fork);
+  if (ws.join) cudaEventDestroy(ws.join);
+  if (ws.aux) cudaStreamDestroy(ws.aux);
   ws = TreeWS();
 }
 
+mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s) {
+  if (n <= 0) return MM_OK;
+  const int bb = std::min(kBBoxMaxBlocks, ceil_div(n, kBBoxThreads));
+  bbox_kernel<<<bb, kBBoxThreads, 0, s>>>(x, n, ws.partials, ws.ticket, ws.root, ws.hist,
+                                          ws.counters);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
 mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
-                   cudaEvent_t* ev) {
+                   cudaEvent_t* ev, bool with_bbox) {
   if (n <= 0) return MM_OK;
   if (n > ws.cap) {
     set_error("tree workspace holds %lld vertices, level has %d", (long long)ws.cap, n);
@@ -775,10 +811,8 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
     if (ev) cudaEventRecord(ev[i], s);
   };
   const int tiles = ceil_div(n, kSortTile);
-  const int bb = std::min(kBBoxMaxBlocks, ceil_div(n, kBBoxThreads));
   mark(0);
-  bbox_kernel<<<bb, kBBoxThreads, 0, s>>>(x, n, ws.partials, ws.ticket, ws.root, ws.hist,
-                                          ws.counters);
+  if (with_bbox) MM_TRY(bh_bbox(x, n, ws, s));
   mark(1);
   morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, ws.root, ws.keys[0], ws.vals[0],
                                                    ws.hist);
@@ -791,16 +825,32 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
                                                  ws.status, ws.ticket, ws.err);
   }
   mark(3);
+  // the radix tree and the position prefix sums both need only the sorted
+  // keys: the tree is built on a second stream (a parallel graph branch
+  // under capture) while the sums run here
+  cudaStream_t ts = ws.aux ? ws.aux : s;
+  if (ws.aux) {
+    MM_CK(cudaEventRecord(ws.fork, s));
+    MM_CK(cudaStreamWaitEvent(ws.aux, ws.fork, 0));
+  }
   if (n > 1)
-    karras_kernel<<<ceil_div(n - 1, 256), 256, 0, s>>>(ws.keys[0], n, ws.lo, ws.hi, ws.left,
-                                                       ws.right, ws.delta, ws.owner, ws.parent);
+    karras_kernel<<<ceil_div(n - 1, 256), 256, 0, ts>>>(ws.keys[0], n, ws.lo, ws.hi, ws.left,
+                                                        ws.right, ws.delta, ws.owner, ws.parent);
   scan_xs_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.xs, ws.incl, ws.tile_sum);
-  tile_scan_kernel<<<1, 1024, 0, s>>>(ws.tile_sum, tiles);
+  const bool fold = tiles <= kFoldTiles;
+  if (!fold) tile_scan_kernel<<<1, 1024, 0, s>>>(ws.tile_sum, tiles);
+  if (ws.aux) {
+    MM_CK(cudaEventRecord(ws.join, ws.aux));
+    MM_CK(cudaStreamWaitEvent(s, ws.join, 0));
+  }
   mark(4);
   TreeView tv{n, ws.lo, ws.hi, ws.left, ws.right, ws.delta, ws.owner, ws.parent};
-  records_kernel<<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(tv, ws.xs, ws.incl, ws.tile_sum,
-                                                          ws.root, theta, leaf, ws.nodeA,
-                                                          ws.nodeB);
+  if (fold)
+    records_kernel<true><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
+        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, ws.nodeA, ws.nodeB);
+  else
+    records_kernel<false><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
+        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, ws.nodeA, ws.nodeB);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;

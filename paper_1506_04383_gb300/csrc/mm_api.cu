@@ -43,6 +43,8 @@ struct mm_hierarchy {
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
   float4* spart = nullptr;           // [kSmallMaxN] fused-level partial sums
+  float4* box = nullptr;             // [kMaxGatherBlocks] update-block boxes
+  unsigned* arrive = nullptr;        // update epilogue arrival counter
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
   int32_t* lsw = nullptr;            // [MM_MAX_LEVELS] sweeps per level
   float* trace = nullptr;
@@ -218,14 +220,25 @@ bool level_exact(const mm_hierarchy* h, int level, bool single) {
   return !single && level == (int)h->levels.size() - 1;
 }
 
-// Library kernels one sweep launches (mirrors sweep_body).
+// Library kernels one sweep of a layout's WHILE loop launches (mirrors
+// sweep_body with in_loop = true).
 int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
   const Level& L = h->levels[level];
-  int64_t k = 2 + (L.n_heavy > 0 ? 1 : 0);  // gather (+ heavy rows) + controller
-  if (exact) return k + 1;
-  k += 1 + 1 + 1;                            // bbox, morton, bottom-up
-  if (L.n > 1) k += 4 * 3 + 1;               // 4 radix passes x 3 kernels, radix tree
-  return k + 1;                              // walk
+  int64_t k = 1 + (L.n_heavy > 0 ? 1 : 0);  // update (+ heavy rows), epilogue fused
+  if (exact) return k + 1;                   // tiled exact sum
+  k += 1 + 4;                                // Morton keys + histograms, 4 sort passes
+  if (L.n > 1) k += 1;                       // radix tree
+  k += 1;                                    // position prefix sums
+  if (ceil_div(L.n, kSortTile) > 128) k += 1;  // tile scan (else folded into records)
+  return k + 1 + 1;                          // records, walk
+}
+
+// Kernels a multi-kernel level launches outside its loop: the bounding
+// square before the first sweep (Barnes-Hut levels).
+int64_t kernels_before_loop(const mm_hierarchy* h, int level, bool exact) {
+  (void)h;
+  (void)level;
+  return exact ? 0 : 1;
 }
 
 SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, SchedParams sp,
@@ -258,20 +271,39 @@ SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, Sch
   return a;
 }
 
-// One sweep on `level`: repulsion, fused update, controller.
+// One sweep on `level`: repulsion, fused update whose last block takes the
+// schedule step.  in_loop: the sweep is the body of a layout's WHILE loop;
+// the update then also leaves the next sweep's bounding square (the first
+// one comes from a bh_bbox before the loop), so the tree build skips it.
 mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState* st,
                      SchedParams sp, float* trace, int trace_cap, int* lsw,
-                     cudaGraphConditionalHandle hnd, bool use_h, cudaStream_t s) {
+                     cudaGraphConditionalHandle hnd, bool use_h, cudaStream_t s,
+                     bool in_loop = false) {
   const Level& L = h->levels[level];
   if (exact) {
     MM_TRY(exact_repulsion(x, L.n, h->F, s));
   } else {
-    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s));
+    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                        nullptr, s, group_of(h->p)));
   }
-  MM_TRY(gather_update(L, x, h->F, st, h->partials, s));
-  MM_TRY(controller(gather_blocks(L), h->partials, st, sp, trace, trace_cap, lsw, hnd, use_h, s));
+  SweepEpilogue ep{};
+  ep.st = st;
+  ep.sp = sp;
+  ep.trace = trace;
+  ep.trace_cap = trace_cap;
+  ep.lsw = lsw;
+  ep.h = hnd;
+  ep.use_h = use_h ? 1 : 0;
+  ep.arrive = h->arrive;
+  if (in_loop && !exact) {
+    ep.box = h->box;
+    ep.root = h->tree.root;
+    ep.hist = h->tree.hist;
+    ep.counters = h->tree.counters;
+    ep.tree_ticket = h->tree.ticket;
+  }
+  MM_TRY(gather_update(L, x, h->F, st, h->partials, s, &ep));
   return MM_OK;
 }
 
@@ -312,6 +344,10 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
                                       h->lsw + level, 1 << 30),
                            s);
       });
+    if (!exact)  // the first sweep's bounding square; later ones come from the update
+      MM_TRY(add_child([&](cudaStream_t s) -> mm_status {
+        return bh_bbox(x, h->levels[level].n, h->tree, s);
+      }));
     cudaGraphConditionalHandle hnd;
     MM_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
     alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
@@ -327,7 +363,7 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
     MM_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
     mm_status r = sweep_body(h, level, exact, x, h->state, sp, h->trace, h->trace_cap,
-                             h->lsw + level, hnd, true, cs);
+                             h->lsw + level, hnd, true, cs, true);
     cudaGraph_t out = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &out);
     if (r != MM_OK) return r;
@@ -639,6 +675,9 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMalloc(&h->state, sizeof(SweepState)));
   MM_CK(cudaMalloc(&h->sstate, sizeof(SweepState)));
   MM_CK(cudaMalloc(&h->spart, sizeof(float4) * (size_t)kSmallMaxN));
+  MM_CK(cudaMalloc(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks));
+  MM_CK(cudaMalloc(&h->arrive, sizeof(unsigned)));
+  MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
   MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
   MM_CK(cudaMalloc(&h->zero, sizeof(int32_t)));
@@ -824,6 +863,15 @@ mm_status graph_child(cudaGraph_t g, cudaStream_t cs, const std::vector<cudaGrap
 mm_status graph_loop(cudaGraph_t g, cudaStream_t cs, const std::vector<cudaGraphNode_t>& deps,
                      mm_hierarchy* h, int level, bool exact, SchedParams sp,
                      cudaGraphNode_t* out) {
+  std::vector<cudaGraphNode_t> pre = deps;
+  if (!exact) {  // the first sweep's bounding square; later ones come from the update
+    cudaGraphNode_t bb;
+    XSel xb{h->xb[0], h->xb[1], &h->state->parity};
+    MM_TRY(graph_child(g, cs, deps, [&](cudaStream_t s) -> mm_status {
+      return bh_bbox(xb, h->levels[level].n, h->tree, s);
+    }, &bb));
+    pre.assign(1, bb);
+  }
   cudaGraphConditionalHandle hnd;
   MM_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
   alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
@@ -833,13 +881,13 @@ mm_status graph_loop(cudaGraph_t g, cudaStream_t cs, const std::vector<cudaGraph
   cp.conditional.handle = hnd;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  MM_CK(cudaGraphAddNode(out, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+  MM_CK(cudaGraphAddNode(out, g, pre.empty() ? nullptr : pre.data(), nullptr, pre.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   MM_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal));
   XSel x{h->xb[0], h->xb[1], &h->state->parity};
   mm_status r = sweep_body(h, level, exact, x, h->state, sp, h->trace, h->trace_cap,
-                           h->lsw + level, hnd, true, cs);
+                           h->lsw + level, hnd, true, cs, true);
   cudaGraph_t o = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &o);
   MM_TRY(r);
@@ -993,7 +1041,10 @@ mm_status layout_batch(mm_hierarchy* h, const mm_params& p, const float* x_init,
       const int32_t sw = lsw[(size_t)i * MM_MAX_LEVELS + l];
       vu += (int64_t)sw * sub->levels[l].n;
       tot += sw;
-      if (!sub->levels[l].fused) kl += (int64_t)sw * kernels_per_sweep(sub, l, level_exact(sub, l, false));
+      if (!sub->levels[l].fused) {
+        const bool ex = level_exact(sub, l, false);
+        kl += kernels_before_loop(sub, l, ex) + (int64_t)sw * kernels_per_sweep(sub, l, ex);
+      }
     }
     if (hs[i].error) err = 1;
   }
@@ -1083,10 +1134,15 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     int64_t kl = 1;  // copy of the result
     for (int i = 0; i < nl; ++i) {
       if (single && i > 0) break;
+      // prolongation (the network's 9 kernels when learned) + schedule reset,
+      // or the initial layout; then the fused kernel or the sweep loop
+      const bool learned = p.learned_prolong && h->net && !single && i < nl - 1;
+      const int64_t start = single ? 1 : (learned ? 10 : 2);
+      const bool ex = level_exact(h, i, single);
       if (h->levels[i].fused)
-        kl += 2 + 1;
+        kl += start + 1;
       else
-        kl += 2 + (int64_t)lsw[i] * kernels_per_sweep(h, i, level_exact(h, i, single));
+        kl += start + kernels_before_loop(h, i, ex) + (int64_t)lsw[i] * kernels_per_sweep(h, i, ex);
     }
     stats->kernel_launches = kl;
   }
@@ -1387,6 +1443,7 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   for (Level& L : h->levels) free_level(L);
   tree_ws_free(h->tree);
   void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart,
+                  h->box, h->arrive,
                   h->zero, h->lsw, h->trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -196,6 +196,8 @@ struct TreeWS {
   uint32_t* ticket = nullptr; // [0] last-block ticket, [1] build epoch
   int* err = nullptr;         // set by a walk that met a broken tree (1) or a
                               // sort pass whose look-back gave up (2)
+  cudaStream_t aux = nullptr; // second branch of the build (radix tree); may be null
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 constexpr int kKeyBits = 16;  // per axis -> 32-bit Morton keys, depth 16
 
@@ -208,8 +210,13 @@ void tree_ws_free(TreeWS& ws);
 // sums, node records).
 // ev (nullable, 6 events) records the stage boundaries for profiling.
 // leaf: cells with at most `leaf` points become leaves (1..kMaxLeaf).
+// with_bbox = false: the root square (and the zeroed sort state) was left
+// by the previous sweep's update epilogue or an explicit bh_bbox.
 mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
-                   cudaEvent_t* ev = nullptr);
+                   cudaEvent_t* ev = nullptr, bool with_bbox = true);
+// Bounding square of x into ws.root; zeroes the sort histograms and
+// counters and starts a new look-back epoch.
+mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s);
 // Warp-synchronous stackless walk: F[v] = sum over accepted cells / leaves.
 // group = false: per-point acceptance (the oracle's Barnes-Hut); true: a
 // cell is accepted for a warp's 32 points together (refines every point's
@@ -231,9 +238,28 @@ constexpr int kMaxHeavyBlocks = kSMs * 8;
 // Upper bound of gather_blocks() for any lanes setting (partials sizing).
 constexpr int kMaxGatherBlocks = kMaxLightBlocks + kMaxHeavyBlocks;
 int gather_blocks(const Level& L);
-// Fused Eq. 2 update over S plus per-block partial sums (3 doubles/block).
+// What the last block of an update launch does once every block's partial
+// sums are in (see gather_update): the controller's schedule step, and
+// optionally the next sweep's bounding square.
+struct SweepEpilogue {
+  SweepState* st;
+  SchedParams sp;
+  float* trace;
+  int trace_cap;
+  int* lsw;
+  cudaGraphConditionalHandle h;
+  int use_h;
+  unsigned* arrive;       // arrival counter, 0 between sweeps
+  float4* box;            // [kMaxGatherBlocks] per-block boxes of x', or null
+  float4* root;           // with box: the tree's root square, sort state
+  uint32_t* hist;
+  uint32_t* counters;
+  unsigned* tree_ticket;
+};
+// Fused Eq. 2 update over S plus per-block partial sums (3 doubles/block);
+// with `epi`, the update ends with the schedule step (no controller launch).
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
-                        double* partials, cudaStream_t s);
+                        double* partials, cudaStream_t s, const SweepEpilogue* epi = nullptr);
 // Reduces the partials, applies the alpha schedule, optionally sets the
 // graph loop condition.
 mm_status controller(int nblocks, const double* partials, SweepState* st, SchedParams sp,
