@@ -408,7 +408,7 @@ def main():
     clk_sum = clk.summary()
     if gp is None:
         prof = mm.sweep_profile(h, 0, xbuf, reps=10)
-        roof = roofline(prof, peaks, src, clk_sum, n)
+        roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")))
     else:
         big = int(np.argmax(np.diff(gp)))
         grp, gcol = made[3][big]
@@ -544,12 +544,13 @@ def ctypes_copy(dst, src):
     ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
 
 
-def roofline(prof, peaks, src, clk, n):
+def roofline(prof, peaks, src, clk, n, exact=False):
     """Dominant kernel of a finest-level sweep against its roofline.
 
     traverse (Barnes-Hut walk): ALU bound; algorithmic work = 10 FP32 ops per
     lane interaction (accepted cell or leaf point), peak = 152 SMs x 128 FP32
-    lanes x 2 (FMA) x SM clock.  gather: HBM bound; algorithmic bytes per
+    lanes x 2 (FMA) x SM clock.  With exact repulsion the same stage is the
+    all-pairs sum: n (n - 1) interactions of 10 FP32 ops.  gather: HBM bound; algorithmic bytes per
     vertex = 4 (row_ptr) + 8 (x_u) + 8 (x'_u) + 8 (F_u) + 4 (rho_u) + 8 per S
     entry (col, d); neighbour positions are L2 hits and not counted.
     sort: HBM bound; 4 look-back passes x (8 B read + 8 B write) per element.
@@ -562,8 +563,8 @@ def roofline(prof, peaks, src, clk, n):
     hbm = peaks.get("hbm_gbs", 6800.0)
     nnzS = prof["nnz_S"]
     kern = {}
-    t_trav = st[names.index("traverse")] / 1e3
-    flops = 10.0 * prof["interactions"]
+    t_trav = max(st[names.index("traverse")], 1e-9) / 1e3
+    flops = 10.0 * (n * (n - 1) if exact else prof["interactions"])
     kern["traverse"] = {"bound": "alu", "achieved": flops / t_trav / 1e12, "peak": alu_peak,
                         "unit": "TFLOP/s", "traffic": None,
                         "note": f"peak = 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"}

@@ -218,6 +218,8 @@ __global__ void count_runs(int m, int vb, const uint64_t* __restrict__ keys,
 // ------------------------------------------------- label propagation ----
 constexpr int kLPWarps = 4;
 constexpr int kLPHash = 1024;  // distinct neighbouring clusters per vertex
+constexpr int kLPHeavyDeg = kLPHash / 2;  // longer rows: a block and a global hash each
+constexpr int kLPHeavyT = 256;
 
 __global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
     int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -237,6 +239,8 @@ __global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
     if (lane == 0) keys[v] = none;
     return;
   }
+  // more neighbours than half the hash: lp_propose_heavy decides
+  if (rp[v + 1] - rp[v] > kLPHeavyDeg) return;
   for (int i = lane; i < kLPHash; i += 32) { hk[wl][i] = -1; hv[wl][i] = 0.f; }
   __syncwarp();
   for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
@@ -282,6 +286,95 @@ __global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
       keys[v] = none;
   }
   (void)tb;
+}
+
+// The proposal of a vertex with more than kLPHeavyDeg neighbours (hubs of
+// power-law graphs): one block per vertex, connection weights per
+// neighbouring cluster in an open-addressing hash of T >= 2 deg slots in
+// global scratch, then the same choice as lp_propose (best eligible
+// cluster, ties to the smallest label, stay unless strictly better).
+__global__ void __launch_bounds__(kLPHeavyT) lp_propose_heavy(
+    const int32_t* __restrict__ hl, const int64_t* __restrict__ hoff,
+    const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+    const float* __restrict__ omega, const float* __restrict__ c, const float* __restrict__ W,
+    const int32_t* __restrict__ labels, float U, uint32_t k0, uint32_t k1, uint32_t round,
+    uint32_t level, uint32_t half, int32_t* hkey, float* hval, uint64_t* keys) {
+  const int v = hl[blockIdx.x];
+  uint32_t z[4];
+  philox4x32_10((uint32_t)v, round, level, 2u, k0, k1, z);
+  if ((z[0] & 1u) != half) return;  // lp_propose wrote "stay"
+  const int64_t base = hoff[blockIdx.x];
+  const int T = (int)(hoff[blockIdx.x + 1] - base);  // a power of two
+  int32_t* hk = hkey + base;
+  float* hv = hval + base;
+  for (int i = threadIdx.x; i < T; i += kLPHeavyT) {
+    hk[i] = -1;
+    hv[i] = 0.f;
+  }
+  __syncthreads();
+  for (int e = rp[v] + threadIdx.x; e < rp[v + 1]; e += kLPHeavyT) {
+    const int L = labels[col[e]];
+    const float w = omega ? omega[e] : 1.f;
+    uint32_t h = ((uint32_t)L * 2654435761u) & (uint32_t)(T - 1);
+    for (int probe = 0; probe < T; ++probe) {
+      const int prev = atomicCAS(&hk[h], -1, L);
+      if (prev == -1 || prev == L) {
+        atomicAdd(&hv[h], w);
+        break;
+      }
+      h = (h + 1) & (uint32_t)(T - 1);
+    }
+  }
+  __syncthreads();
+  const int own = labels[v];
+  const float cv = c[v];
+  float best = -1.f, ownc = 0.f;
+  int bestL = 0x7fffffff;
+  for (int i = threadIdx.x; i < T; i += kLPHeavyT) {
+    const int L = __ldcg(&hk[i]);
+    if (L < 0) continue;
+    const float cn = __ldcg(&hv[i]);
+    if (L == own) { ownc = cn; continue; }
+    if (W[L] + cv > U) continue;
+    if (cn > best || (cn == best && L < bestL)) { best = cn; bestL = L; }
+  }
+  __shared__ float sb[kLPHeavyT / 32], so[kLPHeavyT / 32];
+  __shared__ int sl[kLPHeavyT / 32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oL = __shfl_xor_sync(0xffffffffu, bestL, o);
+    ownc += __shfl_xor_sync(0xffffffffu, ownc, o);
+    if (ob > best || (ob == best && oL < bestL)) { best = ob; bestL = oL; }
+  }
+  if (lane == 0) { sb[wp] = best; sl[wp] = bestL; so[wp] = ownc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    best = sb[0]; bestL = sl[0]; ownc = so[0];
+    for (int k = 1; k < kLPHeavyT / 32; ++k) {
+      ownc += so[k];
+      if (sb[k] > best || (sb[k] == best && sl[k] < bestL)) { best = sb[k]; bestL = sl[k]; }
+    }
+    keys[v] = (best > ownc && bestL != 0x7fffffff) ? (((uint64_t)bestL << 32) | (uint64_t)z[1])
+                                                  : ~(uint64_t)0;
+  }
+}
+
+// Hash size of heavy vertex i: the power of two >= 2 deg.
+__global__ void lp_heavy_sizes(int m, const int32_t* __restrict__ hl,
+                               const int32_t* __restrict__ rp, int32_t* size) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int d = rp[hl[i] + 1] - rp[hl[i]];
+  int T = 1;
+  while (T < 2 * d) T <<= 1;
+  size[i] = T;
+}
+
+__global__ void max_row_kernel(int n, const int32_t* __restrict__ rp, int32_t* out) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) atomicMax(out, rp[u + 1] - rp[u]);
 }
 
 // One thread per run of movers into the same cluster (sorted by priority):
@@ -506,24 +599,21 @@ __global__ void coarse_reduce(int m, int cb, const uint64_t* __restrict__ keys,
   atomicAdd(&rowcnt[(int)(k >> cb)], 1);
 }
 
-__global__ void heavy_list_kernel(int n, const int32_t* __restrict__ sp, int thr, int32_t* list,
-                                  int32_t* count, int32_t* maxdeg) {
+// Rows longer than thr are "heavy": flag them (and track the longest row).
+__global__ void heavy_flags_kernel(int n, const int32_t* __restrict__ sp, int thr,
+                                   int32_t* flag, int32_t* maxdeg) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n) return;
   const int d = sp[u + 1] - sp[u];
   atomicMax(maxdeg, d);
-  if (d > thr) list[atomicAdd(count, 1)] = u;
+  flag[u] = d > thr ? 1 : 0;
 }
 
-__global__ void sort_small_list(int m, int32_t* list) {
-  // single thread insertion sort: heavy lists are short
-  if (blockIdx.x || threadIdx.x) return;
-  for (int i = 1; i < m; ++i) {
-    const int v = list[i];
-    int j = i - 1;
-    while (j >= 0 && list[j] > v) { list[j + 1] = list[j]; --j; }
-    list[j + 1] = v;
-  }
+// Ordered compaction: heavy row u goes to slot pos[u] (ascending u).
+__global__ void heavy_list_kernel(int n, const int32_t* __restrict__ flag,
+                                  const int32_t* __restrict__ pos, int32_t* list) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n && flag[u]) list[pos[u]] = u;
 }
 
 }  // namespace
@@ -643,7 +733,17 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
                      int32_t* labels, cudaStream_t s) {
   if (n <= 0) return MM_OK;
   const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
-  if (n <= kLPSmallN) {
+  int32_t maxdeg = 0;
+  {
+    Tmp md;
+    MM_TRY(tmp_alloc(md, sizeof(int32_t), s));
+    MM_CK(cudaMemsetAsync(md.p, 0, sizeof(int32_t), s));
+    max_row_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, md.as<int32_t>());
+    MM_CK(cudaMemcpyAsync(&maxdeg, md.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaStreamSynchronize(s));
+  }
+  // the single-CTA path holds every row's clusters in a 512-slot hash
+  if (n <= kLPSmallN && maxdeg <= kLPSmallHash / 2) {
     static_assert(sizeof(LPSmem) <= 227 * 1024, "LP kernel exceeds shared memory");
     MM_CK(cudaFuncSetAttribute(lp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sizeof(LPSmem)));
@@ -662,6 +762,40 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
   MM_TRY(tmp_alloc(v1, sizeof(int32_t) * (size_t)n, s));
   TmpSort sws;
   MM_TRY(tmp_sort(sws, n, s));
+  // vertices with more than kLPHeavyDeg neighbours: ordered list, hash
+  // offsets (2 deg rounded up to a power of two each) and scratch
+  Tmp hflag, hpos, hws, hl, hsz, hoff, hkey, hval;
+  int32_t nh = 0;
+  if (maxdeg > kLPHeavyDeg) {
+    MM_TRY(tmp_alloc(hflag, sizeof(int32_t) * (size_t)n, s));
+    MM_TRY(tmp_alloc(hpos, sizeof(int32_t) * ((size_t)n + 1), s));
+    MM_TRY(tmp_alloc(hws, scan_ws_bytes(n), s));
+    MM_TRY(tmp_alloc(hl, sizeof(int32_t) * (size_t)n, s));
+    Tmp dummy;
+    MM_TRY(tmp_alloc(dummy, sizeof(int32_t), s));
+    heavy_flags_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, kLPHeavyDeg, hflag.as<int32_t>(),
+                                                        dummy.as<int32_t>());
+    MM_TRY(scan_exclusive_i32(hflag.as<int32_t>(), hpos.as<int32_t>(), n, hws.p, s));
+    heavy_list_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, hflag.as<int32_t>(),
+                                                       hpos.as<int32_t>(), hl.as<int32_t>());
+    MM_CK(cudaMemcpyAsync(&nh, hpos.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          s));
+    MM_CK(cudaStreamSynchronize(s));
+  }
+  if (nh > 0) {
+    MM_TRY(tmp_alloc(hsz, sizeof(int32_t) * (size_t)nh, s));
+    MM_TRY(tmp_alloc(hoff, sizeof(int64_t) * ((size_t)nh + 1), s));
+    Tmp sws2;
+    MM_TRY(tmp_alloc(sws2, scan_ws_bytes(nh), s));
+    lp_heavy_sizes<<<ceil_div(nh, 256), 256, 0, s>>>(nh, hl.as<int32_t>(), rp, hsz.as<int32_t>());
+    MM_TRY(scan_exclusive_i64(hsz.as<int32_t>(), hoff.as<int64_t>(), nh, sws2.p, s));
+    int64_t total = 0;
+    MM_CK(cudaMemcpyAsync(&total, hoff.as<int64_t>() + nh, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          s));
+    MM_CK(cudaStreamSynchronize(s));
+    MM_TRY(tmp_alloc(hkey, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), s));
+    MM_TRY(tmp_alloc(hval, sizeof(float) * (size_t)std::max<int64_t>(total, 1), s));
+  }
   lp_init<<<ceil_div(n, 256), 256, 0, s>>>(n, c, labels, W.as<float>());
   const int tb = bits_for(n) + 1;
   mm_status st = MM_OK;
@@ -671,6 +805,11 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
       lp_propose<<<ceil_div(n, kLPWarps), kLPWarps * 32, 0, s>>>(
           n, rp, col, omega, c, W.as<float>(), labels, U, key0, key1, (uint32_t)r,
           (uint32_t)level, half, tb, k0.as<uint64_t>(), v0.as<int32_t>());
+      if (nh > 0)
+        lp_propose_heavy<<<nh, kLPHeavyT, 0, s>>>(
+            hl.as<int32_t>(), hoff.as<int64_t>(), rp, col, omega, c, W.as<float>(), labels, U,
+            key0, key1, (uint32_t)r, (uint32_t)level, half, hkey.as<int32_t>(),
+            hval.as<float>(), k0.as<uint64_t>());
       uint64_t* keys;
       int32_t* vals;
       st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(), v1.as<int32_t>(),
@@ -786,21 +925,31 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
     L.walk_warps = L.n >= 20000 ? 16 : 8;  // per-point walk: warps per block
   }
   L.heavy_degree = p.heavy_degree > 0 ? p.heavy_degree : std::max(512, 32 * lanes);
-  Tmp cnt;
-  MM_TRY(tmp_alloc(cnt, 2 * sizeof(int32_t), s));
-  MM_CK(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int32_t), s));
-  MM_CK(cudaMalloc(&L.heavy, sizeof(int32_t) * (size_t)std::max(L.n, 1)));
-  if (L.n > 0)
-    heavy_list_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, L.sp, L.heavy_degree, L.heavy,
-                                                         cnt.as<int32_t>(), cnt.as<int32_t>() + 1);
+  // heavy rows in ascending order (a deterministic processing order):
+  // flags, exclusive scan (the total lands in pos[n]), ordered scatter
+  const int n = std::max(L.n, 1);
+  Tmp flag, pos, ws, mx;
+  MM_TRY(tmp_alloc(flag, sizeof(int32_t) * (size_t)n, s));
+  MM_TRY(tmp_alloc(pos, sizeof(int32_t) * ((size_t)n + 1), s));
+  MM_TRY(tmp_alloc(ws, scan_ws_bytes(n), s));
+  MM_TRY(tmp_alloc(mx, sizeof(int32_t), s));
+  MM_CK(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), s));
+  MM_CK(cudaMalloc(&L.heavy, sizeof(int32_t) * (size_t)n));
   int32_t h[2] = {0, 0};
-  MM_CK(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (L.n > 0) {
+    heavy_flags_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, L.sp, L.heavy_degree,
+                                                          flag.as<int32_t>(), mx.as<int32_t>());
+    MM_TRY(scan_exclusive_i32(flag.as<int32_t>(), pos.as<int32_t>(), L.n, ws.p, s));
+    heavy_list_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, flag.as<int32_t>(),
+                                                         pos.as<int32_t>(), L.heavy);
+    MM_CK(cudaGetLastError());
+    MM_CK(cudaMemcpyAsync(&h[0], pos.as<int32_t>() + L.n, sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaMemcpyAsync(&h[1], mx.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  }
   MM_CK(cudaStreamSynchronize(s));
   L.n_heavy = h[0];
   L.max_deg = h[1];
-  // deterministic processing order of the heavy rows
-  if (L.n_heavy > 1) sort_small_list<<<1, 1, 0, s>>>(L.n_heavy, L.heavy);
-  MM_CK(cudaGetLastError());
   return MM_OK;
 }
 

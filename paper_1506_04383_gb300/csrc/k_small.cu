@@ -448,6 +448,12 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
     long long* prof = (sweep == 0 && crank == 0) ? a.prof : nullptr;
     MM_STAMP(1);
     if (a.exact) {
+      // no tree: the build stamps coincide, the sum is the "walk" interval
+      MM_STAMP(2);
+      MM_STAMP(3);
+      MM_STAMP(4);
+      MM_STAMP(5);
+      MM_STAMP(6);
       const int lane = tid & 31, warp = tid >> 5;
       for (int task = crank + csize * warp; task * 32 < n; task += csize * (kT / 32)) {
         const int u = task * 32 + lane;
