@@ -626,7 +626,7 @@ mm_status validate_graph(int n, int64_t nnz, const int64_t* rp64, const int32_t*
   validate_kernel<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, nnz, rp64, col, rp32_out, fl.as<int>());
   MM_CK(cudaGetLastError());
   int flags = 0;
-  MM_CK(cudaMemcpyAsync(&flags, fl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(fl.p, &flags, s));
   MM_CK(cudaStreamSynchronize(s));
   if (flags) {
     set_error("malformed graph:%s%s%s%s%s", (flags & kBadRowPtr) ? " row_ptr" : "",
@@ -646,17 +646,17 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
     return MM_ERR_UNSUPPORTED;
   }
   int32_t nnzE = 0;
-  MM_CK(cudaMemcpyAsync(&nnzE, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(rp + n, &nnzE, s));
   MM_CK(cudaStreamSynchronize(s));
   int32_t* sp = nullptr;
   SEnt* S = nullptr;
   float* rho = nullptr;
-  MM_CK(cudaMalloc(&sp, sizeof(int32_t) * (size_t)(n + 1)));
-  MM_CK(cudaMalloc(&rho, sizeof(float) * (size_t)std::max(n, 1)));
+  MM_CK(cudaMallocAsync(&sp, sizeof(int32_t) * (size_t)(n + 1), s));
+  MM_CK(cudaMallocAsync(&rho, sizeof(float) * (size_t)std::max(n, 1), s));
   *sp_out = sp;
   *rho_out = rho;
   if (k == 1) {
-    MM_CK(cudaMalloc(&S, sizeof(SEnt) * (size_t)std::max(nnzE, 1)));
+    MM_CK(cudaMallocAsync(&S, sizeof(SEnt) * (size_t)std::max(nnzE, 1), s));
     *s_out = S;
     khop1_kernel<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, rp, col, c, elen, sp, S, rho);
     MM_CK(cudaGetLastError());
@@ -671,7 +671,7 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
   khop2_count<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, cnt.as<int32_t>());
   MM_TRY(scan_exclusive_i64(cnt.as<int32_t>(), off.as<int64_t>(), n, scan_ws.p, s));
   int64_t m64 = 0;
-  MM_CK(cudaMemcpyAsync(&m64, off.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(off.as<int64_t>() + n, &m64, s));
   MM_CK(cudaStreamSynchronize(s));
   if (m64 >= 0x7fffffffLL) {
     set_error("2-hop enumeration has %lld paths (limit 2^31-1)", (long long)m64);
@@ -702,7 +702,7 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
   run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
   MM_TRY(scan_exclusive_i32(head.as<int32_t>(), pos.as<int32_t>(), m, ws2.p, s));
   int32_t uniq = 0;
-  MM_CK(cudaMemcpyAsync(&uniq, pos.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(pos.as<int32_t>() + m, &uniq, s));
   MM_CK(cudaStreamSynchronize(s));
   MM_TRY(tmp_alloc(S_tmp, sizeof(SEnt) * (size_t)std::max(uniq, 1), s));
   // temporary rows include the (u, u) padding runs
@@ -716,9 +716,9 @@ mm_status build_khop(int n, const int32_t* rp, const int32_t* col, const float* 
       rowcnt.as<int32_t>());
   MM_TRY(scan_exclusive_i32(rowcnt.as<int32_t>(), sp, n, ws2.p, s));
   int32_t nnzS = 0;
-  MM_CK(cudaMemcpyAsync(&nnzS, sp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(sp + n, &nnzS, s));
   MM_CK(cudaStreamSynchronize(s));
-  MM_CK(cudaMalloc(&S, sizeof(SEnt) * (size_t)std::max(nnzS, 1)));
+  MM_CK(cudaMallocAsync(&S, sizeof(SEnt) * (size_t)std::max(nnzS, 1), s));
   *s_out = S;
   khop2_finish<<<ceil_div(n, 256), 256, 0, s>>>(n, sp_tmp.as<int32_t>(), S_tmp.as<SEnt>(), sp, S,
                                                 rho);
@@ -739,7 +739,7 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
     MM_TRY(tmp_alloc(md, sizeof(int32_t), s));
     MM_CK(cudaMemsetAsync(md.p, 0, sizeof(int32_t), s));
     max_row_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, md.as<int32_t>());
-    MM_CK(cudaMemcpyAsync(&maxdeg, md.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MM_TRY(read_scalar(md.p, &maxdeg, s));
     MM_CK(cudaStreamSynchronize(s));
   }
   // the single-CTA path holds every row's clusters in a 512-slot hash
@@ -778,8 +778,7 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
     MM_TRY(scan_exclusive_i32(hflag.as<int32_t>(), hpos.as<int32_t>(), n, hws.p, s));
     heavy_list_kernel<<<ceil_div(n, 256), 256, 0, s>>>(n, hflag.as<int32_t>(),
                                                        hpos.as<int32_t>(), hl.as<int32_t>());
-    MM_CK(cudaMemcpyAsync(&nh, hpos.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                          s));
+    MM_TRY(read_scalar(hpos.as<int32_t>() + n, &nh, s));
     MM_CK(cudaStreamSynchronize(s));
   }
   if (nh > 0) {
@@ -790,8 +789,7 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
     lp_heavy_sizes<<<ceil_div(nh, 256), 256, 0, s>>>(nh, hl.as<int32_t>(), rp, hsz.as<int32_t>());
     MM_TRY(scan_exclusive_i64(hsz.as<int32_t>(), hoff.as<int64_t>(), nh, sws2.p, s));
     int64_t total = 0;
-    MM_CK(cudaMemcpyAsync(&total, hoff.as<int64_t>() + nh, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                          s));
+    MM_TRY(read_scalar(hoff.as<int64_t>() + nh, &total, s));
     MM_CK(cudaStreamSynchronize(s));
     MM_TRY(tmp_alloc(hkey, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), s));
     MM_TRY(tmp_alloc(hval, sizeof(float) * (size_t)std::max<int64_t>(total, 1), s));
@@ -825,7 +823,7 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
     // a round without moves leaves a fixed point: every later round would
     // make the same (no) choices
     int moved = 0;
-    MM_CK(cudaMemcpyAsync(&moved, mv.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MM_TRY(read_scalar(mv.p, &moved, s));
     MM_CK(cudaStreamSynchronize(s));
     if (moved == 0) break;
   }
@@ -839,7 +837,7 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
                    const float* c, const int32_t* labels, int32_t* map, Level& out,
                    cudaStream_t s) {
   int32_t nnz = 0;
-  MM_CK(cudaMemcpyAsync(&nnz, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(rp + n, &nnz, s));
   MM_CK(cudaStreamSynchronize(s));
   Tmp used, rank, ws, flag, pos, k0, k1, v0, v1, head, hpos, rowcnt;
   MM_TRY(tmp_alloc(used, sizeof(int32_t) * (size_t)(n + 1), s));
@@ -849,10 +847,10 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   mark_used<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, used.as<int32_t>());
   MM_TRY(scan_exclusive_i32(used.as<int32_t>(), rank.as<int32_t>(), n, ws.p, s));
   int32_t nc = 0;
-  MM_CK(cudaMemcpyAsync(&nc, rank.as<int32_t>() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(rank.as<int32_t>() + n, &nc, s));
   MM_CK(cudaStreamSynchronize(s));
   out.n = nc;
-  MM_CK(cudaMalloc(&out.c, sizeof(float) * (size_t)std::max(nc, 1)));
+  MM_CK(cudaMallocAsync(&out.c, sizeof(float) * (size_t)std::max(nc, 1), s));
   MM_CK(cudaMemsetAsync(out.c, 0, sizeof(float) * (size_t)std::max(nc, 1), s));
   apply_map<<<ceil_div(n, 256), 256, 0, s>>>(n, labels, rank.as<int32_t>(), c, map, out.c);
   MM_TRY(tmp_alloc(flag, sizeof(int32_t) * (size_t)std::max(nnz, 1), s));
@@ -860,7 +858,7 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   cut_flags<<<ceil_div(n, 256), 256, 0, s>>>(n, rp, col, map, flag.as<int32_t>());
   MM_TRY(scan_exclusive_i32(flag.as<int32_t>(), pos.as<int32_t>(), nnz, ws.p, s));
   int32_t m = 0;
-  MM_CK(cudaMemcpyAsync(&m, pos.as<int32_t>() + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(pos.as<int32_t>() + nnz, &m, s));
   MM_CK(cudaStreamSynchronize(s));
   const int cb = bits_for(std::max(nc - 1, 1));
   MM_TRY(tmp_alloc(k0, sizeof(uint64_t) * (size_t)std::max(m, 1), s));
@@ -880,12 +878,12 @@ mm_status contract(int n, const int32_t* rp, const int32_t* col, const float* om
   run_heads<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(m, keys, head.as<int32_t>());
   MM_TRY(scan_exclusive_i32(head.as<int32_t>(), hpos.as<int32_t>(), m, ws.p, s));
   int32_t cnnz = 0;
-  MM_CK(cudaMemcpyAsync(&cnnz, hpos.as<int32_t>() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_TRY(read_scalar(hpos.as<int32_t>() + m, &cnnz, s));
   MM_CK(cudaStreamSynchronize(s));
   out.nnzE = cnnz;
-  MM_CK(cudaMalloc(&out.col, sizeof(int32_t) * (size_t)std::max(cnnz, 1)));
-  MM_CK(cudaMalloc(&out.omega, sizeof(float) * (size_t)std::max(cnnz, 1)));
-  MM_CK(cudaMalloc(&out.rp, sizeof(int32_t) * (size_t)(nc + 1)));
+  MM_CK(cudaMallocAsync(&out.col, sizeof(int32_t) * (size_t)std::max(cnnz, 1), s));
+  MM_CK(cudaMallocAsync(&out.omega, sizeof(float) * (size_t)std::max(cnnz, 1), s));
+  MM_CK(cudaMallocAsync(&out.rp, sizeof(int32_t) * (size_t)(nc + 1), s));
   MM_TRY(tmp_alloc(rowcnt, sizeof(int32_t) * (size_t)(nc + 1), s));
   MM_CK(cudaMemsetAsync(rowcnt.p, 0, sizeof(int32_t) * (size_t)(nc + 1), s));
   coarse_reduce<<<ceil_div(std::max(m, 1), 256), 256, 0, s>>>(
@@ -934,7 +932,7 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
   MM_TRY(tmp_alloc(ws, scan_ws_bytes(n), s));
   MM_TRY(tmp_alloc(mx, sizeof(int32_t), s));
   MM_CK(cudaMemsetAsync(mx.p, 0, sizeof(int32_t), s));
-  MM_CK(cudaMalloc(&L.heavy, sizeof(int32_t) * (size_t)n));
+  MM_CK(cudaMallocAsync(&L.heavy, sizeof(int32_t) * (size_t)n, s));
   int32_t h[2] = {0, 0};
   if (L.n > 0) {
     heavy_flags_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, L.sp, L.heavy_degree,
@@ -943,9 +941,8 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
     heavy_list_kernel<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, flag.as<int32_t>(),
                                                          pos.as<int32_t>(), L.heavy);
     MM_CK(cudaGetLastError());
-    MM_CK(cudaMemcpyAsync(&h[0], pos.as<int32_t>() + L.n, sizeof(int32_t),
-                          cudaMemcpyDeviceToHost, s));
-    MM_CK(cudaMemcpyAsync(&h[1], mx.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MM_TRY(read_scalar(pos.as<int32_t>() + L.n, &h[0], s));
+    MM_TRY(read_scalar(mx.p, &h[1], s));
   }
   MM_CK(cudaStreamSynchronize(s));
   L.n_heavy = h[0];

@@ -741,38 +741,38 @@ size_t tree_status_words(int64_t n) {
   return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortTile) * 256;
 }
 
-mm_status tree_ws_alloc(TreeWS& ws, int64_t n) {
+mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   const size_t N = (size_t)(n > 1 ? n : 2);
   const size_t tiles = (size_t)ceil_div((int64_t)N, kSortTile);
   ws.cap = n;
-  MM_CK(cudaMalloc(&ws.keys[0], sizeof(uint32_t) * N));
-  MM_CK(cudaMalloc(&ws.keys[1], sizeof(uint32_t) * N));
-  MM_CK(cudaMalloc(&ws.vals[0], sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.vals[1], sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.xs, sizeof(float2) * N));
-  MM_CK(cudaMalloc(&ws.lo, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.hi, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.left, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.right, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.delta, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.owner, sizeof(int32_t) * N));
-  MM_CK(cudaMalloc(&ws.parent, sizeof(int32_t) * 2 * N));
-  MM_CK(cudaMalloc(&ws.incl, sizeof(double2) * N));
-  MM_CK(cudaMalloc(&ws.tile_sum, sizeof(double2) * tiles));
-  MM_CK(cudaMalloc(&ws.status, sizeof(unsigned long long) * tree_status_words(N)));
-  MM_CK(cudaMemset(ws.status, 0, sizeof(unsigned long long) * tree_status_words(N)));
-  MM_CK(cudaMalloc(&ws.hist, sizeof(uint32_t) * 4 * 256));
-  MM_CK(cudaMalloc(&ws.counters, sizeof(uint32_t) * 4));
-  MM_CK(cudaMalloc(&ws.nodeA, sizeof(float4) * 2 * N));
-  MM_CK(cudaMalloc(&ws.nodeB, sizeof(int4) * 2 * N));
-  MM_CK(cudaMalloc(&ws.partials, sizeof(float4) * kBBoxMaxBlocks));
-  MM_CK(cudaMalloc(&ws.root, sizeof(float4)));
-  MM_CK(cudaMalloc(&ws.ticket, 2 * sizeof(unsigned)));
-  MM_CK(cudaMemset(ws.ticket, 0, 2 * sizeof(unsigned)));
-  MM_CK(cudaMalloc(&ws.err, sizeof(int)));
-  MM_CK(cudaMemset(ws.err, 0, sizeof(int)));
+  MM_CK(cudaMallocAsync(&ws.keys[0], sizeof(uint32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.keys[1], sizeof(uint32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.vals[0], sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.vals[1], sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.xs, sizeof(float2) * N, s));
+  MM_CK(cudaMallocAsync(&ws.lo, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.hi, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.left, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.right, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.delta, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.owner, sizeof(int32_t) * N, s));
+  MM_CK(cudaMallocAsync(&ws.parent, sizeof(int32_t) * 2 * N, s));
+  MM_CK(cudaMallocAsync(&ws.incl, sizeof(double2) * N, s));
+  MM_CK(cudaMallocAsync(&ws.tile_sum, sizeof(double2) * tiles, s));
+  MM_CK(cudaMallocAsync(&ws.status, sizeof(unsigned long long) * tree_status_words(N), s));
+  MM_CK(cudaMemsetAsync(ws.status, 0, sizeof(unsigned long long) * tree_status_words(N), s));
+  MM_CK(cudaMallocAsync(&ws.hist, sizeof(uint32_t) * 4 * 256, s));
+  MM_CK(cudaMallocAsync(&ws.counters, sizeof(uint32_t) * 4, s));
+  MM_CK(cudaMallocAsync(&ws.nodeA, sizeof(float4) * 2 * N, s));
+  MM_CK(cudaMallocAsync(&ws.nodeB, sizeof(int4) * 2 * N, s));
+  MM_CK(cudaMallocAsync(&ws.partials, sizeof(float4) * kBBoxMaxBlocks, s));
+  MM_CK(cudaMallocAsync(&ws.root, sizeof(float4), s));
+  MM_CK(cudaMallocAsync(&ws.ticket, 2 * sizeof(unsigned), s));
+  MM_CK(cudaMemsetAsync(ws.ticket, 0, 2 * sizeof(unsigned), s));
+  MM_CK(cudaMallocAsync(&ws.err, sizeof(int), s));
+  MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   // unwritten records read as leaves whose escape ends the walk
-  MM_CK(cudaMemset(ws.nodeB, 0xff, sizeof(int4) * 2 * N));
+  MM_CK(cudaMemsetAsync(ws.nodeB, 0xff, sizeof(int4) * 2 * N, s));
   MM_CK(cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking));
   MM_CK(cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming));
   MM_CK(cudaEventCreateWithFlags(&ws.join, cudaEventDisableTiming));

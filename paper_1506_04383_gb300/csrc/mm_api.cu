@@ -466,6 +466,24 @@ struct DeviceGuard {
 mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s);
 mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out);
 
+// Level arrays and workspaces come from the stream-ordered allocator: its
+// pool keeps freed memory for reuse (no release to the driver at every
+// synchronisation), and allocations from many host threads building a batch
+// do not serialise on the driver the way cudaMalloc does.
+void keep_pool(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
 mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
   if (g && g->num_graphs > 1) return build_batch(g, p, s, out);
   MM_TRY(check_params(p));
@@ -481,22 +499,23 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
   *out = h;  // freed by the caller's wrapper on error
   h->p = *p;
   MM_CK(cudaGetDevice(&h->device));
+  keep_pool(h->device);
   MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
   const int n0 = g->n;
   Level L0;
   L0.n = n0;
   L0.nnzE = g->nnz;
-  MM_CK(cudaMalloc(&L0.rp, sizeof(int32_t) * (size_t)(n0 + 1)));
+  MM_CK(cudaMallocAsync(&L0.rp, sizeof(int32_t) * (size_t)(n0 + 1), s));
   h->levels.push_back(L0);
   Level& l0 = h->levels[0];
   MM_TRY(validate_graph(n0, g->nnz, g->row_ptr, g->col, l0.rp, s));
-  MM_CK(cudaMalloc(&l0.col, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1)));
-  MM_CK(cudaMalloc(&l0.omega, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1)));
-  MM_CK(cudaMalloc(&l0.c, sizeof(float) * (size_t)n0));
+  MM_CK(cudaMallocAsync(&l0.col, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1), s));
+  MM_CK(cudaMallocAsync(&l0.omega, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1), s));
+  MM_CK(cudaMallocAsync(&l0.c, sizeof(float) * (size_t)n0, s));
   if (g->nnz)
     MM_CK(cudaMemcpyAsync(l0.col, g->col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToDevice, s));
   if (g->edge_len) {
-    MM_CK(cudaMalloc(&l0.elen, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1)));
+    MM_CK(cudaMallocAsync(&l0.elen, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1), s));
     if (g->nnz)
       MM_CK(cudaMemcpyAsync(l0.elen, g->edge_len, sizeof(float) * g->nnz,
                             cudaMemcpyDeviceToDevice, s));
@@ -520,11 +539,8 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
     int maxc_bits = 0;
     cudaMemsetAsync(dmax, 0, sizeof(int), s);
     max_f32<<<ceil_div(cur.n, 256), 256, 0, s>>>(cur.n, cur.c, dmax);
-    cudaMemcpyAsync(&maxc_bits, dmax, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-      st = cuda_status(cudaGetLastError(), "max reduction", __FILE__, __LINE__);
-      break;
-    }
+    st = read_scalar(dmax, &maxc_bits, s);
+    if (st != MM_OK) break;
     float maxc;
     memcpy(&maxc, &maxc_bits, sizeof(float));
     const double W = std::min(std::pow((double)p->b, hidx + 1), cur.n / f);
@@ -534,7 +550,7 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
     if (st != MM_OK) break;
     Level nxt;
     int32_t* map = nullptr;
-    if (cudaMalloc(&map, sizeof(int32_t) * (size_t)cur.n) != cudaSuccess) {
+    if (cudaMallocAsync(&map, sizeof(int32_t) * (size_t)cur.n, s) != cudaSuccess) {
       st = cuda_status(cudaErrorMemoryAllocation, "cudaMalloc(map)", __FILE__, __LINE__);
       break;
     }
@@ -628,6 +644,7 @@ mm_status build_explicit(int num_levels, const mm_level_desc* d, const float* el
   *out = h;
   h->p = *p;
   MM_CK(cudaGetDevice(&h->device));
+  keep_pool(h->device);
   MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
   for (int l = 0; l < num_levels; ++l) {
     h->levels.push_back(Level());
@@ -666,23 +683,23 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   // ---- workspaces, sized for the largest level
   int n0 = 1;
   for (const Level& L : h->levels) n0 = std::max(n0, L.n);
-  MM_TRY(tree_ws_alloc(h->tree, n0));
-  MM_CK(cudaMalloc(&h->xb[0], sizeof(float2) * (size_t)n0));
-  MM_CK(cudaMalloc(&h->xb[1], sizeof(float2) * (size_t)n0));
-  MM_CK(cudaMalloc(&h->F, sizeof(float2) * (size_t)n0));
+  MM_TRY(tree_ws_alloc(h->tree, n0, s));
+  MM_CK(cudaMallocAsync(&h->xb[0], sizeof(float2) * (size_t)n0, s));
+  MM_CK(cudaMallocAsync(&h->xb[1], sizeof(float2) * (size_t)n0, s));
+  MM_CK(cudaMallocAsync(&h->F, sizeof(float2) * (size_t)n0, s));
   // partials for the largest grid any lanes setting (autotuner) can launch
-  MM_CK(cudaMalloc(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks));
-  MM_CK(cudaMalloc(&h->state, sizeof(SweepState)));
-  MM_CK(cudaMalloc(&h->sstate, sizeof(SweepState)));
-  MM_CK(cudaMalloc(&h->spart, sizeof(float4) * (size_t)kSmallMaxN));
-  MM_CK(cudaMalloc(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks));
-  MM_CK(cudaMalloc(&h->arrive, sizeof(unsigned)));
+  MM_CK(cudaMallocAsync(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks, s));
+  MM_CK(cudaMallocAsync(&h->state, sizeof(SweepState), s));
+  MM_CK(cudaMallocAsync(&h->sstate, sizeof(SweepState), s));
+  MM_CK(cudaMallocAsync(&h->spart, sizeof(float4) * (size_t)kSmallMaxN, s));
+  MM_CK(cudaMallocAsync(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
+  MM_CK(cudaMallocAsync(&h->arrive, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
   MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
-  MM_CK(cudaMalloc(&h->zero, sizeof(int32_t)));
+  MM_CK(cudaMallocAsync(&h->zero, sizeof(int32_t), s));
   MM_CK(cudaMemsetAsync(h->zero, 0, sizeof(int32_t), s));
-  MM_CK(cudaMalloc(&h->lsw, sizeof(int32_t) * MM_MAX_LEVELS));
+  MM_CK(cudaMallocAsync(&h->lsw, sizeof(int32_t) * MM_MAX_LEVELS, s));
   MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
   MM_CK(cudaStreamSynchronize(s));
   return MM_OK;
@@ -721,6 +738,7 @@ mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_
   h->p = *p;
   h->gptr = gp;
   MM_CK(cudaGetDevice(&h->device));
+  keep_pool(h->device);
   MM_CK(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
   std::vector<int64_t> rp(g->n + 1);
   MM_CK(cudaMemcpyAsync(rp.data(), g->row_ptr, sizeof(int64_t) * (g->n + 1),

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 #include "mm.h"
 
 namespace mm {
@@ -170,6 +172,27 @@ mm_status scan_exclusive_i32(const int32_t* in, int32_t* out, int n, void* ws,
 mm_status scan_exclusive_i64(const int32_t* in, int64_t* out, int n, void* ws,
                              cudaStream_t s);
 
+// Reads one small value from the device into *host through a per-thread
+// pinned buffer (a copy to pageable memory goes through the driver's shared
+// staging buffer, which serialises host threads building a batch), then
+// synchronises the stream.
+struct PinnedScratch {
+  void* p = nullptr;
+  ~PinnedScratch() {
+    if (p) cudaFreeHost(p);
+  }
+};
+template <typename T>
+mm_status read_scalar(const void* dev, T* host, cudaStream_t s) {
+  static_assert(sizeof(T) <= 64, "read_scalar reads at most 64 bytes");
+  thread_local PinnedScratch buf;
+  if (!buf.p) MM_CK(cudaHostAlloc(&buf.p, 64, cudaHostAllocDefault));
+  MM_CK(cudaMemcpyAsync(buf.p, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+  MM_CK(cudaStreamSynchronize(s));
+  memcpy(host, buf.p, sizeof(T));
+  return MM_OK;
+}
+
 // ------------------------------------------------------------ quadtree --
 // Workspace of the Barnes-Hut tree, sized for the largest level.
 struct TreeWS {
@@ -202,7 +225,7 @@ struct TreeWS {
 constexpr int kKeyBits = 16;  // per axis -> 32-bit Morton keys, depth 16
 
 size_t tree_status_words(int64_t n);
-mm_status tree_ws_alloc(TreeWS& ws, int64_t n);
+mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s);
 void tree_ws_free(TreeWS& ws);
 
 // Rebuilds the quadtree from the current positions (bbox, Morton keys and
