@@ -408,7 +408,8 @@ def main():
     clk_sum = clk.summary()
     if gp is None:
         prof = mm.sweep_profile(h, 0, xbuf, reps=10)
-        roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")))
+        roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")),
+                        workload=args.workload)
     else:
         big = int(np.argmax(np.diff(gp)))
         grp, gcol = made[3][big]
@@ -544,7 +545,13 @@ def ctypes_copy(dst, src):
     ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
 
 
-def roofline(prof, peaks, src, clk, n, exact=False):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# ncu capture of the kernel on level 0 of the workload.  Re-capture and
+# update (or drop) whenever the kernel changes.
+NCU_TRAFFIC = {"rgg100k": {"traverse": 3.861504e6, "gather": 19.086336e6}}
+
+
+def roofline(prof, peaks, src, clk, n, exact=False, workload=None):
     """Dominant kernel of a finest-level sweep against its roofline.
 
     traverse (Barnes-Hut walk): ALU bound; algorithmic work = 10 FP32 ops per
@@ -576,15 +583,16 @@ def roofline(prof, peaks, src, clk, n, exact=False):
     sbytes = 4 * 16.0 * n
     kern["sort"] = {"bound": "hbm", "achieved": sbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "traffic": None}
-    for v in kern.values():
+    for name_, v in kern.items():
         v["frac"] = v["achieved"] / v["peak"]
         v["peak_source"] = src
+        v["traffic"] = NCU_TRAFFIC.get(workload, {}).get(name_)
     name = names[dom]
     out = dict(kern.get(name, kern["traverse"]))
     out["kernel"] = name if name in kern else "traverse"
     out["stage_ms"] = dict(zip(names, st))
     out["others"] = {k: {kk: vv for kk, vv in v.items() if kk in ("achieved", "peak", "unit",
-                                                                   "frac", "bound")}
+                                                                   "frac", "bound", "traffic")}
                      for k, v in kern.items() if k != out["kernel"]}
     return out
 
