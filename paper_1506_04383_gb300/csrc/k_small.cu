@@ -115,6 +115,73 @@ __device__ __forceinline__ void bsum3(float a, float b, float c, double* red, do
     if (prof && threadIdx.x == 0) prof[i] = clock64();       \
   } while (0)
 
+// Bitonic sort of np keys (np a power of two <= 2048) in shared memory.
+// Every stage whose compare distance j is below 64 pairs elements of the
+// same 64-element block, so a warp does those stages in registers: lane l
+// holds block elements l and l + 32, distance 32 is a swap inside the lane,
+// shorter distances a shuffle.  Only distances >= 64 go through shared
+// memory with a block barrier each (15 of the 66 stages at np = 2048).
+__device__ __forceinline__ unsigned long long bitonic_cx(unsigned long long v, int i, int j,
+                                                         int k) {
+  const unsigned long long p = __shfl_xor_sync(0xffffffffu, v, j);
+  const bool asc = (i & k) == 0, lower = (i & j) == 0;
+  const unsigned long long mn = v < p ? v : p, mx = v < p ? p : v;
+  return lower == asc ? mn : mx;
+}
+
+__device__ __forceinline__ void bitonic_regs(unsigned long long& v0, unsigned long long& v1,
+                                             int i0, int k, int jmax) {
+  for (int j = jmax; j > 0; j >>= 1) {
+    if (j == 32) {
+      // partner of i0 is i0 + 32 = the element in v1
+      const bool asc = (i0 & k) == 0;
+      const unsigned long long mn = v0 < v1 ? v0 : v1, mx = v0 < v1 ? v1 : v0;
+      v0 = asc ? mn : mx;
+      v1 = asc ? mx : mn;
+    } else {
+      v0 = bitonic_cx(v0, i0, j, k);
+      v1 = bitonic_cx(v1, i0 + 32, j, k);
+    }
+  }
+}
+
+__device__ void sort_keys(unsigned long long* keys, int np) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = warp * 64 + lane, i1 = i0 + 32;
+  // fewer than 64 keys: warp 0 sorts them padded with the largest key
+  const bool live = warp * 64 < np;
+  unsigned long long v0 = ~0ull, v1 = ~0ull;
+  if (live) {
+    if (i0 < np) v0 = keys[i0];
+    if (i1 < np) v1 = keys[i1];
+    for (int k = 2; k <= 64; k <<= 1) bitonic_regs(v0, v1, i0, k, k >> 1);
+    if (i0 < np) keys[i0] = v0;
+    if (i1 < np) keys[i1] = v1;
+  }
+  __syncthreads();
+  for (int k = 128; k <= np; k <<= 1) {
+    for (int j = k >> 1; j >= 64; j >>= 1) {
+      for (int i = threadIdx.x; i < np; i += kT) {
+        const int ij = i ^ j;
+        if (ij > i) {
+          const unsigned long long a = keys[i], b = keys[ij];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { keys[i] = b; keys[ij] = a; }
+        }
+      }
+      __syncthreads();
+    }
+    if (live) {
+      v0 = keys[i0];
+      v1 = keys[i1];
+      bitonic_regs(v0, v1, i0, k, 32);
+      keys[i0] = v0;
+      keys[i1] = v1;
+    }
+    __syncthreads();
+  }
+}
+
 __device__ void build_tree(SmallSmem& s, int n, float theta, int leaf, float4* root_sh,
                            double* red, long long* prof) {
   const float2* x = s.xv;
@@ -168,20 +235,7 @@ __device__ void build_tree(SmallSmem& s, int n, float theta, int leaf, float4* r
     s.keys[i] = k;
   }
   __syncthreads();
-  // bitonic sort of np keys
-  for (int k = 2; k <= np; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < np; i += kT) {
-        const int ij = i ^ j;
-        if (ij > i) {
-          const unsigned long long a = s.keys[i], b = s.keys[ij];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { s.keys[i] = b; s.keys[ij] = a; }
-        }
-      }
-      __syncthreads();
-    }
-  }
+  sort_keys(s.keys, np);
   MM_STAMP(3);
   for (int i = tid; i < n; i += kT) {
     const int v = (int)(uint32_t)s.keys[i];
