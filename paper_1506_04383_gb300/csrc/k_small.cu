@@ -353,49 +353,116 @@ __device__ void build_tree(SmallSmem& s, int n, float theta, int leaf, float4* r
 // Group acceptance over the shared-memory records: the task's 32 points
 // accept a cell only when all of them pass the per-point test (the same rule
 // as the multi-kernel group walk); the walk is uniform across the warp.
-__device__ void walk_group(const SmallSmem& s, int n, float2* F, int* err, int crank,
-                           int csize) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int task = crank + csize * warp; task * 32 < n; task += csize * (kT / 32)) {
-    const int pos = task * 32 + lane;
-    const bool valid = pos < n;
-    const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
-    int cur = n > 1 ? 0 : -1;
-    int budget = 2 * n + 2;
-    float fx = 0.f, fy = 0.f;
-    while (cur >= 0) {
-      if (cur >= 2 * n - 1 || --budget < 0) {
-        if (lane == 0) atomicOr(err, 1);
-        break;
-      }
-      const float4 A = s.nodeA[cur];
-      const short4 B = s.nodeB[cur];
-      const float dx = xu.x - A.x, dy = xu.y - A.y;
-      const float q = fmaf(dx, dx, dy * dy);
-      const bool far = !valid || ((pos < B.z || pos >= B.w) && q > A.z);
-      if (__all_sync(0xffffffffu, far)) {
-        const float sc = __fdividef(A.w, q);
-        fx = fmaf(sc, dx, fx);
-        fy = fmaf(sc, dy, fy);
-        cur = B.y;
-      } else if (B.x < 0) {
-        const int pb = max((int)B.z, 0), pe = min((int)B.w, n);
-        for (int p = pb; p < pe; ++p) {
-          const float2 xv = s.xs[p];
-          const float ex = xu.x - xv.x, ey = xu.y - xv.y;
-          const float eq = fmaf(ex, ex, ey * ey);
-          if (p != pos && eq > 0.f) {
-            const float inv = __fdividef(1.f, eq);
-            fx = fmaf(inv, ex, fx);
-            fy = fmaf(inv, ey, fy);
-          }
+//
+// A CTA has few tasks (about 4) and 32 warps, so W warps share a task: the
+// task's first warp walks the tree, recording opened cells of at most
+// kSmallSeedPts points as seeds instead of entering them; the W warps then
+// walk the seed subtrees (seed j by warp j mod W) and their partial sums are
+// added in warp order.  Every cell gets the decision of a single walk.  The
+// seeds and partial sums live in the radix-tree arrays, which are dead
+// between the record build and the next sweep.
+constexpr int kSmallSeedMax = 64;
+constexpr int kSmallSeedPts = 64;
+
+__device__ __forceinline__ void walk_cells(const SmallSmem& s, int n, int cur, int stop,
+                                           float2 xu, int pos, bool valid, float& fx, float& fy,
+                                           int& budget, int* err, int* seeds, int* nseeds) {
+  const int lane = threadIdx.x & 31;
+  while (cur != stop && cur >= 0) {
+    if (cur >= 2 * n - 1 || --budget < 0) {
+      if (lane == 0) atomicOr(err, 1);
+      return;
+    }
+    const float4 A = s.nodeA[cur];
+    const short4 B = s.nodeB[cur];
+    const float dx = xu.x - A.x, dy = xu.y - A.y;
+    const float q = fmaf(dx, dx, dy * dy);
+    const bool far = !valid || ((pos < B.z || pos >= B.w) && q > A.z);
+    if (__all_sync(0xffffffffu, far)) {
+      const float sc = __fdividef(A.w, q);
+      fx = fmaf(sc, dx, fx);
+      fy = fmaf(sc, dy, fy);
+      cur = B.y;
+    } else if (B.x < 0) {
+      const int pb = max((int)B.z, 0), pe = min((int)B.w, n);
+      for (int p = pb; p < pe; ++p) {
+        const float2 xv = s.xs[p];
+        const float ex = xu.x - xv.x, ey = xu.y - xv.y;
+        const float eq = fmaf(ex, ex, ey * ey);
+        if (p != pos && eq > 0.f) {
+          const float inv = __fdividef(1.f, eq);
+          fx = fmaf(inv, ex, fx);
+          fy = fmaf(inv, ey, fy);
         }
-        cur = B.y;
-      } else {
-        cur = B.x;
+      }
+      cur = B.y;
+    } else if (seeds && (int)B.w - (int)B.z <= kSmallSeedPts && *nseeds < kSmallSeedMax) {
+      if (lane == 0) seeds[*nseeds] = cur;
+      __syncwarp();
+      if (lane == 0) *nseeds += 1;
+      __syncwarp();
+      cur = B.y;
+    } else {
+      cur = B.x;
+    }
+  }
+}
+
+// W depends on n and the level's nominal cluster size only (not on the CTAs
+// actually sharing the level), so a level's forces are the same bits in a
+// cluster launch and in the one-CTA batched launch.
+__device__ void walk_group(SmallSmem& s, int n, float2* F, int* err, int crank, int csize,
+                           int nominal) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kT / 32;
+  const int nt = (n + 31) / 32;
+  const int mine = crank < nt ? (nt - 1 - crank) / csize + 1 : 0;  // my tasks
+  const int per = (nt + nominal - 1) / max(nominal, 1);              // tasks per nominal CTA
+  int W = 1;
+  while (W < 16 && 2 * W * per <= kWarps) W <<= 1;
+  const int slots = kWarps / W, slot = warp / W, sub = warp % W;
+  // scratch in the (dead) radix-tree arrays, 16-byte aligned
+  unsigned char* scr = reinterpret_cast<unsigned char*>(
+      ((uintptr_t)reinterpret_cast<unsigned char*>(s.lo) + 15) & ~(uintptr_t)15);
+  float2(*part)[32] = reinterpret_cast<float2(*)[32]>(scr);            // [32 warps][32]
+  int* seeds = reinterpret_cast<int*>(scr + sizeof(float2) * kWarps * 32) + slot * kSmallSeedMax;
+  int* nseeds = reinterpret_cast<int*>(scr + sizeof(float2) * kWarps * 32) +
+                kWarps * kSmallSeedMax + slot;
+  for (int t0 = 0; t0 < mine; t0 += slots) {  // rounds: the same count in every warp
+    const bool live = t0 + slot < mine;
+    const int task = crank + csize * (t0 + slot);
+    const int pos = task * 32 + lane;
+    const bool valid = live && pos < n;
+    const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
+    float fx = 0.f, fy = 0.f;
+    int budget = 2 * n + 2;
+    if (sub == 0 && live) {
+      if (lane == 0) *nseeds = 0;
+      __syncwarp();
+      walk_cells(s, n, n > 1 ? 0 : -1, -1, xu, pos, valid, fx, fy, budget, err,
+                 W > 1 ? seeds : nullptr, nseeds);
+    }
+    if (W > 1) {
+      __syncthreads();
+      const int ns = live ? *nseeds : 0;
+      for (int j = sub; j < ns; j += W) {
+        const int c = seeds[j];
+        walk_cells(s, n, c, s.nodeB[c].y, xu, pos, valid, fx, fy, budget, err, nullptr, nullptr);
+      }
+      part[warp][lane] = make_float2(fx, fy);
+      __syncthreads();
+      if (sub == 0) {
+        float sx = 0.f, sy = 0.f;
+        for (int k = 0; k < W; ++k) {
+          sx += part[slot * W + k][lane].x;
+          sy += part[slot * W + k][lane].y;
+        }
+        fx = sx;
+        fy = sy;
       }
     }
-    if (valid) F[s.vals[pos]] = make_float2(fx, fy);
+    if (sub == 0 && valid) F[s.vals[pos]] = make_float2(fx, fy);
+    if (W > 1) __syncthreads();  // seeds and partial sums are reused next round
   }
 }
 
@@ -527,7 +594,7 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
       build_tree(s, n, a.theta, a.leaf, &root, red, prof);
       MM_STAMP(6);
       if (a.group)
-        walk_group(s, n, F, a.err, crank, csize);
+        walk_group(s, n, F, a.err, crank, csize, a.cluster);
       else
         walk(s, n, F, a.err, crank, csize);
     }
@@ -638,6 +705,11 @@ int g_max_cluster = 0;  // largest cluster the fused kernel can be launched with
 }  // namespace
 
 static_assert(sizeof(SmallSmem) + 1024 <= 227 * 1024, "fused level kernel exceeds shared memory");
+// the walk's scratch (partial sums of 32 warps, seeds of up to 32 task slots
+// and their counts, 16-byte alignment slack) fits the radix-tree arrays
+static_assert(15 + sizeof(float2) * 32 * 32 + sizeof(int) * (32 * kSmallSeedMax + 32) <=
+                  5 * sizeof(int16_t) * kN,
+              "walk scratch exceeds the radix-tree arrays");
 
 size_t small_level_smem() { return sizeof(SmallSmem); }
 
