@@ -544,25 +544,26 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
   SmallSmem& s = *reinterpret_cast<SmallSmem*>(smem_raw);
   __shared__ double red[96];
   __shared__ float4 root;
-  __shared__ int sh_parity, sh_done;
-  __shared__ float sh_alpha;
+  __shared__ int sh_done;
+  // every CTA keeps its own copy of the schedule state and takes the same
+  // (deterministic) steps on it; CTA 0 writes it back at the end
+  __shared__ SweepState lst;
   const int n = a.n, tid = threadIdx.x;
+  if (tid == 0) lst = *a.st;
   float2* F = s.F;
   for (int i = tid; i <= n; i += kT) s.sp[i] = a.sp[i];
   for (int i = tid; i < n; i += kT) s.rho[i] = a.rho[i];
   const int nt = (n + 31) / 32;                                // tasks
   const int mine = crank < nt ? ((nt - 1 - crank) / csize + 1) * 32 : 0;  // my positions
   for (int sweep = 0;; ++sweep) {
-    if (tid == 0) {
-      // written by CTA 0 of this cluster (or an earlier kernel): read at L2
-      sh_parity = __ldcg(&a.st->parity);
-      sh_alpha = (float)__ldcg(&a.st->alpha);
-      if (sweep == 0 && a.prof && crank == 0) a.prof[0] = clock64();
-    }
+    if (tid == 0 && sweep == 0 && a.prof && crank == 0) a.prof[0] = clock64();
     __syncthreads();
-    const float2* xg = sh_parity ? a.b1 : a.b0;
-    float2* xo = sh_parity ? a.b0 : a.b1;
-    const float alpha = sh_alpha;
+    const float2* xg = lst.parity ? a.b1 : a.b0;
+    float2* xo = lst.parity ? a.b0 : a.b1;
+    const float alpha = (float)lst.alpha;
+    // per-vertex partial sums alternate between two buffers: a CTA that
+    // runs ahead into the next sweep cannot overwrite sums still being read
+    float4* part = a.part + (sweep & 1) * kSmallMaxN;
     for (int i = tid; i < n; i += kT) s.xv[i] = __ldcg(&xg[i]);
     __syncthreads();
     const float2* x = s.xv;
@@ -648,32 +649,36 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
           const float ny = (gy + alpha * (f.y - ry)) / r;
           xo[u] = make_float2(nx, ny);
           const float ddx = nx - xu.x, ddy = ny - xu.y;
-          a.part[u] = make_float4(fmaf(ddx, ddx, ddy * ddy), fmaf(xu.x, xu.x, xu.y * xu.y),
-                                  0.5f * st, 0.f);
+          part[u] = make_float4(fmaf(ddx, ddx, ddy * ddy), fmaf(xu.x, xu.x, xu.y * xu.y),
+                                0.5f * st, 0.f);
         }
       }
     }
     cluster_sync(csize);  // every new position and partial is written
     MM_STAMP(8);
-    if (crank == 0) {
+    {
+      // the same reduction, in vertex order, in every CTA
       float psdx = 0.f, psx = 0.f, psst = 0.f;
       for (int u = tid; u < n; u += kT) {
-        const float4 q = __ldcg(&a.part[u]);
+        const float4 q = __ldcg(&part[u]);
         psdx += q.x;
         psx += q.y;
         psst += q.z;
       }
       double tot[3];
       bsum3(psdx, psx, psst, red, tot);
-      if (tid == 0)
-        schedule_step(a.st, a.sched, tot[0], tot[1], tot[2], a.trace, a.trace_cap, a.lsw);
+      if (tid == 0) {
+        const bool done = schedule_step(&lst, a.sched, tot[0], tot[1], tot[2],
+                                        crank == 0 ? a.trace : nullptr, a.trace_cap,
+                                        crank == 0 ? a.lsw : nullptr);
+        sh_done = (done || sweep + 1 >= a.max_sweeps) ? 1 : 0;
+      }
     }
-    cluster_sync(csize);  // the schedule state is updated
-    if (tid == 0) sh_done = (__ldcg(&a.st->done) != 0 || sweep + 1 >= a.max_sweeps) ? 1 : 0;
     __syncthreads();
     MM_STAMP(9);
     if (sh_done) break;
   }
+  if (crank == 0 && tid == 0) *a.st = lst;
 }
 
 __device__ __forceinline__ unsigned cluster_rank() {

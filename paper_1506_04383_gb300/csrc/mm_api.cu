@@ -42,7 +42,7 @@ struct mm_hierarchy {
   double* partials = nullptr;
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
-  float4* spart = nullptr;           // [kSmallMaxN] fused-level partial sums
+  float4* spart = nullptr;           // [2 kSmallMaxN] fused-level partial sums
   float4* box = nullptr;             // [kMaxGatherBlocks] update-block boxes
   unsigned* arrive = nullptr;        // update epilogue arrival counter
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
@@ -691,7 +691,7 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->state, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->sstate, sizeof(SweepState), s));
-  MM_CK(cudaMallocAsync(&h->spart, sizeof(float4) * (size_t)kSmallMaxN, s));
+  MM_CK(cudaMallocAsync(&h->spart, sizeof(float4) * 2 * (size_t)kSmallMaxN, s));
   MM_CK(cudaMallocAsync(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->arrive, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));

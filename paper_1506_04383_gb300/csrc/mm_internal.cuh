@@ -325,7 +325,7 @@ struct SmallArgs {
   int max_sweeps;
   int lanes;       // lanes per S row in the update (power of two <= 32)
   int cluster;     // CTAs that share the level (single-level launches)
-  float4* part;    // [kSmallMaxN] per-vertex partial sums (device scratch)
+  float4* part;    // [2 kSmallMaxN] per-vertex partial sums (two buffers)
   int* err;
   long long* prof; // nullable: clock64 stamps of the first sweep's phases [10]
 };
