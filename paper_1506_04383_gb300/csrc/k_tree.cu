@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kBBoxThreads) bbox_kernel(XSel xs, int n, floa
 // radix sort, in one pass over the positions.
 __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
     XSel xs, int n, const float4* __restrict__ root, uint32_t* __restrict__ keys,
-    int32_t* __restrict__ vals, uint32_t* hist) {
+    int32_t* __restrict__ vals, uint32_t* hist, uint32_t mask) {
   __shared__ uint32_t h[4][256];
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
   __syncthreads();
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
     // clamp in float first: the conversion of out-of-range values is undefined
     const uint32_t ix = (uint32_t)fminf(fmaxf(fx, 0.f), 65535.f);
     const uint32_t iy = (uint32_t)fminf(fmaxf(fy, 0.f), 65535.f);
-    const uint32_t k = (spread16(ix) << 1) | spread16(iy);
+    const uint32_t k = ((spread16(ix) << 1) | spread16(iy)) & mask;
     keys[i] = k;
     vals[i] = i;
 #pragma unroll
@@ -421,7 +421,7 @@ __device__ __forceinline__ int escape_of(const TreeView& t, int h) {
 }
 
 __device__ void write_record(const TreeView& t, int id, double2 sum, float side, float theta,
-                             int leaf, float4* nodeA, int4* nodeB) {
+                             int leaf, int maxdepth, float4* nodeA, int4* nodeB) {
   const int n = t.n;
   if (id >= n - 1) {  // leaf j
     const int j = id - (n - 1);
@@ -435,7 +435,7 @@ __device__ void write_record(const TreeView& t, int id, double2 sum, float side,
   int depth, first;
   if (dd >= 32) {  // duplicate keys: bucket leaf at the deepest level
     if (dp >= 32) return;
-    depth = kKeyBits;
+    depth = maxdepth;
     first = -1;
   } else {
     if (dp >= 0 && (dp >> 1) == (dd >> 1)) return;  // transparent
@@ -473,7 +473,7 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const double2* __restrict__ incl,
                                const double2* __restrict__ tile_off,
                                const float4* __restrict__ root, float theta, int leaf,
-                               float4* nodeA, int4* nodeB) {
+                               int maxdepth, float4* nodeA, int4* nodeB) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
   if (kFold) {
@@ -502,7 +502,7 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
     const double2 b = prefix_at(incl, tile_off, t.hi[id] + 1);
     sum = make_double2(b.x - a.x, b.y - a.y);
   }
-  write_record(t, id, sum, root->z, theta, leaf, nodeA, nodeB);
+  write_record(t, id, sum, root->z, theta, leaf, maxdepth, nodeA, nodeB);
 }
 
 // Guards: node ids must stay in [0, 2n-1) and a walk visits each node at
@@ -801,7 +801,7 @@ mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s) {
 }
 
 mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
-                   cudaEvent_t* ev, bool with_bbox) {
+                   cudaEvent_t* ev, bool with_bbox, bool coarse_keys) {
   if (n <= 0) return MM_OK;
   if (n > ws.cap) {
     set_error("tree workspace holds %lld vertices, level has %d", (long long)ws.cap, n);
@@ -814,11 +814,16 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   mark(0);
   if (with_bbox) MM_TRY(bh_bbox(x, n, ws, s));
   mark(1);
-  morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, ws.root, ws.keys[0], ws.vals[0],
-                                                   ws.hist);
+  // 32-bit keys: four stable 8-bit passes from buffer 0; coarse keys (the
+  // low 8 bits cleared: cells down to depth 12) need only the passes over
+  // the upper three digits, from buffer 1.  Either way the result ends in
+  // buffer 0.
+  const int first = coarse_keys ? 1 : 0;
+  morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, ws.root, ws.keys[first],
+                                                   ws.vals[first], ws.hist,
+                                                   coarse_keys ? 0xffffff00u : 0xffffffffu);
   mark(2);
-  // four stable 8-bit passes; the result is back in buffer 0
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = first; pass < 4; ++pass) {
     const int a = pass & 1;
     onesweep_pass<<<tiles, kSortThreads, 0, s>>>(ws.keys[a], ws.vals[a], ws.keys[a ^ 1],
                                                  ws.vals[a ^ 1], n, pass, ws.hist, ws.counters,
@@ -847,10 +852,12 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   TreeView tv{n, ws.lo, ws.hi, ws.left, ws.right, ws.delta, ws.owner, ws.parent};
   if (fold)
     records_kernel<true><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
-        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, ws.nodeA, ws.nodeB);
+        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, coarse_keys ? 12 : kKeyBits,
+        ws.nodeA, ws.nodeB);
   else
     records_kernel<false><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
-        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, ws.nodeA, ws.nodeB);
+        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, coarse_keys ? 12 : kKeyBits,
+        ws.nodeA, ws.nodeB);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;

@@ -227,7 +227,7 @@ int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
   const Level& L = h->levels[level];
   int64_t k = 1 + (L.n_heavy > 0 ? 1 : 0);  // update (+ heavy rows), epilogue fused
   if (exact) return k + 1;                   // tiled exact sum
-  k += 1 + 4;                                // Morton keys + histograms, 4 sort passes
+  k += 1 + (group_of(h->p) ? 3 : 4);         // Morton keys + histograms, sort passes
   if (L.n > 1) k += 1;                       // radix tree
   k += 1;                                    // position prefix sums
   if (ceil_div(L.n, kSortTile) > 128) k += 1;  // tile scan (else folded into records)
@@ -284,7 +284,8 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   if (exact) {
     MM_TRY(exact_repulsion(x, L.n, h->F, s));
   } else {
-    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop));
+    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop,
+                    group_of(h->p)));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                        nullptr, s, group_of(h->p)));
   }
@@ -1241,7 +1242,8 @@ mm_status tune_levels(mm_hierarchy* h, cudaStream_t s) {
     fill_uniform<<<ceil_div(L.n, 256), 256, 0, s>>>(L.n, sqrtf((float)L.n), 12345u, h->xb[0]);
     XSel x{h->xb[0], h->xb[1], h->zero};
     set_state<<<1, 1, 0, s>>>(h->sstate, 0.008);
-    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s));
+    MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, true,
+                    group_of(h->p)));
     double best = 1e30;
     int best_lanes = L.lanes;
     const int keep = L.lanes;
@@ -1581,7 +1583,7 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   const int n = h->levels[level].n;
   XSel xs{(const float2*)x, (const float2*)x, h->zero};
   if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
-  MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s));
+  MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s, nullptr, true, group_of(h->p)));
   MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s,
                      group_of(h->p)));
   return tree_error(h, s);
@@ -1683,7 +1685,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
       for (int i = 1; i <= 5; ++i) cudaEventRecord(ev[i], s);
       st = exact_repulsion(xs, L.n, h->F, s);
     } else {
-      st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev);
+      st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev, true, group_of(h->p));
       if (st == MM_OK)
         st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                          nullptr, s, group_of(h->p));
@@ -1706,7 +1708,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     }
   }
   if (st == MM_OK && !exact && work) {
-    st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s);
+    st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, true, group_of(h->p));
     if (st == MM_OK)
       st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                        cnt, s, group_of(h->p));

@@ -235,8 +235,12 @@ void tree_ws_free(TreeWS& ws);
 // leaf: cells with at most `leaf` points become leaves (1..kMaxLeaf).
 // with_bbox = false: the root square (and the zeroed sort state) was left
 // by the previous sweep's update epilogue or an explicit bh_bbox.
+// coarse_keys: Morton keys of 12 bits per axis (cells down to depth 12;
+// points in one deepest cell form a bucket), three sort passes instead of
+// four -- used with group acceptance, whose walk does not reproduce the
+// oracle's per-point cells anyway.
 mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_t s,
-                   cudaEvent_t* ev = nullptr, bool with_bbox = true);
+                   cudaEvent_t* ev = nullptr, bool with_bbox = true, bool coarse_keys = false);
 // Bounding square of x into ws.root; zeroes the sort histograms and
 // counters and starts a new look-back epoch.
 mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s);

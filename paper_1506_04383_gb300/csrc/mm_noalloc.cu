@@ -166,7 +166,7 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   // mm_repulsion on a hierarchy built with mm_default_params
   mm_params d;
   mm_default_params(&d);
-  MM_TRY(bh_build(xs, n, theta, leaf_of(d), ws, s));
+  MM_TRY(bh_build(xs, n, theta, leaf_of(d), ws, s, nullptr, true, group_of(d)));
   MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s, group_of(d)));
   int err = 0;
   MM_CK(cudaMemcpyAsync(&err, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
