@@ -408,19 +408,41 @@ __device__ __forceinline__ void walk_cells(const SmallSmem& s, int n, int cur, i
   }
 }
 
-// W depends on n and the level's nominal cluster size only (not on the CTAs
-// actually sharing the level), so a level's forces are the same bits in a
-// cluster launch and in the one-CTA batched launch.
-__device__ void walk_group(SmallSmem& s, int n, float2* F, int* err, int crank, int csize,
-                           int nominal) {
+// The seeds are dealt to kSmallVirt seed groups (seed j to group j mod 8);
+// each group's walks are added in seed order and the groups in a fixed
+// binary tree, ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)), plus the
+// first warp's own partial sum.  A warp of a W-warp task takes 8 / W
+// consecutive groups and adds its complete subtree; the task's first warp
+// adds the W subtotals with the rest of the tree.  The forces are therefore
+// the same bits for every W: in a cluster launch (few tasks per CTA, W up
+// to 8) and in the one-CTA batched launch (many tasks, W = 1).
+constexpr int kSmallVirt = 8;
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+
+// In place: acc[0] = the complete pairwise tree over acc[0 .. width).
+__device__ __forceinline__ void tree_sum(float2 (&acc)[kSmallVirt], int width) {
+#pragma unroll
+  for (int w = kSmallVirt; w > 1; w >>= 1) {
+    if (w <= width) {
+#pragma unroll
+      for (int q = 0; q < kSmallVirt / 2; ++q)
+        if (2 * q + 1 < w) acc[q] = f2add(acc[2 * q], acc[2 * q + 1]);
+    }
+  }
+}
+
+__device__ void walk_group(SmallSmem& s, int n, float2* F, int* err, int crank, int csize) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kWarps = kT / 32;
   const int nt = (n + 31) / 32;
   const int mine = crank < nt ? (nt - 1 - crank) / csize + 1 : 0;  // my tasks
-  const int per = (nt + nominal - 1) / max(nominal, 1);              // tasks per nominal CTA
   int W = 1;
-  while (W < 16 && 2 * W * per <= kWarps) W <<= 1;
+  while (W < kSmallVirt && 2 * W * mine <= kWarps) W <<= 1;
   const int slots = kWarps / W, slot = warp / W, sub = warp % W;
+  const int vper = kSmallVirt / W;  // seed groups per warp
   // scratch in the (dead) radix-tree arrays, 16-byte aligned
   unsigned char* scr = reinterpret_cast<unsigned char*>(
       ((uintptr_t)reinterpret_cast<unsigned char*>(s.lo) + 15) & ~(uintptr_t)15);
@@ -434,35 +456,46 @@ __device__ void walk_group(SmallSmem& s, int n, float2* F, int* err, int crank, 
     const int pos = task * 32 + lane;
     const bool valid = live && pos < n;
     const float2 xu = valid ? s.xs[pos] : make_float2(0.f, 0.f);
-    float fx = 0.f, fy = 0.f;
+    float2 top = make_float2(0.f, 0.f);
     int budget = 2 * n + 2;
     if (sub == 0 && live) {
       if (lane == 0) *nseeds = 0;
       __syncwarp();
-      walk_cells(s, n, n > 1 ? 0 : -1, -1, xu, pos, valid, fx, fy, budget, err,
-                 W > 1 ? seeds : nullptr, nseeds);
+      walk_cells(s, n, n > 1 ? 0 : -1, -1, xu, pos, valid, top.x, top.y, budget, err, seeds,
+                 nseeds);
     }
+    __syncthreads();
+    const int ns = live ? *nseeds : 0;
+    float2 acc[kSmallVirt];
+#pragma unroll
+    for (int q = 0; q < kSmallVirt; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int j = 0; j < ns; ++j) {
+      const int v = j % kSmallVirt;
+      if (v / vper != sub) continue;
+      const int c = seeds[j];
+      float2 t = make_float2(0.f, 0.f);
+      walk_cells(s, n, c, s.nodeB[c].y, xu, pos, valid, t.x, t.y, budget, err, nullptr, nullptr);
+      const int q = v - sub * vper;
+#pragma unroll
+      for (int qq = 0; qq < kSmallVirt; ++qq)
+        if (qq == q) acc[qq] = f2add(acc[qq], t);
+    }
+    tree_sum(acc, vper);
+    float2 total = acc[0];
     if (W > 1) {
-      __syncthreads();
-      const int ns = live ? *nseeds : 0;
-      for (int j = sub; j < ns; j += W) {
-        const int c = seeds[j];
-        walk_cells(s, n, c, s.nodeB[c].y, xu, pos, valid, fx, fy, budget, err, nullptr, nullptr);
-      }
-      part[warp][lane] = make_float2(fx, fy);
+      part[warp][lane] = total;
       __syncthreads();
       if (sub == 0) {
-        float sx = 0.f, sy = 0.f;
-        for (int k = 0; k < W; ++k) {
-          sx += part[slot * W + k][lane].x;
-          sy += part[slot * W + k][lane].y;
-        }
-        fx = sx;
-        fy = sy;
+        float2 w8[kSmallVirt];
+#pragma unroll
+        for (int q = 0; q < kSmallVirt; ++q)
+          w8[q] = q < W ? part[slot * W + q][lane] : make_float2(0.f, 0.f);
+        tree_sum(w8, W);
+        total = w8[0];
       }
     }
-    if (sub == 0 && valid) F[s.vals[pos]] = make_float2(fx, fy);
-    if (W > 1) __syncthreads();  // seeds and partial sums are reused next round
+    if (sub == 0 && valid) F[s.vals[pos]] = f2add(top, total);
+    __syncthreads();  // seeds and partial sums are reused next round
   }
 }
 
@@ -595,7 +628,7 @@ __device__ __forceinline__ void run_level(const SmallArgs& a, int crank, int csi
       build_tree(s, n, a.theta, a.leaf, &root, red, prof);
       MM_STAMP(6);
       if (a.group)
-        walk_group(s, n, F, a.err, crank, csize, a.cluster);
+        walk_group(s, n, F, a.err, crank, csize);
       else
         walk(s, n, F, a.err, crank, csize);
     }
