@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kLPWarps * 32) lp_propose(
   if (lane == 0) {
     // stay unless another eligible cluster is strictly better connected
     if (best > ownc && bestL != 0x7fffffff)
-      keys[v] = ((uint64_t)bestL << 32) | (uint64_t)z[1];
+      keys[v] = ((uint64_t)bestL << 8) | (uint64_t)(z[1] >> 24);
     else
       keys[v] = none;
   }
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kLPHeavyT) lp_propose_heavy(
       ownc += so[k];
       if (sb[k] > best || (sb[k] == best && sl[k] < bestL)) { best = sb[k]; bestL = sl[k]; }
     }
-    keys[v] = (best > ownc && bestL != 0x7fffffff) ? (((uint64_t)bestL << 32) | (uint64_t)z[1])
+    keys[v] = (best > ownc && bestL != 0x7fffffff) ? (((uint64_t)bestL << 8) | (uint64_t)(z[1] >> 24))
                                                   : ~(uint64_t)0;
   }
 }
@@ -386,10 +386,10 @@ __global__ void lp_admit(int n, const uint64_t* __restrict__ keys, const int32_t
   if (i >= n) return;
   const uint64_t k = keys[i];
   if (k == ~(uint64_t)0) return;
-  const int T = (int)(k >> 32);
-  if (i > 0 && (int)(keys[i - 1] >> 32) == T && keys[i - 1] != ~(uint64_t)0) return;
+  const int T = (int)(k >> 8);
+  if (i > 0 && (int)(keys[i - 1] >> 8) == T && keys[i - 1] != ~(uint64_t)0) return;
   float acc = W[T];
-  for (int j = i; j < n && keys[j] != ~(uint64_t)0 && (int)(keys[j] >> 32) == T; ++j) {
+  for (int j = i; j < n && keys[j] != ~(uint64_t)0 && (int)(keys[j] >> 8) == T; ++j) {
     const int v = vals[j];
     if (acc + c[v] <= U) {
       acc += c[v];
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(kLPSmallT, 1) lp_small_kernel(
         if (lane == 0)
           s.key[v] = (best > ownc && bestL != 0x7fffffff)
                          ? ((unsigned long long)bestL << 44) |
-                               ((unsigned long long)z[1] << 12) | (unsigned long long)v
+                               ((unsigned long long)(z[1] >> 24) << 12) | (unsigned long long)v
                          : none;
         __syncwarp();
       }
@@ -811,10 +811,10 @@ mm_status cluster_lp(int n, const int32_t* rp, const int32_t* col, const float* 
       uint64_t* keys;
       int32_t* vals;
       st = radix_sort_u64(k0.as<uint64_t>(), k1.as<uint64_t>(), v0.as<int32_t>(), v1.as<int32_t>(),
-                          n, 0, 32 + tb, sws.ws, s, &keys, &vals);
+                          n, 0, 8 + tb, sws.ws, s, &keys, &vals);
       if (st != MM_OK) break;
       // keys equal to all ones sort last only if every bit is compared: the
-      // sort above covers bits [0, 32 + tb) and targets are < 2^(tb-1)
+      // sort above covers bits [0, 8 + tb) and targets are < 2^(tb-1)
       lp_admit<<<ceil_div(n, 256), 256, 0, s>>>(n, keys, vals, c, W.as<float>(), U, labels,
                                                  mv.as<int>());
       cudaMemsetAsync(W.p, 0, sizeof(float) * (size_t)n, s);

@@ -169,12 +169,13 @@ def test_learned_prolongation_layout(mm):
 
 def test_trained_network_gains_over_plain_prolongation(mm):
     """Trained on the method's own pairs of three small random geometric
-    graphs, the network must (1) cut the prolongation error on an unseen
-    graph's levels to under a third and (2) reach the reference objective --
-    the plain layout's at the default cap of 100 sweeps per level, within
-    the 1% that layout parity uses -- with at most 60% of the sweeps the
-    plain layout needs for it (both at their smallest matching per-level cap
-    in 5, 10, 20, 30, 50, 100)."""
+    graphs, the network must, on three unseen graphs, (1) cut the
+    prolongation error to under a third and (2) reach each graph's reference
+    objective -- the plain layout's at the default cap of 100 sweeps per
+    level, within the 1% that layout parity uses -- with no more sweeps than
+    the plain layout needs for it on any graph and at most half of its
+    sweeps over the three (both at their smallest matching per-level cap in
+    5, 10, 15, 20, 30, 50, 100)."""
     from paper_1506_04383_gb300 import learned
     pairs = []
     for n, sd in [(5000, 40), (10000, 41), (20000, 42)]:
@@ -183,33 +184,38 @@ def test_trained_network_gains_over_plain_prolongation(mm):
     net = mm.Net(learned.init_params(1))
     losses = learned.train(net, pairs, 1500, lr=3e-3, seed=0)
     assert np.mean(losses[-100:]) < 0.2 * np.mean(losses[:100])
-    rp, col, _, _ = graphs.rgg(30000, 8.0, 77)
-    h = mm.build_hierarchy(cu(rp), cu(col))
-    val = learned.level_pairs(h)
     z = learned.zero_net()
-    w = np.array([p["n"] for p in val], dtype=np.float64)
-    plain = np.array([learned.pair_loss(z, p) for p in val])
-    lrn = np.array([learned.pair_loss(net, p) for p in val])
-    assert (w * lrn).sum() < (w * plain).sum() / 3
-    p = mm.default_params()
-    x_ref, st_ref = mm.layout(h, p)
-    bound = mm.objective(h, 0, x_ref, p.alpha_min)[2]
-    bound += 0.01 * abs(bound)
+    tot_plain = tot_learned = 0
+    for nv, sd in [(30000, 77), (30000, 78), (60000, 79)]:
+        rp, col, _, _ = graphs.rgg(nv, 8.0, sd)
+        h = mm.build_hierarchy(cu(rp), cu(col))
+        val = learned.level_pairs(h)
+        w = np.array([p["n"] for p in val], dtype=np.float64)
+        plain = np.array([learned.pair_loss(z, p) for p in val])
+        lrn = np.array([learned.pair_loss(net, p) for p in val])
+        assert (w * lrn).sum() < (w * plain).sum() / 3
+        p = mm.default_params()
+        x_ref, _ = mm.layout(h, p)
+        bound = mm.objective(h, 0, x_ref, p.alpha_min)[2]
+        bound += 0.01 * abs(bound)
 
-    def sweeps_to_match(with_net):
-        for cap in (5, 10, 20, 30, 50, 100):
-            q = mm.default_params()
-            q.max_iters_at_min = cap
-            if with_net:
-                mm.set_net(h, net)
-                q.learned_prolong = 1
-            x, st = mm.layout(h, q)
-            mm.set_net(h, None)
-            if mm.objective(h, 0, x, q.alpha_min)[2] <= bound:
-                return st["total_sweeps"]
-        return None
+        def sweeps_to_match(with_net):
+            for cap in (5, 10, 15, 20, 30, 50, 100):
+                q = mm.default_params()
+                q.max_iters_at_min = cap
+                if with_net:
+                    mm.set_net(h, net)
+                    q.learned_prolong = 1
+                x, st = mm.layout(h, q)
+                mm.set_net(h, None)
+                if mm.objective(h, 0, x, q.alpha_min)[2] <= bound:
+                    return st["total_sweeps"]
+            return None
 
-    s_plain = sweeps_to_match(False)
-    s_learned = sweeps_to_match(True)
-    assert s_plain is not None and s_learned is not None
-    assert 5 * s_learned <= 3 * s_plain, (s_learned, s_plain)
+        s_plain = sweeps_to_match(False)
+        s_learned = sweeps_to_match(True)
+        assert s_plain is not None and s_learned is not None
+        assert s_learned <= s_plain, (nv, sd, s_learned, s_plain)
+        tot_plain += s_plain
+        tot_learned += s_learned
+    assert 2 * tot_learned <= tot_plain, (tot_learned, tot_plain)
