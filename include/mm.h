@@ -62,7 +62,7 @@ typedef struct mm_params {
   float theta;              /* Barnes-Hut opening parameter; 0 = exact via tree*/
   int32_t exact_repulsion;  /* 1: exact O(n^2) entropy sum on every level     */
   int32_t coarsest_n;       /* coarsen while n > coarsest_n (>= 2)            */
-  float f, b;               /* SCLaP W = min(b^(h+1), n/f) (Sec. 3.1)         */
+  float f, b;               /* SCLaP W = min(b^(h+1), |V|/f) (Sec. 3.1)       */
   int32_t lp_rounds;        /* SCLaP rounds l                                 */
   int32_t iters_per_alpha;  /* a: iterations per alpha round                  */
   double alpha0, alpha_factor, alpha_min;
@@ -128,7 +128,8 @@ const char* mm_last_error(void);
 /*
  * Builds the coarsening hierarchy of Sec. 3.1 on the device: level 0 is the
  * input graph; level h+1 is the contraction of a size-constrained label
- * propagation clustering of level h with U = max(max c, min(b^(h+1), n/f)).
+ * propagation clustering of level h with U = max(max c, min(b^(h+1), |V|/f)),
+ * |V| the input graph's vertex count.
  * A contraction that shrinks the graph by at most 10 percent sets f := 0.7f.
  * For every level it also builds the pair set S (k hops) with target
  * distances d (Sec. 3.2: sqrt(c_u) + sqrt(c_v) per edge on coarse levels)

@@ -258,8 +258,9 @@ def params(**kw):
 
 def build_hierarchy(rp, col, p, elen=None):
     """Coarsening (Sec. 3.1).  Level h is clustered by SCLaP with
-    U = max(max c, W), W = min(b^(h+1), n/f); the contraction becomes level
-    h+1.  A contraction that shrinks the graph by at most 10 percent sets
+    U = max(max c, W), W = min(b^(h+1), |V|/f) with |V| the input graph's
+    vertex count (the unit of the node weights c, and their sum on every
+    level); the contraction becomes level h+1.  A contraction that shrinks the graph by at most 10 percent sets
     f := 0.7 f.  One that merges nothing is discarded (f := 0.7 f, retried up
     to max_stalls times).  Coarsening stops at n <= coarsest_n."""
     rp, col = _i64(rp), _i32(col)
@@ -273,7 +274,7 @@ def build_hierarchy(rp, col, p, elen=None):
            and stalls < p["max_stalls"]):
         cur = levels[-1]
         h = len(levels) - 1
-        W = min(p["b"] ** (h + 1), cur["n"] / f)
+        W = min(p["b"] ** (h + 1), n / f)
         U = max(float(np.max(cur["c"])), W)
         labels = sclap(cur["rp"], cur["col"], cur["c"], U, p["lp_rounds"], p["seed"], h,
                        ew=cur["ew"])

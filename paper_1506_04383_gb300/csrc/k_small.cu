@@ -49,17 +49,6 @@ struct __align__(16) SmallSmem {
   int8_t delta[kN];
 };
 
-// Error-free float-float addition (Knuth's two-sum, then renormalise): the
-// prefix sums keep ~44 significant bits using only FP32 arithmetic.
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  const float s = a.x + b.x;
-  const float v = s - a.x;
-  float e = (a.x - (s - v)) + (b.x - v);
-  e += a.y + b.y;
-  const float hi = s + e;
-  return make_float2(hi, e - (hi - s));
-}
-
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
   v &= 0xffffu;
   v = (v | (v << 8)) & 0x00ff00ffu;
@@ -90,8 +79,7 @@ __device__ __forceinline__ int s_escape(const SmallSmem& s, int n, int h) {
 }
 
 // Block-wide sums of three per-thread partials: warp shuffles in FP32, the 32
-// warp totals summed in FP64 by thread 0 only (FP64 issue rate on this part
-// is a small fraction of FP32).  Result valid in thread 0.
+// warp totals in float-float by warp 0.  Result valid in thread 0.
 __device__ __forceinline__ void bsum3(float a, float b, float c, double* red, double out[3]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -100,13 +88,25 @@ __device__ __forceinline__ void bsum3(float a, float b, float c, double* red, do
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
+  float* fr = reinterpret_cast<float*>(red);
   __syncthreads();
-  if (lane == 0) { red[warp] = a; red[32 + warp] = b; red[64 + warp] = c; }
+  if (lane == 0) { fr[warp] = a; fr[32 + warp] = b; fr[64 + warp] = c; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double x = 0, y = 0, z = 0;
-    for (int w = 0; w < kT / 32; ++w) { x += red[w]; y += red[32 + w]; z += red[64 + w]; }
-    out[0] = x; out[1] = y; out[2] = z;
+  if (warp == 0) {
+    float2 p = make_float2(lane < kT / 32 ? fr[lane] : 0.f, 0.f);
+    float2 q = make_float2(lane < kT / 32 ? fr[32 + lane] : 0.f, 0.f);
+    float2 r = make_float2(lane < kT / 32 ? fr[64 + lane] : 0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      p = ff_add(p, ff_shfl_xor(p, o));
+      q = ff_add(q, ff_shfl_xor(q, o));
+      r = ff_add(r, ff_shfl_xor(r, o));
+    }
+    if (lane == 0) {
+      out[0] = (double)p.x + (double)p.y;
+      out[1] = (double)q.x + (double)q.y;
+      out[2] = (double)r.x + (double)r.y;
+    }
   }
 }
 

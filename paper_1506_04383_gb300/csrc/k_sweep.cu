@@ -10,8 +10,9 @@
 // subtraction is the one of Eq. 3).  The kernel streams the CSR of S once:
 // G lanes cooperate on one row (G chosen from the mean row length so a row
 // is read as consecutive 8-byte entries), rows longer than a threshold are
-// handled by a whole block each, and per-block FP64 partials of
-// sum|x'-x|^2, sum|x|^2 and the stress feed the controller.
+// handled by a whole block each, and per-block FP32 partials of
+// sum|x'-x|^2, sum|x|^2 and the stress, added in float-float, feed the
+// controller.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -68,10 +69,12 @@ __device__ __forceinline__ void finish_vertex(int u, const RowAcc& a, float2 xu,
   s_st = fmaf(0.5f, a.st, s_st);
 }
 
-// Per-thread FP32 partials -> warp totals (FP32 shuffles) -> FP64 block sums
-// by thread 0 (FP64 issue rate on this part is a small fraction of FP32).
+// Per-thread FP32 partials -> block totals in FP32 (warp shuffles, then the
+// warp totals in warp 0); a block adds a few thousand terms at most, the
+// blocks' totals are added in float-float by the last block.  Result in
+// thread 0.
 template <int kT>
-__device__ __forceinline__ void block_reduce3(float a, float b, float c, double* out) {
+__device__ __forceinline__ float4 block_sum3(float a, float b, float c) {
   __shared__ float sh[3][kT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -82,31 +85,34 @@ __device__ __forceinline__ void block_reduce3(float a, float b, float c, double*
   }
   if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double x = 0, y = 0, z = 0;
-    for (int w = 0; w < kT / 32; ++w) { x += sh[0][w]; y += sh[1][w]; z += sh[2][w]; }
-    out[0] = x; out[1] = y; out[2] = z;
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) {
+    a = lane < kT / 32 ? sh[0][lane] : 0.f;
+    b = lane < kT / 32 ? sh[1][lane] : 0.f;
+    c = lane < kT / 32 ? sh[2][lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    r = make_float4(a, b, c, 0.f);
   }
+  return r;
 }
 
-// FP64 variant for the controller (reduces per-block FP64 partials).
+// Float-float sums of per-block totals parts[0 .. nparts), each thread
+// taking every kT-th block, then the block tree.  Result in thread 0.
 template <int kT>
-__device__ __forceinline__ void block_reduce3d(double a, double b, double c, double* out) {
-  __shared__ double sh[3][kT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
+__device__ __forceinline__ void sum_parts(const float4* parts, int nparts, double out[3]) {
+  float2 a = make_float2(0.f, 0.f), b = a, c = a;
+  for (int i = threadIdx.x; i < nparts; i += kT) {
+    const float4 q = __ldcg(&parts[i]);
+    a = ff_add(a, make_float2(q.x, 0.f));
+    b = ff_add(b, make_float2(q.y, 0.f));
+    c = ff_add(c, make_float2(q.z, 0.f));
   }
-  if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double x = 0, y = 0, z = 0;
-    for (int w = 0; w < kT / 32; ++w) { x += sh[0][w]; y += sh[1][w]; z += sh[2][w]; }
-    out[0] = x; out[1] = y; out[2] = z;
-  }
+  block_ffsum3<kT>(a, b, c, out);
 }
 
 template <int kT>
@@ -138,18 +144,14 @@ __device__ __forceinline__ float4 block_box(Box b) {
 // square, zeroes the sort state and starts a new look-back epoch, so the
 // next sweep needs no separate controller or bounding-box launch.
 template <int kT>
-__device__ void update_tail(float s_dx, float s_x, float s_st, const Box& box, double* parts,
+__device__ void update_tail(float s_dx, float s_x, float s_st, const Box& box, float4* parts,
                             int part_off, int nparts, int epi, const SweepEpilogue& ep) {
-  __shared__ double tot[3];
   __shared__ bool last;
-  block_reduce3<kT>(s_dx, s_x, s_st, tot);
+  const float4 tot = block_sum3<kT>(s_dx, s_x, s_st);
   float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ep.box) bb = block_box<kT>(box);
   if (threadIdx.x == 0) {
-    double* p = parts + 3 * (size_t)(part_off + blockIdx.x);
-    p[0] = tot[0];
-    p[1] = tot[1];
-    p[2] = tot[2];
+    parts[part_off + blockIdx.x] = tot;
     if (ep.box) ep.box[part_off + blockIdx.x] = bb;
     if (epi) {
       __threadfence();
@@ -160,20 +162,16 @@ __device__ void update_tail(float s_dx, float s_x, float s_st, const Box& box, d
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double a = 0, b = 0, c = 0;
   float4 r = make_float4(CUDART_INF_F, CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F);
-  for (int i = threadIdx.x; i < nparts; i += kT) {
-    a += __ldcg(&parts[3 * i]);
-    b += __ldcg(&parts[3 * i + 1]);
-    c += __ldcg(&parts[3 * i + 2]);
-    if (ep.box) {
+  if (ep.box) {
+    for (int i = threadIdx.x; i < nparts; i += kT) {
       const float4 q = __ldcg(&ep.box[i]);
       r.x = fminf(r.x, q.x); r.y = fminf(r.y, q.y);
       r.z = fmaxf(r.z, q.z); r.w = fmaxf(r.w, q.w);
     }
   }
-  __shared__ double out[3];
-  block_reduce3d<kT>(a, b, c, out);
+  double out[3];
+  sum_parts<kT>(parts, nparts, out);
   if (ep.box) {
     Box q;
     q.x0 = r.x; q.y0 = r.y; q.x1 = r.z; q.y1 = r.w;
@@ -200,7 +198,7 @@ template <int G>
 __global__ void __launch_bounds__(kGatherThreads) gather_light(
     int n, const int32_t* __restrict__ sp, const SEnt* __restrict__ S,
     const float* __restrict__ rho, XSel xs, const float2* __restrict__ F,
-    const SweepState* st, int heavy, double* partials, int nparts, int epi, SweepEpilogue ep) {
+    const SweepState* st, int heavy, float4* partials, int nparts, int epi, SweepEpilogue ep) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
   const float alpha = (float)st->alpha;
@@ -240,7 +238,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
 __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
     const int32_t* __restrict__ heavy_list, int n_heavy, const int32_t* __restrict__ sp,
     const SEnt* __restrict__ S, const float* __restrict__ rho, XSel xs,
-    const float2* __restrict__ F, const SweepState* st, double* partials, int part_off,
+    const float2* __restrict__ F, const SweepState* st, float4* partials, int part_off,
     int nparts, int epi, SweepEpilogue ep) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
@@ -288,18 +286,11 @@ constexpr int kCtlThreads = 256;
 // alpha, alpha_min); at alpha_min iterate until the change is below
 // eps_final or max_iters_at_min iterations.
 __global__ void __launch_bounds__(kCtlThreads) controller_kernel(
-    int nparts, const double* __restrict__ partials, SweepState* st, SchedParams sp,
+    int nparts, const float4* __restrict__ partials, SweepState* st, SchedParams sp,
     float* trace, int trace_cap, int* level_sweeps_out, cudaGraphConditionalHandle h,
     int use_h) {
-  double a = 0, b = 0, c = 0;
-  for (int i = threadIdx.x; i < nparts; i += kCtlThreads) {
-    a += partials[3 * i];
-    b += partials[3 * i + 1];
-    c += partials[3 * i + 2];
-  }
-  __shared__ double out[3];
-  block_reduce3d<kCtlThreads>(a, b, c, out);
-  __syncthreads();
+  double out[3];
+  sum_parts<kCtlThreads>(partials, nparts, out);
   if (threadIdx.x != 0) return;
   const bool done = schedule_step(st, sp, out[0], out[1], out[2], trace, trace_cap,
                                   level_sweeps_out);
@@ -373,7 +364,7 @@ __global__ void copy_current_kernel(XSel xs, int n, float2* out) {
 }
 
 template <int G>
-void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st, double* partials,
+void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st, float4* partials,
                   int blocks, int nparts, int epi, const SweepEpilogue& ep, cudaStream_t s) {
   gather_light<G><<<blocks, kGatherThreads, 0, s>>>(L.n, L.sp, L.s, L.rho, x, F, st,
                                                     L.heavy_degree, partials, nparts, epi, ep);
@@ -393,7 +384,7 @@ int gather_heavy_blocks(const Level& L) {
 int gather_blocks(const Level& L) { return gather_light_blocks(L) + gather_heavy_blocks(L); }
 
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
-                        double* partials, cudaStream_t s, const SweepEpilogue* epi) {
+                        float4* partials, cudaStream_t s, const SweepEpilogue* epi) {
   if (L.n <= 0) return MM_OK;
   const int lb = gather_light_blocks(L);
   const int hb = gather_heavy_blocks(L);
@@ -420,7 +411,7 @@ mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepStat
   return MM_OK;
 }
 
-mm_status controller(int nblocks, const double* partials, SweepState* st, SchedParams sp,
+mm_status controller(int nblocks, const float4* partials, SweepState* st, SchedParams sp,
                      float* trace, int trace_cap, int* level_sweeps_out,
                      cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s) {
   controller_kernel<<<1, kCtlThreads, 0, s>>>(nblocks, partials, st, sp, trace, trace_cap,

@@ -40,7 +40,7 @@ struct mm_hierarchy {
   mm::TreeWS tree;
   float2* xb[2] = {nullptr, nullptr};
   float2* F = nullptr;
-  double* partials = nullptr;
+  float4* partials = nullptr;        // [kMaxGatherBlocks] per-block FP32 sums
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
   float4* spart = nullptr;           // [2 kSmallMaxN] fused-level partial sums
@@ -545,7 +545,10 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
     if (st != MM_OK) break;
     float maxc;
     memcpy(&maxc, &maxc_bits, sizeof(float));
-    const double W = std::min(std::pow((double)p->b, hidx + 1), cur.n / f);
+    // |V| of Sec. 3.1 is the input graph's vertex count: W bounds a cluster's
+    // weight, and the weights c count input vertices (their sum is n0 on
+    // every level)
+    const double W = std::min(std::pow((double)p->b, hidx + 1), n0 / f);
     const float U = (float)std::max((double)maxc, W);
     st = cluster_lp(cur.n, cur.rp, cur.col, cur.omega, cur.c, U, p->lp_rounds, p->seed, hidx,
                     labels, s);
@@ -690,7 +693,7 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->xb[1], sizeof(float2) * (size_t)n0, s));
   MM_CK(cudaMallocAsync(&h->F, sizeof(float2) * (size_t)n0, s));
   // partials for the largest grid any lanes setting (autotuner) can launch
-  MM_CK(cudaMallocAsync(&h->partials, sizeof(double) * 3 * (size_t)kMaxGatherBlocks, s));
+  MM_CK(cudaMallocAsync(&h->partials, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->state, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->sstate, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->spart, sizeof(float4) * 2 * (size_t)kSmallMaxN, s));

@@ -61,6 +61,58 @@ struct SchedParams {
   int32_t iters_per_alpha, max_iters_at_min, early_exit, level_cap;
 };
 
+// Error-free float-float addition (Knuth's two-sum, then renormalise): sums
+// of (hi, lo) pairs keep ~44 significant bits with FP32 arithmetic only.
+// The reductions the schedule needs use it instead of FP64, whose issue rate
+// on this part is a small fraction of FP32's.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float v = s - a.x;
+  float e = (a.x - (s - v)) + (b.x - v);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+__device__ __forceinline__ float2 ff_shfl_xor(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// Block-wide float-float sums of three per-thread values, in a fixed order
+// (warp trees, then the warp totals' tree in warp 0).  kT threads (a multiple
+// of 32, at most 1024); every thread must call it.  Result in thread 0.
+template <int kT>
+__device__ __forceinline__ void block_ffsum3(float2 a, float2 b, float2 c, double out[3]) {
+  __shared__ float2 sh[3][kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a = ff_add(a, ff_shfl_xor(a, o));
+    b = ff_add(b, ff_shfl_xor(b, o));
+    c = ff_add(c, ff_shfl_xor(c, o));
+  }
+  __syncthreads();
+  if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
+  __syncthreads();
+  if (warp == 0) {
+    const float2 z = make_float2(0.f, 0.f);
+    a = lane < kT / 32 ? sh[0][lane] : z;
+    b = lane < kT / 32 ? sh[1][lane] : z;
+    c = lane < kT / 32 ? sh[2][lane] : z;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a = ff_add(a, ff_shfl_xor(a, o));
+      b = ff_add(b, ff_shfl_xor(b, o));
+      c = ff_add(c, ff_shfl_xor(c, o));
+    }
+    if (lane == 0) {
+      out[0] = (double)a.x + (double)a.y;
+      out[1] = (double)b.x + (double)b.y;
+      out[2] = (double)c.x + (double)c.y;
+    }
+  }
+}
+
 // One step of the alpha schedule of Sec. 3.2 after a sweep with reductions
 // sdx = sum|x'-x|^2, sx = sum|x|^2 and stress: at most iters_per_alpha
 // iterations per alpha (fewer when the relative change |x'-x|/|x| drops
@@ -71,7 +123,11 @@ struct SchedParams {
 __device__ __forceinline__ bool schedule_step(SweepState* st, const SchedParams& sp, double sdx,
                                               double sx, double stress, float* trace,
                                               int trace_cap, int* level_sweeps_out) {
-  const double rel = sx > 0 ? sqrt(sdx) / sqrt(sx) : (sdx == 0 ? 0.0 : (double)INFINITY);
+  // the relative change in FP32 (the sums are FP64; FP64 square roots and
+  // divisions are long instruction sequences on this part)
+  const float fsdx = (float)sdx, fsx = (float)sx;
+  const double rel = fsx > 0.f ? (double)(sqrtf(fsdx) / sqrtf(fsx))
+                               : (fsdx == 0.f ? 0.0 : (double)INFINITY);
   const double alpha = st->alpha;
   const int t = st->total;
   if (trace && t < trace_cap) {
@@ -286,10 +342,10 @@ struct SweepEpilogue {
 // Fused Eq. 2 update over S plus per-block partial sums (3 doubles/block);
 // with `epi`, the update ends with the schedule step (no controller launch).
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
-                        double* partials, cudaStream_t s, const SweepEpilogue* epi = nullptr);
+                        float4* partials, cudaStream_t s, const SweepEpilogue* epi = nullptr);
 // Reduces the partials, applies the alpha schedule, optionally sets the
 // graph loop condition.
-mm_status controller(int nblocks, const double* partials, SweepState* st, SchedParams sp,
+mm_status controller(int nblocks, const float4* partials, SweepState* st, SchedParams sp,
                      float* trace, int trace_cap, int* level_sweeps_out,
                      cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s);
 // Writes the prolongated positions into xf_direct, or into xc.next() when
