@@ -28,8 +28,7 @@ struct RowAcc {
   float gx, gy, sx, sy, st;
 };
 
-__device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const float2* x) {
-  const float2 xv = __ldg(&x[en.col]);
+__device__ __forceinline__ void accumulate_v(RowAcc& a, float2 xu, SEnt en, float2 xv) {
   const float dx = xu.x - xv.x, dy = xu.y - xv.y;
   const float q = fmaf(dx, dx, dy * dy);
   const float inv = q > 0.f ? rsqrtf(q) : 0.f;   // 1/|x_u - x_v|, 0 if coincident
@@ -43,6 +42,36 @@ __device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const 
   a.sy = fmaf(dy, inv2, a.sy);
   const float t = dist - en.d;
   a.st = fmaf(w * t, t, a.st);
+}
+
+__device__ __forceinline__ void accumulate(RowAcc& a, float2 xu, SEnt en, const float2* x) {
+  accumulate_v(a, xu, en, __ldg(&x[en.col]));
+}
+
+// Entries b + lg, b + lg + G, ... < e of one S row, four at a time: the four
+// entry loads, then the four position loads, are issued back to back (the
+// row -> entry -> position chain is three dependent loads; batching them
+// keeps four of each in flight per lane).  Same order of additions as one
+// entry at a time.
+template <int G>
+__device__ __forceinline__ void accumulate_row(RowAcc& a, float2 xu, const SEnt* __restrict__ S,
+                                               int b, int e, int lg, const float2* x) {
+  constexpr int kU = 4;
+  for (int k0 = b + lg; k0 < e; k0 += kU * G) {
+    SEnt en[kU];
+    float2 xv[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const int k = k0 + j * G;
+      en[j] = k < e ? S[k] : SEnt{0, 1.f};
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j)
+      xv[j] = k0 + j * G < e ? __ldg(&x[en[j].col]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kU; ++j)
+      if (k0 + j * G < e) accumulate_v(a, xu, en[j], xv[j]);
+  }
 }
 
 // Bounding box accumulator (starts empty: min = +huge, max = -huge).
@@ -216,7 +245,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
       if (e - b <= heavy) {
         mine = true;
         xu = x[u];
-        for (int k = b + lg; k < e; k += G) accumulate(a, xu, S[k], x);
+        accumulate_row<G>(a, xu, S, b, e, lg, x);
       }
     }
     if (G > 1) {

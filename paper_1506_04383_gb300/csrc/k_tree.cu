@@ -553,6 +553,7 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
           const float2 xv = xs[p];
           const float ex = xu.x - xv.x, ey = xu.y - xv.y;
           const float eq = fmaf(ex, ex, ey * ey);
+          // the point itself (and any coincident one) has eq == 0: r = 0
           if (eq > 0.f) {
             const float inv = __fdividef(1.f, eq);
             fx = fmaf(inv, ex, fx);
@@ -654,7 +655,7 @@ __global__ void traverse_group_kernel(int n, int W, int seed, const float2* __re
           const float2 xv = xs[p];
           const float ex = xu.x - xv.x, ey = xu.y - xv.y;
           const float eq = fmaf(ex, ex, ey * ey);
-          if (p != pos && eq > 0.f) {
+          if (eq > 0.f) {
             const float inv = __fdividef(1.f, eq);
             fx = fmaf(inv, ex, fx);
             fy = fmaf(inv, ey, fy);
