@@ -120,15 +120,15 @@ __global__ void __launch_bounds__(kBBoxThreads) bbox_kernel(XSel xs, int n, floa
 // Morton keys (16 bits per axis) and the four 8-bit digit histograms of the
 // radix sort, in one pass over the positions.
 __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
-    XSel xs, int n, const float4* __restrict__ root, uint32_t* __restrict__ keys,
+    XSel xs, int n, int tile, const float4* __restrict__ root, uint32_t* __restrict__ keys,
     int32_t* __restrict__ vals, uint32_t* hist, uint32_t mask) {
   __shared__ uint32_t h[4][256];
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
   __syncthreads();
   const float2* x = xs.cur();
   const float4 r = *root;
-  const int base = blockIdx.x * kSortTile;
-  for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
+  const int base = blockIdx.x * tile;
+  for (int j = threadIdx.x; j < tile; j += kSortThreads) {
     const int i = base + j;
     if (i >= n) break;
     const float2 p = x[i];
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
 // always finishes.
 constexpr int kSpinLimit = 1 << 22;
 
+template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     int32_t* __restrict__ vout, int n, int pass, const uint32_t* __restrict__ hist,
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
   __shared__ int tile_sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int shift = 8 * pass;
-  const int tiles = (n + kSortTile - 1) / kSortTile;
+  constexpr int kTile = kSortThreads * IPT;
+  const int tiles = (n + kTile - 1) / kTile;
   if (threadIdx.x == 0) tile_sh = (int)atomicAdd(&counters[pass], 1u);
   for (int i = threadIdx.x; i < kWarps * 256; i += blockDim.x) (&whist[0][0])[i] = 0u;
   if (threadIdx.x < 32) {
@@ -194,13 +196,13 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
   }
   __syncthreads();
   const int tile = tile_sh;
-  const int64_t base = (int64_t)tile * kSortTile + warp * (32 * kSortIPT);
-  uint32_t key[kSortIPT];
-  int32_t val[kSortIPT];
-  uint32_t dig[kSortIPT];
-  unsigned peers[kSortIPT];
+  const int64_t base = (int64_t)tile * kTile + warp * (32 * IPT);
+  uint32_t key[IPT];
+  int32_t val[IPT];
+  uint32_t dig[IPT];
+  unsigned peers[IPT];
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < IPT; ++j) {
     const int64_t idx = base + j * 32 + lane;
     const unsigned valid = __ballot_sync(0xffffffffu, idx < n);
     peers[j] = 0;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < IPT; ++j) {
     uint32_t pos = 0;
     const bool valid = peers[j] != 0;
     if (valid) pos = whist[warp][dig[j]] + __popc(peers[j] & lt);
@@ -325,17 +327,19 @@ __global__ void karras_kernel(const uint32_t* __restrict__ k, int n, int32_t* lo
   if (i < n - 1) karras_node(k, n, i, lo, hi, left, right, delta, owner, parent);
 }
 
-// Per tile of kSortTile sorted positions: the FP64 inclusive prefix sums of
-// the sorted positions within the tile (the tile total goes to tile_sum).
+// Per tile of kSortThreads * IPT sorted positions: the FP64 inclusive prefix
+// sums of the sorted positions within the tile (the tile total goes to
+// tile_sum).
+template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) scan_xs_kernel(
     XSel xs, const int32_t* __restrict__ vals, int n, float2* __restrict__ xsorted,
     double2* __restrict__ incl, double2* __restrict__ tile_sum) {
-  const int base = blockIdx.x * kSortTile + threadIdx.x * kSortIPT;
+  const int base = blockIdx.x * (kSortThreads * IPT) + threadIdx.x * IPT;
   const float2* x = xs.cur();
-  float2 v[kSortIPT];
+  float2 v[IPT];
   double sx = 0.0, sy = 0.0;
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < IPT; ++j) {
     const int i = base + j;
     v[j] = make_float2(0.f, 0.f);
     if (i < n) {
@@ -361,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads) scan_xs_kernel(
   for (int w = 0; w < warp; ++w) { wx += shx[w]; wy += shy[w]; }
   double rx = wx + ix - sx, ry = wy + iy - sy;
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < IPT; ++j) {
     rx += v[j].x;
     ry += v[j].y;
     if (base + j < n) incl[base + j] = make_double2(rx, ry);
@@ -455,9 +459,10 @@ __device__ void write_record(const TreeView& t, int id, double2 sum, float side,
 
 // Sum of the sorted positions [0, k): tile offset + inclusive sum in tile.
 __device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
-                                             const double2* __restrict__ tile_off, int k) {
+                                             const double2* __restrict__ tile_off, int tile,
+                                             int k) {
   if (k == 0) return make_double2(0.0, 0.0);
-  const double2 a = tile_off[(k - 1) / kSortTile];
+  const double2 a = tile_off[(k - 1) / tile];
   const double2 b = incl[k - 1];
   return make_double2(a.x + b.x, a.y + b.y);
 }
@@ -465,29 +470,44 @@ __device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
 // Node-parallel records: a cell's position sum is the difference of two
 // prefix sums over its sorted range.
 // kFold: tile_off holds the raw tile totals (no tile scan ran) and every
-// block scans them itself (few tiles: cheaper than one more launch).
-constexpr int kFoldTiles = 128;
+// block scans them itself (few tiles: cheaper than one more launch): lane l
+// of warp 0 adds a run of kFoldTiles / 32 consecutive tiles, a warp scan
+// offsets the runs.
+constexpr int kFoldTiles = 256;
 
 template <bool kFold>
 __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const double2* __restrict__ incl,
-                               const double2* __restrict__ tile_off,
+                               const double2* __restrict__ tile_off, int tile,
                                const float4* __restrict__ root, float theta, int leaf,
                                int maxdepth, float4* nodeA, int4* nodeB) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
   if (kFold) {
-    // exclusive prefix of the tile totals, in tile order (one thread: at
-    // most kFoldTiles FP64 adds, the same order as the tile scan kernel)
+    constexpr int kPer = kFoldTiles / 32;
     __shared__ double2 off[kFoldTiles];
-    const int tiles = (n + kSortTile - 1) / kSortTile;
-    if (threadIdx.x == 0) {
-      double rx = 0.0, ry = 0.0;
-      for (int i = 0; i < tiles; ++i) {
-        off[i] = make_double2(rx, ry);
-        rx += tile_off[i].x;
-        ry += tile_off[i].y;
+    const int tiles = (n + tile - 1) / tile;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x, b0 = lane * kPer;
+      double sx = 0.0, sy = 0.0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (b0 + q < tiles) { sx += tile_off[b0 + q].x; sy += tile_off[b0 + q].y; }
+      double ix = sx, iy = sy;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double tx = __shfl_up_sync(0xffffffffu, ix, o);
+        const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+        if (lane >= o) { ix += tx; iy += ty; }
       }
+      double rx = ix - sx, ry = iy - sy;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (b0 + q < tiles) {
+          off[b0 + q] = make_double2(rx, ry);
+          rx += tile_off[b0 + q].x;
+          ry += tile_off[b0 + q].y;
+        }
     }
     __syncthreads();
     tile_off = off;
@@ -498,8 +518,8 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
     const float2 p = xsorted[id - (n - 1)];
     sum = make_double2(p.x, p.y);
   } else {
-    const double2 a = prefix_at(incl, tile_off, t.lo[id]);
-    const double2 b = prefix_at(incl, tile_off, t.hi[id] + 1);
+    const double2 a = prefix_at(incl, tile_off, tile, t.lo[id]);
+    const double2 b = prefix_at(incl, tile_off, tile, t.hi[id] + 1);
     sum = make_double2(b.x - a.x, b.y - a.y);
   }
   write_record(t, id, sum, root->z, theta, leaf, maxdepth, nodeA, nodeB);
@@ -739,12 +759,12 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
 }  // namespace
 
 size_t tree_status_words(int64_t n) {
-  return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortTile) * 256;
+  return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortMinTile) * 256;
 }
 
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   const size_t N = (size_t)(n > 1 ? n : 2);
-  const size_t tiles = (size_t)ceil_div((int64_t)N, kSortTile);
+  const size_t tiles = (size_t)ceil_div((int64_t)N, kSortMinTile);
   ws.cap = n;
   MM_CK(cudaMallocAsync(&ws.keys[0], sizeof(uint32_t) * N, s));
   MM_CK(cudaMallocAsync(&ws.keys[1], sizeof(uint32_t) * N, s));
@@ -811,7 +831,9 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(ev[i], s);
   };
-  const int tiles = ceil_div(n, kSortTile);
+  const int ipt = sort_ipt(n);
+  const int tile = kSortThreads * ipt;
+  const int tiles = ceil_div(n, tile);
   mark(0);
   if (with_bbox) MM_TRY(bh_bbox(x, n, ws, s));
   mark(1);
@@ -820,15 +842,19 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   // the upper three digits, from buffer 1.  Either way the result ends in
   // buffer 0.
   const int first = coarse_keys ? 1 : 0;
-  morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, ws.root, ws.keys[first],
+  morton_hist_kernel<<<tiles, kSortThreads, 0, s>>>(x, n, tile, ws.root, ws.keys[first],
                                                    ws.vals[first], ws.hist,
                                                    coarse_keys ? 0xffffff00u : 0xffffffffu);
   mark(2);
   for (int pass = first; pass < 4; ++pass) {
     const int a = pass & 1;
-    onesweep_pass<<<tiles, kSortThreads, 0, s>>>(ws.keys[a], ws.vals[a], ws.keys[a ^ 1],
-                                                 ws.vals[a ^ 1], n, pass, ws.hist, ws.counters,
-                                                 ws.status, ws.ticket, ws.err);
+    auto pass_kernel = ipt == 8   ? onesweep_pass<8>
+                       : ipt == 4 ? onesweep_pass<4>
+                       : ipt == 2 ? onesweep_pass<2>
+                                  : onesweep_pass<1>;
+    pass_kernel<<<tiles, kSortThreads, 0, s>>>(ws.keys[a], ws.vals[a], ws.keys[a ^ 1],
+                                               ws.vals[a ^ 1], n, pass, ws.hist, ws.counters,
+                                               ws.status, ws.ticket, ws.err);
   }
   mark(3);
   // the radix tree and the position prefix sums both need only the sorted
@@ -842,7 +868,11 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   if (n > 1)
     karras_kernel<<<ceil_div(n - 1, 256), 256, 0, ts>>>(ws.keys[0], n, ws.lo, ws.hi, ws.left,
                                                         ws.right, ws.delta, ws.owner, ws.parent);
-  scan_xs_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.xs, ws.incl, ws.tile_sum);
+  auto scan_kernel = ipt == 8   ? scan_xs_kernel<8>
+                     : ipt == 4 ? scan_xs_kernel<4>
+                     : ipt == 2 ? scan_xs_kernel<2>
+                                : scan_xs_kernel<1>;
+  scan_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.xs, ws.incl, ws.tile_sum);
   const bool fold = tiles <= kFoldTiles;
   if (!fold) tile_scan_kernel<<<1, 1024, 0, s>>>(ws.tile_sum, tiles);
   if (ws.aux) {
@@ -853,12 +883,12 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   TreeView tv{n, ws.lo, ws.hi, ws.left, ws.right, ws.delta, ws.owner, ws.parent};
   if (fold)
     records_kernel<true><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
-        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, coarse_keys ? 12 : kKeyBits,
-        ws.nodeA, ws.nodeB);
+        tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
+        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB);
   else
     records_kernel<false><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
-        tv, ws.xs, ws.incl, ws.tile_sum, ws.root, theta, leaf, coarse_keys ? 12 : kKeyBits,
-        ws.nodeA, ws.nodeB);
+        tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
+        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;

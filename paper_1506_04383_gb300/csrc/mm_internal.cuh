@@ -206,6 +206,16 @@ struct SortWS {
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortThreads * kSortIPT;
+// The tree build's sort and prefix-sum tiles hold kSortThreads * ipt keys,
+// ipt the largest of 8, 4, 2, 1 that still gives a tile per SM (small levels
+// get many small tiles instead of a few large ones); workspaces are sized
+// for the smallest tile.
+constexpr int kSortMinTile = kSortThreads;
+inline int sort_ipt(int64_t n) {
+  for (int ipt = kSortIPT; ipt > 1; ipt >>= 1)
+    if (ceil_div(n, (int64_t)kSortThreads * ipt) >= kSMs) return ipt;
+  return 1;
+}
 
 mm_status sort_ws_alloc(SortWS& ws, int64_t max_n);
 void sort_ws_free(SortWS& ws);

@@ -45,7 +45,7 @@ struct Carve {
 
 constexpr Carve carve() {
   constexpr size_t N = kNoAllocMaxN;
-  constexpr size_t tiles = (N + kSortTile - 1) / kSortTile;
+  constexpr size_t tiles = (N + kSortMinTile - 1) / kSortMinTile;
   Carve c{};
   size_t o = 0;
   c.keys0 = o; o += up(4 * N);
