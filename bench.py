@@ -548,7 +548,7 @@ def ctypes_copy(dst, src):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # ncu capture of the kernel on level 0 of the workload.  Re-capture and
 # update (or drop) whenever the kernel changes.
-NCU_TRAFFIC = {"rgg100k": {"traverse": 3.861504e6, "gather": 19.086336e6}}
+NCU_TRAFFIC = {"rgg100k": {"traverse": 3.834624e6, "gather": 19.096576e6}}
 
 
 def roofline(prof, peaks, src, clk, n, exact=False, workload=None):
