@@ -124,6 +124,45 @@ def _bh_check(mm, x, theta, leaf=1, group=0):
     return same.mean()
 
 
+def _exact_at(x64, idx, chunk=16):
+    """Exact F and sum of 1/distance at the sampled vertices idx."""
+    F = np.zeros((len(idx), 2))
+    mag = np.zeros(len(idx))
+    for a in range(0, len(idx), chunk):
+        d = x64[idx[a:a + chunk], None, :] - x64[None, :, :]
+        q = (d ** 2).sum(-1)
+        with np.errstate(divide="ignore"):
+            inv = np.where(q > 0, 1.0 / q, 0.0)
+            mag[a:a + chunk] = np.where(q > 0, 1.0 / np.sqrt(q), 0.0).sum(1)
+        F[a:a + chunk] = (d * inv[..., None]).sum(1)
+    return F, mag
+
+
+@pytest.mark.parametrize("n", [70_000, 80_000, 160_000, 320_000])
+def test_bh_across_sort_tile_widths(mm, n):
+    # the tree build sizes its sort and prefix-sum tiles from n: 1 key per
+    # thread with the separate tile-total scan (70k), 2, 4 and 8 keys per
+    # thread with the folded one (80k, 160k, 320k); checked on 256 sampled
+    # vertices against the oracle's Barnes-Hut (per-point walk) and against
+    # the exact sum within the Barnes-Hut bound (default walk)
+    x = f32(graphs.uniform_positions(n, 90 + n % 7, 0.0, math.sqrt(n)))
+    x64 = x.astype(np.float64)
+    idx = np.sort(np.random.default_rng(5).choice(n, 256, replace=False))
+    Fe, mag = _exact_at(x64, idx)
+    rp, col = graphs.path(n)
+    theta = 0.5
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1, leaf_size=1, bh_group=0)
+    F = mm.repulsion(h, 0, cu(x), theta).cpu().numpy().astype(np.float64)[idx]
+    Fo = oracle.repulsion_bh(x64, theta)[idx]
+    same = np.all(np.abs(F - Fo) <= 2e-4 * mag[:, None], axis=1)
+    assert same.mean() >= 0.99, same.mean()
+    del h
+    h, _ = hier(mm, rp, col, coarsest_n=n, k=1)
+    Fg = mm.repulsion(h, 0, cu(x), theta).cpu().numpy().astype(np.float64)[idx]
+    err = np.sqrt(((Fg - Fe) ** 2).sum(1))
+    assert np.all(err <= 2 * theta ** 2 * mag * (1 + 1e-3) + 2e-4 * mag)
+
+
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
 def test_bh_matches_oracle_uniform(mm, theta):
     x = f32(graphs.uniform_positions(3001, 77, 0.0, 50.0))
