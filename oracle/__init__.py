@@ -76,7 +76,9 @@ def _load():
         lib.orc_build_S.restype = i64
         lib.orc_repulsion_exact.argtypes = [i32, P, P]
         lib.orc_repulsion_bh.argtypes = [i32, P, f64, ctypes.c_int, P, P]
-        lib.orc_sweep.argtypes = [i32, P, P, P, P, P, f64, ctypes.c_int, f64, ctypes.c_int, P, P]
+        lib.orc_sweep.argtypes = [i32, P, P, P, P, P, f64, ctypes.c_int, f64, ctypes.c_int, P,
+                                  i32, P, P]
+        lib.orc_repulsion_h.argtypes = [i32, P, P, i32, P]
         lib.orc_objective.argtypes = [i32, P, P, P, P, f64, P]
         lib.orc_sclap.argtypes = [i32, P, P, P, P, f64, ctypes.c_int, u64, i32, P]
         lib.orc_contract.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P]
@@ -160,9 +162,24 @@ def repulsion_bh(x, theta: float, max_depth: int = MAX_DEPTH, counts: bool = Fal
     return (F, nacc) if counts else F
 
 
+def repulsion_h(x, cmap) -> np.ndarray:
+    """The first two sums of Eq. 3 (Sec. 3.2, "Faster Local Improvement"):
+    exact r-values within u's coarse representative, one nu-scaled r-value
+    towards the midpoint of every other one.  cmap maps the current level's
+    vertices to the vertices of the approximating level."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 2)
+    cmap = _i32(cmap)
+    nc = int(cmap.max()) + 1 if len(cmap) else 0
+    F = np.zeros_like(x)
+    lib.orc_repulsion_h(len(x), _p(x), _p(cmap), nc, _p(F))
+    return F
+
+
 def sweep(x, S, alpha: float, rep_mode: int = 0, theta: float = 0.5,
-          max_depth: int = MAX_DEPTH):
-    """One Jacobi iteration of Eq. 2.  rep_mode 0 = exact, 1 = Barnes-Hut.
+          max_depth: int = MAX_DEPTH, cmap=None):
+    """One Jacobi iteration of Eq. 2.  rep_mode 0 = exact, 1 = Barnes-Hut,
+    2 = the hierarchy approximation of Eq. 3 with the map cmap.
 
     Returns (x_new, stats) with stats = [sum|dx|^2, sum|x|^2, stress(x)]."""
     lib = _load()
@@ -170,9 +187,11 @@ def sweep(x, S, alpha: float, rep_mode: int = 0, theta: float = 0.5,
     x = _f64(x).reshape(-1, 2)
     out = np.zeros_like(x)
     st = np.zeros(3, dtype=np.float64)
+    cm = _i32(cmap) if cmap is not None else None
+    nc = int(cm.max()) + 1 if cm is not None and len(cm) else 0
     lib.orc_sweep(len(x), _p(x), _p(_i64(sp)), _p(_i32(scol)), _p(_f64(sd)),
                   _p(_f64(rho)), float(alpha), int(rep_mode), float(theta),
-                  int(max_depth), _p(out), _p(st))
+                  int(max_depth), _p(cm), nc, _p(out), _p(st))
     return out, st
 
 
@@ -243,7 +262,7 @@ DEFAULTS = dict(
     k=2, theta=0.5, exact_repulsion=0, coarsest_n=2, f=20.0, b=2.0, lp_rounds=10,
     iters_per_alpha=2, alpha0=1.0, alpha_factor=0.3, alpha_min=0.008, eps=1e-4,
     eps_final=1e-4, max_iters_at_min=100, early_exit=1, seed=1506, max_levels=64,
-    max_stalls=10,
+    max_stalls=10, approx_levels=0,
 )
 
 
@@ -314,7 +333,7 @@ def alpha_rounds(p):
     return out
 
 
-def schedule(S, x, p, rep_mode: int, trace=None, start_at_min: bool = False):
+def schedule(S, x, p, rep_mode: int, trace=None, start_at_min: bool = False, cmap=None):
     """Rounds of Jacobi iterations (Sec. 3.2): at most iters_per_alpha
     iterations per alpha, fewer if the relative change drops below eps; at
     alpha_min iterate until the relative change is below eps_final (capped at
@@ -333,7 +352,7 @@ def schedule(S, x, p, rep_mode: int, trace=None, start_at_min: bool = False):
         tol = p["eps_final"] if at_min else p["eps"]
         it = 0
         while True:
-            x, st = sweep(x, S, alpha, rep_mode, p["theta"])
+            x, st = sweep(x, S, alpha, rep_mode, p["theta"], cmap=cmap)
             rel = relative_change(st)
             it += 1
             sweeps += 1
@@ -357,24 +376,48 @@ def initial_layout(L, p, level_index):
     return place_coarsest(L["c"], p["seed"], level_index)
 
 
+def approx_map(levels, level: int, h: int):
+    """Map of level `level`'s vertices to the level used by Eq. 3: h levels
+    down, or the coarsest level if there are fewer (Sec. 3.2)."""
+    top = len(levels) - 1
+    t = min(level + h, top)
+    m = np.arange(levels[level]["n"], dtype=np.int64)
+    for j in range(level, t):
+        m = levels[j]["map"][m]
+    return m.astype(np.int32)
+
+
 def layout(rp, col, p, elen=None, x_init=None, levels=None, trace=None):
     """Multilevel maxent-stress layout (Sec. 3).  alpha is set to alpha0
     once, at the start (coarsest level), and reduced by rounds down to
     alpha_min; the finer levels refine at alpha_min.  With x_init the whole
-    schedule runs on the finest level only, from x_init.  Returns (x, info)."""
+    schedule runs on the finest level only, from x_init.  approx_levels = h
+    > 0 takes the entropy sum of every level but the coarsest from Eq. 3
+    (MulMent_h); the coarsest level always uses the exact sum.  Returns
+    (x, info)."""
     if levels is None:
         levels = build_hierarchy(rp, col, p, elen=elen)
-    rep_fine = 0 if p["exact_repulsion"] else 1
+    top = len(levels) - 1
+    happ = int(p["approx_levels"])
+
+    def mode(level):
+        if p["exact_repulsion"]:
+            return 0, None
+        if happ > 0 and level < top:
+            return 2, approx_map(levels, level, happ)
+        return 1, None
+
     sweeps = []
     if x_init is not None:
-        x, s = schedule(levels[0]["S"], x_init, p, rep_fine, trace)
+        rm, cm = mode(0)
+        x, s = schedule(levels[0]["S"], x_init, p, rm, trace, cmap=cm)
         return x, dict(levels=levels, sweeps=[s])
-    top = len(levels) - 1
     x = initial_layout(levels[top], p, top)
     x, s = schedule(levels[top]["S"], x, p, 0, trace)
     sweeps.append(s)
     for h in range(top - 1, -1, -1):
         x = prolong(levels[h]["map"], x, levels[h + 1]["c"], p["seed"], h)
-        x, s = schedule(levels[h]["S"], x, p, rep_fine, trace, start_at_min=True)
+        rm, cm = mode(h)
+        x, s = schedule(levels[h]["S"], x, p, rm, trace, start_at_min=True, cmap=cm)
         sweeps.append(s)
     return x, dict(levels=levels, sweeps=sweeps[::-1])

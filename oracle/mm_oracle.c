@@ -27,6 +27,8 @@
  *   orc_sclap              pinned by invariants and order-free cases
  *   orc_contract           pinned (hand-worked example, invariants)
  *   orc_prolong            pinned (radius bound, distribution moments)
+ *   orc_repulsion_h        pinned (identity map and single cluster equal the
+ *                                  exact sum; far-field error order; scaling)
  */
 #include <math.h>
 #include <stdint.h>
@@ -195,6 +197,52 @@ void orc_repulsion_exact(int32_t n, const double* x, double* F) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The hierarchy approximation of the entropy sum, Eq. 3 (Sec. 3.2, "Faster  */
+/* Local Improvement"), without its last term (the sum over E, subtracted by */
+/* the caller exactly as for the other modes):                               */
+/*   F_u = sum_{v != u, M(v) = M(u)} r(u,v)                                   */
+/*       + sum_{v' != M(u)} nu(v') (x_u - x'_{v'}) / |x_u - x'_{v'}|^2        */
+/* M maps the n current-level vertices to the nc vertices of the level used  */
+/* for the approximation (h levels down, or the coarsest), nu(v') counts the */
+/* current-level vertices mapped to v', and x'_{v'} is their midpoint, each  */
+/* current-level vertex weighted by what it stands for on the current level, */
+/* i.e. once: x'_{v'} = (1/nu(v')) sum_{M(v) = v'} x_v.                       */
+/* ------------------------------------------------------------------------ */
+void orc_repulsion_h(int32_t n, const double* x, const int32_t* cmap, int32_t nc,
+                     double* F) {
+  double* xc = (double*)calloc(2 * (size_t)(nc > 0 ? nc : 1), sizeof(double));
+  double* nu = (double*)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
+  for (int32_t v = 0; v < n; ++v) {
+    nu[cmap[v]] += 1.0;
+    xc[2 * cmap[v]] += x[2 * v];
+    xc[2 * cmap[v] + 1] += x[2 * v + 1];
+  }
+  for (int32_t c = 0; c < nc; ++c) {
+    if (nu[c] > 0.0) { xc[2 * c] /= nu[c]; xc[2 * c + 1] /= nu[c]; }
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int32_t u = 0; u < n; ++u) {
+    double fx = 0.0, fy = 0.0;
+    /* close vertices: the same coarse representative, exact r-values */
+    for (int32_t v = 0; v < n; ++v) {
+      if (v == u || cmap[v] != cmap[u]) continue;
+      double rx, ry;
+      rvalue(x, u, v, &rx, &ry);
+      fx += rx; fy += ry;
+    }
+    /* far vertices: one r-value per other coarse vertex, scaled by nu */
+    for (int32_t c = 0; c < nc; ++c) {
+      if (c == cmap[u] || nu[c] == 0.0) continue;
+      double dx = x[2 * u] - xc[2 * c], dy = x[2 * u + 1] - xc[2 * c + 1];
+      double q = dx * dx + dy * dy;
+      if (q > 0.0) { fx += nu[c] * dx / q; fy += nu[c] * dy / q; }
+    }
+    F[2 * u] = fx; F[2 * u + 1] = fy;
+  }
+  free(xc); free(nu);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Barnes-Hut quadtree (Barnes and Hut 1986; cited in Sec. 2.2 and as the    */
 /* approximation used by the maxent-stress solver of Gansner et al., Sec.    */
 /* 2.3).  A classic recursive pointer quadtree over the bounding square of   */
@@ -343,17 +391,22 @@ void orc_repulsion_bh(int32_t n, const double* x, double theta, int max_depth,
 /* rep_mode 0: the entropy sum is taken literally, pair by pair.             */
 /* rep_mode 1: the entropy sum is the Barnes-Hut total minus the exact       */
 /*             r-values over S (the subtraction of Eq. 3).                   */
+/* rep_mode 2: the entropy sum is Eq. 3: orc_repulsion_h with the map cmap   */
+/*             to nc coarse vertices, minus the exact r-values over S.       */
 /* stats[0] = sum |x'-x|^2, stats[1] = sum |x|^2 (relative change,           */
 /* Sec. 3.2), stats[2] = stress of x over the unordered pairs of S (Eq. 1).  */
 /* ------------------------------------------------------------------------ */
 void orc_sweep(int32_t n, const double* x, const int64_t* sp,
                const int32_t* scol, const double* sd, const double* rho,
                double alpha, int rep_mode, double theta, int max_depth,
-               double* xout, double* stats) {
+               const int32_t* cmap, int32_t nc, double* xout, double* stats) {
   double* F = NULL;
-  if (rep_mode == 1) {
+  if (rep_mode == 1 || rep_mode == 2) {
     F = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
-    orc_repulsion_bh(n, x, theta, max_depth, F, NULL);
+    if (rep_mode == 1)
+      orc_repulsion_bh(n, x, theta, max_depth, F, NULL);
+    else
+      orc_repulsion_h(n, x, cmap, nc, F);
   }
   double s_dx = 0.0, s_x = 0.0, s_stress = 0.0;
 #pragma omp parallel
@@ -378,7 +431,7 @@ void orc_sweep(int32_t n, const double* x, const int64_t* sp,
         s_stress += 0.5 * w * (dist - d) * (dist - d);
       }
       double ex = 0.0, ey = 0.0;      /* sum over v not in S_u */
-      if (rep_mode == 1) {
+      if (rep_mode == 1 || rep_mode == 2) {
         ex = F[2 * u] - sx; ey = F[2 * u + 1] - sy;
       } else {
         for (int64_t e = sp[u]; e < sp[u + 1]; ++e) inS[scol[e]] = 1;

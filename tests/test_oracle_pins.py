@@ -377,3 +377,90 @@ def test_layout_small_multilevel_runs():
     M_lay = oracle.objective(x, S, 0.008)[2]
     M_rand = oracle.objective(graphs.uniform_positions(144, 1, 0, 12), S, 0.008)[2]
     assert M_lay < M_rand
+
+
+# ------------------------------------------------- Eq. 3 (MulMent_h) ---
+def test_repulsion_h_identity_and_single_cluster_are_exact():
+    # Sec. 3.2: with M the identity Eq. 3 is the exact sum of Eq. 2; with one
+    # cluster holding every vertex its first sum is the exact sum and the
+    # second is empty
+    x = graphs.uniform_positions(60, 4, 0.0, 10.0)
+    F = oracle.repulsion_exact(x)
+    scale = np.abs(F).max()
+    assert np.abs(oracle.repulsion_h(x, np.arange(60)) - F).max() <= 1e-12 * scale
+    assert np.abs(oracle.repulsion_h(x, np.zeros(60, dtype=np.int32)) - F).max() <= 1e-12 * scale
+
+
+def _two_clusters(D, rng_seed=3):
+    rng = np.random.default_rng(rng_seed)
+    a = rng.uniform(-1, 1, (5, 2))
+    b = rng.uniform(-1, 1, (7, 2)) + np.array([D, 0.0])
+    x = np.vstack([a, b])
+    cmap = np.array([0] * 5 + [1] * 7, dtype=np.int32)
+    return x, cmap
+
+
+def test_repulsion_h_far_field_error_is_third_order():
+    # the far cluster is replaced by nu = 7 copies of its midpoint: with the
+    # plain midpoint the first-order (dipole) term of the expansion vanishes,
+    # so the error at the near cluster falls as 1/D^3 (a weighted midpoint
+    # or a wrong nu would leave a 1/D^2 or 1/D error); exact within a cluster
+    errs = []
+    for D in (20.0, 40.0, 80.0):
+        x, cmap = _two_clusters(D)
+        Fh = oracle.repulsion_h(x, cmap)
+        Fe = oracle.repulsion_exact(x)
+        errs.append(np.abs(Fh[:5] - Fe[:5]).max())
+        # the near part is exact: removing the far cluster's exact and
+        # approximated contributions leaves the same numbers
+        far_exact = np.zeros((5, 2))
+        for i in range(5):
+            d = x[i] - x[5:]
+            far_exact[i] = (d / (d ** 2).sum(1, keepdims=True)).sum(0)
+        mid = x[5:].mean(0)
+        d = x[:5] - mid
+        far_h = 7 * d / (d ** 2).sum(1, keepdims=True)
+        assert np.allclose(Fh[:5] - far_h, Fe[:5] - far_exact, rtol=0, atol=1e-12)
+    assert 6.5 <= errs[0] / errs[1] <= 9.5, errs
+    assert 6.5 <= errs[1] / errs[2] <= 9.5, errs
+
+
+def test_repulsion_h_equivariance_and_scaling():
+    x = graphs.uniform_positions(40, 9, 0.0, 8.0)
+    cmap = np.random.default_rng(2).integers(0, 6, 40).astype(np.int32)
+    F = oracle.repulsion_h(x, cmap)
+    c, s = math.cos(0.7), math.sin(0.7)
+    R = np.array([[c, -s], [s, c]])
+    assert np.allclose(oracle.repulsion_h(x + np.array([3.0, -5.0]), cmap), F, atol=1e-10)
+    assert np.allclose(oracle.repulsion_h(x @ R.T, cmap), F @ R.T, atol=1e-10)
+    assert np.allclose(oracle.repulsion_h(2.5 * x, cmap), F / 2.5, atol=1e-10)
+
+
+def test_sweep_h_with_identity_map_is_the_exact_sweep():
+    rp, col = graphs.grid(6, 7)
+    n = len(rp) - 1
+    S = oracle.build_S(rp, col, 2)
+    x = graphs.uniform_positions(n, 5, 0.0, 6.0)
+    xe, ste = oracle.sweep(x, S, 0.3, 0)
+    xh, sth = oracle.sweep(x, S, 0.3, 2, cmap=np.arange(n))
+    assert np.abs(xh - xe).max() <= 1e-10 * np.abs(xe).max()
+    assert np.allclose(sth, ste, rtol=1e-12)
+
+
+def test_layout_h_runs_and_maps_compose():
+    rp, col = graphs.grid(12, 12)
+    p = oracle.params(k=2, coarsest_n=2, seed=4, approx_levels=2)
+    levels = oracle.build_hierarchy(rp, col, p)
+    # the composed map of level 0 is the two maps applied in turn
+    m = oracle.approx_map(levels, 0, 2)
+    assert np.array_equal(m, levels[1]["map"][levels[0]["map"]])
+    assert m.max() + 1 == levels[2]["n"]
+    top = len(levels) - 1
+    assert np.array_equal(oracle.approx_map(levels, top - 1, 5),
+                          levels[top - 1]["map"])
+    x, info = oracle.layout(rp, col, p, levels=levels)
+    assert np.all(np.isfinite(x))
+    S = levels[0]["S"]
+    M_lay = oracle.objective(x, S, 0.008)[2]
+    M_rand = oracle.objective(graphs.uniform_positions(144, 1, 0, 12), S, 0.008)[2]
+    assert M_lay < M_rand
