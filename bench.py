@@ -60,6 +60,11 @@ WORKLOADS = {
                            "2M-vertex random geometric graph (mean degree 8), k=2, theta=0.5; "
                            "timed at the smallest per-level sweep cap whose objective matches "
                            "the plain layout's"),
+    "del16h": dict(kind="delaunay", n=1 << 16, seed=1506, k=1, theta=0.5, coarsest_n=2,
+                   approx=10, hsweep=(0, 1, 2, 3, 5, 7, 10), nolearn=True,
+                   desc="MulMent_h (Eq. 3): Delaunay triangulation of 2^16 uniform points, k=1, "
+                        "coarsen to 2, entropy sum from the level h=10 below; table over "
+                        "h = 0 (exact), 1, 2, 3, 5, 7, 10 as in the paper's del16 h table"),
     "batch512": dict(kind="batch", count=512, seed=1506, k=2, theta=0.5, coarsest_n=2,
                      desc="512 graphs, lognormal sizes (median 3000, sigma 1) in [200, 50000], "
                           "thirds grids / random geometric (mean degree 6-12) / random trees, "
@@ -176,6 +181,8 @@ def params_of(mm, w):
                   max_iters_at_min=w["single"] - 10)
     else:
         kw.update(theta=w["theta"], coarsest_n=w["coarsest_n"])
+    if w.get("approx"):
+        kw.update(approx_levels=w["approx"])
     return kw
 
 
@@ -256,14 +263,22 @@ def cpu_baseline(w, rp, col, budget_s=15.0, per_step=None):
     x = graphs.uniform_positions(n, 1506, 0.0, math.sqrt(n))
     exact = bool(w.get("exact"))
     theta = w.get("theta", 0.5)
+    mode, cmap, what = (0 if exact else 1), None, ("exact" if exact else
+                                                    "Barnes-Hut theta=%g" % theta)
+    if w.get("approx"):
+        # the oracle's own coarsening supplies the map to the level h below
+        po = oracle.params(k=w["k"], coarsest_n=w["coarsest_n"], approx_levels=w["approx"])
+        levels = oracle.build_hierarchy(rp, col, po)
+        mode, cmap = 2, oracle.approx_map(levels, 0, w["approx"])
+        what = f"Eq. 3 (h={w['approx']}, {int(cmap.max()) + 1} representatives)"
     sweeps, t0 = 0, time.perf_counter()
     while True:
-        x, _ = oracle.sweep(x, S, 0.3, 0 if exact else 1, theta)
+        x, _ = oracle.sweep(x, S, 0.3, mode, theta, cmap=cmap)
         sweeps += 1
         el = time.perf_counter() - t0
         if (per_step and sweeps >= per_step) or (not per_step and el >= budget_s):
             break
-    sample = (f"{sweeps} {'exact' if exact else 'Barnes-Hut theta=%g' % theta} Eq. 2 sweeps "
+    sample = (f"{sweeps} {what} Eq. 2 sweeps "
               f"of the finest level (n={n}, |S|={len(S[1])}), FP64 oracle, OpenMP")
     return n * sweeps / el, oracle.num_threads(), sample, el
 
@@ -354,7 +369,8 @@ def main():
     if args.autotune:
         tune = mm.autotune(h, max_rel_drift=0.01)
     learned_cmp = None
-    if w.get("learned") or (args.learned and gp is None and not w.get("single")):
+    if w.get("learned") or (args.learned and gp is None and not w.get("single")
+                            and not w.get("nolearn")):
         net, tr = train_prolongation(mm, p)
         cmp_, best = learned_vs_plain(mm, h, p, net)
         learned_cmp = {"training": tr, **cmp_}
@@ -406,7 +422,9 @@ def main():
     # roofline of the dominant kernel on the finest level, live with events
     peaks, src = measured_peaks()
     clk_sum = clk.summary()
-    if gp is None:
+    if w.get("approx"):
+        roof = roofline_h(mm, h, xbuf, int(w["approx"]), peaks, src, clk_sum)
+    elif gp is None:
         prof = mm.sweep_profile(h, 0, xbuf, reps=10)
         roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")),
                         workload=args.workload)
@@ -443,6 +461,8 @@ def main():
                "d2h_bytes_per_step": int(xh.nbytes),
                "time_to_layout_s": statistics.mean(times)}
 
+    htab = h_table(mm, drp, dcol, w, kw) if w.get("hsweep") else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample, el = cpu_baseline(w, rp, col, budget_s=args.cpu_budget)
@@ -467,6 +487,7 @@ def main():
             "objective_M": M,
             "batch_vs_plain": batch_cmp,
             "learned_vs_plain": learned_cmp,
+            "h_table": htab,
             "autotune": tune,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -549,6 +570,71 @@ def ctypes_copy(dst, src):
 # ncu capture of the kernel on level 0 of the workload.  Re-capture and
 # update (or drop) whenever the kernel changes.
 NCU_TRAFFIC = {"rgg100k": {"traverse": 3.834624e6, "gather": 19.096576e6}}
+
+
+def h_table(mm, drp, dcol, w, kw, reps=2):
+    """Layouts with the entropy sum of Eq. 3 from h levels below (h = 0: the
+    exact sum on every level), the shape of the paper's h table on del16:
+    time per layout (CUDA events, L2 flushed), sweeps and M (Eq. 1 at
+    alpha = 0.008, exact)."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for hh in w["hsweep"]:
+        kh = dict(kw, approx_levels=hh)
+        if hh == 0:
+            kh.update(exact_repulsion=1)
+        p = mm.default_params(**kh)
+        h = mm.build_hierarchy(drp, dcol, p)
+        x, st = mm.layout(h, p)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            x, st = mm.layout(h, p)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        rows.append({"h": hh, "ms": round(min(ts), 3), "sweeps": st["total_sweeps"],
+                     "levels": st["num_levels"], "M": mm.objective(h, 0, x, 0.008)[2]})
+        del h
+    return rows
+
+
+def roofline_h(mm, h, x, hh, peaks, src, clk, reps=10):
+    """The Eq. 3 sums on the finest level (mm_repulsion_h: midpoints, then one
+    thread per vertex over all other representatives and its own group):
+    FP32-ALU bound, 10 FP32 ops per pair term, n (n' - 1) far terms plus
+    sum_c m_c (m_c - 1) near terms for groups of sizes m_c."""
+    import numpy as np
+    import torch
+    n = h.level_info(0)[0]
+    top = h.levels() - 1
+    # composed map of level 0 (sizes of the groups)
+    m = np.arange(n)
+    for j in range(0, min(hh, top)):
+        m = mm.level_export(h, j)["map"].cpu().numpy()[m]
+    sizes = np.bincount(m)
+    nt = len(sizes)
+    terms = n * (nt - 1) + float((sizes * (sizes - 1)).sum())
+    mm.repulsion_h(h, 0, x)
+    evs = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        mm.repulsion_h(h, 0, x)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / reps
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    ach = 10.0 * terms / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src, "kernel": "approx_force",
+            "note": f"peak = 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz; {nt} representatives, "
+                    f"{terms:.4g} pair terms per call, {ms * 1e3:.1f} us per call"}
 
 
 def roofline(prof, peaks, src, clk, n, exact=False, workload=None):

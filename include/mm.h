@@ -87,7 +87,11 @@ typedef struct mm_params {
                             /* classic test), 1 = per group of 32 Morton-     */
                             /* consecutive points (a cell far from all of     */
                             /* them; refines each point's per-point sum)      */
-  int32_t reserved[3];
+  int32_t approx_levels;    /* h of MulMent_h: 0 = Barnes-Hut / exact as set  */
+                            /* above; h > 0 = the entropy sum of Eq. 3 with   */
+                            /* the level h levels down (or the coarsest) on   */
+                            /* every level but the coarsest (Sec. 3.2)        */
+  int32_t reserved[2];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */
@@ -210,6 +214,21 @@ mm_status mm_level_export(const mm_hierarchy* h, int32_t level,
 mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha,
                    const float* x_in, float* x_out, double* stats,
                    void* stream);
+
+/*
+ * The first two sums of Eq. 3 (Sec. 3.2, "Faster Local Improvement") on
+ * `level` of a hierarchy built with approx_levels = h > 0: exact r-values
+ * between u and the other vertices with the same representative M(u) on
+ * level min(level + h, coarsest), plus nu(v') r(x_u, x'_{v'}) for every
+ * other representative v', with nu(v') its number of vertices on `level`
+ * and x'_{v'} their midpoint (from x).  On the coarsest level M is the
+ * identity and the result is the exact sum.
+ *   x device [2n], F_out device [2n] (n of `level`); stream-ordered.
+ * Errors: MM_ERR_INVALID_ARG (null pointers, level out of range, a
+ * hierarchy built with approx_levels = 0, a batch hierarchy), MM_ERR_CUDA.
+ */
+mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* F_out,
+                         void* stream);
 
 /*
  * The long-range sum F_u = sum_{v != u} r(u,v) over all vertices of `level`

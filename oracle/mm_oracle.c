@@ -220,12 +220,24 @@ void orc_repulsion_h(int32_t n, const double* x, const int32_t* cmap, int32_t nc
   for (int32_t c = 0; c < nc; ++c) {
     if (nu[c] > 0.0) { xc[2 * c] /= nu[c]; xc[2 * c + 1] /= nu[c]; }
   }
+  /* the vertices of every representative, in ascending order */
+  int64_t* off = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
+  int32_t* mem = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t v = 0; v < n; ++v) off[cmap[v] + 1] += 1;
+  for (int32_t c = 0; c < nc; ++c) off[c + 1] += off[c];
+  {
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nc + 1));
+    memcpy(fill, off, sizeof(int64_t) * ((size_t)nc + 1));
+    for (int32_t v = 0; v < n; ++v) mem[fill[cmap[v]]++] = v;
+    free(fill);
+  }
 #pragma omp parallel for schedule(dynamic, 64)
   for (int32_t u = 0; u < n; ++u) {
     double fx = 0.0, fy = 0.0;
     /* close vertices: the same coarse representative, exact r-values */
-    for (int32_t v = 0; v < n; ++v) {
-      if (v == u || cmap[v] != cmap[u]) continue;
+    for (int64_t j = off[cmap[u]]; j < off[cmap[u] + 1]; ++j) {
+      int32_t v = mem[j];
+      if (v == u) continue;
       double rx, ry;
       rvalue(x, u, v, &rx, &ry);
       fx += rx; fy += ry;
@@ -239,7 +251,7 @@ void orc_repulsion_h(int32_t n, const double* x, const int32_t* cmap, int32_t nc
     }
     F[2 * u] = fx; F[2 * u + 1] = fy;
   }
-  free(xc); free(nu);
+  free(xc); free(nu); free(off); free(mem);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -758,6 +758,10 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
 
 }  // namespace
 
+bool tree_tile_scan(int64_t n) {
+  return ceil_div(n, (int64_t)kSortThreads * sort_ipt(n)) > kFoldTiles;
+}
+
 size_t tree_status_words(int64_t n) {
   return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortMinTile) * 256;
 }

@@ -44,6 +44,7 @@ struct mm_hierarchy {
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
   float4* spart = nullptr;           // [2 kSmallMaxN] fused-level partial sums
+  float4* xc = nullptr;              // Eq. 3 midpoints and counts (approx_levels > 0)
   float4* box = nullptr;             // [kMaxGatherBlocks] update-block boxes
   unsigned* arrive = nullptr;        // update epilogue arrival counter
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
@@ -120,7 +121,8 @@ __global__ void set_state(SweepState* st, double alpha) {
 }
 
 void free_level(Level& L) {
-  void* ptrs[] = {L.rp, L.col, L.omega, L.c, L.elen, L.map, L.sp, L.s, L.rho, L.heavy};
+  void* ptrs[] = {L.rp,  L.col,   L.omega, L.c,       L.elen,   L.map, L.sp,
+                  L.s,   L.rho,   L.heavy, L.hmap,    L.members, L.moff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -144,7 +146,7 @@ mm_status check_params(const mm_params* p) {
       p->lp_rounds < 0 || p->iters_per_alpha < 1 || p->max_iters_at_min < 1 ||
       !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
       p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS || p->leaf_size < 0 ||
-      p->leaf_size > kMaxLeaf) {
+      p->leaf_size > kMaxLeaf || p->approx_levels < 0 || p->approx_levels > MM_MAX_LEVELS) {
     set_error("parameter out of range");
     return MM_ERR_INVALID_ARG;
   }
@@ -221,25 +223,29 @@ bool level_exact(const mm_hierarchy* h, int level, bool single) {
   return !single && level == (int)h->levels.size() - 1;
 }
 
+// The level takes its entropy sum from Eq. 3 (a map to a coarser level).
+bool level_approx(const mm_hierarchy* h, int level) {
+  return h->p.approx_levels > 0 && h->levels[level].hmap != nullptr;
+}
+
 // Library kernels one sweep of a layout's WHILE loop launches (mirrors
 // sweep_body with in_loop = true).
 int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
   const Level& L = h->levels[level];
   int64_t k = 1 + (L.n_heavy > 0 ? 1 : 0);  // update (+ heavy rows), epilogue fused
   if (exact) return k + 1;                   // tiled exact sum
+  if (level_approx(h, level)) return k + 2;  // midpoints, Eq. 3 sums
   k += 1 + (group_of(h->p) ? 3 : 4);         // Morton keys + histograms, sort passes
   if (L.n > 1) k += 1;                       // radix tree
   k += 1;                                    // position prefix sums
-  if (ceil_div(L.n, kSortTile) > 128) k += 1;  // tile scan (else folded into records)
+  if (tree_tile_scan(L.n)) k += 1;           // tile scan (else folded into records)
   return k + 1 + 1;                          // records, walk
 }
 
 // Kernels a multi-kernel level launches outside its loop: the bounding
 // square before the first sweep (Barnes-Hut levels).
 int64_t kernels_before_loop(const mm_hierarchy* h, int level, bool exact) {
-  (void)h;
-  (void)level;
-  return exact ? 0 : 1;
+  return exact || level_approx(h, level) ? 0 : 1;
 }
 
 SmallArgs small_args(mm_hierarchy* h, int level, bool exact, SweepState* st, SchedParams sp,
@@ -282,8 +288,11 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
                      cudaGraphConditionalHandle hnd, bool use_h, cudaStream_t s,
                      bool in_loop = false) {
   const Level& L = h->levels[level];
+  const bool approx = !exact && level_approx(h, level);
   if (exact) {
     MM_TRY(exact_repulsion(x, L.n, h->F, s));
+  } else if (approx) {
+    MM_TRY(approx_repulsion(L, x, h->xc, h->F, s));
   } else {
     MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop,
                     group_of(h->p)));
@@ -299,7 +308,7 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   ep.h = hnd;
   ep.use_h = use_h ? 1 : 0;
   ep.arrive = h->arrive;
-  if (in_loop && !exact) {
+  if (in_loop && !exact && !approx) {
     ep.box = h->box;
     ep.root = h->tree.root;
     ep.hist = h->tree.hist;
@@ -347,7 +356,8 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
                                       h->lsw + level, 1 << 30),
                            s);
       });
-    if (!exact)  // the first sweep's bounding square; later ones come from the update
+    if (!exact && !level_approx(h, level))  // the first sweep's bounding square; later ones
+                                             // come from the update
       MM_TRY(add_child([&](cudaStream_t s) -> mm_status {
         return bh_bbox(x, h->levels[level].n, h->tree, s);
       }));
@@ -675,6 +685,18 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
     const int lim = p->fused_max_n == 0 ? kSmallMaxN : std::min(p->fused_max_n, kSmallMaxN);
     L.fused = p->fused_max_n >= 0 && L.n <= lim;
   }
+  // Eq. 3: every level but the coarsest takes its entropy sum from the level
+  // approx_levels below (the fused kernel has no Eq. 3 path: those levels
+  // run the sweep kernels)
+  int max_nt = 0;
+  if (p->approx_levels > 0 && !p->exact_repulsion) {
+    for (size_t lv = 0; lv + 1 < h->levels.size(); ++lv) {
+      Level& L = h->levels[lv];
+      MM_TRY(approx_setup(L, h->levels, (int)lv, p->approx_levels, s));
+      L.fused = false;
+      max_nt = std::max(max_nt, L.nt);
+    }
+  }
   MM_TRY(small_level_setup());
   {
     Level& C = h->levels.back();
@@ -698,6 +720,7 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->state, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->sstate, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->spart, sizeof(float4) * 2 * (size_t)kSmallMaxN, s));
+  if (max_nt > 0) MM_CK(cudaMallocAsync(&h->xc, sizeof(float4) * (size_t)max_nt, s));
   MM_CK(cudaMallocAsync(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->arrive, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));
@@ -1473,7 +1496,7 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   cudaDeviceSynchronize();
   for (Level& L : h->levels) free_level(L);
   tree_ws_free(h->tree);
-  void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart,
+  void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart, h->xc,
                   h->box, h->arrive,
                   h->zero, h->lsw, h->trace};
   for (void* p : ptrs)
@@ -1591,6 +1614,28 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s,
                      group_of(h->p)));
   return tree_error(h, s);
+}
+
+mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* F_out,
+                         void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x || !F_out) {
+    set_error("NULL buffer");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (h->p.approx_levels <= 0 || h->p.exact_repulsion) {
+    set_error("mm_repulsion_h needs a hierarchy built with approx_levels > 0 "
+              "(and exact_repulsion = 0)");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& L = h->levels[level];
+  XSel xs{(const float2*)x, (const float2*)x, h->zero};
+  // the coarsest level maps to itself: Eq. 3 is then the exact sum
+  if (!L.hmap) return exact_repulsion(xs, L.n, (float2*)F_out, s);
+  return approx_repulsion(L, xs, h->xc, (float2*)F_out, s);
 }
 
 mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init, float* x_out,

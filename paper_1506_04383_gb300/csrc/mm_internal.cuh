@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstring>
+#include <vector>
 
 #include "mm.h"
 
@@ -195,6 +196,13 @@ struct Level {
   int32_t walk_warps = 0;    // warps per block in the tree walk (0 = default)
   bool fused = false;        // whole level in the single-CTA kernel
   double sum_c = 0;
+  // Eq. 3 (approx_levels = h > 0, all levels but the coarsest): the map to
+  // the level h levels down (or the coarsest, nt vertices), the level's
+  // vertices grouped by it (ascending ids) and the groups' offsets
+  int32_t* hmap = nullptr;    // [n]
+  int32_t* members = nullptr; // [n]
+  int32_t* moff = nullptr;    // [nt+1]
+  int32_t nt = 0;
 };
 
 // ----------------------------------------------------------- primitives --
@@ -291,6 +299,9 @@ struct TreeWS {
 constexpr int kKeyBits = 16;  // per axis -> 32-bit Morton keys, depth 16
 
 size_t tree_status_words(int64_t n);
+// Whether the tree build of n points scans its tile totals in a kernel of
+// its own (else the record kernel folds them in).
+bool tree_tile_scan(int64_t n);
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s);
 void tree_ws_free(TreeWS& ws);
 
@@ -323,6 +334,14 @@ constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
 inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
 // Tiled exact sum F[v] = sum_{u != v} r(v, u).
 mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
+
+// ------------------------------------------------------ Eq. 3 (MulMent_h) --
+// Builds L's map to level min(level + h, top) and its member groups.
+mm_status approx_setup(Level& L, const std::vector<Level>& levels, int level, int h,
+                       cudaStream_t s);
+// F = the first two sums of Eq. 3 for the current positions; xc holds the
+// nt midpoints and counts (x', nu) afterwards.
+mm_status approx_repulsion(const Level& L, XSel x, float4* xc, float2* F, cudaStream_t s);
 
 // ---------------------------------------------------------------- sweep --
 constexpr int kGatherThreads = 256;

@@ -31,7 +31,7 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc",
            "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
-           "mm_layout_levels"]
+           "mm_layout_levels", "mm_repulsion_h"]
 MM_NET_PARAMS = 17860
 
 
@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
         ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
         ("leaf_size", ctypes.c_int32), ("bh_group", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("approx_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -153,6 +153,7 @@ def load(path: str = LIB_PATH):
     lib.mm_net_train_step.argtypes = [P, P, f32, P, P]
     lib.mm_hierarchy_set_net.argtypes = [P, P]
     lib.mm_layout_levels.argtypes = [P, P, P, P]
+    lib.mm_repulsion_h.argtypes = [P, i32, P, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -319,6 +320,15 @@ def repulsion(h: Hierarchy, level: int, x, theta: float, stream=None):
     x = _dev(x, torch.float32, "x")
     F = torch.empty_like(x)
     _check(load().mm_repulsion(h.handle, level, _ptr(x), float(theta), _ptr(F), _stream(stream)))
+    return F
+
+
+def repulsion_h(h: Hierarchy, level: int, x, stream=None):
+    """The first two sums of Eq. 3 (MulMent_h) on `level` (hierarchy built
+    with approx_levels > 0)."""
+    x = _dev(x, torch.float32, "x")
+    F = torch.empty_like(x)
+    _check(load().mm_repulsion_h(h.handle, level, _ptr(x), _ptr(F), _stream(stream)))
     return F
 
 

@@ -65,7 +65,8 @@ def test_struct_layout_matches_c(tmp_path):
           printf("%zu %zu %zu %zu %zu\\n", sizeof(mm_prolong_sample),
                  offsetof(mm_prolong_sample, n_coarse), offsetof(mm_prolong_sample, seed),
                  offsetof(mm_prolong_sample, level), offsetof(mm_prolong_sample, x_target));
-          printf("%zu\\n", offsetof(mm_params, learned_prolong));
+          printf("%zu %zu\\n", offsetof(mm_params, learned_prolong),
+                 offsetof(mm_params, approx_levels));
           return 0;
         }
     """))
@@ -83,7 +84,7 @@ def test_struct_layout_matches_c(tmp_path):
     Q = mm.ProlongSample
     assert [int(t) for t in c.split()] == [ctypes.sizeof(Q), Q.n_coarse.offset, Q.seed.offset,
                                            Q.level.offset, Q.x_target.offset]
-    assert int(d) == P.learned_prolong.offset
+    assert [int(t) for t in d.split()] == [P.learned_prolong.offset, P.approx_levels.offset]
 
 
 def test_product_path_does_not_import_oracle():
