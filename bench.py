@@ -65,6 +65,15 @@ WORKLOADS = {
                    desc="MulMent_h (Eq. 3): Delaunay triangulation of 2^16 uniform points, k=1, "
                         "coarsen to 2, entropy sum from the level h=10 below; table over "
                         "h = 0 (exact), 1, 2, 3, 5, 7, 10 as in the paper's del16 h table"),
+    "dyn16": dict(kind="delaunay", n=1 << 16, seed=1506, k=1, theta=0.5, coarsest_n=2,
+                  approx=7, dynamic=(5.0, 16), nolearn=True,
+                  dyn_table=((1.0, 2), (1.0, 16), (5.0, 2), (5.0, 16)), dyn_h=(0, 7),
+                  desc="dynamic update (Sec. 4.3): Delaunay 2^16, k=1; G laid out from scratch "
+                       "(MulMent_7), 5% of its non-tree edges replaced by edges to vertices at "
+                       "distance <= 16; the timed step lays out the perturbed graph from G's "
+                       "layout at alpha = 0.008 on the finest level of a hierarchy cut after "
+                       "h = 7 levels (MulMent_7); table over x in {1, 5}%, D in {2, 16}, "
+                       "h in {0, 7} against the scratch layout"),
     "batch512": dict(kind="batch", count=512, seed=1506, k=2, theta=0.5, coarsest_n=2,
                      desc="512 graphs, lognormal sizes (median 3000, sigma 1) in [200, 50000], "
                           "thirds grids / random geometric (mean degree 6-12) / random trees, "
@@ -352,9 +361,24 @@ def main():
     n = len(rp) - 1
     kw = params_of(mm, w)
     p = mm.default_params(**kw)
+    x_init = None
+    dyn = None
+    if w.get("dynamic"):
+        # the update algorithm: G laid out from scratch, then the perturbed
+        # graph from G's layout on a hierarchy cut after h levels
+        rpG, colG = rp, col
+        hG = mm.build_hierarchy(torch.from_numpy(rpG).cuda(), torch.from_numpy(colG).cuda(), p)
+        xG, _ = mm.layout(hG, p)
+        del hG
+        pct, D = w["dynamic"]
+        rp, col = perturbed(rpG, colG, pct, D, w["seed"])
+        kw = dict(kw, max_levels=w["approx"] + 1, alpha0=0.008)
+        p = mm.default_params(**kw)
+        x_init = xG
+        args.e2e_steps = 0  # the host API lays out from scratch, not from a layout
+        dyn = dyn_table(mm, rpG, colG, w)
     drp = torch.from_numpy(rp).cuda()
     dcol = torch.from_numpy(col).cuda()
-    x_init = None
     if w.get("single"):
         from paper_1506_04383_gb300 import graphs
         x_init = torch.from_numpy(graphs.uniform_positions(n, 1506).astype(np.float32)).cuda()
@@ -488,6 +512,7 @@ def main():
             "batch_vs_plain": batch_cmp,
             "learned_vs_plain": learned_cmp,
             "h_table": htab,
+            "dynamic_table": dyn,
             "autotune": tune,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -599,6 +624,69 @@ def h_table(mm, drp, dcol, w, kw, reps=2):
         rows.append({"h": hh, "ms": round(min(ts), 3), "sweeps": st["total_sweeps"],
                      "levels": st["num_levels"], "M": mm.objective(h, 0, x, 0.008)[2]})
         del h
+    return rows
+
+
+_PERTURBED = {}
+
+
+def perturbed(rp, col, pct, D, seed):
+    """graphs.perturb_edges, computed once per (x, D, seed) in a run."""
+    from paper_1506_04383_gb300 import graphs
+    key = (len(rp), pct, D, seed)
+    if key not in _PERTURBED:
+        _PERTURBED[key] = graphs.perturb_edges(rp, col, pct, D, seed)
+    return _PERTURBED[key]
+
+
+def dyn_table(mm, rpG, colG, w, reps=2):
+    """Update vs scratch layouts of perturbed graphs (Sec. 4.3): for every
+    (x %, D) the perturbed graph Q is laid out from scratch with MulMent_h and
+    updated from the scratch layout of G (alpha = 0.008, finest level of a
+    hierarchy cut after h levels; h = 0: one level, exact sum).  Times are
+    CUDA events with L2 flushed (min of reps), M is Eq. 1 at alpha = 0.008."""
+    import torch
+    from paper_1506_04383_gb300 import graphs
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(h, p, x0=None):
+        x, st = mm.layout(h, p, x_init=x0)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            x, st = mm.layout(h, p, x_init=x0)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts), st, x
+
+    base = dict(k=w["k"], coarsest_n=w["coarsest_n"])
+    pert = {(pct, D): perturbed(rpG, colG, pct, D, w["seed"]) for pct, D in w["dyn_table"]}
+    rows = []
+    for hh in w["dyn_h"]:
+        ks = dict(base, approx_levels=hh, exact_repulsion=1 if hh == 0 else 0)
+        ps = mm.default_params(**ks)
+        hG = mm.build_hierarchy(torch.from_numpy(rpG).cuda(), torch.from_numpy(colG).cuda(), ps)
+        xG, _ = mm.layout(hG, ps)
+        del hG
+        for pct, D in w["dyn_table"]:
+            rq, cq = pert[(pct, D)]
+            drq, dcq = torch.from_numpy(rq).cuda(), torch.from_numpy(cq).cuda()
+            hs = mm.build_hierarchy(drq, dcq, ps)
+            t_s, st_s, x_s = timed(hs, ps)
+            M_s = mm.objective(hs, 0, x_s, 0.008)[2]
+            pu = mm.default_params(**dict(ks, max_levels=hh + 1, alpha0=0.008))
+            hu = mm.build_hierarchy(drq, dcq, pu)
+            t_u, st_u, x_u = timed(hu, pu, xG)
+            M_u = mm.objective(hs, 0, x_u, 0.008)[2]
+            rows.append({"x_pct": pct, "D": D, "h": hh, "scratch_ms": round(t_s, 3),
+                         "update_ms": round(t_u, 3), "speedup": round(t_s / t_u, 2),
+                         "scratch_sweeps": st_s["total_sweeps"],
+                         "update_sweeps": st_u["total_sweeps"], "M_scratch": M_s,
+                         "M_update": M_u})
+            del hs, hu
     return rows
 
 

@@ -260,3 +260,75 @@ def concat_graphs(graphs):
     rps.append(np.array([off_e]))
     return (np.concatenate(rps).astype(np.int64), np.concatenate(cols).astype(np.int32),
             np.array(gp, dtype=np.int32))
+
+
+def _within(rp, col, a: int, D: int, seen):
+    """Vertices at hop distance 2..D from a (level-synchronous BFS; `seen`
+    is a boolean scratch array of n entries, left all False)."""
+    frontier = np.array([a], dtype=np.int64)
+    seen[a] = True
+    touched = [frontier]
+    out = []
+    for d in range(1, D + 1):
+        if len(frontier) == 0:
+            break
+        deg = rp[frontier + 1] - rp[frontier]
+        tot = int(deg.sum())
+        if tot == 0:
+            break
+        starts = np.repeat(rp[frontier] - np.concatenate([[0], np.cumsum(deg)[:-1]]), deg)
+        nb = np.unique(col[starts + np.arange(tot)].astype(np.int64))
+        nb = nb[~seen[nb]]
+        seen[nb] = True
+        touched.append(nb)
+        if d >= 2:
+            out.append(nb)
+        frontier = nb
+    for t in touched:
+        seen[t] = False
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+
+
+def perturb_edges(rp, col, pct: float, D: int, seed: int):
+    """The dynamic-graph model of the paper's experiments (Sec. 4.3): a BFS
+    spanning tree from a random vertex is kept, pct % of the undirected edges
+    that are not in it are removed at random (the graph stays connected), and
+    as many new edges are inserted, each between a random vertex and a random
+    vertex at distance 1 < d <= D in the original graph.  Returns the
+    perturbed CSR (same vertex ids)."""
+    import scipy.sparse as sps
+    import scipy.sparse.csgraph as csg
+    rng = _rng(seed)
+    n = len(rp) - 1
+    src = np.repeat(np.arange(n), np.diff(rp))
+    und = src < col
+    eu, ev = src[und].astype(np.int64), col[und].astype(np.int64)
+    m = len(eu)
+    A = sps.csr_matrix((np.ones(len(col)), col, rp), shape=(n, n))
+    start = int(rng.integers(n))
+    T = csg.breadth_first_tree(A, start, directed=False).tocoo()
+    tree = set(zip(np.minimum(T.row, T.col).tolist(), np.maximum(T.row, T.col).tolist()))
+    tkey = np.array(sorted(a * n + b for a, b in tree), dtype=np.int64)
+    non_tree = np.nonzero(~np.isin(eu * n + ev, tkey))[0]
+    k = int(round(pct / 100.0 * m))
+    k = min(k, len(non_tree))
+    drop = rng.choice(non_tree, size=k, replace=False) if k else np.zeros(0, dtype=np.int64)
+    keep = np.ones(m, dtype=bool)
+    keep[drop] = False
+    edges = set(zip(eu[keep].tolist(), ev[keep].tolist()))
+    added = 0
+    seen = np.zeros(n, dtype=bool)
+    while added < k:
+        a = int(rng.integers(n))
+        cand = _within(rp, col, a, D, seen)
+        if len(cand) == 0:
+            continue
+        b = int(cand[int(rng.integers(len(cand)))])
+        e = (min(a, b), max(a, b))
+        if e in edges:
+            continue
+        edges.add(e)
+        added += 1
+    u = np.array([e[0] for e in edges], dtype=np.int64)
+    v = np.array([e[1] for e in edges], dtype=np.int64)
+    return csr_from_edges(n, u, v)

@@ -125,3 +125,32 @@ def test_layout_h_and_barnes_hut_reach_comparable_objectives(mm):
         x, st = mm.layout(h, p)
         out[hh] = mm.objective(h, 0, x, 0.008)[2]
     assert abs(out[1] - out[0]) <= 0.05 * abs(out[0]), out
+
+
+@pytest.mark.parametrize("hh", [0, 3])
+def test_dynamic_update_matches_oracle(mm, hh):
+    # Sec. 4.3, update algorithm: the perturbed graph Q is laid out from a
+    # layout of the original G, starting at alpha = 0.008 on the finest level
+    # of Q's hierarchy cut after h levels (h = 0: the exact sum).  Same
+    # hierarchy and start on both sides; objectives within 1%.
+    rp, col, _, _ = graphs.rgg(2000, 8.0, 65)
+    xG, _ = oracle.layout(rp, col, oracle.params(k=1, coarsest_n=20))
+    qrp, qcol = graphs.perturb_edges(rp, col, 5.0, 16, 4)
+    ku = dict(k=1, coarsest_n=2, alpha0=0.008, max_levels=hh + 1, approx_levels=hh,
+              exact_repulsion=1 if hh == 0 else 0)
+    po = oracle.params(**ku)
+    levels = oracle.build_hierarchy(qrp, qcol, po)
+    assert len(levels) == hh + 1
+    xo, _ = oracle.layout(qrp, qcol, po, x_init=xG, levels=levels)
+    p = mm.default_params(**ku)
+    h = mm.build_hierarchy_levels(oracle_levels_to_device(levels), p)
+    x, st = mm.layout(h, p, x_init=cu(f32(xG)))
+    assert st["num_levels"] == hh + 1
+    xs = x.cpu().numpy().astype(np.float64)
+    S = levels[0]["S"]
+    Mg = oracle.objective(xs, S, 0.008)[2]
+    Mo = oracle.objective(xo, S, 0.008)[2]
+    assert abs(Mg - Mo) <= 0.01 * abs(Mo), (Mg, Mo)
+    # the update starts from a good layout: far better than a random start
+    M0 = oracle.objective(graphs.uniform_positions(len(xs), 2, 0, 40), S, 0.008)[2]
+    assert Mg < M0
