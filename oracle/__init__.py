@@ -79,6 +79,7 @@ def _load():
         lib.orc_sweep.argtypes = [i32, P, P, P, P, P, f64, ctypes.c_int, f64, ctypes.c_int, P,
                                   i32, P, P]
         lib.orc_repulsion_h.argtypes = [i32, P, P, i32, P]
+        lib.orc_full_stress.argtypes = [i32, P, P, P, P]
         lib.orc_objective.argtypes = [i32, P, P, P, P, f64, P]
         lib.orc_sclap.argtypes = [i32, P, P, P, P, f64, ctypes.c_int, u64, i32, P]
         lib.orc_contract.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P]
@@ -204,6 +205,17 @@ def objective(x, S, alpha: float):
     lib.orc_objective(len(x), _p(x), _p(_i64(sp)), _p(_i32(scol)), _p(_f64(sd)),
                       float(alpha), _p(out))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def full_stress(rp, col, x):
+    """Full stress over all connected unordered pairs with hop distances and
+    w = d^-2, the stress-minimising scale s and the stress at s x (Sec. 4,
+    methodology).  Returns (F(x), s, F(s x), pairs)."""
+    lib = _load()
+    x = _f64(x).reshape(-1, 2)
+    out = np.zeros(4, dtype=np.float64)
+    lib.orc_full_stress(len(x), _p(_i64(rp)), _p(_i32(col)), _p(x), _p(out))
+    return float(out[0]), float(out[1]), float(out[2]), int(out[3])
 
 
 def sclap(rp, col, c, U: float, rounds: int, seed: int, level: int, ew=None):

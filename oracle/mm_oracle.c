@@ -29,6 +29,8 @@
  *   orc_prolong            pinned (radius bound, distribution moments)
  *   orc_repulsion_h        pinned (identity map and single cluster equal the
  *                                  exact sum; far-field error order; scaling)
+ *   orc_full_stress        pinned (path on a line, K2 and scaled closed forms;
+ *                                  distances equal a library BFS)
  */
 #include <math.h>
 #include <stdint.h>
@@ -663,4 +665,54 @@ void orc_place_coarsest(int32_t n, const double* c, uint64_t seed,
     x[2 * v] = rad * cos(phi);
     x[2 * v + 1] = rad * sin(phi);
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full stress and its optimal scale (Sec. 4, methodology):                  */
+/*   F(x) = sum over unordered pairs {u,v} of w_uv (|x_u - x_v| - d_uv)^2    */
+/* with d_uv the shortest-path (hop) distance and w_uv = d_uv^-2, and the    */
+/* scalar s minimising sum w (s |x_u - x_v| - d)^2:                          */
+/*   s = sum w d |x_u - x_v| / sum w |x_u - x_v|^2,                          */
+/*   F(s x) = sum w d^2 - (sum w d |dx|)^2 / sum w |dx|^2.                   */
+/* One breadth-first search per source (plain queue).  out[0] = F(x),        */
+/* out[1] = s, out[2] = F(s x), out[3] = number of connected pairs.          */
+/* ------------------------------------------------------------------------ */
+void orc_full_stress(int32_t n, const int64_t* rp, const int32_t* col, const double* x,
+                     double* out) {
+  double F = 0.0, A = 0.0, B = 0.0, C = 0.0, pairs = 0.0;
+#pragma omp parallel reduction(+ : F, A, B, C, pairs)
+  {
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int32_t s = 0; s < n; ++s) {
+      for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+      int32_t head = 0, tail = 0;
+      dist[s] = 0;
+      queue[tail++] = s;
+      while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+          int32_t v = col[e];
+          if (dist[v] < 0) { dist[v] = dist[u] + 1; queue[tail++] = v; }
+        }
+      }
+      for (int32_t v = s + 1; v < n; ++v) {       /* unordered pairs */
+        if (dist[v] <= 0) continue;
+        double d = (double)dist[v], w = 1.0 / (d * d);
+        double dx = x[2 * s] - x[2 * v], dy = x[2 * s + 1] - x[2 * v + 1];
+        double len = sqrt(dx * dx + dy * dy);
+        F += w * (len - d) * (len - d);
+        A += w * d * len;
+        B += w * len * len;
+        C += w * d * d;
+        pairs += 1.0;
+      }
+    }
+    free(dist); free(queue);
+  }
+  out[0] = F;
+  out[1] = B > 0.0 ? A / B : 0.0;
+  out[2] = B > 0.0 ? C - A * A / B : C;
+  out[3] = pairs;
 }

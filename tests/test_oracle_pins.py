@@ -464,3 +464,42 @@ def test_layout_h_runs_and_maps_compose():
     M_lay = oracle.objective(x, S, 0.008)[2]
     M_rand = oracle.objective(graphs.uniform_positions(144, 1, 0, 12), S, 0.008)[2]
     assert M_lay < M_rand
+
+
+# --------------------------------------------- full stress and scale s ---
+def test_full_stress_path_on_a_line():
+    # a path drawn on a line with unit spacing realises every distance:
+    # F = 0 and s = 1; drawn at spacing 2, F = one per pair and s = 1/2
+    rp, col = graphs.path(12)
+    x = np.stack([np.arange(12.0), np.zeros(12)], 1)
+    F, s, Fs, pairs = oracle.full_stress(rp, col, x)
+    assert pairs == 66 and F == pytest.approx(0.0, abs=1e-12) and s == pytest.approx(1.0)
+    F, s, Fs, pairs = oracle.full_stress(rp, col, 2.0 * x)
+    assert F == pytest.approx(66.0) and s == pytest.approx(0.5) and Fs == pytest.approx(0.0, abs=1e-9)
+
+
+def test_full_stress_two_vertices():
+    rp, col = graphs.path(2)
+    x = np.array([[0.0, 0.0], [3.0, 4.0]])   # |dx| = 5, d = 1
+    F, s, Fs, pairs = oracle.full_stress(rp, col, x)
+    assert F == pytest.approx(16.0) and s == pytest.approx(0.2) and Fs == pytest.approx(0.0, abs=1e-12)
+
+
+def test_full_stress_matches_library_shortest_paths():
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    sps = pytest.importorskip("scipy.sparse")
+    rp, col, _, _ = graphs.rgg(300, 6.0, 12)
+    n = len(rp) - 1
+    x = graphs.uniform_positions(n, 3, 0.0, 10.0)
+    D = csg.shortest_path(sps.csr_matrix((np.ones(len(col)), col, rp), shape=(n, n)),
+                          unweighted=True)
+    iu = np.triu_indices(n, 1)
+    d = D[iu]
+    L = np.sqrt(((x[iu[0]] - x[iu[1]]) ** 2).sum(1))
+    w = 1.0 / d ** 2
+    F_ref = (w * (L - d) ** 2).sum()
+    s_ref = (w * d * L).sum() / (w * L * L).sum()
+    F, s, Fs, pairs = oracle.full_stress(rp, col, x)
+    assert pairs == len(d)
+    assert F == pytest.approx(F_ref, rel=1e-12) and s == pytest.approx(s_ref, rel=1e-12)
+    assert Fs == pytest.approx((w * (s_ref * L - d) ** 2).sum(), rel=1e-9)
