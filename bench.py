@@ -601,7 +601,8 @@ def h_table(mm, drp, dcol, w, kw, reps=2):
     """Layouts with the entropy sum of Eq. 3 from h levels below (h = 0: the
     exact sum on every level), the shape of the paper's h table on del16:
     time per layout (CUDA events, L2 flushed), sweeps and M (Eq. 1 at
-    alpha = 0.008, exact)."""
+    alpha = 0.008, exact), F (full stress over all pairs, hop distances) and
+    the stress-minimising scale s with F(s x) (Sec. 4, methodology)."""
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     rows = []
@@ -621,8 +622,10 @@ def h_table(mm, drp, dcol, w, kw, reps=2):
             b.record()
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
+        F, s, Fs, _ = mm.full_stress(h, x)
         rows.append({"h": hh, "ms": round(min(ts), 3), "sweeps": st["total_sweeps"],
-                     "levels": st["num_levels"], "M": mm.objective(h, 0, x, 0.008)[2]})
+                     "levels": st["num_levels"], "M": mm.objective(h, 0, x, 0.008)[2],
+                     "F": F, "s": s, "F_scaled": Fs})
         del h
     return rows
 
@@ -644,7 +647,8 @@ def dyn_table(mm, rpG, colG, w, reps=2):
     (x %, D) the perturbed graph Q is laid out from scratch with MulMent_h and
     updated from the scratch layout of G (alpha = 0.008, finest level of a
     hierarchy cut after h levels; h = 0: one level, exact sum).  Times are
-    CUDA events with L2 flushed (min of reps), M is Eq. 1 at alpha = 0.008."""
+    CUDA events with L2 flushed (min of reps), M is Eq. 1 at alpha = 0.008, F
+    the full stress over all pairs (Sec. 4)."""
     import torch
     from paper_1506_04383_gb300 import graphs
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -681,11 +685,13 @@ def dyn_table(mm, rpG, colG, w, reps=2):
             hu = mm.build_hierarchy(drq, dcq, pu)
             t_u, st_u, x_u = timed(hu, pu, xG)
             M_u = mm.objective(hs, 0, x_u, 0.008)[2]
+            F_s = mm.full_stress(hs, x_s)[0]
+            F_u = mm.full_stress(hs, x_u)[0]
             rows.append({"x_pct": pct, "D": D, "h": hh, "scratch_ms": round(t_s, 3),
                          "update_ms": round(t_u, 3), "speedup": round(t_s / t_u, 2),
                          "scratch_sweeps": st_s["total_sweeps"],
                          "update_sweeps": st_u["total_sweeps"], "M_scratch": M_s,
-                         "M_update": M_u})
+                         "M_update": M_u, "F_scratch": F_s, "F_update": F_u})
             del hs, hu
     return rows
 

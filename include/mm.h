@@ -231,6 +231,20 @@ mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* 
                          void* stream);
 
 /*
+ * Full stress of a layout of the input graph (level 0) and its optimal scale
+ * (Sec. 4, methodology): F(x) = sum over unordered vertex pairs of
+ * w (|x_u - x_v| - d)^2 with d the hop distance and w = d^-2; s minimises
+ * sum w (s |x_u - x_v| - d)^2.  Breadth-first searches from every vertex on
+ * the device (64 sources per pass), O(n m) work: graphs of at most 131072
+ * vertices with unit edge lengths (no edge_len).
+ *   x device [2n]; out host [4] = {F(x), s, F(s x), number of pairs}.
+ *   Synchronises the stream.
+ * Errors: MM_ERR_INVALID_ARG (null pointers, batch hierarchy),
+ * MM_ERR_UNSUPPORTED (edge lengths given, n > 131072), MM_ERR_CUDA.
+ */
+mm_status mm_full_stress(mm_hierarchy* h, const float* x, double* out, void* stream);
+
+/*
  * The long-range sum F_u = sum_{v != u} r(u,v) over all vertices of `level`
  * (the quantity Barnes-Hut approximates).  theta > 0: quadtree with that
  * opening parameter; theta == 0: quadtree opened completely (exact);

@@ -1616,6 +1616,27 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   return tree_error(h, s);
 }
 
+mm_status mm_full_stress(mm_hierarchy* h, const float* x, double* out, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, 0));
+  if (!x || !out) {
+    set_error("NULL buffer");
+    return MM_ERR_INVALID_ARG;
+  }
+  const Level& L = h->levels[0];
+  if (L.elen) {
+    set_error("mm_full_stress takes unit edge lengths (hop distances); edge_len was given");
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (L.n > kFullStressMaxN) {
+    set_error("mm_full_stress takes at most %d vertices (all pairs), got %d", kFullStressMaxN,
+              L.n);
+    return MM_ERR_UNSUPPORTED;
+  }
+  DeviceGuard dg(h->device);
+  return full_stress(L.n, L.rp, L.col, (const float2*)x, out, (cudaStream_t)stream);
+}
+
 mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* F_out,
                          void* stream) {
   g_err.clear();

@@ -343,6 +343,13 @@ mm_status approx_setup(Level& L, const std::vector<Level>& levels, int level, in
 // nt midpoints and counts (x', nu) afterwards.
 mm_status approx_repulsion(const Level& L, XSel x, float4* xc, float2* F, cudaStream_t s);
 
+// ---------------------------------------------------- full stress (Sec. 4) --
+// out = {F(x), s, F(s x), connected pairs} over all unordered pairs of the
+// unit-length graph (rp, col) with hop distances; synchronises the stream.
+mm_status full_stress(int n, const int32_t* rp, const int32_t* col, const float2* x,
+                      double out[4], cudaStream_t s);
+constexpr int kFullStressMaxN = 1 << 17;
+
 // ---------------------------------------------------------------- sweep --
 constexpr int kGatherThreads = 256;
 constexpr int kMaxLightBlocks = kSMs * 16;

@@ -31,7 +31,7 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc",
            "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
-           "mm_layout_levels", "mm_repulsion_h"]
+           "mm_layout_levels", "mm_repulsion_h", "mm_full_stress"]
 MM_NET_PARAMS = 17860
 
 
@@ -154,6 +154,7 @@ def load(path: str = LIB_PATH):
     lib.mm_hierarchy_set_net.argtypes = [P, P]
     lib.mm_layout_levels.argtypes = [P, P, P, P]
     lib.mm_repulsion_h.argtypes = [P, i32, P, P, P]
+    lib.mm_full_stress.argtypes = [P, P, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -330,6 +331,15 @@ def repulsion_h(h: Hierarchy, level: int, x, stream=None):
     F = torch.empty_like(x)
     _check(load().mm_repulsion_h(h.handle, level, _ptr(x), _ptr(F), _stream(stream)))
     return F
+
+
+def full_stress(h: Hierarchy, x, stream=None):
+    """Full stress F(x), optimal scale s, F(s x) and the number of pairs for a
+    layout of the input graph (Sec. 4)."""
+    x = _dev(x, torch.float32, "x")
+    out = (ctypes.c_double * 4)()
+    _check(load().mm_full_stress(h.handle, _ptr(x), out, _stream(stream)))
+    return float(out[0]), float(out[1]), float(out[2]), int(out[3])
 
 
 def repulsion_noalloc(x, theta: float, F_out=None, stream=None):

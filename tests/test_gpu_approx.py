@@ -154,3 +154,39 @@ def test_dynamic_update_matches_oracle(mm, hh):
     # the update starts from a good layout: far better than a random start
     M0 = oracle.objective(graphs.uniform_positions(len(xs), 2, 0, 40), S, 0.008)[2]
     assert Mg < M0
+
+
+# ------------------------------------------------ full stress (Sec. 4) ---
+@pytest.mark.parametrize("case", ["rgg", "grid", "path"])
+def test_full_stress_matches_oracle(mm, case):
+    # all-pairs hop distances by 64-source breadth-first searches on the
+    # device against the oracle's one-source-at-a-time searches; sizes span
+    # several 64-source batches and a ragged last batch
+    if case == "rgg":
+        rp, col, pts, _ = graphs.rgg(2500, 8.0, 66)
+        n = len(rp) - 1
+        x = pts * math.sqrt(n)
+    elif case == "grid":
+        rp, col = graphs.grid(37, 29)
+        n = len(rp) - 1
+        x = graphs.uniform_positions(n, 3, 0.0, 30.0)
+    else:
+        rp, col = graphs.path(130)
+        n = 130
+        x = np.stack([np.arange(130.0), np.zeros(130)], 1)
+    h = mm.build_hierarchy(cu(rp), cu(col), mm.default_params(k=1, coarsest_n=n))
+    xf = f32(x)
+    F, s, Fs, pairs = mm.full_stress(h, cu(xf))
+    Fo, so, Fso, po = oracle.full_stress(rp, col, xf.astype(np.float64))
+    assert pairs == po == n * (n - 1) // 2
+    assert F == pytest.approx(Fo, rel=1e-4, abs=1e-3)
+    assert s == pytest.approx(so, rel=1e-4)
+    assert Fs == pytest.approx(Fso, rel=1e-4, abs=1e-3)
+
+
+def test_full_stress_refuses_weighted_and_large_graphs(mm):
+    rp, col = graphs.path(10)
+    el = np.full(len(col), 2.0, dtype=np.float32)
+    h = mm.build_hierarchy(cu(rp), cu(col), mm.default_params(k=1, coarsest_n=10), edge_len=cu(el))
+    with pytest.raises(mm.MMError):
+        mm.full_stress(h, cu(f32(np.zeros((10, 2)))))
