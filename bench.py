@@ -648,7 +648,7 @@ def dyn_table(mm, rpG, colG, w, reps=2):
     updated from the scratch layout of G (alpha = 0.008, finest level of a
     hierarchy cut after h levels; h = 0: one level, exact sum).  Times are
     CUDA events with L2 flushed (min of reps), M is Eq. 1 at alpha = 0.008, F
-    the full stress over all pairs (Sec. 4)."""
+    the full stress over all pairs at the stress-minimising scale (Sec. 4)."""
     import torch
     from paper_1506_04383_gb300 import graphs
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -685,8 +685,8 @@ def dyn_table(mm, rpG, colG, w, reps=2):
             hu = mm.build_hierarchy(drq, dcq, pu)
             t_u, st_u, x_u = timed(hu, pu, xG)
             M_u = mm.objective(hs, 0, x_u, 0.008)[2]
-            F_s = mm.full_stress(hs, x_s)[0]
-            F_u = mm.full_stress(hs, x_u)[0]
+            F_s = mm.full_stress(hs, x_s)[2]   # at the stress-minimising scale
+            F_u = mm.full_stress(hs, x_u)[2]
             rows.append({"x_pct": pct, "D": D, "h": hh, "scratch_ms": round(t_s, 3),
                          "update_ms": round(t_u, 3), "speedup": round(t_s / t_u, 2),
                          "scratch_sweeps": st_s["total_sweeps"],
