@@ -316,6 +316,19 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def job_time_and_value(local_ms, vu_per_step, steps, world, device):
+    """Replicas: the job's time is the slowest rank's timed region (max over
+    ranks), and its value is every rank's vertex updates over that time."""
+    total = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total, world * vu_per_step * steps / (total / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,13 +441,8 @@ def main():
         barrier()
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     vu = stats[-1]["vertex_updates"]
-    value = world * vu * args.steps / (total_ms / 1e3)
+    total_ms, value = job_time_and_value(sum(step_ms), vu, args.steps, world, "cuda")
     launches = sum(s["kernel_launches"] for s in stats)
 
     # quality: objective of the final layout (Eq. 1 at alpha = 0.008)

@@ -9,7 +9,8 @@
  * Maxent-Stress Optimization", arXiv 1506.04383) and cites the passage it
  * follows.  Arithmetic is double precision throughout.
  *
- * Conventions (the readings of the paper are listed in the design doc):
+ * Conventions (where the paper leaves a choice, the function comment states
+ * the reading taken):
  *   positions      x[2*v+0], x[2*v+1]
  *   CSR            rp[n+1] (int64), col[nnz] (int32), symmetric, no loops
  *   coincident pair (|x_u - x_v| == 0): unit vector and r-value are 0,
