@@ -90,7 +90,9 @@ typedef struct mm_params {
   int32_t approx_levels;    /* h of MulMent_h: 0 = Barnes-Hut / exact as set  */
                             /* above; h > 0 = the entropy sum of Eq. 3 with   */
                             /* the level h levels down (or the coarsest) on   */
-                            /* every level but the coarsest (Sec. 3.2)        */
+                            /* every level but the coarsest (Sec. 3.2); those */
+                            /* levels run the sweep kernels (no fused level   */
+                            /* kernel); single graphs only (batches: error)   */
   int32_t reserved[2];
 } mm_params;
 
@@ -143,7 +145,8 @@ const char* mm_last_error(void);
  *   out     receives the hierarchy; free with mm_free_hierarchy
  * Errors: MM_ERR_INVALID_ARG (malformed graph or params),
  * MM_ERR_NOT_CONNECTED, MM_ERR_OOM, MM_ERR_UNSUPPORTED (k not 1 or 2,
- * more than 2^31 - 1 pair entries), MM_ERR_CUDA.  Synchronises `stream`.
+ * more than 2^31 - 1 pair entries, approx_levels > 0 with num_graphs > 1),
+ * MM_ERR_CUDA.  Synchronises `stream`.
  */
 mm_status mm_build_hierarchy(const mm_graph* g, const mm_params* p,
                              void* stream, mm_hierarchy** out);

@@ -747,6 +747,10 @@ __global__ void slice_csr(int n, int64_t e0, int a, const int64_t* __restrict__ 
 // batched layout equals its own unbatched layout.
 mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out) {
   MM_TRY(check_params(p));
+  if (p->approx_levels > 0) {
+    set_error("approx_levels (Eq. 3) is not available for batches of graphs");
+    return MM_ERR_UNSUPPORTED;
+  }
   if (!g->graph_ptr || g->n < 1 || !g->row_ptr) {
     set_error("a batch needs graph_ptr (host) and a CSR");
     return MM_ERR_INVALID_ARG;
