@@ -190,3 +190,11 @@ def test_full_stress_refuses_weighted_and_large_graphs(mm):
     h = mm.build_hierarchy(cu(rp), cu(col), mm.default_params(k=1, coarsest_n=10), edge_len=cu(el))
     with pytest.raises(mm.MMError):
         mm.full_stress(h, cu(f32(np.zeros((10, 2)))))
+
+
+def test_approx_levels_refused_for_batches(mm):
+    gs = [graphs.grid(10, 10), graphs.grid(8, 12)]
+    rp, col, gp = graphs.concat_graphs(gs)
+    p = mm.default_params(k=2, coarsest_n=2, approx_levels=2)
+    with pytest.raises(mm.MMError):
+        mm.build_hierarchy(cu(rp), cu(col), p, graph_ptr=gp)
