@@ -13,8 +13,8 @@
 // Per level, once (build): the composed map M and the members of every
 // coarse vertex, sorted by vertex id (a stable radix sort of (M(v), v)),
 // with segment offsets.  Per sweep: one warp per coarse vertex sums its
-// members' positions (fixed order), then one thread per vertex (in member
-// order) adds the far sum over all coarse midpoints and the exact near sum
+// members' positions (fixed order), then four threads per vertex (in member
+// order) add the far sum over all coarse midpoints and the exact near sum
 // over its own group, both staged through shared memory in tiles (FP32-pipe
 // bound: n (n' - 1) far plus sum_c m_c (m_c - 1) near pair terms).
 #include <cuda_runtime.h>
@@ -85,12 +85,18 @@ __global__ void midpoints_kernel(int nt, const int32_t* __restrict__ moff,
 // the near sums (more than this many distinct groups in one block -- small
 // groups -- and each thread walks its own group directly).
 constexpr int kStagedGroups = 8;
+// Threads per vertex: the vertex's far and near terms are dealt round robin
+// to kSplit lanes and added back with shuffles in a fixed order, so a level
+// of n vertices runs kSplit * n threads (a single thread per vertex leaves
+// most warp slots empty on levels of ~10^5 vertices).
+constexpr int kSplit = 4;
+constexpr int kVertsPerBlock = kApproxThreads / kSplit;
 
-// One thread per vertex, taken in member order (u = members[i], so a block
-// covers whole groups or runs of them).  Far sum: every other coarse
-// midpoint, tiles of (x', nu) in shared memory, u's own representative
-// skipped.  Near sum: the exact r-values over u's own group, staged in
-// tiles of positions shared by the block's threads of that group (the point
+// kSplit threads per vertex, vertices taken in member order (u = members[i],
+// so a block covers whole groups or runs of them).  Far sum: every other
+// coarse midpoint, tiles of (x', nu) in shared memory, u's own representative
+// skipped.  Near sum: the exact r-values over u's own group, staged in tiles
+// of positions shared by the block's threads of that group (the point
 // itself and coincident points have |x_u - x_v| = 0 and add nothing).
 __global__ void __launch_bounds__(kApproxThreads) approx_force_kernel(
     int n, XSel xs, const int32_t* __restrict__ hmap, const int32_t* __restrict__ moff,
@@ -99,39 +105,36 @@ __global__ void __launch_bounds__(kApproxThreads) approx_force_kernel(
   __shared__ float4 tile[kApproxThreads];
   __shared__ float2 near[kApproxThreads];
   const float2* x = xs.cur();
-  const int i = blockIdx.x * kApproxThreads + threadIdx.x;
+  const int sub = threadIdx.x % kSplit;
+  const int i0 = blockIdx.x * kVertsPerBlock;
+  const int i = i0 + threadIdx.x / kSplit;
   const bool live = i < n;
   const int u = live ? members[i] : 0;
   const float2 xu = live ? x[u] : make_float2(0.f, 0.f);
   const int cu = live ? hmap[u] : -1;
   float fx = 0.f, fy = 0.f;
+  auto term = [&](float2 p, float wgt, bool on) {
+    const float dx = xu.x - p.x, dy = xu.y - p.y;
+    const float q = fmaf(dx, dx, dy * dy);
+    const float s = (on && q > 0.f) ? __fdividef(wgt, q) : 0.f;
+    fx = fmaf(s, dx, fx);
+    fy = fmaf(s, dy, fy);
+  };
   for (int t0 = 0; t0 < nt; t0 += kApproxThreads) {
     const int cnt = min(kApproxThreads, nt - t0);
     if (threadIdx.x < cnt) tile[threadIdx.x] = xc[t0 + threadIdx.x];
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < cnt; ++k) {
+#pragma unroll 4
+    for (int k = sub; k < cnt; k += kSplit) {
       const float4 c = tile[k];
-      const float dx = xu.x - c.x, dy = xu.y - c.y;
-      const float q = fmaf(dx, dx, dy * dy);
       // the own representative carries no far term; coincident: r = 0
-      const float s = (t0 + k != cu && q > 0.f) ? __fdividef(c.z, q) : 0.f;
-      fx = fmaf(s, dx, fx);
-      fy = fmaf(s, dy, fy);
+      term(make_float2(c.x, c.y), c.z, t0 + k != cu);
     }
     __syncthreads();
   }
   // groups present in this block (members are sorted by group)
-  const int i0 = blockIdx.x * kApproxThreads;
   const int c0 = hmap[members[i0]];
-  const int c1 = hmap[members[min(n - 1, i0 + kApproxThreads - 1)]];
-  auto pair = [&](float2 p) {
-    const float dx = xu.x - p.x, dy = xu.y - p.y;
-    const float q = fmaf(dx, dx, dy * dy);
-    const float s = q > 0.f ? __fdividef(1.f, q) : 0.f;
-    fx = fmaf(s, dx, fx);
-    fy = fmaf(s, dy, fy);
-  };
+  const int c1 = hmap[members[min(n - 1, i0 + kVertsPerBlock - 1)]];
   if (c1 - c0 < kStagedGroups) {
     for (int c = c0; c <= c1; ++c) {
       const int b = moff[c], e = moff[c + 1];
@@ -139,15 +142,23 @@ __global__ void __launch_bounds__(kApproxThreads) approx_force_kernel(
         const int cnt = min(kApproxThreads, e - t0);
         if (threadIdx.x < cnt) near[threadIdx.x] = x[members[t0 + threadIdx.x]];
         __syncthreads();
-        if (cu == c)
-          for (int k = 0; k < cnt; ++k) pair(near[k]);
+        if (cu == c) {
+#pragma unroll 4
+          for (int k = sub; k < cnt; k += kSplit) term(near[k], 1.f, true);
+        }
         __syncthreads();
       }
     }
   } else if (live) {
-    for (int j = moff[cu]; j < moff[cu + 1]; ++j) pair(x[members[j]]);
+    for (int j = moff[cu] + sub; j < moff[cu + 1]; j += kSplit) term(x[members[j]], 1.f, true);
   }
-  if (live) F[u] = make_float2(fx, fy);
+  // the kSplit partial sums of a vertex sit in consecutive lanes
+#pragma unroll
+  for (int o = 1; o < kSplit; o <<= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+  }
+  if (live && sub == 0) F[u] = make_float2(fx, fy);
 }
 
 }  // namespace
@@ -207,7 +218,7 @@ mm_status approx_repulsion(const Level& L, XSel x, float4* xc, float2* F, cudaSt
   }
   midpoints_kernel<<<ceil_div((int64_t)L.nt * 32, 256), 256, 0, s>>>(L.nt, L.moff, L.members, x,
                                                                       xc);
-  approx_force_kernel<<<ceil_div(L.n, kApproxThreads), kApproxThreads, 0, s>>>(
+  approx_force_kernel<<<ceil_div(L.n, kVertsPerBlock), kApproxThreads, 0, s>>>(
       L.n, x, L.hmap, L.moff, L.members, L.nt, xc, F);
   MM_CK(cudaGetLastError());
   return MM_OK;
