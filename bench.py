@@ -261,55 +261,76 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(w, rp, col, budget_s=15.0, per_step=None):
-    """The FP64 oracle as it stands: Barnes-Hut (or exact) Eq. 2 sweeps of the
-    finest level on the host cores.  Returns (vertex-updates/s, cores, sample)."""
-    import numpy as np
-    import oracle
-    from paper_1506_04383_gb300 import graphs
-    n = len(rp) - 1
-    S = oracle.build_S(rp, col, w["k"])
-    x = graphs.uniform_positions(n, 1506, 0.0, math.sqrt(n))
-    exact = bool(w.get("exact"))
-    theta = w.get("theta", 0.5)
-    mode, cmap, what = (0 if exact else 1), None, ("exact" if exact else
-                                                    "Barnes-Hut theta=%g" % theta)
-    if w.get("approx"):
-        # the oracle's own coarsening supplies the map to the level h below
-        po = oracle.params(k=w["k"], coarsest_n=w["coarsest_n"], approx_levels=w["approx"])
-        levels = oracle.build_hierarchy(rp, col, po)
-        mode, cmap = 2, oracle.approx_map(levels, 0, w["approx"])
-        what = f"Eq. 3 (h={w['approx']}, {int(cmap.max()) + 1} representatives)"
-    sweeps, t0 = 0, time.perf_counter()
-    while True:
-        x, _ = oracle.sweep(x, S, 0.3, mode, theta, cmap=cmap)
-        sweeps += 1
-        el = time.perf_counter() - t0
-        if (per_step and sweeps >= per_step) or (not per_step and el >= budget_s):
-            break
-    sample = (f"{sweeps} {what} Eq. 2 sweeps "
-              f"of the finest level (n={n}, |S|={len(S[1])}), FP64 oracle, OpenMP")
-    return n * sweeps / el, oracle.num_threads(), sample, el
+class OracleSweeps:
+    """The FP64 oracle as it stands, prepared once for the finest level of a
+    workload: Barnes-Hut, exact or Eq. 3 sweeps of Eq. 2 on the host cores."""
+
+    def __init__(self, w, rp, col):
+        import oracle
+        from paper_1506_04383_gb300 import graphs
+        self.oracle = oracle
+        self.n = len(rp) - 1
+        self.S = oracle.build_S(rp, col, w["k"])
+        self.x = graphs.uniform_positions(self.n, 1506, 0.0, math.sqrt(self.n))
+        exact = bool(w.get("exact"))
+        self.theta = w.get("theta", 0.5)
+        self.mode, self.cmap = (0 if exact else 1), None
+        self.what = "exact" if exact else "Barnes-Hut theta=%g" % self.theta
+        if w.get("approx"):
+            # the oracle's own coarsening supplies the map to the level h below
+            po = oracle.params(k=w["k"], coarsest_n=w["coarsest_n"],
+                               approx_levels=w["approx"])
+            levels = oracle.build_hierarchy(rp, col, po)
+            self.mode, self.cmap = 2, oracle.approx_map(levels, 0, w["approx"])
+            self.what = f"Eq. 3 (h={w['approx']}, {int(self.cmap.max()) + 1} representatives)"
+
+    def run(self, sweeps=None, budget_s=None):
+        """Runs `sweeps` sweeps (or until budget_s elapsed); returns
+        (sweeps, seconds)."""
+        done, t0 = 0, time.perf_counter()
+        while True:
+            self.x, _ = self.oracle.sweep(self.x, self.S, 0.3, self.mode, self.theta,
+                                          cmap=self.cmap)
+            done += 1
+            el = time.perf_counter() - t0
+            if (sweeps and done >= sweeps) or (budget_s and el >= budget_s):
+                return done, el
+
+    def sample(self, sweeps):
+        return (f"{sweeps} {self.what} Eq. 2 sweeps of the finest level (n={self.n}, "
+                f"|S|={len(self.S[1])}), FP64 oracle, OpenMP")
+
+
+def cpu_baseline(w, rp, col, budget_s=15.0):
+    """The oracle's throughput on the host cores over a bounded sample (after
+    a short warm-up).  Returns (vertex-updates/s, cores, sample, seconds)."""
+    o = OracleSweeps(w, rp, col)
+    o.run(budget_s=min(1.0, budget_s / 10))
+    sweeps, el = o.run(budget_s=budget_s)
+    return o.n * sweeps / el, o.oracle.num_threads(), o.sample(sweeps), el
 
 
 def run_reference(args, w, rank, world):
+    """The reference arm: the oracle, prepared once; every step is the same
+    number of sweeps (calibrated in the warm-up to about 0.5 s of work)."""
     if rank != 0:
         return 0
     rp, col = make_graph(w)
-    steps = []
-    for i in range(args.warmup + args.steps):
-        v, cores, sample, el = cpu_baseline(w, rp, col, per_step=1)
-        if i >= args.warmup:
-            steps.append((v, el))
-    value = sum(len(rp) - 1 for _ in steps) / sum(el for _, el in steps)
+    o = OracleSweeps(w, rp, col)
+    done, el = o.run(budget_s=0.5)
+    per_step = max(1, int(done * 0.5 / max(el, 1e-9)))
+    for _ in range(args.warmup):
+        o.run(sweeps=per_step)
+    times = [o.run(sweeps=per_step)[1] for _ in range(args.steps)]
+    value = o.n * per_step * args.steps / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * statistics.mean(el for _, el in steps),
+            "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "desc": w["desc"], "n": len(rp) - 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "per step: " + sample},
+            "config": {"workload": args.workload, "desc": w["desc"], "n": o.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.oracle.num_threads(),
+                             "kind": "oracle", "sample": "per step: " + o.sample(per_step)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
