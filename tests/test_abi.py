@@ -95,3 +95,34 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "mm_oracle" not in text, f
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("struct_version", 0, 1), ("k", 3, 7), ("theta", -0.5, 1), ("coarsest_n", 0, 1),
+    ("alpha_factor", 1.5, 1), ("max_levels", 0, 1), ("leaf_size", 65, 1),
+    ("approx_levels", -1, 1), ("approx_levels", 1000, 1)])
+def test_parameters_are_checked_before_any_device_work(lib, field, value, status):
+    # host-only: the parameter check runs before the graph or the device is
+    # touched, so a descriptor without buffers is enough
+    import ctypes
+    from paper_1506_04383_gb300 import mm
+    g = mm.Graph(n=4, nnz=0, row_ptr=None, col=None, edge_len=None, num_graphs=1,
+                 graph_ptr=None)
+    p = mm.default_params()
+    setattr(p, field, value)
+    out = ctypes.c_void_p()
+    st = lib.mm_build_hierarchy(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(out))
+    assert st == status, lib.mm_last_error()
+    assert out.value is None
+    assert lib.mm_last_error() != b""
+
+
+def test_null_graph_buffers_are_refused_on_the_host(lib):
+    import ctypes
+    from paper_1506_04383_gb300 import mm
+    g = mm.Graph(n=4, nnz=6, row_ptr=None, col=None, edge_len=None, num_graphs=1,
+                 graph_ptr=None)
+    p = mm.default_params()
+    out = ctypes.c_void_p()
+    st = lib.mm_build_hierarchy(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(out))
+    assert st == 1 and b"graph" in lib.mm_last_error()
