@@ -503,3 +503,37 @@ def test_full_stress_matches_library_shortest_paths():
     assert pairs == len(d)
     assert F == pytest.approx(F_ref, rel=1e-12) and s == pytest.approx(s_ref, rel=1e-12)
     assert Fs == pytest.approx((w * (s_ref * L - d) ** 2).sum(), rel=1e-9)
+
+
+# --------------------------------------- whole multilevel layout, closed form ---
+@pytest.mark.parametrize("n", [3, 4, 5])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_layout_complete_graph_ends_as_stress_optimal_polygon(n, seed):
+    # K_n with k = 1: S holds every pair, so Eq. 2 has no entropy term and the
+    # whole multilevel run (coarsening, coarsest placement, prolongation,
+    # schedule) must end at a stress minimum; for n = 3, 4, 5 that is the
+    # regular n-gon whose circumradius R minimises sum (chord - 1)^2 over all
+    # pairs: R = sum m_j L_j / sum m_j L_j^2 with L_j = 2 sin(pi j / n) and m_j
+    # chords of each length
+    rp, col = graphs.complete(n)
+    x, info = oracle.layout(rp, col, oracle.params(k=1, coarsest_n=2, seed=seed))
+    js = np.arange(1, n // 2 + 1)
+    m = np.where(2 * js == n, n / 2, n)
+    L = 2 * np.sin(np.pi * js / n)
+    R = (m * L).sum() / (m * L * L).sum()
+    r = np.sqrt(((x - x.mean(0)) ** 2).sum(1))
+    assert np.allclose(r, R, rtol=2e-3), (r, R)
+    D = np.sort(np.sqrt(((x[:, None] - x[None]) ** 2).sum(-1))[np.triu_indices(n, 1)])
+    chords = np.sort(np.concatenate([np.full(int(mj), R * Lj) for mj, Lj in zip(m, L)]))
+    assert np.allclose(D, chords, rtol=3e-3), (D, chords)
+    assert len(info["levels"]) >= 2
+
+
+def test_layout_path3_with_k2_ends_collinear_at_unit_spacing():
+    # P3 with k = 2: S holds every pair (distances 1, 1, 2), no entropy term;
+    # the stress-free layout is the path on a line at unit spacing
+    rp, col = graphs.path(3)
+    x, _ = oracle.layout(rp, col, oracle.params(k=2, coarsest_n=2, seed=1,
+                                                 max_iters_at_min=2000, eps_final=1e-9))
+    d = [np.linalg.norm(x[0] - x[1]), np.linalg.norm(x[1] - x[2]), np.linalg.norm(x[0] - x[2])]
+    assert np.allclose(d, [1.0, 1.0, 2.0], rtol=1e-3), d
