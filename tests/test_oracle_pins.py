@@ -537,3 +537,23 @@ def test_layout_path3_with_k2_ends_collinear_at_unit_spacing():
                                                  max_iters_at_min=2000, eps_final=1e-9))
     d = [np.linalg.norm(x[0] - x[1]), np.linalg.norm(x[1] - x[2]), np.linalg.norm(x[0] - x[2])]
     assert np.allclose(d, [1.0, 1.0, 2.0], rtol=1e-3), d
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (12, 2), (24, 1), (24, 2)])
+def test_layout_cycle_ends_as_the_fixed_point_polygon(n, seed):
+    # C_n with k = 1 and the exact entropy sum: run to convergence, the whole
+    # multilevel layout ends at the regular n-gon of radius
+    # R* = (1 + sqrt(1 + 2 alpha (n - 3))) / (4 sin(pi / n)) at alpha_min, the
+    # fixed point of Eq. 2 on a regular polygon (see the sweep pins above)
+    rp, col = graphs.cycle(n)
+    x, _ = oracle.layout(rp, col, oracle.params(k=1, coarsest_n=2, seed=seed,
+                                                 exact_repulsion=1, max_iters_at_min=3000,
+                                                 eps_final=1e-10))
+    alpha = 0.008
+    Rs = (1 + math.sqrt(1 + 2 * alpha * (n - 3))) / (4 * math.sin(math.pi / n))
+    c = x.mean(0)
+    r = np.sqrt(((x - c) ** 2).sum(1))
+    assert np.allclose(r, Rs, rtol=1e-4), (r.min(), r.max(), Rs)
+    # neighbours along the cycle are adjacent corners of the polygon
+    d = np.sqrt(((x - np.roll(x, 1, axis=0)) ** 2).sum(1))
+    assert np.allclose(d, 2 * Rs * math.sin(math.pi / n), rtol=1e-4)
