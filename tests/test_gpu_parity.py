@@ -523,3 +523,36 @@ def test_layout_host_api(mm):
     x, st = mm.layout_host(rp, col, mm.default_params(k=2, coarsest_n=2))
     assert x.shape == (400, 2) and np.all(np.isfinite(x))
     assert st["vertex_updates"] > 0
+
+
+@pytest.mark.parametrize("n", [12, 24])
+def test_layout_cycle_ends_as_the_fixed_point_polygon(mm, n):
+    # the whole multilevel layout on the device (k = 1, exact entropy sum, run
+    # to convergence) ends at the regular n-gon of the Eq. 2 fixed-point
+    # radius R* at alpha_min, as the oracle's does
+    rp, col = graphs.cycle(n)
+    h, p = hier(mm, rp, col, k=1, coarsest_n=2, exact_repulsion=1, max_iters_at_min=3000,
+                eps_final=1e-10)
+    x, st = mm.layout(h, p)
+    x = x.cpu().numpy().astype(np.float64)
+    Rs = (1 + math.sqrt(1 + 2 * 0.008 * (n - 3))) / (4 * math.sin(math.pi / n))
+    r = np.sqrt(((x - x.mean(0)) ** 2).sum(1))
+    assert np.allclose(r, Rs, rtol=1e-4), (r.min(), r.max(), Rs)
+    d = np.sqrt(((x - np.roll(x, 1, axis=0)) ** 2).sum(1))
+    assert np.allclose(d, 2 * Rs * math.sin(math.pi / n), rtol=1e-4)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_layout_complete_graph_ends_as_stress_optimal_polygon(mm, n):
+    # K_n, k = 1: S holds every pair (no entropy term); the device layout ends
+    # at the regular n-gon whose circumradius minimises the stress
+    rp, col = graphs.complete(n)
+    h, p = hier(mm, rp, col, k=1, coarsest_n=2)
+    x, st = mm.layout(h, p)
+    x = x.cpu().numpy().astype(np.float64)
+    js = np.arange(1, n // 2 + 1)
+    m = np.where(2 * js == n, n / 2, n)
+    L = 2 * np.sin(np.pi * js / n)
+    R = (m * L).sum() / (m * L * L).sum()
+    r = np.sqrt(((x - x.mean(0)) ** 2).sum(1))
+    assert np.allclose(r, R, rtol=2e-3), (r, R)
