@@ -27,3 +27,40 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "grid32"
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    c.lines = []
+    assert c.summary()["samples"] == 0
+
+
+def test_roofline_of_the_dominant_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+    names = ["bbox", "morton_hist", "sort", "radix_tree_scan", "records", "traverse", "gather",
+             "controller"]
+    ms = [0.008, 0.008, 0.046, 0.018, 0.012, 0.110, 0.021, 0.008]
+    prof = {"stage_names": names, "stage_ms": ms, "nnz_S": 2_000_000, "interactions": 4.0e7}
+    peaks = {"hbm_gbs": 6784.5, "sm_max_mhz": 2070.0}
+    r = bench.roofline(prof, peaks, "measured", {}, 100_000, workload="rgg100k")
+    assert r["kernel"] == "traverse" and r["bound"] == "alu"
+    assert abs(r["achieved"] - 10 * 4.0e7 / 110e-6 / 1e12) < 1e-9
+    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["traffic"] == bench.NCU_TRAFFIC["rgg100k"]["traverse"]
+    g = r["others"]["gather"]
+    assert g["bound"] == "hbm" and abs(g["achieved"] - (100_000 * 32 + 2_000_000 * 8) / 21e-6 / 1e9) < 1e-6
+    # an exact-repulsion level counts n (n - 1) pair interactions
+    r2 = bench.roofline(prof, peaks, "measured", {}, 1024, exact=True)
+    assert abs(r2["achieved"] - 10 * 1024 * 1023 / 110e-6 / 1e12) < 1e-9
