@@ -81,7 +81,8 @@ def _load():
         lib.orc_repulsion_h.argtypes = [i32, P, P, i32, P]
         lib.orc_full_stress.argtypes = [i32, P, P, P, P]
         lib.orc_objective.argtypes = [i32, P, P, P, P, f64, P]
-        lib.orc_sclap.argtypes = [i32, P, P, P, P, f64, ctypes.c_int, u64, i32, P]
+        lib.orc_objective_sampled.argtypes = [i32, P, P, P, P, f64, i64, u64, P]
+        lib.orc_sclap.argtypes = [i32, P, P, P, P, f64, ctypes.c_int, u64, i32, P, P]
         lib.orc_contract.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_contract.restype = i32
         lib.orc_prolong.argtypes = [i32, P, P, P, u64, i32, P]
@@ -207,6 +208,24 @@ def objective(x, S, alpha: float):
     return float(out[0]), float(out[1]), float(out[2])
 
 
+def objective_sampled(x, S, alpha: float, samples: int = 10_000_000, seed: int = 1506):
+    """Eq. 1 with the stress over S exact and the ln-sum over pairs outside
+    S estimated from `samples` random pairs (for graphs whose O(n^2) sum is
+    out of reach; Sec. 4 calls the exact measures infeasible for large
+    graphs).  Returns dict(stress, lnsum, M, se_lnsum, se_M, kept); the
+    standard errors are those of the sample mean.  The same seed draws the
+    same pairs, so two layouts of one graph are compared on common pairs."""
+    lib = _load()
+    sp, scol, sd, _ = S
+    x = _f64(x).reshape(-1, 2)
+    out = np.zeros(5, dtype=np.float64)
+    lib.orc_objective_sampled(len(x), _p(x), _p(_i64(sp)), _p(_i32(scol)), _p(_f64(sd)),
+                              float(alpha), int(samples), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                              _p(out))
+    return dict(stress=float(out[0]), lnsum=float(out[1]), M=float(out[2]),
+                se_lnsum=float(out[3]), se_M=float(alpha * out[3]), kept=int(out[4]))
+
+
 def full_stress(rp, col, x):
     """Full stress over all connected unordered pairs with hop distances and
     w = d^-2, the stress-minimising scale s and the stress at s x (Sec. 4,
@@ -218,14 +237,23 @@ def full_stress(rp, col, x):
     return float(out[0]), float(out[1]), float(out[2]), int(out[3])
 
 
-def sclap(rp, col, c, U: float, rounds: int, seed: int, level: int, ew=None):
-    """Size-constrained label propagation (Sec. 3.1); returns labels."""
+def sclap(rp, col, c, U: float, rounds: int, seed: int, level: int, ew=None, order=None):
+    """Size-constrained label propagation (Sec. 3.1); returns labels.
+
+    order: optional [rounds, n] visiting orders, one permutation per round,
+    in place of the seeded random order (tests fix the random draws this
+    way)."""
     lib = _load()
     rp, col = _i64(rp), _i32(col)
     n = len(rp) - 1
     labels = np.zeros(max(n, 1), dtype=np.int32)
+    od = None
+    if order is not None:
+        od = _i32(order).reshape(-1, n)
+        if od.shape[0] < rounds or any(sorted(r.tolist()) != list(range(n)) for r in od):
+            raise ValueError("order must hold one permutation of the vertices per round")
     lib.orc_sclap(n, _p(rp), _p(col), _p(_f64(ew)), _p(_f64(c)), float(U), int(rounds),
-                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(level), _p(labels))
+                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(level), _p(od), _p(labels))
     return labels[:n]
 
 
@@ -287,13 +315,16 @@ def params(**kw):
     return p
 
 
-def build_hierarchy(rp, col, p, elen=None):
+def build_hierarchy(rp, col, p, elen=None, log=None):
     """Coarsening (Sec. 3.1).  Level h is clustered by SCLaP with
     U = max(max c, W), W = min(b^(h+1), |V|/f) with |V| the input graph's
     vertex count (the unit of the node weights c, and their sum on every
     level); the contraction becomes level h+1.  A contraction that shrinks the graph by at most 10 percent sets
     f := 0.7 f.  One that merges nothing is discarded (f := 0.7 f, retried up
-    to max_stalls times).  Coarsening stops at n <= coarsest_n."""
+    to max_stalls times).  Coarsening stops at n <= coarsest_n.
+
+    log: optional list; every clustering attempt appends
+    (h, W, U, f, n, n_coarse, kept) with the values it used."""
     rp, col = _i64(rp), _i32(col)
     n = len(rp) - 1
     lv = dict(n=n, rp=rp, col=col, ew=np.ones(len(col)), c=np.ones(n),
@@ -311,7 +342,10 @@ def build_hierarchy(rp, col, p, elen=None):
                        ew=cur["ew"])
         mp, cc, crp, ccol, cew = contract(cur["rp"], cur["col"], cur["c"], labels, ew=cur["ew"])
         nc = len(cc)
-        if nc >= cur["n"] or nc < 2:
+        kept = not (nc >= cur["n"] or nc < 2)
+        if log is not None:
+            log.append((h, W, U, f, cur["n"], nc, kept))
+        if not kept:
             f *= 0.7
             stalls += 1
             continue

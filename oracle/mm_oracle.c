@@ -509,6 +509,76 @@ void orc_objective(int32_t n, const double* x, const int64_t* sp,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Eq. 1 for graphs too large for the O(n^2) ln-sum: the stress over S is    */
+/* summed exactly, the ln-sum over the unordered pairs not in S is estimated */
+/* from `samples` uniformly drawn ordered pairs u != v (an unordered pair is */
+/* then uniform too): pairs in S are rejected, the rest give ln |x_u - x_v|  */
+/* (0 for coincident points).  With N = n(n-1)/2 - |S|/2 pairs outside S,   */
+/* the estimate is N * mean and its standard error N * sd / sqrt(kept).     */
+/* Draw i uses Philox counter (i, 0, 0, 5), key = seed; u and v are 64-bit   */
+/* draws reduced mod n.  S rows must be sorted ascending (binary search).    */
+/* out[0] = stress, out[1] = ln-sum estimate, out[2] = M estimate,           */
+/* out[3] = standard error of out[1], out[4] = samples kept.                 */
+/* ------------------------------------------------------------------------ */
+static int in_row(const int32_t* scol, int64_t a, int64_t b, int32_t v) {
+  while (a < b) {
+    int64_t m = a + (b - a) / 2;
+    if (scol[m] == v) return 1;
+    if (scol[m] < v) a = m + 1; else b = m;
+  }
+  return 0;
+}
+
+void orc_objective_sampled(int32_t n, const double* x, const int64_t* sp,
+                           const int32_t* scol, const double* sd, double alpha,
+                           int64_t samples, uint64_t seed, double* out) {
+  /* fixed chunks, each summed in order, then the chunks in order: the     */
+  /* result does not depend on the thread count or schedule                */
+  enum { CH = 256 };
+  double cs[CH], c1[CH], c2[CH], ck[CH];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < CH; ++c) {
+    double st = 0.0, s1 = 0.0, s2 = 0.0, kk = 0.0;
+    int32_t u0 = (int32_t)((int64_t)n * c / CH), u1 = (int32_t)((int64_t)n * (c + 1) / CH);
+    for (int32_t u = u0; u < u1; ++u)
+      for (int64_t e = sp[u]; e < sp[u + 1]; ++e) {
+        int32_t v = scol[e];
+        if (v <= u) continue;
+        double d = sd[e], w = 1.0 / (d * d);
+        double dx = x[2 * u] - x[2 * v], dy = x[2 * u + 1] - x[2 * v + 1];
+        double dist = sqrt(dx * dx + dy * dy);
+        st += w * (dist - d) * (dist - d);
+      }
+    int64_t i0 = samples * c / CH, i1 = samples * (c + 1) / CH;
+    for (int64_t i = i0; i < i1; ++i) {
+      uint32_t z[4];
+      draw4(seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, 5u, z);
+      int32_t u = (int32_t)((((uint64_t)z[0] << 32) | z[1]) % (uint64_t)n);
+      int32_t v = (int32_t)((((uint64_t)z[2] << 32) | z[3]) % (uint64_t)n);
+      if (u == v || in_row(scol, sp[u], sp[u + 1], v)) continue;
+      double dx = x[2 * u] - x[2 * v], dy = x[2 * u + 1] - x[2 * v + 1];
+      double q = dx * dx + dy * dy;
+      double l = q > 0.0 ? 0.5 * log(q) : 0.0;
+      s1 += l;
+      s2 += l * l;
+      kk += 1.0;
+    }
+    cs[c] = st; c1[c] = s1; c2[c] = s2; ck[c] = kk;
+  }
+  double stress = 0.0, sum = 0.0, sum2 = 0.0, kept = 0.0;
+  for (int c = 0; c < CH; ++c) { stress += cs[c]; sum += c1[c]; sum2 += c2[c]; kept += ck[c]; }
+  double N = 0.5 * (double)n * (double)(n - 1) - 0.5 * (double)sp[n];
+  double mean = kept > 0.0 ? sum / kept : 0.0;
+  double var = kept > 1.0 ? (sum2 - kept * mean * mean) / (kept - 1.0) : 0.0;
+  if (var < 0.0) var = 0.0;
+  out[0] = stress;
+  out[1] = N * mean;
+  out[2] = stress - alpha * N * mean;
+  out[3] = kept > 0.0 ? N * sqrt(var / kept) : 0.0;
+  out[4] = kept;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Size-constrained label propagation, SCLaP (Sec. 3.1).  Start from         */
 /* singletons; each round visits the vertices in a random order and moves a  */
 /* vertex to the neighbouring cluster of strongest connection (sum of edge   */
@@ -516,11 +586,14 @@ void orc_objective(int32_t n, const double* x, const int64_t* sp,
 /* c(v) <= U).  Ties keep the current cluster if it is among the best, else  */
 /* take the smallest cluster id.  At most `rounds` rounds; stops early when  */
 /* a round moves nothing.  The random order is a Fisher-Yates shuffle drawn  */
-/* from Philox with counter (i, round, level, 3).                            */
+/* from Philox with counter (i, round, level, 3); a caller may pass the      */
+/* orders instead (order_in: rounds x n, row r = the visiting order of round */
+/* r; NULL = the Philox shuffle), the way a test fixes the random draws.     */
 /* ------------------------------------------------------------------------ */
 void orc_sclap(int32_t n, const int64_t* rp, const int32_t* col,
                const double* ew, const double* c, double U, int rounds,
-               uint64_t seed, int32_t level, int32_t* labels) {
+               uint64_t seed, int32_t level, const int32_t* order_in,
+               int32_t* labels) {
   double* wt = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double* conn = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
@@ -528,13 +601,17 @@ void orc_sclap(int32_t n, const int64_t* rp, const int32_t* col,
   char* mark = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
   for (int32_t v = 0; v < n; ++v) { labels[v] = v; wt[v] = c[v]; }
   for (int r = 0; r < rounds; ++r) {
-    for (int32_t i = 0; i < n; ++i) order[i] = i;
-    for (int32_t i = n - 1; i > 0; --i) {
-      uint32_t z[4];
-      draw4(seed, (uint32_t)i, (uint32_t)r, (uint32_t)level, 3u, z);
-      uint64_t big = ((uint64_t)z[0] << 32) | z[1];
-      int32_t j = (int32_t)(big % (uint64_t)(i + 1));
-      int32_t tmp = order[i]; order[i] = order[j]; order[j] = tmp;
+    if (order_in) {
+      for (int32_t i = 0; i < n; ++i) order[i] = order_in[(size_t)r * n + i];
+    } else {
+      for (int32_t i = 0; i < n; ++i) order[i] = i;
+      for (int32_t i = n - 1; i > 0; --i) {
+        uint32_t z[4];
+        draw4(seed, (uint32_t)i, (uint32_t)r, (uint32_t)level, 3u, z);
+        uint64_t big = ((uint64_t)z[0] << 32) | z[1];
+        int32_t j = (int32_t)(big % (uint64_t)(i + 1));
+        int32_t tmp = order[i]; order[i] = order[j]; order[j] = tmp;
+      }
     }
     int64_t moved = 0;
     for (int32_t i = 0; i < n; ++i) {

@@ -248,6 +248,58 @@ def test_objective_regular_polygon(k, n):
     assert M == pytest.approx(exp_stress - alpha * total, rel=1e-12)
 
 
+def test_objective_sampled_regular_polygon_closed_form():
+    # the estimator of the ln-sum (pairs outside S drawn at random) against
+    # the same closed form: within 5 standard errors; the stress over S is
+    # summed exactly
+    n, R, alpha, k = 400, 7.0, 0.008, 2
+    rp, col = graphs.cycle(n)
+    S = oracle.build_S(rp, col, k)
+    x = polygon(n, R)
+    total = 0.5 * n * ((n - 1) * math.log(R) + math.log(n))
+    exp_stress = 0.0
+    for m in range(1, k + 1):
+        dist = 2 * R * math.sin(math.pi * m / n)
+        total -= n * math.log(dist)
+        exp_stress += n * (dist - m) ** 2 / m ** 2
+    est = oracle.objective_sampled(x, S, alpha, samples=400000, seed=3)
+    assert est["stress"] == pytest.approx(exp_stress, rel=1e-12)
+    assert 0 < est["se_lnsum"] < 2e-3 * abs(total)
+    assert abs(est["lnsum"] - total) <= 5 * est["se_lnsum"]
+    assert est["M"] == pytest.approx(est["stress"] - alpha * est["lnsum"], rel=1e-12)
+    assert est["se_M"] == pytest.approx(alpha * est["se_lnsum"], rel=1e-12)
+    # rejected draws: u == v (1/n of them) and pairs in S (2k/n of them)
+    assert abs(est["kept"] / 400000 - (1 - (2 * k + 1) / n)) < 0.005
+
+
+def test_objective_sampled_against_the_exact_sum_and_its_error_bars():
+    rp, col = graphs.grid(25, 20)
+    n = len(rp) - 1
+    S = oracle.build_S(rp, col, 2)
+    x = graphs.uniform_positions(n, 17, 0.0, 30.0)
+    stress, lns, M = oracle.objective(x, S, 0.008)
+    z = []
+    for seed in range(8):
+        est = oracle.objective_sampled(x, S, 0.008, samples=200000, seed=seed)
+        assert est["stress"] == pytest.approx(stress, rel=1e-12)
+        z.append((est["lnsum"] - lns) / est["se_lnsum"])
+    # unbiased with the stated error: z-scores of 8 independent estimates
+    assert max(abs(v) for v in z) < 4.5
+    assert abs(np.mean(z)) < 4.5 / math.sqrt(8)
+    # the same seed draws the same pairs
+    a = oracle.objective_sampled(x, S, 0.008, samples=50000, seed=4)
+    b = oracle.objective_sampled(x, S, 0.008, samples=50000, seed=4)
+    assert a == b
+
+
+def test_objective_sampled_coincident_points_give_zero():
+    rp, col = graphs.path(50)
+    S = oracle.build_S(rp, col, 1)
+    est = oracle.objective_sampled(np.ones((50, 2)), S, 0.008, samples=10000, seed=1)
+    assert est["lnsum"] == 0.0 and est["se_lnsum"] == 0.0
+    assert est["stress"] == pytest.approx(49.0)  # 49 edges at distance 0, d = 1
+
+
 # --------------------------------------------------------------------------
 # SCLaP (Sec. 3.1): invariants and order-free cases
 # --------------------------------------------------------------------------
@@ -285,6 +337,213 @@ def test_sclap_size_bound_and_partition(U):
     w = _cluster_weights(lab, c)
     assert max(w.values()) <= U
     assert len(w) < n  # something merged
+
+
+# Hand-worked rounds with the visiting order fixed (the order is the random
+# draw of Sec. 3.1; passing it in makes the outcome checkable by hand).
+def _wgraph(n, edges):
+    """Symmetric CSR with per-entry weights omega from (u, v, w) triples."""
+    adj = [[] for _ in range(n)]
+    for u, v, w in edges:
+        adj[u].append((v, w))
+        adj[v].append((u, w))
+    rp = np.zeros(n + 1, dtype=np.int64)
+    col, ew = [], []
+    for u in range(n):
+        for v, w in sorted(adj[u]):
+            col.append(v)
+            ew.append(w)
+        rp[u + 1] = len(col)
+    return rp, np.array(col, dtype=np.int32), np.array(ew, dtype=np.float64)
+
+
+def test_sclap_strongest_connection_not_most_neighbours_nor_first():
+    # p = 5 sees three clusters: {0} by one edge of omega 0.5 (its first
+    # neighbour in row order), {1, 2} by two edges of omega 1 (the most
+    # neighbours, after 1 joined 2 over their omega-10 edge) and {3} by one
+    # edge of omega 3: the strongest connection, sum 3 > 2 > 0.5, wins.
+    rp, col, ew = _wgraph(6, [(1, 2, 10.0), (1, 5, 1.0), (2, 5, 1.0), (3, 5, 3.0),
+                              (0, 5, 0.5), (4, 3, 0.25)])
+    order = [[1, 2, 5, 3, 0, 4]]
+    lab = oracle.sclap(rp, col, np.ones(6), U=10.0, rounds=1, seed=0, level=0, ew=ew,
+                       order=order)
+    # 1 -> {2}; 2 stays; 5 -> {3}; 3 stays (its cluster holds 5, omega 3);
+    # 0 -> {3, 5} (its only neighbour); 4 -> {3, 5, 0} (its only neighbour)
+    assert lab.tolist() == [3, 2, 2, 3, 3, 3]
+
+
+def test_sclap_tie_keeps_own_cluster():
+    # 2 joins 3 first (its only neighbour); then 3's own cluster {2, 3} has
+    # connection 2 and the cluster {0, 1} (formed over omega 10) also 2:
+    # a tie with the own cluster among the best keeps it, although label 1
+    # is smaller.
+    rp, col, ew = _wgraph(4, [(0, 1, 10.0), (0, 3, 1.0), (1, 3, 1.0), (2, 3, 2.0)])
+    lab = oracle.sclap(rp, col, np.ones(4), U=10.0, rounds=1, seed=0, level=0, ew=ew,
+                       order=[[0, 2, 3, 1]])
+    assert lab.tolist() == [1, 1, 3, 3]
+
+
+def test_sclap_tie_elsewhere_takes_smallest_label():
+    # 4's two neighbouring clusters {0, 3} (label 3, reached through vertex 0,
+    # the first entry of 4's row) and {2, 1} (label 1) both connect with 1;
+    # its own singleton connects with 0: the smallest label, 1, wins.
+    rp, col, ew = _wgraph(5, [(0, 3, 10.0), (2, 1, 10.0), (0, 4, 1.0), (2, 4, 1.0)])
+    lab = oracle.sclap(rp, col, np.ones(5), U=10.0, rounds=1, seed=0, level=0, ew=ew,
+                       order=[[0, 2, 4, 3, 1]])
+    assert lab.tolist() == [3, 1, 1, 3, 1]
+
+
+def test_sclap_overload_forces_second_best_and_bound_is_inclusive():
+    # U = 3: vertex 0 weighs 3, so 3 cannot join it (3 + 1 > U) and takes
+    # its second-strongest cluster {1}; 2 then joins {1, 3} reaching exactly
+    # U (weight + c(v) <= U is allowed); 0 can join nothing.
+    rp, col, ew = _wgraph(4, [(0, 3, 3.0), (1, 3, 2.0), (2, 3, 1.0)])
+    c = np.array([3.0, 1.0, 1.0, 1.0])
+    lab = oracle.sclap(rp, col, c, U=3.0, rounds=1, seed=0, level=0, ew=ew,
+                       order=[[3, 1, 2, 0]])
+    assert lab.tolist() == [0, 1, 1, 1]
+    # with room for it, the strongest cluster {0} is taken
+    lab = oracle.sclap(rp, col, c, U=4.0, rounds=1, seed=0, level=0, ew=ew,
+                       order=[[3, 1, 2, 0]])
+    assert lab[3] == 0
+
+
+def test_sclap_converged_labels_are_locally_optimal():
+    # After label propagation has converged (a round moved nothing), no
+    # vertex has a neighbouring cluster that would fit it (weight + c(v) <=
+    # U) and connects more strongly than its own cluster (Sec. 3.1: a vertex
+    # moves to the strongest connection).  Random omega makes this differ
+    # from counting neighbours.
+    rp, col, _, _ = graphs.rgg(1500, 7.0, 31, tune=False)
+    n = len(rp) - 1
+    rng = np.random.default_rng(5)
+    src = np.repeat(np.arange(n), np.diff(rp))
+    key = np.minimum(src, col).astype(np.int64) * n + np.maximum(src, col)
+    _, inv = np.unique(key, return_inverse=True)
+    ew = rng.uniform(0.1, 5.0, inv.max() + 1)[inv]   # symmetric omega
+    c = rng.integers(1, 4, n).astype(np.float64)
+    U = 9.0
+    lab = oracle.sclap(rp, col, c, U=U, rounds=400, seed=8, level=2, ew=ew)
+    wt = np.zeros(n)
+    np.add.at(wt, lab, c)
+    assert wt.max() <= U
+    checked = 0
+    for v in range(n):
+        conn = {}
+        for e in range(rp[v], rp[v + 1]):
+            L = int(lab[col[e]])
+            conn[L] = conn.get(L, 0.0) + ew[e]
+        own = conn.get(int(lab[v]), 0.0)
+        for L, s in conn.items():
+            if L != lab[v] and wt[L] + c[v] <= U:
+                assert s <= own + 1e-12, (v, L, s, own)
+                checked += 1
+    assert checked > n // 2  # the condition was tested on many candidate moves
+
+
+# --------------------------------------------------------------------------
+# Coarsening schedule (Sec. 3.1): W = min(b^(h+1), |V|/f), U = max(max c, W),
+# f := 0.7 f after a contraction that shrinks by at most 10 %, a contraction
+# that merges nothing discarded (f := 0.7 f, retried)
+# --------------------------------------------------------------------------
+def test_coarsening_schedule_hand_worked_on_a_star():
+    # A star with centre 0 and 199 leaves (|V| = 200).  Leaves touch only the
+    # centre, so on every level the centre's cluster grows to floor(U)
+    # (integral weights) whatever the visiting order, nothing else merges,
+    # and each level is again a star.  Worked by hand, attempt by attempt
+    # (f_j = 20 * 0.7^j):
+    #   h  f    W = min(2^(h+1), 200/f)   U = max(max c, W)  n -> n'
+    #   0  f0   min(2, 10)      = 2        2                 200 -> 199  1 %: f := 0.7 f
+    #   1  f1   min(4, 14.29)   = 4        4                 199 -> 197  f := 0.7 f
+    #   2  f2   min(8, 20.41)   = 8        8                 197 -> 193  f := 0.7 f
+    #   3  f3   min(16, 29.15)  = 16       16                193 -> 185  f := 0.7 f
+    #   4  f4   min(32, 41.65)  = 32       32                185 -> 169  8.6 %: f := 0.7 f
+    #   5  f5   min(64, 59.50)  = 59.50    59.50             169 -> 142  16 %: f kept
+    #   6  f5   59.50                      59.50 (centre 59) nothing merges: discarded, f := 0.7 f
+    #   6  f6   min(128, 85.00) = 85.00    85.00             142 -> 117  f kept
+    #   7  f6   85.00                      85.00 (centre 84) discarded, f := 0.7 f
+    #   7  f7   min(256, 121.43)           121.43            117 -> 80
+    #   8  f7   121.43                     (centre 121)      discarded, f := 0.7 f
+    #   8  f8   min(512, 173.47)           173.47             80 -> 28
+    #   9  f8   173.47                     (centre 173)      discarded, f := 0.7 f
+    #   9  f9.. 247.81, ...: the whole star merges into one vertex (n' < 2):
+    #      discarded, f := 0.7 f, until max_stalls = 10 ends the coarsening
+    n = 200
+    rp, col = graphs.csr_from_edges(n, np.zeros(n - 1, dtype=int), np.arange(1, n))
+    log = []
+    p = oracle.params(k=1, coarsest_n=2, seed=11)
+    levels = oracle.build_hierarchy(rp, col, p, log=log)
+    assert [L["n"] for L in levels] == [200, 199, 197, 193, 185, 169, 142, 117, 80, 28]
+    assert [float(L["c"].max()) for L in levels] == [1, 2, 4, 8, 16, 32, 59, 84, 121, 173]
+    T, F = True, False
+    rows = [  # (h, f, W, U, n, n', kept)
+        (0, 20.0, 2.0, 2.0, 200, 199, T),
+        (1, 14.0, 4.0, 4.0, 199, 197, T),
+        (2, 9.8, 8.0, 8.0, 197, 193, T),
+        (3, 6.86, 16.0, 16.0, 193, 185, T),
+        (4, 4.802, 32.0, 32.0, 185, 169, T),
+        (5, 3.3614, 59.499018266, 59.499018266, 169, 142, T),
+        (6, 3.3614, 59.499018266, 59.499018266, 142, 142, F),
+        (6, 2.35298, 84.998597523, 84.998597523, 142, 117, T),
+        (7, 2.35298, 84.998597523, 84.998597523, 117, 117, F),
+        (7, 1.647086, 121.426567890, 121.426567890, 117, 80, T),
+        (8, 1.647086, 121.426567890, 121.426567890, 80, 80, F),
+        (8, 1.1529602, 173.466525557, 173.466525557, 80, 28, T),
+        (9, 1.1529602, 173.466525557, 173.466525557, 28, 28, F),
+    ]
+    assert len(log) == len(rows) + 9
+    for got, want in zip(log, rows):
+        assert got[0] == want[0] and got[4:] == want[4:], (got, want)
+        assert got[1:4] == pytest.approx((want[2], want[3], want[1]), rel=1e-9), (got, want)
+    f = 1.1529602
+    for got in log[len(rows):]:
+        f *= 0.7
+        assert got[0] == 9 and got[3] == pytest.approx(f, rel=1e-9)
+        assert got[5] == 1 and not got[6]
+
+
+# --------------------------------------------------------------------------
+# Initial layout of the coarsest level (Sec. 3.1 'Initial Layout')
+# --------------------------------------------------------------------------
+def test_place_coarsest_radius_and_moments():
+    # more than two coarsest vertices: polar placement around the origin,
+    # angle uniform in [0, 2 pi), radius uniform in [0, sqrt(sum c))
+    n = 200000
+    c = np.tile([1.0, 2.0, 5.0], n // 3 + 1)[:n]
+    x = oracle.place_coarsest(c, seed=5, level=7)
+    R = math.sqrt(c.sum())
+    r = np.sqrt((x ** 2).sum(1))
+    assert np.all(r < R)
+    t = r / R
+    assert abs(t.mean() - 0.5) < 0.005 and abs(t.var() - 1 / 12) < 0.002
+    ang = np.arctan2(x[:, 1], x[:, 0])
+    assert abs(np.cos(ang).mean()) < 0.01 and abs(np.sin(ang).mean()) < 0.01
+    assert abs((np.cos(ang) ** 2).mean() - 0.5) < 0.01
+    # the angle histogram is flat (8 sectors, 5 sigma)
+    hist = np.histogram(ang, bins=8, range=(-math.pi, math.pi))[0]
+    assert np.all(np.abs(hist - n / 8) < 5 * math.sqrt(n / 8))
+    # reproducible; another seed or level draws other numbers; and not the
+    # prolongation's draws (another Philox counter)
+    assert np.array_equal(x, oracle.place_coarsest(c, seed=5, level=7))
+    assert not np.array_equal(x, oracle.place_coarsest(c, seed=6, level=7))
+    assert not np.array_equal(x, oracle.place_coarsest(c, seed=5, level=8))
+    xp = oracle.prolong(np.zeros(n, dtype=np.int32), np.zeros((1, 2)), np.array([c.sum()]),
+                        seed=5, level=7)
+    assert not np.allclose(x, xp)
+
+
+def test_initial_layout_two_vertices_at_target_distance():
+    # two coarsest vertices are placed at their target distance, which on a
+    # coarse level is sqrt(c_u) + sqrt(c_v) (Sec. 3.2); that is a fixed
+    # point of Eq. 2 with S = E (one sweep leaves it in place)
+    rp, col = graphs.path(2)
+    c = np.array([4.0, 9.0])
+    S = oracle.build_S(rp, col, 1, c=c, coarse=True)
+    L = dict(n=2, S=S, c=c)
+    x = oracle.initial_layout(L, oracle.params(), 3)
+    assert np.linalg.norm(x[0] - x[1]) == pytest.approx(5.0, rel=1e-15)
+    x1, st = oracle.sweep(x, S, 1.0, 0)
+    assert np.allclose(x1, x, atol=1e-12)
 
 
 # --------------------------------------------------------------------------
