@@ -118,6 +118,11 @@ typedef struct mm_layout_stats {
   double final_rel_change;
   double final_stress;                 /* stress over S of the finest level   */
   int64_t kernel_launches;             /* library kernels launched by the call*/
+  float level_rel_change[MM_MAX_LEVELS]; /* relative change |x'-x|/|x| of each */
+                                       /* level's last sweep (Sec. 3.2): below */
+                                       /* eps_final = converged, else the level*/
+                                       /* stopped at max_iters_at_min; batches:*/
+                                       /* the largest over the graphs          */
 } mm_layout_stats;
 
 typedef struct mm_hierarchy mm_hierarchy;
@@ -300,7 +305,8 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
  * tree workspace lives in one fixed static device array of the library
  * (under 8 MiB, held on every GPU that loads libmm.so until exit).
  *   n      number of points, 1 <= n <= 32768 (larger n: MM_ERR_INVALID_ARG)
- *   x      device [2n] positions; F_out device [2n] receives
+ *   x      device [2n] positions; F_out device [2n] receives (both device
+ *          memory of the current device, else MM_ERR_INVALID_ARG)
  *          F_u ~ sum_{v != u} r(u,v) with opening parameter theta >= 0
  *          (theta = 0: exact through the tree), with the walk of the
  *          default parameters (leaf_size, bh_group of mm_default_params)
@@ -311,6 +317,32 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x,
  */
 mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta,
                                float* F_out, void* stream);
+
+/*
+ * Self-test of the timeout path of the library's bounded device waits (no
+ * paper counterpart; a deployment check).  Launches one block of the radix
+ * sort's look-back pass on a two-tile key set whose first tile never runs,
+ * so the block waits for a status word that nothing writes.  The wait gives
+ * up after spin_limit polls (1 <= spin_limit <= 2^22; the library's own
+ * sorts use 2^22), the kernel finishes and the context stays usable.
+ * Returns MM_ERR_TIMEOUT when the wait gave up, as intended, MM_OK if it did
+ * not (a broken timeout path), MM_ERR_INVALID_ARG for a spin_limit out of
+ * range.  The same MM_ERR_TIMEOUT is what mm_sweep / mm_layout /
+ * mm_repulsion return when a real look-back wait gives up.  Allocates a few
+ * KB with cudaMallocAsync on `stream`; synchronises it.
+ */
+mm_status mm_selftest_wait_timeout(int32_t spin_limit, void* stream);
+
+/*
+ * Measured FP32 FMA throughput of the current device (no paper counterpart; a
+ * measurement aid): `reps` timed launches (after one warm-up) of a kernel of
+ * independent FMA chains filling every SM, CUDA events on `stream`.
+ * *tflops = FP32 TFLOP/s (2 flops per FMA); ms_per_launch (nullable) = mean
+ * launch time.  The ALU-bound kernels' rooflines use it as their peak.
+ * Synchronises the stream.
+ */
+mm_status mm_measure_fp32_peak(int32_t reps, double* tflops, double* ms_per_launch,
+                               void* stream);
 
 /* Result of mm_autotune (host struct). */
 typedef struct mm_tune_result {

@@ -899,10 +899,10 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
   const double avg = L.n > 0 ? (double)L.nnzS / L.n : 0.0;
   int lanes = p.gather_lanes;
   if (lanes <= 0) {
-    // enough lanes to fill the GPU (152 SMs x 2048 threads) when n is small,
+    // enough lanes to fill the GPU (SMs x 2048 threads) when n is small,
     // never more than the mean row length
     lanes = 1;
-    const int64_t want = (int64_t)kSMs * 2048 / std::max(L.n, 1);
+    const int64_t want = (int64_t)num_sms() * 2048 / std::max(L.n, 1);
     while (lanes < 32 && 2 * lanes <= want && lanes < avg) lanes <<= 1;
   }
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) {
@@ -917,7 +917,7 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
     // helpers per task only add seed overhead once the SMs are full)
     const int64_t tasks = std::max<int64_t>(1, (L.n + 31) / 32);
     int w = 1;
-    while (w < 16 && (int64_t)w * tasks < (int64_t)24 * kSMs) w <<= 1;
+    while (w < 16 && (int64_t)w * tasks < (int64_t)24 * num_sms()) w <<= 1;
     L.walk_warps = w;
   } else {
     L.walk_warps = L.n >= 20000 ? 16 : 8;  // per-point walk: warps per block

@@ -101,8 +101,8 @@ mm_status objective_exact(const Level& L, const float2* x, double alpha, double 
   const int n = L.n;
   const int nt = ceil_div(std::max(n, 1), kT);
   const int64_t npairs = (int64_t)nt * (nt + 1) / 2;
-  const int pb = (int)std::min<int64_t>(npairs, kSMs * 8);
-  const int sb = std::max(1, std::min(ceil_div(n, kT), kSMs * 4));
+  const int pb = (int)std::min<int64_t>(npairs, num_sms() * 8);
+  const int sb = std::max(1, std::min(ceil_div(n, kT), num_sms() * 4));
   double* parts = nullptr;
   MM_CK(cudaMalloc(&parts, sizeof(double) * (size_t)(pb + 2 * sb)));
   pairs_ln_kernel<<<pb, kT, 0, s>>>(x, n, nt, npairs, parts);

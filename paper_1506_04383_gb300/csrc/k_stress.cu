@@ -116,7 +116,7 @@ mm_status full_stress(int n, const int32_t* rp, const int32_t* col, const float2
     return MM_OK;
   }
   const int batches = ceil_div(n, 64);
-  const int grid = std::min(batches, 2 * kSMs);
+  const int grid = std::min(batches, 2 * num_sms());
   unsigned long long* scratch = nullptr;
   double* part = nullptr;
   MM_CK(cudaMallocAsync(&scratch, sizeof(unsigned long long) * 3 * (size_t)n * grid, s));

@@ -403,11 +403,11 @@ void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st,
 
 int gather_light_blocks(const Level& L) {
   const int groups = kGatherThreads / std::max(1, L.lanes);
-  return std::max(1, std::min(ceil_div(L.n, groups), kMaxLightBlocks));
+  return std::max(1, std::min(ceil_div(L.n, groups), 16 * num_sms()));
 }
 
 int gather_heavy_blocks(const Level& L) {
-  return L.n_heavy > 0 ? std::min(L.n_heavy, kMaxHeavyBlocks) : 0;
+  return L.n_heavy > 0 ? std::min(L.n_heavy, 8 * num_sms()) : 0;
 }
 
 int gather_blocks(const Level& L) { return gather_light_blocks(L) + gather_heavy_blocks(L); }

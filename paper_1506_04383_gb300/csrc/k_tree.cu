@@ -35,7 +35,7 @@ namespace mm {
 namespace {
 
 constexpr int kBBoxThreads = 256;
-constexpr int kBBoxMaxBlocks = 2 * kSMs;
+constexpr int kBBoxMaxBlocks = 2 * kMaxSMs;  // buffer bound; grids: 2 x num_sms()
 constexpr int kNone = -2;  // lane is active
 
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
@@ -153,16 +153,18 @@ __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
 // decoupled look-back: a block takes the next tile in order, publishes its
 // per-digit counts, accumulates the counts of the preceding tiles from their
 // status words (epoch | flag | value; flag 1 = tile count, 2 = inclusive
-// prefix) and scatters.  Waits are bounded: after kSpinLimit polls the block
-// raises err[0] |= 2 and treats the missing tile as empty, so the kernel
-// always finishes.
+// prefix) and scatters.  Waits are bounded: after spin_limit polls (the
+// library passes kSpinLimit, about 0.1-1 s of polling) the block raises
+// err[0] |= 2 and treats the missing tile as empty, so the kernel always
+// finishes; every scatter stays inside [0, n) either way.
 constexpr int kSpinLimit = 1 << 22;
 
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     int32_t* __restrict__ vout, int n, int pass, const uint32_t* __restrict__ hist,
-    uint32_t* counters, unsigned long long* status, const unsigned* ticket, int* err) {
+    uint32_t* counters, unsigned long long* status, const unsigned* ticket, int* err,
+    int spin_limit) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t whist[kWarps][256];
   __shared__ uint32_t dbase[256];
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
         const unsigned long long w = vst[(size_t)t * 256 + d];
         const uint32_t flag = (uint32_t)(w >> 30) & 3u;
         if ((w & 0xffffffff00000000ull) != ep || flag == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             atomicOr(err, 2);
             break;
           }
@@ -818,7 +820,7 @@ void tree_ws_free(TreeWS& ws) {
 
 mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s) {
   if (n <= 0) return MM_OK;
-  const int bb = std::min(kBBoxMaxBlocks, ceil_div(n, kBBoxThreads));
+  const int bb = std::min(2 * num_sms(), ceil_div(n, kBBoxThreads));
   bbox_kernel<<<bb, kBBoxThreads, 0, s>>>(x, n, ws.partials, ws.ticket, ws.root, ws.hist,
                                           ws.counters);
   MM_CK(cudaGetLastError());
@@ -858,7 +860,7 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
                                   : onesweep_pass<1>;
     pass_kernel<<<tiles, kSortThreads, 0, s>>>(ws.keys[a], ws.vals[a], ws.keys[a ^ 1],
                                                ws.vals[a ^ 1], n, pass, ws.hist, ws.counters,
-                                               ws.status, ws.ticket, ws.err);
+                                               ws.status, ws.ticket, ws.err, kSpinLimit);
   }
   mark(3);
   // the radix tree and the position prefix sums both need only the sorted
@@ -933,6 +935,49 @@ mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s) {
   exact_kernel<<<ceil_div(n, kExactThreads), kExactThreads, 0, s>>>(x, n, F);
   MM_CK(cudaGetLastError());
   return MM_OK;
+}
+
+// Self-test of the bounded look-back wait (a measurement and deployment aid,
+// no paper counterpart).  One block of the sort pass is launched on a key
+// set of two tiles with the tile counter preset to 1, so it takes tile 1 and
+// waits for tile 0, which never runs: nothing ever publishes the status word
+// it polls.  The wait must give up after spin_limit polls, raise error bit 2
+// and let the kernel finish (all its reads and writes stay inside the
+// buffers allocated here).  *timed_out = 1 if it did.
+mm_status lookback_selftest(int spin_limit, int* timed_out, cudaStream_t s) {
+  constexpr int kTile = kSortThreads;  // one key per thread
+  constexpr int n = 2 * kTile;
+  struct Bufs {
+    uint32_t kin[n], kout[n], hist[4 * 256], counters[4];
+    int32_t vin[n], vout[n];
+    unsigned long long status[4 * 2 * 256];
+    unsigned ticket[2];
+    int err;
+  };
+  Bufs* d = nullptr;
+  MM_CK(cudaMallocAsync((void**)&d, sizeof(Bufs), s));
+  mm_status st = MM_OK;
+  int err = 0;
+  const uint32_t one = 1u;
+  // zero everything; tile counter 1 (the block takes tile 1); epoch 1 (the
+  // zeroed status words carry epoch 0, so none is ever valid)
+  if (cudaMemsetAsync(d, 0, sizeof(Bufs), s) != cudaSuccess ||
+      cudaMemcpyAsync(&d->counters[0], &one, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(&d->ticket[1], &one, 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    st = cuda_status(cudaGetLastError(), "look-back self-test set-up", __FILE__, __LINE__);
+  } else {
+    onesweep_pass<1><<<1, kSortThreads, 0, s>>>(d->kin, d->vin, d->kout, d->vout, n, 0, d->hist,
+                                                d->counters, d->status, d->ticket, &d->err,
+                                                spin_limit);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&err, &d->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "look-back self-test", __FILE__, __LINE__);
+  }
+  cudaFreeAsync(d, s);
+  *timed_out = (err & 2) ? 1 : 0;
+  return st;
 }
 
 }  // namespace mm

@@ -48,7 +48,7 @@ struct mm_hierarchy {
   float4* box = nullptr;             // [kMaxGatherBlocks] update-block boxes
   unsigned* arrive = nullptr;        // update epilogue arrival counter
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
-  int32_t* lsw = nullptr;            // [MM_MAX_LEVELS] sweeps per level
+  int32_t* lsw = nullptr;            // [2 MM_MAX_LEVELS] sweeps, last rel. change per level
   float* trace = nullptr;
   int trace_cap = 0;
   int level_cap = 0;
@@ -211,6 +211,10 @@ mm_status tree_error(mm_hierarchy* h, cudaStream_t s) {
   MM_CK(cudaStreamSynchronize(s));
   if (e) {
     cudaMemsetAsync(h->tree.err, 0, sizeof(int), s);
+    if (e & 2) {
+      set_error("a bounded device wait gave up (the sort's look-back)");
+      return MM_ERR_TIMEOUT;
+    }
     set_error("internal error: Barnes-Hut walk met an inconsistent tree");
     return MM_ERR_CUDA;
   }
@@ -728,8 +732,8 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->zero, sizeof(int32_t), s));
   MM_CK(cudaMemsetAsync(h->zero, 0, sizeof(int32_t), s));
-  MM_CK(cudaMallocAsync(&h->lsw, sizeof(int32_t) * MM_MAX_LEVELS, s));
-  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaMallocAsync(&h->lsw, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
   MM_CK(cudaStreamSynchronize(s));
   return MM_OK;
 }
@@ -1074,18 +1078,21 @@ mm_status layout_batch(mm_hierarchy* h, const mm_params& p, const float* x_init,
   for (mm_hierarchy* sub : h->subs) MM_TRY(ensure_trace(sub, p));
   if (!h->gexec || !same_schedule(h->gparams, p)) MM_TRY(build_graph_batch(h, p));
   for (mm_hierarchy* sub : h->subs)
-    MM_CK(cudaMemsetAsync(sub->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+    MM_CK(cudaMemsetAsync(sub->lsw, 0, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
   MM_CK(cudaGraphLaunch(h->gexec, s));
   const int64_t n = h->gptr.back();
   MM_CK(cudaMemcpyAsync(x_out, h->xcat, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
   const int G = (int)h->subs.size();
   std::vector<SweepState> hs(G);
-  std::vector<int32_t> lsw((size_t)G * MM_MAX_LEVELS);
+  // per graph: sweeps per level, then the bits of each level's last
+  // relative change (2 x MM_MAX_LEVELS words)
+  constexpr size_t kL = 2 * MM_MAX_LEVELS;
+  std::vector<int32_t> lsw((size_t)G * kL);
   for (int i = 0; i < G; ++i) {
     MM_CK(cudaMemcpyAsync(&hs[i], h->subs[i]->state, sizeof(SweepState), cudaMemcpyDeviceToHost,
                           s));
-    MM_CK(cudaMemcpyAsync(&lsw[(size_t)i * MM_MAX_LEVELS], h->subs[i]->lsw,
-                          sizeof(int32_t) * MM_MAX_LEVELS, cudaMemcpyDeviceToHost, s));
+    MM_CK(cudaMemcpyAsync(&lsw[(size_t)i * kL], h->subs[i]->lsw, sizeof(int32_t) * kL,
+                          cudaMemcpyDeviceToHost, s));
   }
   MM_CK(cudaStreamSynchronize(s));
   int64_t vu = 0, kl = h->batch_launches;
@@ -1095,7 +1102,7 @@ mm_status layout_batch(mm_hierarchy* h, const mm_params& p, const float* x_init,
     const int nl = (int)sub->levels.size();
     maxl = std::max(maxl, nl);
     for (int l = 0; l < nl; ++l) {
-      const int32_t sw = lsw[(size_t)i * MM_MAX_LEVELS + l];
+      const int32_t sw = lsw[(size_t)i * kL + l];
       vu += (int64_t)sw * sub->levels[l].n;
       tot += sw;
       if (!sub->levels[l].fused) {
@@ -1119,7 +1126,10 @@ mm_status layout_batch(mm_hierarchy* h, const mm_params& p, const float* x_init,
         const int r = nl - 1 - l;
         const int slot = maxl - 1 - r;
         stats->level_n[slot] += sub->levels[l].n;
-        stats->level_sweeps[slot] += lsw[(size_t)i * MM_MAX_LEVELS + l];
+        stats->level_sweeps[slot] += lsw[(size_t)i * kL + l];
+        float rel;
+        memcpy(&rel, &lsw[(size_t)i * kL + MM_MAX_LEVELS + l], sizeof(rel));
+        if (!(rel <= stats->level_rel_change[slot])) stats->level_rel_change[slot] = rel;
       }
     }
   }
@@ -1165,12 +1175,12 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     MM_TRY(build_graph(h, p, single));
   if (single)
     MM_CK(cudaMemcpyAsync(h->xb[0], x_init, sizeof(float2) * n0, cudaMemcpyDeviceToDevice, s));
-  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
   MM_CK(cudaGraphLaunch(h->gexec, s));
   XSel x{h->xb[0], h->xb[1], &h->state->parity};
   MM_TRY(copy_current(x, n0, (float2*)x_out, s));
   SweepState hs;
-  int32_t lsw[MM_MAX_LEVELS];
+  int32_t lsw[2 * MM_MAX_LEVELS];
   MM_CK(cudaMemcpyAsync(&hs, h->state, sizeof(hs), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaMemcpyAsync(lsw, h->lsw, sizeof(lsw), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
@@ -1181,6 +1191,7 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
     for (int i = 0; i < nl; ++i) {
       stats->level_n[i] = h->levels[i].n;
       stats->level_sweeps[i] = lsw[i];
+      memcpy(&stats->level_rel_change[i], &lsw[MM_MAX_LEVELS + i], sizeof(float));
       vu += (int64_t)lsw[i] * h->levels[i].n;
     }
     stats->total_sweeps = hs.total;
@@ -1406,6 +1417,25 @@ mm_status autotune(mm_hierarchy* h, const float* thetas, int n_theta, double dri
 }
 
 }  // namespace
+
+int num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 152;
+  }
+  v = std::min(v, kMaxSMs);
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 }  // namespace mm
 
 using namespace mm;
@@ -1456,6 +1486,23 @@ const char* mm_status_string(mm_status s) {
 }
 
 const char* mm_last_error(void) { return g_err.c_str(); }
+
+
+mm_status mm_selftest_wait_timeout(int32_t spin_limit, void* stream) {
+  g_err.clear();
+  if (spin_limit < 1 || spin_limit > (1 << 22)) {
+    set_error("spin_limit must be in [1, 2^22], got %d", spin_limit);
+    return MM_ERR_INVALID_ARG;
+  }
+  int timed_out = 0;
+  MM_TRY(lookback_selftest(spin_limit, &timed_out, (cudaStream_t)stream));
+  if (!timed_out) {
+    set_error("the look-back wait on a status word that nothing publishes did not give up");
+    return MM_OK;
+  }
+  set_error("a bounded device wait gave up (the sort's look-back), as the self-test intends");
+  return MM_ERR_TIMEOUT;
+}
 
 mm_status mm_build_hierarchy(const mm_graph* g, const mm_params* p, void* stream,
                              mm_hierarchy** out) {
@@ -2019,7 +2066,7 @@ mm_status mm_layout_levels(mm_hierarchy* h, const mm_params* p, float* const* le
     h->gexec = nullptr;
   }
   MM_TRY(build_graph(h, q, false, level_x));
-  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * MM_MAX_LEVELS, s));
+  MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
   MM_CK(cudaGraphLaunch(h->gexec, s));
   MM_CK(cudaStreamSynchronize(s));
   // the recording graph is not kept: the next mm_layout builds its own

@@ -28,7 +28,13 @@ mm_status cuda_status(cudaError_t e, const char* what, const char* file, int lin
     if (s_ != MM_OK) return s_;           \
   } while (0)
 
-constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+// Capacity bound for buffers sized by the SM count (per-block partials);
+// grids are sized by num_sms(), the device's own count (152 on GB300: two
+// dies of 76 SMs), clamped to this bound.
+constexpr int kMaxSMs = 256;
+// Multiprocessor count of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device).
+int num_sms();
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -160,7 +166,12 @@ __device__ __forceinline__ bool schedule_step(SweepState* st, const SchedParams&
     st->done = 1;
   }
   if (st->level_sweeps >= sp.level_cap) st->done = 1;
-  if (level_sweeps_out) *level_sweeps_out = st->level_sweeps;
+  if (level_sweeps_out) {
+    // [0, MM_MAX_LEVELS): sweeps per level; the next MM_MAX_LEVELS words
+    // hold the FP32 relative change of each level's latest sweep
+    *level_sweeps_out = st->level_sweeps;
+    level_sweeps_out[MM_MAX_LEVELS] = __float_as_int((float)rel);
+  }
   return st->done != 0;
 }
 
@@ -221,7 +232,7 @@ constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kSortMinTile = kSortThreads;
 inline int sort_ipt(int64_t n) {
   for (int ipt = kSortIPT; ipt > 1; ipt >>= 1)
-    if (ceil_div(n, (int64_t)kSortThreads * ipt) >= kSMs) return ipt;
+    if (ceil_div(n, (int64_t)kSortThreads * ipt) >= num_sms()) return ipt;
   return 1;
 }
 
@@ -334,6 +345,9 @@ constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
 inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
 // Tiled exact sum F[v] = sum_{u != v} r(v, u).
 mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
+// One block of the sort pass waits on a status word that nothing publishes;
+// *timed_out = 1 when the bounded wait gave up (error bit 2) as it must.
+mm_status lookback_selftest(int spin_limit, int* timed_out, cudaStream_t s);
 
 // ------------------------------------------------------ Eq. 3 (MulMent_h) --
 // Builds L's map to level min(level + h, top) and its member groups.
@@ -352,8 +366,8 @@ constexpr int kFullStressMaxN = 1 << 17;
 
 // ---------------------------------------------------------------- sweep --
 constexpr int kGatherThreads = 256;
-constexpr int kMaxLightBlocks = kSMs * 16;
-constexpr int kMaxHeavyBlocks = kSMs * 8;
+constexpr int kMaxLightBlocks = kMaxSMs * 16;  // buffer bounds; grids use num_sms()
+constexpr int kMaxHeavyBlocks = kMaxSMs * 8;
 // Upper bound of gather_blocks() for any lanes setting (partials sizing).
 constexpr int kMaxGatherBlocks = kMaxLightBlocks + kMaxHeavyBlocks;
 int gather_blocks(const Level& L);

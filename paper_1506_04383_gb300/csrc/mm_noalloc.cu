@@ -18,8 +18,17 @@
 // __device__ array is only a host stand-in, not a usable device pointer).
 // Make that first call before any stream capture.
 //
+// Every call synchronises the stream before it returns (it reads the walk's
+// error flag back to the host).
+//
 // Sharing: every call uses the same array and it keeps the previous call's
 // contents; the walk's error flag is cleared at the start of each call.
+// The sort's look-back status words rely on the zero fill at module load:
+// they are tagged with a build epoch that starts at 0 and that every call
+// advances, so no word left by an earlier call (or the initial zeros) can be
+// taken for one of the current call.  Node records of an earlier, larger
+// call stay in the array; the walk never reads past the current call's
+// 2n - 1 records.
 // Calls whose GPU work overlaps (different streams, different host threads)
 // race on the array and must be serialised by the caller.
 #include <cuda_runtime.h>
@@ -67,7 +76,7 @@ constexpr Carve carve() {
   c.counters = o; o += up(4 * 4);
   c.nodeA = o; o += up(16 * 2 * N);
   c.nodeB = o; o += up(16 * 2 * N);
-  c.partials = o; o += up(16 * 2 * kSMs);
+  c.partials = o; o += up(16 * 2 * kMaxSMs);
   c.root = o; o += up(16);
   c.ticket = o; o += up(8);
   c.err = o; o += up(4);
@@ -126,6 +135,22 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
               kNoAllocMaxN);
     return MM_ERR_INVALID_ARG;
   }
+  // x and F_out must be device memory of the current device: that is the
+  // device whose copy of the array is resolved below and used by the kernels
+  int dev = 0;
+  MM_CK(cudaGetDevice(&dev));
+  const void* ptrs[2] = {x, F_out};
+  for (const void* q : ptrs) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        at.device != dev) {
+      cudaGetLastError();
+      set_error("mm_repulsion_noalloc: x and F_out must be device memory of the current "
+                "device (%d)", dev);
+      return MM_ERR_INVALID_ARG;
+    }
+  }
   void* base = nullptr;
   MM_TRY(scratch_address(&base));
   cudaStream_t s = (cudaStream_t)stream;
@@ -171,6 +196,10 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   int err = 0;
   MM_CK(cudaMemcpyAsync(&err, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   MM_CK(cudaStreamSynchronize(s));
+  if (err & 2) {
+    set_error("a bounded device wait gave up (the sort's look-back)");
+    return MM_ERR_TIMEOUT;
+  }
   if (err) {
     set_error("internal error: Barnes-Hut walk met an inconsistent tree");
     return MM_ERR_CUDA;

@@ -31,7 +31,8 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_contract", "mm_prolong", "mm_layout_host", "mm_repulsion_noalloc",
            "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
-           "mm_layout_levels", "mm_repulsion_h", "mm_full_stress"]
+           "mm_layout_levels", "mm_repulsion_h", "mm_full_stress",
+           "mm_selftest_wait_timeout", "mm_measure_fp32_peak"]
 MM_NET_PARAMS = 17860
 
 
@@ -94,7 +95,8 @@ class LayoutStats(ctypes.Structure):
                 ("level_n", ctypes.c_int32 * MM_MAX_LEVELS),
                 ("level_sweeps", ctypes.c_int32 * MM_MAX_LEVELS),
                 ("final_alpha", ctypes.c_double), ("final_rel_change", ctypes.c_double),
-                ("final_stress", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("final_stress", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("level_rel_change", ctypes.c_float * MM_MAX_LEVELS)]
 
     def as_dict(self):
         nl = self.num_levels
@@ -102,7 +104,8 @@ class LayoutStats(ctypes.Structure):
                     vertex_updates=int(self.vertex_updates),
                     level_n=list(self.level_n[:nl]), level_sweeps=list(self.level_sweeps[:nl]),
                     final_alpha=self.final_alpha, final_rel_change=self.final_rel_change,
-                    final_stress=self.final_stress, kernel_launches=int(self.kernel_launches))
+                    final_stress=self.final_stress, kernel_launches=int(self.kernel_launches),
+                    level_rel_change=[float(v) for v in self.level_rel_change[:nl]])
 
 
 _lib = None
@@ -155,6 +158,8 @@ def load(path: str = LIB_PATH):
     lib.mm_layout_levels.argtypes = [P, P, P, P]
     lib.mm_repulsion_h.argtypes = [P, i32, P, P, P]
     lib.mm_full_stress.argtypes = [P, P, P, P]
+    lib.mm_selftest_wait_timeout.argtypes = [i32, P]
+    lib.mm_measure_fp32_peak.argtypes = [i32, P, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -345,15 +350,44 @@ def full_stress(h: Hierarchy, x, stream=None):
 def repulsion_noalloc(x, theta: float, F_out=None, stream=None):
     """Barnes-Hut F for up to 32768 points with the library's fixed static
     scratch (the call allocates no device memory itself; the output buffer
-    is the caller's).  Calls that overlap on the GPU race on the shared
+    is the caller's).  x is a contiguous float32 [n, 2] CUDA tensor; F_out,
+    if given, a float32 [n, 2] CUDA tensor on the same device.  The call runs
+    on x's device.  Calls that overlap on the GPU race on the shared
     scratch."""
     _require_cuda()
     x = _dev(x, torch.float32, "x")
+    if x.dim() != 2 or x.shape[1] != 2:
+        raise ValueError(f"x must have shape [n, 2], got {tuple(x.shape)}")
     if F_out is None:
         F_out = torch.empty_like(x)
-    _check(load().mm_repulsion_noalloc(x.shape[0], _ptr(x), float(theta), _ptr(F_out),
-                                       _stream(stream)))
+    F_out = _dev(F_out, torch.float32, "F_out")
+    if F_out.shape != x.shape:
+        raise ValueError(f"F_out must have shape {tuple(x.shape)}, got {tuple(F_out.shape)}")
+    if F_out.device != x.device:
+        raise ValueError(f"F_out is on {F_out.device}, x on {x.device}")
+    with torch.cuda.device(x.device):
+        _check(load().mm_repulsion_noalloc(x.shape[0], _ptr(x), float(theta), _ptr(F_out),
+                                           _stream(stream)))
     return F_out
+
+
+def measure_fp32_peak(reps: int = 20, stream=None):
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms per
+    launch)."""
+    _require_cuda()
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().mm_measure_fp32_peak(int(reps), ctypes.byref(t), ctypes.byref(ms),
+                                       _stream(stream)))
+    return t.value, ms.value
+
+
+def selftest_wait_timeout(spin_limit: int = 4096, stream=None) -> int:
+    """Runs the library's self-test of its bounded device waits: a look-back
+    wait on a status word that nothing writes must give up after spin_limit
+    polls.  Returns the raw status (MM_ERR_TIMEOUT = the wait gave up, as
+    intended; MM_OK = it did not)."""
+    _require_cuda()
+    return int(load().mm_selftest_wait_timeout(int(spin_limit), _stream(stream)))
 
 
 def layout(h: Hierarchy, params: Params = None, x_init=None, x_out=None, stream=None):

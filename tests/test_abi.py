@@ -60,8 +60,9 @@ def test_struct_layout_matches_c(tmp_path):
           printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mm_params), offsetof(mm_params, alpha0),
                  offsetof(mm_params, seed), offsetof(mm_params, traverse_warps),
                  sizeof(mm_graph), offsetof(mm_graph, graph_ptr));
-          printf("%zu %zu %zu\\n", sizeof(mm_layout_stats),
-                 offsetof(mm_layout_stats, level_sweeps), offsetof(mm_layout_stats, final_stress));
+          printf("%zu %zu %zu %zu\\n", sizeof(mm_layout_stats),
+                 offsetof(mm_layout_stats, level_sweeps), offsetof(mm_layout_stats, final_stress),
+                 offsetof(mm_layout_stats, level_rel_change));
           printf("%zu %zu %zu %zu %zu\\n", sizeof(mm_prolong_sample),
                  offsetof(mm_prolong_sample, n_coarse), offsetof(mm_prolong_sample, seed),
                  offsetof(mm_prolong_sample, level), offsetof(mm_prolong_sample, x_target));
@@ -80,7 +81,7 @@ def test_struct_layout_matches_c(tmp_path):
                                            P.traverse_warps.offset, ctypes.sizeof(G),
                                            G.graph_ptr.offset]
     assert [int(t) for t in b.split()] == [ctypes.sizeof(S), S.level_sweeps.offset,
-                                           S.final_stress.offset]
+                                           S.final_stress.offset, S.level_rel_change.offset]
     Q = mm.ProlongSample
     assert [int(t) for t in c.split()] == [ctypes.sizeof(Q), Q.n_coarse.offset, Q.seed.offset,
                                            Q.level.offset, Q.x_target.offset]
