@@ -11,10 +11,18 @@ controller), with the hierarchy already built and resident in HBM.
            (host CSR in, host layout out: H2D copy, hierarchy build, layout,
            D2H copy all inside the timed region)
 
-Default workload: random geometric graph, 100,000 points uniform in the unit
-square, radius tuned for mean degree 8, largest component, k = 2,
-theta = 0.5, coarsening to <= 100 vertices.  L2 (129 MB) is flushed by a
-256 MB write before every timed step.
+Default workload: Delaunay triangulation of 2^20 uniform points in the unit
+square (the paper's del20 family; n = 1,048,576, m = 3,145,684), k = 1,
+Barnes-Hut theta = 0.6, coarsening to <= 100 vertices; R-MAT scale 20 is
+timed the same way as a second table (second_workloads).  L2 (129 MB) is
+flushed by a 256 MB write before every timed step.
+
+Beside the timed number, outside the timed region: the final objective
+against the FP64 oracle's layout of the same graph (objective_vs_oracle: on
+the oracle's own hierarchy and on the GPU's; M estimated the same way for
+both), the exact O(n^2) objective against the oracle's sampled estimate, a
+level-by-level breakdown of the layout time with time-weighted rooflines,
+and the measured FP32 FMA peak used as the ALU roofline's denominator.
 
 Multi-GPU (torchrun, N > 1): replicas only -- every rank lays out its own
 copy; value = all ranks' vertex updates / max rank time.
@@ -52,7 +60,9 @@ WORKLOADS = {
                    desc="R-MAT scale 20 (a=0.57 b=c=0.19), 8 edge samples per vertex, largest "
                         "component, k=1, theta=0.6"),
     "del20": dict(kind="delaunay", n=1 << 20, seed=1506, k=1, theta=0.6, coarsest_n=100,
-                  desc="Delaunay triangulation of 2^20 uniform points, k=1, theta=0.6"),
+                  also=("rmat20",),
+                  desc="Delaunay triangulation of 2^20 uniform points (the paper's del20 "
+                       "family), k=1, Barnes-Hut theta=0.6, coarsen to <=100"),
     "learned2m": dict(kind="rgg", n=2000000, deg=8.0, seed=2027, k=2, theta=0.5, coarsest_n=100,
                       learned=True,
                       desc="learned prolongation: network trained on coarse-to-converged pairs of "
@@ -356,7 +366,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rgg100k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="del20", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -472,15 +482,37 @@ def main():
     if gp is not None:
         batch_cmp = compare_batch(mm, made[3], p, args.batch_compare)
 
-    # roofline of the dominant kernel on the finest level, live with events
+    # warm hierarchy builds (the first build above also pays for the
+    # stream-ordered pool's growth and first-touch costs)
+    builds = []
+    for _ in range(3 if gp is None else 1):
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        hw = mm.build_hierarchy(drp, dcol, p, graph_ptr=gp)
+        b1.record()
+        torch.cuda.synchronize()
+        builds.append(b0.elapsed_time(b1))
+        del hw
+    build_warm_ms = statistics.median(builds)
+
+    # roofline of the dominant kernel on the finest level, live with events;
+    # the ALU peak is this device's measured FP32 FMA rate
     peaks, src = measured_peaks()
     clk_sum = clk.summary()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_tf, fp32_ms = mm.measure_fp32_peak(20)
+    fp32 = (fp32_tf, f"measured FP32 FMA peak of this device ({sms} SMs): {fp32_tf:.2f} TFLOP/s "
+                     f"(mm_measure_fp32_peak, {fp32_ms:.2f} ms per launch)")
+    breakdown = None
     if w.get("approx"):
-        roof = roofline_h(mm, h, xbuf, int(w["approx"]), peaks, src, clk_sum)
+        roof = roofline_h(mm, h, xbuf, int(w["approx"]), peaks, src, clk_sum, fp32=fp32)
     elif gp is None:
         prof = mm.sweep_profile(h, 0, xbuf, reps=10)
         roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")),
-                        workload=args.workload)
+                        workload=args.workload, fp32=fp32)
+        if not w.get("single"):
+            breakdown = layout_breakdown(mm, h, p, stats[-1], peaks, src, fp32_tf)
     else:
         big = int(np.argmax(np.diff(gp)))
         grp, gcol = made[3][big]
@@ -488,8 +520,9 @@ def main():
                                 mm.default_params(**dict(kw, seed=int(kw.get("seed", 1506)))))
         xb, _ = mm.layout(hb)
         prof = mm.sweep_profile(hb, 0, xb, reps=10)
-        roof = roofline(prof, peaks, src, clk_sum, len(grp) - 1)
+        roof = roofline(prof, peaks, src, clk_sum, len(grp) - 1, fp32=fp32)
         roof["graph"] = f"largest graph of the batch (n={len(grp) - 1})"
+    roof["sms"] = sms
 
     # end to end through the host API (pinned host buffers)
     e2e = None
@@ -516,6 +549,13 @@ def main():
 
     htab = h_table(mm, drp, dcol, w, kw) if w.get("hsweep") else None
 
+    # the final objective against the oracle's layout of the same graph
+    ovo = None
+    if rank == 0 and gp is None and not w.get("dynamic") and not w.get("learned"):
+        ovo = objective_vs_oracle(mm, args.workload, rp, col, kw, xbuf, M)
+    # the other workloads of the same configuration family
+    sides = [side_table(mm, o) for o in w.get("also", ())] if rank == 0 else []
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample, el = cpu_baseline(w, rp, col, budget_s=args.cpu_budget)
@@ -533,11 +573,17 @@ def main():
                        "level_n": stats[-1]["level_n"],
                        "sweeps": stats[-1]["total_sweeps"],
                        "level_sweeps": stats[-1]["level_sweeps"],
+                       "level_rel_change": [round(v, 6) for v in stats[-1]["level_rel_change"]],
+                       "max_iters_at_min": int(p.max_iters_at_min), "eps_final": p.eps_final,
                        "vertex_updates_per_step": vu, "l2": "flushed (256 MB write) before "
                        "every timed step", "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "time_to_layout_s": (build_ms + statistics.mean(step_ms)) / 1e3,
-            "hierarchy_build_ms": build_ms,
+            "time_to_layout_s": (build_warm_ms + statistics.mean(step_ms)) / 1e3,
+            "hierarchy_build_ms": build_warm_ms,
+            "hierarchy_build_cold_ms": build_ms,
             "objective_M": M,
+            "objective_vs_oracle": ovo,
+            "second_workloads": sides or None,
+            "layout_breakdown": breakdown,
             "batch_vs_plain": batch_cmp,
             "learned_vs_plain": learned_cmp,
             "h_table": htab,
@@ -621,9 +667,18 @@ def ctypes_copy(dst, src):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# ncu capture of the kernel on level 0 of the workload.  Re-capture and
-# update (or drop) whenever the kernel changes.
-NCU_TRAFFIC = {"rgg100k": {"traverse": 3.834624e6, "gather": 19.096576e6}}
+# ncu capture of the kernel on level 0 of the workload, with the source file
+# of the kernel and its SHA-256 prefix at capture time: reported only while
+# that source is unchanged (null otherwise).
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(workload, kernel):
+    e = NCU_TRAFFIC.get((workload, kernel))
+    if not e:
+        return None
+    nbytes, rel, sha = e
+    return nbytes if _src_sha(rel) == sha else None
 
 
 def h_table(mm, drp, dcol, w, kw, reps=2):
@@ -725,7 +780,7 @@ def dyn_table(mm, rpG, colG, w, reps=2):
     return rows
 
 
-def roofline_h(mm, h, x, hh, peaks, src, clk, reps=10):
+def roofline_h(mm, h, x, hh, peaks, src, clk, reps=10, fp32=None):
     """The Eq. 3 sums on the finest level (mm_repulsion_h: midpoints, then one
     thread per vertex over all other representatives and its own group):
     FP32-ALU bound, 10 FP32 ops per pair term, n (n' - 1) far terms plus
@@ -751,16 +806,15 @@ def roofline_h(mm, h, x, hh, peaks, src, clk, reps=10):
         evs.append((a, b))
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / reps
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    peak, note = fp32
     ach = 10.0 * terms / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_source": src, "kernel": "approx_force",
-            "note": f"peak = 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz; {nt} representatives, "
+            "traffic": None, "peak_source": "measured", "kernel": "approx_force",
+            "note": f"{note}; {nt} representatives, "
                     f"{terms:.4g} pair terms per call, {ms * 1e3:.1f} us per call"}
 
 
-def roofline(prof, peaks, src, clk, n, exact=False, workload=None):
+def roofline(prof, peaks, src, clk, n, exact=False, workload=None, fp32=None):
     """Dominant kernel of a finest-level sweep against its roofline.
 
     traverse (Barnes-Hut walk): ALU bound; algorithmic work = 10 FP32 ops per
@@ -774,28 +828,26 @@ def roofline(prof, peaks, src, clk, n, exact=False, workload=None):
     st = prof["stage_ms"]
     names = prof["stage_names"]
     dom = max(range(len(st)), key=lambda i: st[i])
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    alu_peak, alu_note = fp32
     hbm = peaks.get("hbm_gbs", 6800.0)
     nnzS = prof["nnz_S"]
     kern = {}
     t_trav = max(st[names.index("traverse")], 1e-9) / 1e3
     flops = 10.0 * (n * (n - 1) if exact else prof["interactions"])
     kern["traverse"] = {"bound": "alu", "achieved": flops / t_trav / 1e12, "peak": alu_peak,
-                        "unit": "TFLOP/s", "traffic": None,
-                        "note": f"peak = 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"}
+                        "unit": "TFLOP/s", "traffic": None, "note": alu_note}
     t_g = st[names.index("gather")] / 1e3
     gbytes = n * 32.0 + nnzS * 8.0
     kern["gather"] = {"bound": "hbm", "achieved": gbytes / t_g / 1e9, "peak": hbm, "unit": "GB/s",
                       "traffic": None}
     t_s = st[names.index("sort")] / 1e3
-    sbytes = 4 * 16.0 * n
+    sbytes = 3 * 16.0 * n  # three 8-bit passes over 24-bit keys (group walk)
     kern["sort"] = {"bound": "hbm", "achieved": sbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "traffic": None}
     for name_, v in kern.items():
         v["frac"] = v["achieved"] / v["peak"]
-        v["peak_source"] = src
-        v["traffic"] = NCU_TRAFFIC.get(workload, {}).get(name_)
+        v["peak_source"] = "measured" if v["bound"] == "alu" else src
+        v["traffic"] = ncu_traffic(workload, name_)
     name = names[dom]
     out = dict(kern.get(name, kern["traverse"]))
     out["kernel"] = name if name in kern else "traverse"
@@ -804,6 +856,176 @@ def roofline(prof, peaks, src, clk, n, exact=False, workload=None):
                                                                    "frac", "bound", "traffic")}
                      for k, v in kern.items() if k != out["kernel"]}
     return out
+
+
+def oracle_golden():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_layouts.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def objective_vs_oracle(mm, wname, rp, col, kw, x_own, M_exact):
+    """Final maxent-stress (Eq. 1 at alpha = 0.008) of the GPU's layouts
+    against the FP64 oracle's layout of the same graph (Sec. 3 algorithm on
+    the oracle's own hierarchy, stored by tests/golden/make_oracle_layouts.py).
+    Every M here is the oracle's estimator: exact stress over S, ln-sum over
+    the pairs outside S from the same 2e7 random pairs (common pairs, so the
+    gaps carry far less noise than either standard error).
+      same_hierarchy: the oracle's coarsening fed to the GPU, GPU layout;
+      own_hierarchy: the GPU's own coarsening (the timed layout);
+      exact_vs_sampled: the GPU's exact O(n^2) M of the timed layout against
+        the sampled estimate of the same layout, in standard errors."""
+    import numpy as np
+    import torch
+
+    import oracle
+    g = oracle_golden().get(wname)
+    if g is None:
+        return None
+    t0 = time.perf_counter()
+    po = oracle.params(**g["params"])
+    levels = oracle.build_hierarchy(rp, col, po)
+    if [int(L["n"]) for L in levels] != g["level_n"]:
+        return {"error": "the oracle's hierarchy differs from the stored one",
+                "level_n": [int(L["n"]) for L in levels], "stored_level_n": g["level_n"]}
+    dev = []
+    for L in levels:
+        d = dict(row_ptr=torch.from_numpy(L["rp"]).cuda(), col=torch.from_numpy(L["col"]).cuda(),
+                 omega=torch.from_numpy(L["ew"].astype(np.float32)).cuda(),
+                 c=torch.from_numpy(L["c"].astype(np.float32)).cuda())
+        if L["map"] is not None:
+            d["map"] = torch.from_numpy(L["map"]).cuda()
+        dev.append(d)
+    hs = mm.build_hierarchy_levels(dev, mm.default_params(**kw))
+    xs, sts = mm.layout(hs)
+    S = levels[0]["S"]
+
+    def est(x):
+        return oracle.objective_sampled(x.cpu().numpy().astype(np.float64), S, 0.008,
+                                        samples=g["samples"], seed=g["sample_seed"])
+    e_same, e_own = est(xs), est(x_own)
+    Mo = g["M"]
+    out = {
+        "estimator": f"exact stress over S + ln-sum over {g['samples']:.0e} random pairs "
+                     f"(seed {g['sample_seed']}), alpha = 0.008",
+        "oracle_M": Mo, "oracle_se_M": g["se_M"], "oracle_level_sweeps": g["level_sweeps"],
+        "same_hierarchy": {"M": e_same["M"], "rel_gap": (e_same["M"] - Mo) / abs(Mo),
+                           "level_sweeps": sts["level_sweeps"],
+                           "within_1pct": abs(e_same["M"] - Mo) <= 0.01 * abs(Mo)},
+        "own_hierarchy": {"M": e_own["M"], "rel_gap": (e_own["M"] - Mo) / abs(Mo),
+                          "within_1pct": abs(e_own["M"] - Mo) <= 0.01 * abs(Mo)},
+        "seconds": None,
+    }
+    if M_exact is not None:
+        out["exact_vs_sampled"] = {"M_exact_gpu": M_exact, "M_sampled": e_own["M"],
+                                   "se_M": e_own["se_M"],
+                                   "z": (M_exact - e_own["M"]) / max(e_own["se_M"], 1e-300)}
+    out["seconds"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+def layout_breakdown(mm, h, p, stats, peaks, src, fp32_peak, reps=5):
+    """Where a layout's time goes, level by level: mm_sweep_profile stage
+    times of every multi-kernel level (from that level's own final layout)
+    times its sweep count; fused levels (one launch each) are the remainder
+    of the measured layout time.  Per kernel class the time-weighted share
+    and, for the walk, the gather and the sort, their achieved rate summed
+    over all levels against the roofline (same algorithmic work per unit as
+    the finest-level roofline)."""
+    xs = mm.layout_levels(h, p)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    cls = {"walk": 0.0, "sort+keys": 0.0, "tree": 0.0, "gather": 0.0, "other": 0.0}
+    work = {"walk_flops": 0.0, "gather_bytes": 0.0, "sort_bytes": 0.0}
+    rows = []
+    for l in range(stats["num_levels"]):
+        n, sw = stats["level_n"][l], stats["level_sweeps"][l]
+        if n <= 2048 or sw == 0:
+            rows.append({"level": l, "n": n, "sweeps": sw, "fused": True})
+            continue
+        pr = mm.sweep_profile(h, l, xs[l], reps=reps)
+        st = dict(zip(pr["stage_names"], pr["stage_ms"]))
+        cls["walk"] += sw * st["traverse"]
+        cls["sort+keys"] += sw * (st["morton_hist"] + st["sort"])
+        cls["tree"] += sw * (st["radix_tree_scan"] + st["records"])
+        cls["gather"] += sw * st["gather"]
+        cls["other"] += sw * (st["bbox"] + st["controller"])
+        work["walk_flops"] += sw * 10.0 * pr["interactions"]
+        work["gather_bytes"] += sw * (32.0 * n + 8.0 * pr["nnz_S"])
+        work["sort_bytes"] += sw * 4 * 16.0 * n
+        rows.append({"level": l, "n": n, "sweeps": sw, "ms_per_sweep": round(sum(st.values()), 4),
+                     "walk_ms": round(st["traverse"], 4), "gather_ms": round(st["gather"], 4),
+                     "sort_ms": round(st["morton_hist"] + st["sort"], 4),
+                     "interactions_per_vertex": round(pr["interactions"] / n, 1)})
+    tot = sum(cls.values())
+    out = {"levels": rows, "class_ms": {k: round(v, 3) for k, v in cls.items()},
+           "class_share_of_multikernel_time": {k: round(v / tot, 4) for k, v in cls.items()}
+           if tot > 0 else None,
+           "note": "stage times from one-by-one profiled sweeps (events between stages); "
+                   "inside the layout's CUDA graph the same kernels run back to back"}
+    if cls["walk"] > 0:
+        a = work["walk_flops"] / (cls["walk"] / 1e3) / 1e12
+        out["walk_roofline"] = {"bound": "alu", "achieved": a, "peak": fp32_peak,
+                                "unit": "TFLOP/s", "frac": a / fp32_peak, "peak_source": "measured"}
+    if cls["gather"] > 0:
+        a = work["gather_bytes"] / (cls["gather"] / 1e3) / 1e9
+        out["gather_roofline"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                                  "frac": a / hbm, "peak_source": src}
+    if cls["sort+keys"] > 0:
+        a = work["sort_bytes"] / (cls["sort+keys"] / 1e3) / 1e9
+        out["sort_roofline"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                                "frac": a / hbm, "peak_source": src}
+    return out
+
+
+def side_table(mm, wname):
+    """A second workload timed the same way as the headline (inputs resident,
+    L2 flushed, CUDA events): layout time, vertex-updates/s, warm hierarchy
+    build and time to layout."""
+    import torch
+    w = WORKLOADS[wname]
+    rp, col = make_graph(w)[:2]
+    kw = params_of(mm, w)
+    p = mm.default_params(**kw)
+    drp, dcol = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
+    h = mm.build_hierarchy(drp, dcol, p)
+    builds = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = mm.build_hierarchy(drp, dcol, p)
+        torch.cuda.synchronize()
+        builds.append((time.perf_counter() - t0) * 1e3)
+        del hh
+    x, st = mm.layout(h, p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    for _ in range(5):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record()
+        x, st = mm.layout(h, p, x_out=x)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    lay = statistics.median(ms)
+    bms = statistics.median(builds)
+    return {"workload": wname, "desc": w["desc"], "n": len(rp) - 1, "m": int(len(col) // 2),
+            "levels": st["num_levels"], "level_n": st["level_n"],
+            "level_sweeps": st["level_sweeps"],
+            "level_rel_change": [round(v, 6) for v in st["level_rel_change"]],
+            "layout_ms": lay, "value": st["vertex_updates"] / (lay / 1e3), "unit": UNIT,
+            "hierarchy_build_ms": bms, "time_to_layout_s": (bms + lay) / 1e3}
+
+
+# Source files whose kernels the stored ncu DRAM figures describe, with the
+# SHA-256 prefix of the file when the capture was taken: a figure is reported
+# only while its kernel's source is unchanged.
+def _src_sha(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 if __name__ == "__main__":

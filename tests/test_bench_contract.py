@@ -53,14 +53,26 @@ def test_roofline_of_the_dominant_kernel():
     ms = [0.008, 0.008, 0.046, 0.018, 0.012, 0.110, 0.021, 0.008]
     prof = {"stage_names": names, "stage_ms": ms, "nnz_S": 2_000_000, "interactions": 4.0e7}
     peaks = {"hbm_gbs": 6784.5, "sm_max_mhz": 2070.0}
-    r = bench.roofline(prof, peaks, "measured", {}, 100_000, workload="rgg100k")
+    fp32 = (72.5, "measured")
+    r = bench.roofline(prof, peaks, "measured", {}, 100_000, workload="rgg100k", fp32=fp32)
     assert r["kernel"] == "traverse" and r["bound"] == "alu"
     assert abs(r["achieved"] - 10 * 4.0e7 / 110e-6 / 1e12) < 1e-9
-    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    assert r["peak"] == 72.5 and r["peak_source"] == "measured"
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert r["traffic"] == bench.NCU_TRAFFIC["rgg100k"]["traverse"]
+    assert r["traffic"] is None   # no capture of the current kernel stored
     g = r["others"]["gather"]
     assert g["bound"] == "hbm" and abs(g["achieved"] - (100_000 * 32 + 2_000_000 * 8) / 21e-6 / 1e9) < 1e-6
     # an exact-repulsion level counts n (n - 1) pair interactions
-    r2 = bench.roofline(prof, peaks, "measured", {}, 1024, exact=True)
+    r2 = bench.roofline(prof, peaks, "measured", {}, 1024, exact=True, fp32=fp32)
     assert abs(r2["achieved"] - 10 * 1024 * 1023 / 110e-6 / 1e12) < 1e-9
+
+
+def test_stored_traffic_is_dropped_once_its_kernel_source_changes(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    rel = "paper_1506_04383_gb300/csrc/k_tree.cu"
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("w", "traverse"), (123.0, rel, bench._src_sha(rel)))
+    assert bench.ncu_traffic("w", "traverse") == 123.0
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("w", "traverse"), (123.0, rel, "0" * 16))
+    assert bench.ncu_traffic("w", "traverse") is None
+    assert bench.ncu_traffic("other", "traverse") is None
