@@ -22,12 +22,23 @@ Pins (tests under ``tests/test_oracle_*.py``, all CPU):
     2-D multipole remainder bound for far clusters.
   * ``objective`` against closed forms for K2 and for a regular polygon (the
     product identity prod_j 2 sin(pi j / n) = n).
-  * ``sclap`` by invariants (partition, size bound U) and order-free cases
-    (perfect matching, star).
+  * ``sclap`` by invariants (partition, size bound U), order-free cases
+    (perfect matching, star), hand-worked rounds with the visiting order
+    passed in (strongest connection rather than most neighbours or first
+    neighbour, both tie rules, the inclusive overload bound that forces the
+    second-best cluster) and local optimality of converged labels on a
+    weighted random graph.
+  * ``build_hierarchy``'s schedule (W = min(b^(h+1), |V|/f), U, f := 0.7 f
+    after a shrink of at most 10 %, discarded empty contractions) level by
+    level against a hand-worked star.
   * ``contract`` against a hand-worked example and invariants.
-  * ``prolong`` by its radius bound and distribution moments.
-Multilevel ``layout`` composes pinned steps; its end-to-end result has no
-closed form ("parity unpinned" beyond the pinned steps).
+  * ``prolong`` and ``place_coarsest`` by their radius bounds and
+    distribution moments; two coarsest vertices at their target distance.
+  * ``objective_sampled`` (the ln-sum outside S from random pairs) against
+    the polygon closed form and the exact sum, within its standard error.
+Multilevel ``layout`` composes pinned steps; beyond that its end-to-end
+result is pinned by closed-form final layouts of small graphs (complete
+graphs, cycles, a path).
 """
 from __future__ import annotations
 

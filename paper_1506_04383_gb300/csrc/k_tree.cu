@@ -606,20 +606,6 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
 
 constexpr int kSeedPoints = 256;  // a seed subtree holds at most this many points
 
-// Group acceptance: the 32 Morton-consecutive points of a task walk
-// together and accept a cell only when every one of them passes the
-// per-point test (w / |x_u - c| < theta, u not inside).  A per-point
-// accepted cell is then either accepted too or opened into children, so each
-// point's sum refines its per-point Barnes-Hut sum and the error is at most
-// the per-point walk's.  The walk is uniform across the warp: one vote per
-// cell, no wait markers, no divergent control flow.
-//
-// W warps share one task (a block holds tpb tasks).  The task's first warp
-// walks the tree; an opened cell of at most `seed` points is not entered but
-// recorded as a seed (up to kSeedMax), and the seeds' subtrees are then
-// walked by the task's W warps, seed j by warp j mod W.  Every cell gets the
-// same decision as in a single walk; the W partial sums are added in warp
-// order, so results are reproducible.  W = 1 is the plain single-warp walk.
 constexpr int kSeedMax = 128;
 constexpr int kGroupMaxWarps = 16;  // warps per block
 
@@ -629,86 +615,158 @@ struct GroupShared {
   float2 part[kGroupMaxWarps][32];      // per warp
 };
 
+// Packed FP32 pairs (fma.rn.f32x2 and friends, native on sm_100 and later:
+// one instruction for both lanes of a float2).  Positions, offsets and the
+// force accumulator are (x, y) pairs, so one packed operation does the work
+// of two scalar ones.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Approximate reciprocal (the PTX rcp.approx instruction: one special-
+// function-unit operation, relative error below 2^-22); q > 0 here.
+__device__ __forceinline__ float rcp_approx(float q) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+  return r;
+}
+
+// Group acceptance: the 32 Morton-consecutive points of a task walk the
+// tree together (pre-order over first-child / escape links) and accept a
+// cell only when every one of them passes the per-point test (w / |x_u - c|
+// < theta, u not inside); a per-point accepted cell is then accepted too or
+// opened into children, so each point's sum refines its per-point
+// Barnes-Hut sum.  The walk is uniform across the warp: one vote per cell.
+// W warps may share a task (small levels): the first warp records opened
+// cells of at most `seed` points as seeds (up to kSeedMax) instead of
+// entering them, the task's W warps then walk the seed subtrees (seed j by
+// warp j mod W), and the W partial sums are added in warp order, so results
+// are reproducible.
+//
+// Per visit the bookkeeping is kept small: the walk is a plain loop (a
+// separate instance for the seeding walk); the acceptance test of a lane
+// without a point always passes (its position is +inf and its index -1)
+// instead of being tested; the point-in-cell test is one unsigned
+// comparison; the accepted-cell term is computed on every visit and masked
+// (no branch), the next cell is a select, and only the exact leaf sum is a
+// (warp-uniform) branch; the leaf sum has no branch (a coincident point has
+// a zero offset, and the clamped squared distance keeps its term at zero);
+// and the position / offset / accumulator arithmetic is done on packed
+// (x, y) pairs.
+template <bool kCount, bool kSeeding>
+__device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, int pos,
+                                          unsigned long long xu, const float2* __restrict__ xs,
+                                          const float4* __restrict__ nodeA,
+                                          const int4* __restrict__ nodeB, unsigned long long& acc,
+                                          int& budget, bool& broken, int* seeds, int& nseeds,
+                                          unsigned& visits, unsigned& inter) {
+  const unsigned nodes = 2u * (unsigned)n - 1u;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(xs);
+  while (cur != stop) {
+    if ((unsigned)cur >= nodes || --budget < 0) {
+      broken = true;
+      return;
+    }
+    const float4 A = __ldg(&nodeA[cur]);
+    const int4 B = __ldg(&nodeB[cur]);
+    if (kCount) ++visits;
+    const unsigned long long d = sub2(xu, pk2(A.x, A.y));
+    const float2 df = upk2(d);
+    const float q = fmaf(df.x, df.x, df.y * df.y);
+    const bool far = (unsigned)(pos - B.z) >= (unsigned)(B.w - B.z) && q > A.z;
+    const bool take = __all_sync(0xffffffffu, far);
+    // count / distance^2 of the accepted cell, 0 when the cell is not taken
+    const float s = take ? A.w * rcp_approx(q) : 0.f;
+    acc = fma2(pk2(s, s), d, acc);
+    if (kCount && take) ++inter;
+    const bool leaf = !take && B.x < 0;
+    if (leaf) {  // uniform: every lane read the same record
+      const int pb = max(B.z, 0), pe = min(B.w, n);
+#pragma unroll 4
+      for (int p = pb; p < pe; ++p) {
+        const unsigned long long e = sub2(xu, __ldg(&xp[p]));
+        const float2 ef = upk2(e);
+        const float r = rcp_approx(fmaxf(fmaf(ef.x, ef.x, ef.y * ef.y), 1e-30f));
+        acc = fma2(pk2(r, r), e, acc);
+      }
+      if (kCount) inter += (unsigned)max(pe - pb, 0);
+    }
+    if (kSeeding && !take && !leaf && B.w - B.z <= seed && nseeds < kSeedMax) {
+      if (lane == 0) seeds[nseeds] = cur;
+      __syncwarp();
+      if (lane == 0) ++nseeds;
+      __syncwarp();
+      cur = B.y;
+    } else {
+      cur = (take || leaf) ? B.y : B.x;
+    }
+  }
+}
+
 template <bool kCount>
-__global__ void traverse_group_kernel(int n, int W, int seed, const float2* __restrict__ xs,
-                                      const int32_t* __restrict__ vals,
-                                      const float4* __restrict__ nodeA,
-                                      const int4* __restrict__ nodeB, float2* __restrict__ F,
-                                      unsigned long long* counters, int* err) {
+__global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
+    int n, int W, int seed, const float2* __restrict__ xs, const int32_t* __restrict__ vals,
+    const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float2* __restrict__ F,
+    unsigned long long* counters, int* err) {
   __shared__ GroupShared sh;
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  const int slot = wb / W, w = wb % W;  // task slot in the block, warp in the task
+  const int slot = wb / W, w = wb % W;
   const int tpb = (blockDim.x >> 5) / W;
   const int64_t task = (int64_t)blockIdx.x * tpb + slot;
-  const bool live = task * 32 < n;  // a whole warp is live or not
-  const int pos = (int)(task * 32) + lane;
-  const bool valid = live && pos < n;
-  const float2 xu = valid ? xs[pos] : make_float2(0.f, 0.f);
+  const bool live = task * 32 < n;
+  const int p0 = (int)(task * 32) + lane;
+  const bool valid = live && p0 < n;
+  // a lane without a point: position +inf and index -1, so its acceptance
+  // test always passes and it never vetoes a cell
+  const int pos = valid ? p0 : -1;
+  const float2 x0 = valid ? xs[p0] : make_float2(CUDART_INF_F, CUDART_INF_F);
+  const unsigned long long xu = pk2(x0.x, x0.y);
+  unsigned long long acc = pk2(0.f, 0.f);
   int* seeds = sh.seeds[slot];
   int& nseeds = sh.nseeds[slot];
-  float fx = 0.f, fy = 0.f;
   unsigned visits = 0, inter = 0;
-  const int nodes = 2 * n - 1;
   int budget = 2 * n + 2;
   bool broken = false;
-  // One vote walk from `cur` until `stop`; seeds are recorded when `seeding`.
-  auto walk = [&](int cur, int stop, bool seeding) {
-    while (cur != stop && cur >= 0) {
-      if (cur >= nodes || --budget < 0) {
-        broken = true;
-        return;
-      }
-      const float4 A = __ldg(&nodeA[cur]);
-      const int4 B = __ldg(&nodeB[cur]);
-      if (kCount) ++visits;
-      const float dx = xu.x - A.x, dy = xu.y - A.y;
-      const float q = fmaf(dx, dx, dy * dy);
-      const bool far = !valid || ((pos < B.z || pos >= B.w) && q > A.z);
-      if (__all_sync(0xffffffffu, far)) {
-        const float sc = __fdividef(A.w, q);
-        fx = fmaf(sc, dx, fx);
-        fy = fmaf(sc, dy, fy);
-        if (kCount) ++inter;
-        cur = B.y;
-      } else if (B.x < 0) {
-        const int pb = max(B.z, 0), pe = min(B.w, n);
-#pragma unroll 4
-        for (int p = pb; p < pe; ++p) {
-          const float2 xv = xs[p];
-          const float ex = xu.x - xv.x, ey = xu.y - xv.y;
-          const float eq = fmaf(ex, ex, ey * ey);
-          if (eq > 0.f) {
-            const float inv = __fdividef(1.f, eq);
-            fx = fmaf(inv, ex, fx);
-            fy = fmaf(inv, ey, fy);
-          }
-          if (kCount) ++inter;
-        }
-        cur = B.y;
-      } else if (seeding && B.w - B.z <= seed && nseeds < kSeedMax) {
-        if (lane == 0) seeds[nseeds] = cur;
-        __syncwarp();
-        if (lane == 0) ++nseeds;
-        __syncwarp();
-        cur = B.y;
-      } else {
-        cur = B.x;
-      }
-    }
-  };
   if (w == 0 && live) {
     if (lane == 0) nseeds = 0;
     __syncwarp();
-    walk(n > 1 ? 0 : -1, -1, W > 1 && seed > 0);
+    if (W > 1 && seed > 0)
+      vote_walk<kCount, true>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                              budget, broken, seeds, nseeds, visits, inter);
+    else
+      vote_walk<kCount, false>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                               budget, broken, seeds, nseeds, visits, inter);
   }
+  float2 f = upk2(acc);
   if (W > 1) {
     __syncthreads();
     const int ns = live ? nseeds : 0;
     for (int j = w; j < ns && !broken; j += W) {
       const int c = seeds[j];
-      walk(c, __ldg(&nodeB[c]).y, false);
+      vote_walk<kCount, false>(c, __ldg(&nodeB[c]).y, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                               budget, broken, seeds, nseeds, visits, inter);
     }
-    sh.part[wb][lane] = make_float2(fx, fy);
+    f = upk2(acc);
+    sh.part[wb][lane] = f;
     __syncthreads();
     if (w == 0) {
       float sx = 0.f, sy = 0.f;
@@ -716,12 +774,11 @@ __global__ void traverse_group_kernel(int n, int W, int seed, const float2* __re
         sx += sh.part[slot * W + k][lane].x;
         sy += sh.part[slot * W + k][lane].y;
       }
-      fx = sx;
-      fy = sy;
+      f = make_float2(sx, sy);
     }
   }
   if (broken && lane == 0) atomicOr(err, 1);
-  if (w == 0 && valid) F[vals[pos]] = make_float2(fx, fy);
+  if (w == 0 && valid) F[vals[p0]] = f;
   if (kCount) {
     unsigned tot = valid ? inter : 0u;
 #pragma unroll
@@ -901,24 +958,20 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
 }
 
 mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
-                      unsigned long long* counters, cudaStream_t s, bool group) {
+                      unsigned long long* counters, cudaStream_t s, int mode) {
   if (n <= 0) return MM_OK;
   const int wpb = warps_per_block > 0 ? warps_per_block : 4;
   const int warps = ceil_div(n, 32);
   const int blocks = ceil_div(warps, wpb);
-  if (group) {
+  if (mode != 0) {
     // W warps share a task of 32 points; blocks of at least 8 warps
     const int tasks = ceil_div(n, 32);
     const int W = std::max(1, std::min(kGroupMaxWarps, wpb));
     const int tpb = std::max(1, 8 / W);
     const int seed = W > 1 ? kSeedPoints : 0;
-    const int blocks2 = ceil_div(tasks, tpb);
-    if (counters)
-      traverse_group_kernel<true><<<blocks2, tpb * W * 32, 0, s>>>(
-          n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, counters, ws.err);
-    else
-      traverse_group_kernel<false><<<blocks2, tpb * W * 32, 0, s>>>(
-          n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, nullptr, ws.err);
+    auto kern = counters ? traverse_vote_kernel<true> : traverse_vote_kernel<false>;
+    kern<<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(n, W, seed, ws.xs, ws.vals[0], ws.nodeA,
+                                                      ws.nodeB, F, counters, ws.err);
   } else if (counters) {
     traverse_kernel<true><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB,
                                                        F, counters, ws.err);

@@ -146,7 +146,8 @@ mm_status check_params(const mm_params* p) {
       p->lp_rounds < 0 || p->iters_per_alpha < 1 || p->max_iters_at_min < 1 ||
       !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
       p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS || p->leaf_size < 0 ||
-      p->leaf_size > kMaxLeaf || p->approx_levels < 0 || p->approx_levels > MM_MAX_LEVELS) {
+      p->leaf_size > kMaxLeaf || p->approx_levels < 0 || p->approx_levels > MM_MAX_LEVELS ||
+      p->bh_group < 0 || p->bh_group > 1) {
     set_error("parameter out of range");
     return MM_ERR_INVALID_ARG;
   }
@@ -301,7 +302,7 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
     MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop,
                     group_of(h->p)));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
-                       nullptr, s, group_of(h->p)));
+                       nullptr, s, h->p.bh_group));
   }
   SweepEpilogue ep{};
   ep.st = st;
@@ -1302,7 +1303,7 @@ mm_status tune_levels(mm_hierarchy* h, cudaStream_t s) {
     int best_w = 4;
     for (int w = 1; w <= 16; w <<= 1) {
       double ms = 0;
-      MM_TRY(time_ms(s, 5, [&]() { return bh_traverse(L.n, h->tree, h->F, w, nullptr, s, group_of(h->p)); }, &ms));
+      MM_TRY(time_ms(s, 5, [&]() { return bh_traverse(L.n, h->tree, h->F, w, nullptr, s, h->p.bh_group); }, &ms));
       if (ms < best) { best = ms; best_w = w; }
     }
     L.walk_warps = best_w;
@@ -1663,7 +1664,7 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
   MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s, nullptr, true, group_of(h->p)));
   MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s,
-                     group_of(h->p)));
+                     h->p.bh_group));
   return tree_error(h, s);
 }
 
@@ -1809,7 +1810,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
       st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev, true, group_of(h->p));
       if (st == MM_OK)
         st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
-                         nullptr, s, group_of(h->p));
+                         nullptr, s, h->p.bh_group);
     }
     cudaEventRecord(ev[6], s);
     if (st == MM_OK) st = gather_update(L, xs, h->F, h->sstate, h->partials, s);
@@ -1832,7 +1833,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, true, group_of(h->p));
     if (st == MM_OK)
       st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
-                       cnt, s, group_of(h->p));
+                       cnt, s, h->p.bh_group);
   }
   unsigned long long hc[2] = {0, 0};
   if (st == MM_OK) {

@@ -336,8 +336,10 @@ mm_status bh_bbox(XSel x, int n, TreeWS& ws, cudaStream_t s);
 // group = false: per-point acceptance (the oracle's Barnes-Hut); true: a
 // cell is accepted for a warp's 32 points together (refines every point's
 // per-point sum).
+// mode: 0 = per-point walk, 1 = group acceptance over 32 Morton-consecutive
+// points (one per lane)
 mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
-                      unsigned long long* counters, cudaStream_t s, bool group = false);
+                      unsigned long long* counters, cudaStream_t s, int mode = 0);
 
 constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
 
@@ -471,6 +473,11 @@ mm_status gemm_bf16(const void* A, int M, int K, const void* B, int N, const flo
                     int relu, void* outb, float* outf, int* err, cudaStream_t s);
 
 mm_status gemm_setup();
+// part[b][r][c] = sum over the b-th of `parts` contiguous vertex ranges of
+// A[v][r] * B[v][c] on the tensor cores (A BF16 [n x R], R in {16, 128};
+// B BF16 [n x 64]; part FP32 [parts x R x 64]); err |= 4 on a wait timeout.
+mm_status gemm_tn_partials(const void* A, int n, int R, const void* B, float* part, int parts,
+                           int* err, cudaStream_t s);
 
 // ------------------------------------------------- learned prolongation ---
 constexpr int kNetHidden = 64;
