@@ -441,7 +441,8 @@ def main():
                             and not w.get("nolearn")):
         net, tr = train_prolongation(mm, p)
         cmp_, best = learned_vs_plain(mm, h, p, net)
-        learned_cmp = {"training": tr, **cmp_}
+        learned_cmp = {"training": tr, **cmp_,
+                       "tensor_core_rooflines": mpnn_roofline(mm, n, measured_peaks()[0])}
         if w.get("learned"):
             if best is None:
                 best = mm.default_params()
@@ -977,6 +978,37 @@ def layout_breakdown(mm, h, p, stats, peaks, src, fp32_peak, reps=5):
         out["sort_roofline"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
                                 "frac": a / hbm, "peak_source": src}
     return out
+
+
+def mpnn_roofline(mm, n, peaks):
+    """The learned prolongation's two tensor-core kernels at the width of a
+    hidden layer on this workload's n vertices (mm_net_gemm_profile, CUDA
+    events): the layer product H W^T ([n x 128] x [128 x 64], BF16 out) and
+    the weight-gradient partials Hcat^T dZ ([n x 128]^T x [n x 64], FP32
+    partials).  Both do 2 n 128 64 flops; their algorithmic bytes are the
+    BF16 operands read once and the output written once.  Tensor fraction
+    against the measured BF16 GEMM rate (burst), HBM fraction against the
+    measured copy bandwidth."""
+    f_ms, b_ms = mm.net_gemm_profile(n, reps=20)
+    flops = 2.0 * n * 128 * 64
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    parts = min(torch_sms(), max(1, (n + 63) // 64))
+    out = {}
+    for name, ms, nbytes in (("layer_product", f_ms, 2.0 * n * (128 + 64) + 2.0 * 64 * 128),
+                             ("weight_gradient", b_ms, 2.0 * n * (128 + 64)
+                              + 4.0 * parts * 128 * 64)):
+        tf = flops / (ms / 1e3) / 1e12
+        gb = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "tflops": tf, "tensor_frac": tf / bf16, "gbs": gb,
+                     "hbm_frac": gb / hbm, "n": n, "bound": "hbm"}
+    out["peaks"] = {"bf16_tflops": bf16, "hbm_gbs": hbm, "source": "MEASURED_PEAKS.json"}
+    return out
+
+
+def torch_sms():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def side_table(mm, wname):

@@ -377,7 +377,7 @@ mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta,
  * for testing (no paper counterpart): C = A * B^T on the tcgen05 tensor
  * cores with BF16 inputs and FP32 accumulation, optional bias[N] and ReLU.
  *   A device BF16 [M x K] row-major, B device BF16 [N x K] row-major,
- *   K a multiple of 16 in [16, 128], N = 64 or 128, both 16-byte aligned;
+ *   K a multiple of 16 in [16, 128], N = 64 or 128, all buffers 16-byte aligned;
  *   out_f32 (device FP32 [M x N]) and/or out_bf16 (device BF16 [M x N]).
  * Synchronises the stream (reports a tensor-core wait that gave up as
  * MM_ERR_TIMEOUT).
@@ -385,6 +385,30 @@ mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta,
 mm_status mm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A,
                        const void* B, const float* bias, int32_t relu,
                        float* out_f32, void* out_bf16, void* stream);
+
+/*
+ * The tensor-core weight-gradient product of the learned prolongation's
+ * dense layers, exposed for testing (no paper counterpart):
+ *   out[R x 64] = A^T B = sum over v of A[v][r] * B[v][c]
+ * on the tcgen05 tensor cores with BF16 inputs and FP32 accumulation (one
+ * partial per vertex range, the partials added in a fixed order).
+ *   A device BF16 [n x R] row-major, R = 16 or 128; B device BF16 [n x 64]
+ *   row-major; both 16-byte aligned; out device FP32 [R x 64].
+ * Allocates its partials with cudaMallocAsync on `stream`; synchronises it.
+ */
+mm_status mm_gemm_bf16_tn(int32_t n, int32_t R, const void* A, const void* B,
+                          float* out, void* stream);
+
+/*
+ * Timing of the two tensor-core kernels of the learned prolongation at the
+ * width of a hidden layer (no paper counterpart; a measurement aid): the
+ * layer product [n x 128] x [128 x 64] (BF16 out) and the weight-gradient
+ * partials [n x 128]^T x [n x 64], each launched `reps` times after a
+ * warm-up on internally allocated operands, CUDA events on `stream`.
+ * ms (host [2]) receives the mean milliseconds per launch of each.
+ * Synchronises the stream.
+ */
+mm_status mm_net_gemm_profile(int32_t n, int32_t reps, double* ms, void* stream);
 
 /*
  * Learned prolongation (no paper counterpart; an extension of the

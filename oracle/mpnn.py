@@ -32,7 +32,8 @@ The method fixes BF16 operands with FP32 accumulation for the dense layers.
 With ``quant=bf16_round`` the forward and backward passes round to BF16 at
 exactly the points where those operands are formed -- the features, both
 halves of every [H | A H], every W_l, every ReLU output H_l, and, in the
-backward pass, dZ_l and W_l before dZ_l W_l^T -- and stay FP64 elsewhere.
+backward pass, dZ_l (for both [H | A H]^T dZ_l and dZ_l W_l^T) and W_l --
+and stay FP64 elsewhere.
 Without it (the default) everything is FP64.
 
 Pins (tests/test_oracle_mpnn.py): analytic gradients against central finite
@@ -184,7 +185,9 @@ def backward(P, rp, col, cache, a, b, r, g, o, t, cp, quant=None):
     for l in range(LAYERS - 1, -1, -1):
         Hc, Z = cache["layers"][l]
         dZ = dH * (Z > 0)
-        G[f"W{l}"] = Hc.T @ dZ
+        # the weight gradient of a dense layer is a BF16 x BF16 product with
+        # FP32 accumulation on the device: dZ is rounded as for dZ W^T below
+        G[f"W{l}"] = Hc.T @ q(dZ)
         G[f"b{l}"] = dZ.sum(0)
         dHc = q(dZ) @ q(P[f"W{l}"]).T
         d = Hc.shape[1] // 2

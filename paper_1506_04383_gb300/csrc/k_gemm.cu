@@ -1,6 +1,8 @@
-// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05) with an
+// BF16 tensor-core GEMMs on the 5th-generation tensor cores (tcgen05) with an
 // FP32 accumulator in tensor memory, for the dense layers of the learned
-// prolongation:   C[M x N] = A[M x K] * B[N x K]^T  (+ bias, ReLU)
+// prolongation: the layer products (gemm_tc_kernel, below) and the weight
+// gradients (gemm_tn_partial_kernel, further down).
+//   C[M x N] = A[M x K] * B[N x K]^T  (+ bias, ReLU)
 // A and B are row-major with K contiguous (both "K-major").  One CTA of 128
 // threads computes a 128-row tile:
 //   * warp 0 allocates N tensor-memory columns (128 lanes x N FP32);
@@ -14,6 +16,8 @@
 //     tcgen05.ld 32x32b and runs the epilogue (bias, ReLU, BF16 or FP32
 //     store); warp 0 frees the tensor memory.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "mm_internal.cuh"
@@ -150,16 +154,198 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(
       ld16(tbase + (uint32_t)c0, r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < M) {
+        // the lane's 16 consecutive outputs of its row, written as whole
+        // 16-byte vectors (every 32-byte sector filled by one thread)
+        float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          float v = __uint_as_float(r[j]);
-          if (bias) v += bias[c0 + j];
-          if (relu) v = fmaxf(v, 0.f);
-          if (outb) outb[(size_t)row * N + c0 + j] = __float2bfloat16_rn(v);
-          if (outf) outf[(size_t)row * N + c0 + j] = v;
+          v[j] = __uint_as_float(r[j]);
+          if (bias) v[j] += bias[c0 + j];
+          if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        if (outb) {
+          uint32_t pk[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(outb + (size_t)row * N + c0);
+          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        if (outf) {
+          float4* dst = reinterpret_cast<float4*>(outf + (size_t)row * N + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
       }
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N));
+  }
+}
+
+// ------------------------------------------------------------------------
+// Weight gradients of the dense layers on the tensor cores:
+//   part[b][r][c] = sum over CTA b's vertices v of A[v][r] * B[v][c]
+// with A = Hcat (BF16 [n x R], R = 16 or 128) and B = dZ (BF16 [n x 64]);
+// the caller adds the per-CTA partials in a fixed order.  In GEMM terms the
+// contraction runs over the vertices, so both operands arrive with the
+// contracted index slowest (row-major over vertices).  Each CTA (128
+// threads, one per SM, a contiguous range of vertices) stages 64 vertices at
+// a time, transposing 8 x 8 blocks of BF16 in registers so that A^T (R rows,
+// padded to 128 with zeros) and B^T (64 rows) land in the same K-major
+// no-swizzle layout as gemm_tc_kernel's operands; one thread issues the four
+// K = 16 MMAs (M = 128, N = 64) of the chunk into one FP32 accumulator in
+// tensor memory and commits them to an mbarrier, which every thread waits
+// on (bounded) before the buffers are refilled.  Finally each warp reads its
+// 32 accumulator rows with tcgen05.ld and writes the first R rows.
+constexpr int kTnChunk = 64;                              // vertices per stage
+constexpr int kTnSmem = (kTnChunk / 16) * (4096 + 64 * 32);  // A + B tiles
+
+// Transposes an 8 x 8 block of BF16 held as 8 rows of 8 (row i = u[i]):
+// out[j] holds column j, element i from u[i].
+__device__ __forceinline__ void transpose8x8(const uint4 (&u)[8], uint4 (&out)[8]) {
+  uint32_t w[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    w[i][0] = u[i].x; w[i][1] = u[i].y; w[i][2] = u[i].z; w[i][3] = u[i].w;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int word = j >> 1;
+    const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;  // high or low halves of two words
+    uint32_t o[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) o[p] = __byte_perm(w[2 * p][word], w[2 * p + 1][word], sel);
+    out[j] = make_uint4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+__global__ void __launch_bounds__(kGemmThreads) gemm_tn_partial_kernel(
+    const __nv_bfloat16* __restrict__ A, int n, int R, const __nv_bfloat16* __restrict__ B,
+    float* __restrict__ part, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  constexpr int N = 64;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  const int v0 = (int)((int64_t)n * blockIdx.x / G), v1 = (int)((int64_t)n * (blockIdx.x + 1) / G);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + (kTnChunk / 16) * 4096;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // rows R..127 of A^T stay zero for the whole run
+  for (int i = tid; i < kTnSmem / 16; i += kGemmThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = make_idesc(kTileM, N);
+  bool ok = true;
+  int chunks = 0;
+  for (int base = v0; base < v1 && ok; base += kTnChunk, ++chunks) {
+    // stage: each of the R + 64 blocks of 8 vertices x 8 columns (of A,
+    // then of B) is loaded, transposed and stored by one thread
+    const int na = (R / 8) * 8;  // A blocks: R/8 column groups x 8 vertex groups
+    for (int tb = tid; tb < na + 64; tb += kGemmThreads) {
+      const bool isA = tb < na;
+      const int t = isA ? tb : tb - na;
+      const int cg = t >> 3, vg = t & 7;  // column group, vertex group
+      const int ld = isA ? R : N;
+      const __nv_bfloat16* src = isA ? A : B;
+      uint4 u[8], o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int v = base + vg * 8 + i;
+        u[i] = v < v1 ? *reinterpret_cast<const uint4*>(src + (size_t)v * ld + cg * 8)
+                      : make_uint4(0u, 0u, 0u, 0u);
+      }
+      transpose8x8(u, o);
+      // o[j] = row (cg * 8 + j) of the transposed operand, K chunk vg
+      unsigned char* dst = isA ? sA : sB;
+      const int slice = isA ? 4096 : N * 32;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int m = cg * 8 + j;
+        const int off = (vg >> 1) * slice + (m >> 3) * 256 + (vg & 1) * 128 + (m & 7) * 16;
+        *reinterpret_cast<uint4*>(dst + off) = o[j];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+#pragma unroll
+      for (int s = 0; s < kTnChunk / 16; ++s) {
+        const uint64_t ad = make_desc(a0 + s * 4096, 128, 256);
+        const uint64_t bd = make_desc(b0 + s * (N * 32), 128, 256);
+        const uint32_t acc = (chunks > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar)));
+    }
+    // the chunk's MMAs done (phase = chunk parity) before the buffers are
+    // refilled or the accumulator read; bounded
+    bool done = false;
+    const uint32_t par = (uint32_t)(chunks & 1);
+    for (int spin = 0; spin < kSpin && !done; ++spin) {
+      uint32_t d;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.b32 %0, 1, 0, p;\n}"
+          : "=r"(d)
+          : "r"(smem_addr(&mbar)), "r"(par));
+      done = d != 0;
+    }
+    ok = __syncthreads_and(done ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!ok && tid == 0 && err) atomicOr(err, 4);
+  // epilogue: row m = warp * 32 + lane of the accumulator; rows < R kept
+  const int m = warp * 32 + lane;
+  float* out = part + (size_t)blockIdx.x * R * N;
+  if (ok && chunks > 0) {
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      ld16(tbase + (uint32_t)c0, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < R) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(out + (size_t)m * N + c0 + j) =
+              make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                          __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+      }
+    }
+  } else if (m < R) {
+    for (int c = 0; c < N; c += 4)
+      *reinterpret_cast<float4*>(out + (size_t)m * N + c) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -192,6 +378,45 @@ mm_status gemm_setup() {
   return MM_OK;
 }
 
+mm_status gemm_tn_partials(const void* A, int n, int R, const void* B, float* part, int parts,
+                           int* err, cudaStream_t s) {
+  if (n < 0 || (R != 16 && R != 128) || parts < 1 || !A || !B || !part) {
+    set_error("gemm_tn: need R in {16, 128}, parts >= 1");
+    return MM_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)part & 15)) {
+    set_error("gemm_tn: A, B and part must be 16-byte aligned");
+    return MM_ERR_INVALID_ARG;
+  }
+  gemm_tn_partial_kernel<<<parts, kGemmThreads, kTnSmem, s>>>(
+      (const __nv_bfloat16*)A, n, R, (const __nv_bfloat16*)B, part, err);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+namespace {
+// out[i] = sum over p of part[p][i], in order p = 0, 1, ... (FP32)
+__global__ void sum_parts_kernel(int parts, int m, const float* __restrict__ part,
+                                 float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  float s = 0.f;
+  for (int p = 0; p < parts; ++p) s += part[(size_t)p * m + i];
+  out[i] = s;
+}
+}  // namespace
+
+int gemm_tn_parts(int n) { return std::max(1, std::min(num_sms(), ceil_div(n, kTnChunk))); }
+
+mm_status gemm_tn_bf16(const void* A, int n, int R, const void* B, float* out, float* part,
+                       int* err, cudaStream_t s) {
+  const int parts = gemm_tn_parts(n);
+  MM_TRY(gemm_tn_partials(A, n, R, B, part, parts, err, s));
+  sum_parts_kernel<<<ceil_div(R * 64, 256), 256, 0, s>>>(parts, R * 64, part, out);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
 mm_status gemm_bf16(const void* A, int M, int K, const void* B, int N, const float* bias,
                     int relu, void* outb, float* outf, int* err, cudaStream_t s) {
   if (M < 0 || K < 16 || K > 128 || K % 16 || (N != 64 && N != 128) || !A || !B ||
@@ -199,8 +424,9 @@ mm_status gemm_bf16(const void* A, int M, int K, const void* B, int N, const flo
     set_error("gemm: need 16 <= K <= 128 (multiple of 16), N in {64, 128}");
     return MM_ERR_INVALID_ARG;
   }
-  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
-    set_error("gemm: A and B must be 16-byte aligned");
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)outb & 15) ||
+      ((uintptr_t)outf & 15)) {
+    set_error("gemm: A, B and the outputs must be 16-byte aligned");
     return MM_ERR_INVALID_ARG;
   }
   if (M == 0) return MM_OK;

@@ -2099,6 +2099,105 @@ mm_status mm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const voi
   return MM_OK;
 }
 
+mm_status mm_gemm_bf16_tn(int32_t n, int32_t R, const void* A, const void* B, float* out,
+                          void* stream) {
+  g_err.clear();
+  if (n < 0 || (R != 16 && R != 128) || !A || !B || !out) {
+    set_error("mm_gemm_bf16_tn: need n >= 0, R in {16, 128}, device A, B, out");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    MM_CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)R * 64, s));
+    MM_CK(cudaStreamSynchronize(s));
+    return MM_OK;
+  }
+  int* err = nullptr;
+  float* part = nullptr;
+  MM_CK(cudaMallocAsync(&err, sizeof(int), s));
+  MM_CK(cudaMallocAsync(&part, sizeof(float) * (size_t)gemm_tn_parts(n) * R * 64, s));
+  MM_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  mm_status st = gemm_tn_bf16(A, n, R, B, out, part, err, s);
+  int he = 0;
+  cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(part, s);
+  cudaFreeAsync(err, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  MM_TRY(st);
+  MM_CK(e);
+  if (he) {
+    set_error("tensor-core wait gave up");
+    return MM_ERR_TIMEOUT;
+  }
+  return MM_OK;
+}
+
+mm_status mm_net_gemm_profile(int32_t n, int32_t reps, double* ms, void* stream) {
+  g_err.clear();
+  if (n < 128 || reps < 1 || !ms) {
+    set_error("mm_net_gemm_profile: need n >= 128, reps >= 1, ms");
+    return MM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  MM_TRY(gemm_setup());
+  const size_t nA = (size_t)n * 128, nB = (size_t)n * 64;
+  void *A = nullptr, *W = nullptr, *C = nullptr, *G = nullptr;
+  float *out = nullptr, *part = nullptr;
+  int* err = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  mm_status st = MM_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == MM_OK) st = cuda_status(e, what, __FILE__, __LINE__);
+  };
+  ck(cudaMallocAsync(&A, 2 * nA, s), "alloc");
+  ck(cudaMallocAsync(&W, 2 * 64 * 128, s), "alloc");
+  ck(cudaMallocAsync(&C, 2 * nB, s), "alloc");
+  ck(cudaMallocAsync(&G, 2 * nB, s), "alloc");
+  ck(cudaMallocAsync(&out, sizeof(float) * 128 * 64, s), "alloc");
+  ck(cudaMallocAsync(&part, sizeof(float) * (size_t)gemm_tn_parts(n) * 128 * 64, s), "alloc");
+  ck(cudaMallocAsync(&err, sizeof(int), s), "alloc");
+  // operand values do not change the work: a constant bit pattern (BF16 1/8)
+  if (st == MM_OK) {
+    ck(cudaMemsetAsync(A, 0x3e, 2 * nA, s), "memset");
+    ck(cudaMemsetAsync(W, 0x3e, 2 * 64 * 128, s), "memset");
+    ck(cudaMemsetAsync(G, 0x3e, 2 * nB, s), "memset");
+    ck(cudaMemsetAsync(err, 0, sizeof(int), s), "memset");
+  }
+  for (auto& e : ev) ck(cudaEventCreate(&e), "event");
+  float t0 = 0.f, t1 = 0.f;
+  if (st == MM_OK) {
+    // one warm-up of each, then reps launches of each between events
+    st = gemm_bf16(A, n, 128, W, 64, nullptr, 0, C, nullptr, err, s);
+    if (st == MM_OK) st = gemm_tn_partials(A, n, 128, G, part, gemm_tn_parts(n), err, s);
+    ck(cudaEventRecord(ev[0], s), "record");
+    for (int r = 0; r < reps && st == MM_OK; ++r)
+      st = gemm_bf16(A, n, 128, W, 64, nullptr, 0, C, nullptr, err, s);
+    ck(cudaEventRecord(ev[1], s), "record");
+    for (int r = 0; r < reps && st == MM_OK; ++r)
+      st = gemm_tn_partials(A, n, 128, G, part, gemm_tn_parts(n), err, s);
+    ck(cudaEventRecord(ev[2], s), "record");
+    ck(cudaEventSynchronize(ev[2]), "sync");
+    ck(cudaEventElapsedTime(&t0, ev[0], ev[1]), "elapsed");
+    ck(cudaEventElapsedTime(&t1, ev[1], ev[2]), "elapsed");
+  }
+  int he = 0;
+  if (err) cudaMemcpy(&he, err, sizeof(int), cudaMemcpyDeviceToHost);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  void* bufs[] = {A, W, C, G, out, part, err};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, s);
+  cudaStreamSynchronize(s);
+  MM_TRY(st);
+  if (he) {
+    set_error("tensor-core wait gave up");
+    return MM_ERR_TIMEOUT;
+  }
+  ms[0] = t0 / reps;
+  ms[1] = t1 / reps;
+  return MM_OK;
+}
+
 mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta, double max_rel_drift,
                       mm_tune_result* out, void* stream) {
   g_err.clear();

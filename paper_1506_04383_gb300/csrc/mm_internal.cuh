@@ -478,6 +478,11 @@ mm_status gemm_setup();
 // B BF16 [n x 64]; part FP32 [parts x R x 64]); err |= 4 on a wait timeout.
 mm_status gemm_tn_partials(const void* A, int n, int R, const void* B, float* part, int parts,
                            int* err, cudaStream_t s);
+// out[R x 64] = sum_v A[v]^T B[v] (partials then a fixed-order sum); part
+// holds gemm_tn_parts(n) x R x 64 floats.
+int gemm_tn_parts(int n);
+mm_status gemm_tn_bf16(const void* A, int n, int R, const void* B, float* out, float* part,
+                       int* err, cudaStream_t s);
 
 // ------------------------------------------------- learned prolongation ---
 constexpr int kNetHidden = 64;

@@ -32,7 +32,8 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_autotune", "mm_gemm_bf16", "mm_net_create", "mm_net_free", "mm_net_params",
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
            "mm_layout_levels", "mm_repulsion_h", "mm_full_stress",
-           "mm_selftest_wait_timeout", "mm_measure_fp32_peak"]
+           "mm_selftest_wait_timeout", "mm_measure_fp32_peak", "mm_gemm_bf16_tn",
+           "mm_net_gemm_profile"]
 MM_NET_PARAMS = 17860
 
 
@@ -160,6 +161,8 @@ def load(path: str = LIB_PATH):
     lib.mm_full_stress.argtypes = [P, P, P, P]
     lib.mm_selftest_wait_timeout.argtypes = [i32, P]
     lib.mm_measure_fp32_peak.argtypes = [i32, P, P, P]
+    lib.mm_gemm_bf16_tn.argtypes = [i32, i32, P, P, P, P]
+    lib.mm_net_gemm_profile.argtypes = [i32, i32, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -447,6 +450,28 @@ def gemm_bf16(A, B, bias=None, relu=False, out_bf16=False, stream=None):
     _check(load().mm_gemm_bf16(M, N, K, _ptr(A), _ptr(B), _ptr(bias), int(relu), _ptr(C),
                                _ptr(Cb), _stream(stream)))
     return (C, Cb) if out_bf16 else C
+
+
+def gemm_bf16_tn(A, B, stream=None):
+    """out = A^T B on the tensor cores: A BF16 [n x R] (R = 16 or 128), B BF16
+    [n x 64]; returns FP32 [R x 64]."""
+    A = _dev(A, torch.bfloat16, "A")
+    B = _dev(B, torch.bfloat16, "B")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[0] != B.shape[0] or B.shape[1] != 64:
+        raise ValueError("need A [n x R] and B [n x 64]")
+    out = torch.empty((A.shape[1], 64), dtype=torch.float32, device=A.device)
+    _check(load().mm_gemm_bf16_tn(A.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(out),
+                                  _stream(stream)))
+    return out
+
+
+def net_gemm_profile(n: int, reps: int = 20, stream=None):
+    """ms per launch of the layer product [n x 128] x [128 x 64] and of the
+    weight-gradient partials [n x 128]^T x [n x 64] on the tensor cores."""
+    _require_cuda()
+    ms = (ctypes.c_double * 2)()
+    _check(load().mm_net_gemm_profile(int(n), int(reps), ms, _stream(stream)))
+    return float(ms[0]), float(ms[1])
 
 
 def objective(h: Hierarchy, level: int, x, alpha: float, stream=None):

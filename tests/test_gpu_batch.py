@@ -63,3 +63,47 @@ def test_autotune_keeps_objective(mm):
         assert lanes in (0, 1, 2, 4, 8, 16, 32) and warps in (0, 2, 4, 8, 16)
     x, st = mm.layout(h)
     assert np.all(np.isfinite(x.cpu().numpy()))
+
+
+def _oracle_levels_from_device(mm, h, k):
+    """The device hierarchy's levels (exported) in the oracle's format: the
+    oracle then lays out the graph on exactly these levels."""
+    import oracle
+    levels = []
+    for l in range(h.levels()):
+        e = mm.level_export(h, l)
+        n = e["c"].numel()
+        L = dict(n=n, rp=e["row_ptr"].cpu().numpy().astype(np.int64),
+                 col=e["col"].cpu().numpy().astype(np.int32),
+                 ew=e["omega"].cpu().numpy().astype(np.float64),
+                 c=e["c"].cpu().numpy().astype(np.float64), elen=None, coarse=l > 0,
+                 map=e["map"].cpu().numpy().astype(np.int32) if l < h.levels() - 1 else None)
+        L["S"] = oracle.build_S(L["rp"], L["col"], k, c=L["c"], coarse=L["coarse"])
+        levels.append(L)
+    return levels
+
+
+def test_batched_layouts_match_oracle_on_the_same_hierarchies(mm):
+    # a few graphs of one batch: each graph's part of the batched layout
+    # against the FP64 oracle's layout of that graph on the same levels (the
+    # device's per-graph hierarchy, exported; graph i uses seed + i); final
+    # objective (Eq. 1 at alpha = 0.008) within 1 %
+    import oracle
+    sizes = [1500, 400, 3000, 800]
+    gs, (rp, col, gp) = _batch(sizes, 91)
+    kw = dict(k=2, theta=0.5, coarsest_n=2, seed=1506)
+    p = mm.default_params(**kw)
+    hb = mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), p,
+                            graph_ptr=gp)
+    xb, st = mm.layout(hb, p)
+    xb = xb.cpu().numpy().astype(np.float64)
+    for i, (grp, gcol) in enumerate(gs):
+        pi = mm.default_params(**dict(kw, seed=1506 + i))
+        h = mm.build_hierarchy(torch.from_numpy(grp).cuda(), torch.from_numpy(gcol).cuda(), pi)
+        levels = _oracle_levels_from_device(mm, h, kw["k"])
+        po = oracle.params(**dict(kw, seed=1506 + i))
+        xo, _ = oracle.layout(grp, gcol, po, levels=levels)
+        S = levels[0]["S"]
+        Mb = oracle.objective(xb[gp[i]:gp[i + 1]], S, 0.008)[2]
+        Mo = oracle.objective(xo, S, 0.008)[2]
+        assert abs(Mb - Mo) <= 0.01 * abs(Mo), (i, Mb, Mo)

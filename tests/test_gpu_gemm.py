@@ -32,3 +32,29 @@ def test_gemm_bias_relu_bf16(mm):
     ref = np.maximum(A.double().numpy() @ B.double().numpy().T + bias.double().numpy(), 0)
     np.testing.assert_allclose(C.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
     np.testing.assert_allclose(Cb.float().cpu().numpy(), ref, rtol=1e-2, atol=1e-2)
+
+
+@pytest.mark.parametrize("n,R", [(64, 128), (1000, 128), (4099, 16), (30001, 128), (7, 16),
+                                 (200000, 128)])
+def test_weight_gradient_gemm_matches_fp64(mm, n, R):
+    # out = A^T B, contracted over the n rows (the vertices): K = n is split
+    # into per-CTA vertex ranges (ragged last chunk, zero rows padding A^T to
+    # 128 when R = 16) whose FP32 partials are added in a fixed order.  FP32
+    # accumulation of n products: |error| <= n * 2^-23 of the sum of |terms|
+    # (bounded here by 2e-7 n relative plus an absolute floor)
+    g = torch.Generator(device="cpu").manual_seed(n + R)
+    A = torch.randn(n, R, generator=g).to(torch.bfloat16)
+    B = torch.randn(n, 64, generator=g).to(torch.bfloat16)
+    C = mm.gemm_bf16_tn(A.cuda(), B.cuda()).cpu().numpy()
+    a, b = A.double().numpy(), B.double().numpy()
+    ref = a.T @ b
+    bound = (2e-7 * n + 1e-6) * (np.abs(a).T @ np.abs(b)) + 1e-6
+    assert np.all(np.abs(C - ref) <= bound)
+    # the result does not depend on the call (fixed-order reduction)
+    C2 = mm.gemm_bf16_tn(A.cuda(), B.cuda()).cpu().numpy()
+    assert np.array_equal(C, C2)
+
+
+def test_net_gemm_profile_reports_positive_times(mm):
+    f, b = mm.net_gemm_profile(1 << 16, reps=3)
+    assert f > 0 and b > 0

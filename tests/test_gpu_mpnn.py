@@ -1,13 +1,22 @@
 """The learned prolongation on the GPU against the oracle (oracle/mpnn.py).
 
-The network's dense layers take BF16 operands with FP32 accumulation.  The
-oracle's quantised mode rounds to BF16 at the same points and computes the
-rest in FP64, so the device agrees with it up to FP32 accumulation order and
-the odd element that lands on the other side of a BF16 rounding boundary
-(one BF16 step is 2^-8 relative): 1% on drifts and losses, 2% norm-wise on
-gradients.  Against the plain FP64 oracle the BF16 rounding of the inputs
-itself shows (gradients here are differences of large terms, up to ~10%
-apart), so that comparison checks direction: cosine similarity >= 0.98.
+The network's dense layers -- forward products and weight gradients, on the
+tensor cores -- take BF16 operands with FP32 accumulation.  The oracle's
+quantised mode rounds to BF16 at the same points and computes the rest in
+FP64, so the device agrees with it up to FP32 accumulation order and the odd
+element that lands on the other side of a BF16 rounding boundary (one BF16
+step is 2^-8 relative).  Element by element:
+  * drift (the network's offset o_v, both coordinates of every vertex):
+    |o - o_q| <= 0.03 max|o_q| + 0.01 |o_q|;
+  * every element of every gradient tensor G (weights and biases of the four
+    layers): |G - G_q| <= 0.005 max|G_q| + 0.01 |G_q|;
+  * the loss: relative 1e-3.
+The max-scaled term covers elements whose exact value is near zero (a
+difference of large terms, where one flipped BF16 rounding of an input moves
+the result by a few BF16 steps of the terms).  Against the plain FP64 oracle
+the BF16 rounding of the inputs itself shows (gradients here are differences
+of large terms, up to ~10% apart), so that comparison checks direction:
+cosine similarity >= 0.98.
 """
 import numpy as np
 import pytest
@@ -107,8 +116,10 @@ def test_forward_and_loss_match_oracle(mm):
     xo, Lo, _, _ = oracle_run(P, s)
     base = s["xc"][s["mp"]] + r
     drift = x.cpu().numpy() - base
-    assert rel(drift, xq - base) < 0.01
-    assert L == pytest.approx(Lq, rel=0.01)
+    dq = xq - base
+    assert np.all(np.abs(drift - dq) <= 0.03 * np.abs(dq).max() + 0.01 * np.abs(dq))
+    assert rel(drift, dq) < 0.01
+    assert L == pytest.approx(Lq, rel=1e-3)
     assert rel(drift, xo - base) < 0.05
     assert L == pytest.approx(Lo, rel=0.03)
 
@@ -122,10 +133,29 @@ def test_gradients_match_oracle(mm):
     _, Lq, Gq, _ = oracle_run(P, s, Q)
     _, Lo, Go, _ = oracle_run(P, s)
     G = unflat(g)
-    assert L == pytest.approx(Lq, rel=0.01)
+    assert L == pytest.approx(Lq, rel=1e-3)
     for k in ["W3", "b3", "W2", "b2", "W1", "b1", "W0", "b0"]:
+        e = np.abs(G[k] - Gq[k])
+        tol = 0.005 * np.abs(Gq[k]).max() + 0.01 * np.abs(Gq[k])
+        assert np.all(e <= tol), (k, float((e / tol).max()))
         assert rel(G[k], Gq[k]) < 0.02, k
         assert cos(G[k], Go[k]) > 0.98, k
+
+
+@pytest.mark.parametrize("seed,pseed", [(3, 7), (9, 4)])
+def test_gradients_match_oracle_element_by_element_more_samples(mm, seed, pseed):
+    s = sample(seed=seed)
+    P = params(pseed)
+    net = mm.Net(flat(P))
+    smp, keep = device_sample(mm, s)
+    g, L = net.gradients(smp)
+    _, Lq, Gq, _ = oracle_run(P, s, Q)
+    G = unflat(g)
+    assert L == pytest.approx(Lq, rel=1e-3)
+    for k in ["W3", "b3", "W2", "b2", "W1", "b1", "W0", "b0"]:
+        e = np.abs(G[k] - Gq[k])
+        tol = 0.005 * np.abs(Gq[k]).max() + 0.01 * np.abs(Gq[k])
+        assert np.all(e <= tol), (k, float((e / tol).max()))
 
 
 def test_training_reduces_loss_like_the_oracle(mm):
