@@ -93,7 +93,12 @@ typedef struct mm_params {
                             /* every level but the coarsest (Sec. 3.2); those */
                             /* levels run the sweep kernels (no fused level   */
                             /* kernel); single graphs only (batches: error)   */
-  int32_t reserved[2];
+  int32_t level_order;      /* 1: mm_build_hierarchy renumbers every level so */
+                            /* that clusters are consecutive, in the order of */
+                            /* the coarser level (memory locality of the      */
+                            /* sweeps; level-0 positions still cross the ABI  */
+                            /* in the caller's numbering); 0: input numbering */
+  int32_t reserved[1];
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */

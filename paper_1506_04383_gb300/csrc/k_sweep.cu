@@ -387,9 +387,10 @@ __global__ void init_coarsest_kernel(int n, const float* __restrict__ c, const S
   }
 }
 
-__global__ void copy_current_kernel(XSel xs, int n, float2* out) {
+__global__ void copy_current_kernel(XSel xs, int n, const int32_t* __restrict__ perm,
+                                    float2* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = xs.cur()[i];
+  if (i < n) out[i] = xs.cur()[perm ? perm[i] : i];
 }
 
 template <int G>
@@ -474,9 +475,9 @@ mm_status init_coarsest(int n, const float* c, const SEnt* s0, uint64_t seed, in
   return MM_OK;
 }
 
-mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s) {
+mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s, const int32_t* perm) {
   if (n <= 0) return MM_OK;
-  copy_current_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, n, out);
+  copy_current_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, n, perm, out);
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

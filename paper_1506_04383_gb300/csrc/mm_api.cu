@@ -40,6 +40,8 @@ struct mm_hierarchy {
   mm::TreeWS tree;
   float2* xb[2] = {nullptr, nullptr};
   float2* F = nullptr;
+  mm::LevelOrder ord;                 // hierarchy order of the levels (level 0 mapped)
+  float2* pbuf[2] = {nullptr, nullptr};  // level-0 positions in internal order
   float4* partials = nullptr;        // [kMaxGatherBlocks] per-block FP32 sums
   mm::SweepState* state = nullptr;   // layout schedule state
   mm::SweepState* sstate = nullptr;  // standalone calls
@@ -147,7 +149,7 @@ mm_status check_params(const mm_params* p) {
       !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
       p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS || p->leaf_size < 0 ||
       p->leaf_size > kMaxLeaf || p->approx_levels < 0 || p->approx_levels > MM_MAX_LEVELS ||
-      p->bh_group < 0 || p->bh_group > 1) {
+      p->bh_group < 0 || p->bh_group > 1 || p->level_order < 0 || p->level_order > 1) {
     set_error("parameter out of range");
     return MM_ERR_INVALID_ARG;
   }
@@ -408,7 +410,8 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
     if (st == MM_OK) st = add_loop(top, level_exact(h, top, false));
     if (st == MM_OK && level_out && level_out[top])
       st = add_child([&](cudaStream_t s) -> mm_status {
-        return copy_current(x, C.n, (float2*)level_out[top], s);
+        return copy_current(x, C.n, (float2*)level_out[top], s,
+                            top == 0 ? h->ord.perm0 : nullptr);
       });
     for (int lv = top - 1; lv >= 0 && st == MM_OK; --lv) {
       const Level& L = h->levels[lv];
@@ -438,7 +441,8 @@ mm_status build_graph(mm_hierarchy* h, const mm_params& p, bool single,
       if (st == MM_OK) st = add_loop(lv, level_exact(h, lv, false));
       if (st == MM_OK && level_out && level_out[lv])
         st = add_child([&](cudaStream_t s) -> mm_status {
-          return copy_current(x, L.n, (float2*)level_out[lv], s);
+          return copy_current(x, L.n, (float2*)level_out[lv], s,
+                              lv == 0 ? h->ord.perm0 : nullptr);
         });
     }
   }
@@ -480,6 +484,79 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+// Level-0 positions cross the C-ABI in the caller's numbering; a
+// renumbered hierarchy (level_order) works in its internal order.  in:
+// the caller's positions -> an internal copy in pbuf[k] (or x itself).
+const float2* x_in_internal(mm_hierarchy* h, int level, const float* x, int k, cudaStream_t s,
+                            mm_status* st) {
+  *st = MM_OK;
+  if (level != 0 || !h->ord.perm0) return (const float2*)x;
+  *st = permute_positions(h->levels[0].n, h->ord.inv0, (const float2*)x, h->pbuf[k], s);
+  return h->pbuf[k];
+}
+// out: internal positions (or forces) of level 0 -> the caller's numbering
+mm_status x_out_user(mm_hierarchy* h, int level, const float2* xi, float* out, cudaStream_t s) {
+  if (level != 0 || !h->ord.perm0) return MM_OK;
+  return permute_positions(h->levels[0].n, h->ord.perm0, xi, (float2*)out, s);
+}
+
+__global__ void i32_to_i64_k(int n, const int32_t* __restrict__ a, int64_t* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+__global__ void split_sent_k(int64_t m, const SEnt* __restrict__ s, int32_t* col, float* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  if (col) col[i] = s[i].col;
+  if (d) d[i] = s[i].d;
+}
+__global__ void map_user_k(int n, const int32_t* __restrict__ perm0,
+                           const int32_t* __restrict__ map, int32_t* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) out[v] = map[perm0[v]];
+}
+__global__ void gather_f32_k(int n, const int32_t* __restrict__ idx, const float* __restrict__ a,
+                             float* __restrict__ b) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) b[v] = a[idx[v]];
+}
+
+// Level 0 of a renumbered hierarchy as the caller numbers it: the caller's
+// CSR (kept), node weights and map gathered through the permutation, and
+// the pair set S rebuilt on the caller's CSR (rows ascending, as
+// mm_build_hierarchy builds it).
+mm_status export_level0_user(const mm_hierarchy* h, int64_t* row_ptr, int32_t* col, float* omega,
+                             float* c, int32_t* map, int64_t* s_ptr, int32_t* s_col, float* s_d,
+                             float* rho, cudaStream_t s) {
+  const Level& L = h->levels[0];
+  const LevelOrder& o = h->ord;
+  const int n = L.n;
+  if (row_ptr) i32_to_i64_k<<<ceil_div(n + 1, 256), 256, 0, s>>>(n + 1, o.rp_user, row_ptr);
+  if (col && L.nnzE)
+    MM_CK(cudaMemcpyAsync(col, o.col_user, 4 * L.nnzE, cudaMemcpyDeviceToDevice, s));
+  if (omega && L.nnzE)
+    MM_CK(cudaMemcpyAsync(omega, o.omega_user, 4 * L.nnzE, cudaMemcpyDeviceToDevice, s));
+  if (c) gather_f32_k<<<ceil_div(n, 256), 256, 0, s>>>(n, o.perm0, L.c, c);
+  if (map && L.map) map_user_k<<<ceil_div(n, 256), 256, 0, s>>>(n, o.perm0, L.map, map);
+  if (s_ptr || s_col || s_d || rho) {
+    int32_t* sp = nullptr;
+    SEnt* se = nullptr;
+    float* r = nullptr;
+    int64_t nnzS = 0;
+    MM_TRY(build_khop(n, o.rp_user, o.col_user, o.elen_user, nullptr, h->p.k, &sp, &se, &r,
+                      &nnzS, s));
+    if (s_ptr) i32_to_i64_k<<<ceil_div(n + 1, 256), 256, 0, s>>>(n + 1, sp, s_ptr);
+    if ((s_col || s_d) && nnzS)
+      split_sent_k<<<ceil_div(nnzS, 256), 256, 0, s>>>(nnzS, se, s_col, s_d);
+    if (rho) MM_CK(cudaMemcpyAsync(rho, r, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    cudaFreeAsync(sp, s);
+    cudaFreeAsync(se, s);
+    cudaFreeAsync(r, s);
+  }
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
 
 mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s);
 mm_status build_batch(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierarchy** out);
@@ -596,6 +673,7 @@ mm_status build(const mm_graph* g, const mm_params* p, cudaStream_t s, mm_hierar
   cudaFreeAsync(dmax, s);
   cudaFreeAsync(labels, s);
   MM_TRY(st);
+  if (p->level_order) MM_TRY(renumber_levels(h->levels, h->ord, s));
 
   return finish_levels(h, p, s);
 }
@@ -720,6 +798,10 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->xb[0], sizeof(float2) * (size_t)n0, s));
   MM_CK(cudaMallocAsync(&h->xb[1], sizeof(float2) * (size_t)n0, s));
   MM_CK(cudaMallocAsync(&h->F, sizeof(float2) * (size_t)n0, s));
+  if (h->ord.perm0) {
+    MM_CK(cudaMallocAsync(&h->pbuf[0], sizeof(float2) * (size_t)h->levels[0].n, s));
+    MM_CK(cudaMallocAsync(&h->pbuf[1], sizeof(float2) * (size_t)h->levels[0].n, s));
+  }
   // partials for the largest grid any lanes setting (autotuner) can launch
   MM_CK(cudaMallocAsync(&h->partials, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->state, sizeof(SweepState), s));
@@ -1048,7 +1130,7 @@ mm_status build_graph_batch(mm_hierarchy* h, const mm_params& p) {
           continue;
         }
         XSel x{sub->xb[0], sub->xb[1], &sub->state->parity};
-        MM_TRY(copy_current(x, n, h->xcat + h->gptr[i], s));
+        MM_TRY(copy_current(x, n, h->xcat + h->gptr[i], s, sub->ord.perm0));
         launches += 1;
       }
       return MM_OK;
@@ -1174,12 +1256,16 @@ mm_status layout(mm_hierarchy* h, const mm_params* pin, const float* x_init, flo
   MM_TRY(ensure_trace(h, p));
   if (!h->gexec || h->gsingle != (single ? 1 : 0) || !same_schedule(h->gparams, p))
     MM_TRY(build_graph(h, p, single));
-  if (single)
-    MM_CK(cudaMemcpyAsync(h->xb[0], x_init, sizeof(float2) * n0, cudaMemcpyDeviceToDevice, s));
+  if (single) {
+    if (h->ord.perm0)
+      MM_TRY(permute_positions(n0, h->ord.inv0, (const float2*)x_init, h->xb[0], s));
+    else
+      MM_CK(cudaMemcpyAsync(h->xb[0], x_init, sizeof(float2) * n0, cudaMemcpyDeviceToDevice, s));
+  }
   MM_CK(cudaMemsetAsync(h->lsw, 0, sizeof(int32_t) * 2 * MM_MAX_LEVELS, s));
   MM_CK(cudaGraphLaunch(h->gexec, s));
   XSel x{h->xb[0], h->xb[1], &h->state->parity};
-  MM_TRY(copy_current(x, n0, (float2*)x_out, s));
+  MM_TRY(copy_current(x, n0, (float2*)x_out, s, h->ord.perm0));
   SweepState hs;
   int32_t lsw[2 * MM_MAX_LEVELS];
   MM_CK(cudaMemcpyAsync(&hs, h->state, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1470,6 +1556,7 @@ void mm_default_params(mm_params* p) {
   p->traverse_warps = 0;
   p->leaf_size = 16;
   p->bh_group = 1;
+  p->level_order = 1;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1550,7 +1637,9 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   tree_ws_free(h->tree);
   void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart, h->xc,
                   h->box, h->arrive,
-                  h->zero, h->lsw, h->trace};
+                  h->zero, h->lsw, h->trace, h->pbuf[0], h->pbuf[1], h->ord.perm0,
+                  h->ord.inv0, h->ord.rp_user, h->ord.col_user, h->ord.omega_user,
+                  h->ord.elen_user};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -1591,6 +1680,8 @@ mm_status mm_level_export(const mm_hierarchy* h, int32_t level, int64_t* row_ptr
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
   const int nb = ceil_div(L.n + 1, 256);
+  if (level == 0 && h->ord.perm0) return export_level0_user(h, row_ptr, col, omega, c, map,
+                                                           s_ptr, s_col, s_d, rho, s);
   if (row_ptr) i32_to_i64<<<nb, 256, 0, s>>>(L.n + 1, L.rp, row_ptr);
   if (col && L.nnzE) MM_CK(cudaMemcpyAsync(col, L.col, 4 * L.nnzE, cudaMemcpyDeviceToDevice, s));
   if (omega && L.nnzE)
@@ -1616,7 +1707,12 @@ mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha, const float* x_
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
-  XSel x{(const float2*)x_in, (const float2*)x_out, h->zero};
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x_in, 0, s, &cst);
+  MM_TRY(cst);
+  const bool mapped = level == 0 && h->ord.perm0;
+  float2* xo = mapped ? h->pbuf[1] : (float2*)x_out;
+  XSel x{xi, xo, h->zero};
   set_state<<<1, 1, 0, s>>>(h->sstate, alpha);
   MM_CK(cudaGetLastError());
   SchedParams sp = sched_of(h->p, 1 << 30);
@@ -1626,13 +1722,14 @@ mm_status mm_sweep(mm_hierarchy* h, int32_t level, double alpha, const float* x_
   if (L.fused) {
     SmallArgs a = small_args(h, level, h->p.exact_repulsion != 0, h->sstate, sp, nullptr, 0,
                              nullptr, 1);
-    a.b0 = const_cast<float2*>((const float2*)x_in);
-    a.b1 = (float2*)x_out;
+    a.b0 = const_cast<float2*>(xi);
+    a.b1 = xo;
     MM_TRY(small_level(a, s));
   } else {
     MM_TRY(sweep_body(h, level, h->p.exact_repulsion != 0, x, h->sstate, sp, nullptr, 0,
                       nullptr, 0, false, s));
   }
+  MM_TRY(x_out_user(h, level, xo, x_out, s));
   if (stats) {
     SweepState hs;
     MM_CK(cudaMemcpyAsync(&hs, h->sstate, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1660,11 +1757,19 @@ mm_status mm_repulsion(mm_hierarchy* h, int32_t level, const float* x, float the
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int n = h->levels[level].n;
-  XSel xs{(const float2*)x, (const float2*)x, h->zero};
-  if (theta < 0.f) return exact_repulsion(xs, n, (float2*)F_out, s);
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x, 0, s, &cst);
+  MM_TRY(cst);
+  const bool mapped = level == 0 && h->ord.perm0;
+  float2* Fi = mapped ? h->pbuf[1] : (float2*)F_out;
+  XSel xs{xi, xi, h->zero};
+  if (theta < 0.f) {
+    MM_TRY(exact_repulsion(xs, n, Fi, s));
+    return x_out_user(h, level, Fi, F_out, s);
+  }
   MM_TRY(bh_build(xs, n, theta, leaf_of(h->p), h->tree, s, nullptr, true, group_of(h->p)));
-  MM_TRY(bh_traverse(n, h->tree, (float2*)F_out, h->p.traverse_warps, nullptr, s,
-                     h->p.bh_group));
+  MM_TRY(bh_traverse(n, h->tree, Fi, h->p.traverse_warps, nullptr, s, h->p.bh_group));
+  MM_TRY(x_out_user(h, level, Fi, F_out, s));
   return tree_error(h, s);
 }
 
@@ -1686,7 +1791,10 @@ mm_status mm_full_stress(mm_hierarchy* h, const float* x, double* out, void* str
     return MM_ERR_UNSUPPORTED;
   }
   DeviceGuard dg(h->device);
-  return full_stress(L.n, L.rp, L.col, (const float2*)x, out, (cudaStream_t)stream);
+  // the caller's numbering of x matches the caller's CSR
+  const int32_t* rp = h->ord.rp_user ? h->ord.rp_user : L.rp;
+  const int32_t* col = h->ord.rp_user ? h->ord.col_user : L.col;
+  return full_stress(L.n, rp, col, (const float2*)x, out, (cudaStream_t)stream);
 }
 
 mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* F_out,
@@ -1705,10 +1813,18 @@ mm_status mm_repulsion_h(mm_hierarchy* h, int32_t level, const float* x, float* 
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
-  XSel xs{(const float2*)x, (const float2*)x, h->zero};
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x, 0, s, &cst);
+  MM_TRY(cst);
+  const bool mapped = level == 0 && h->ord.perm0;
+  float2* Fi = mapped ? h->pbuf[1] : (float2*)F_out;
+  XSel xs{xi, xi, h->zero};
   // the coarsest level maps to itself: Eq. 3 is then the exact sum
-  if (!L.hmap) return exact_repulsion(xs, L.n, (float2*)F_out, s);
-  return approx_repulsion(L, xs, h->xc, (float2*)F_out, s);
+  if (!L.hmap)
+    MM_TRY(exact_repulsion(xs, L.n, Fi, s));
+  else
+    MM_TRY(approx_repulsion(L, xs, h->xc, Fi, s));
+  return x_out_user(h, level, Fi, F_out, s);
 }
 
 mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init, float* x_out,
@@ -1734,6 +1850,10 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
   const bool exact = h->p.exact_repulsion != 0;
+  // level 0 in the hierarchy's own order (as the layout runs it)
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x, 0, s, &cst);
+  MM_TRY(cst);
   if (L.fused) {
     // fused level kernel: phases from clock64 stamps of one sweep (stage
     // order: stage x, bbox, sort, radix tree, prefix sums, records, walk or
@@ -1752,7 +1872,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
       set_state<<<1, 1, 0, s>>>(h->sstate, 0.3);
       MM_CK(cudaMemsetAsync(prof, 0, 10 * sizeof(long long), s));
       SmallArgs a = small_args(h, level, exact, h->sstate, sp, nullptr, 0, nullptr, 1);
-      a.b0 = const_cast<float2*>((const float2*)x);
+      a.b0 = const_cast<float2*>(xi);
       a.b1 = tmp;
       a.prof = prof;
       st = small_level(a, s);
@@ -1793,7 +1913,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
   MM_CK(cudaMalloc(&tmp, sizeof(float2) * (size_t)std::max(L.n, 1)));
   MM_CK(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
   MM_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
-  XSel xs{(const float2*)x, tmp, h->zero};
+  XSel xs{xi, tmp, h->zero};
   cudaEvent_t ev[9];
   for (auto& e : ev) MM_CK(cudaEventCreate(&e));
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -2219,7 +2339,10 @@ mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x, double al
   }
   DeviceGuard dg(h->device);
   double out[3];
-  MM_TRY(objective_exact(h->levels[level], (const float2*)x, alpha, out, (cudaStream_t)stream));
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x, 0, (cudaStream_t)stream, &cst);
+  MM_TRY(cst);
+  MM_TRY(objective_exact(h->levels[level], xi, alpha, out, (cudaStream_t)stream));
   if (stress) *stress = out[0];
   if (lnsum) *lnsum = out[1];
   if (M) *M = out[2];

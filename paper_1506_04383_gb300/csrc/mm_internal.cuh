@@ -216,6 +216,22 @@ struct Level {
   int32_t nt = 0;
 };
 
+// Hierarchy order (k_order.cu): every level of a library-built hierarchy is
+// renumbered so that clusters are consecutive, in the order of the coarser
+// level.  Level 0's permutation and the caller's level-0 CSR are kept.
+struct LevelOrder {
+  int32_t* perm0 = nullptr;      // [n0] caller's vertex -> internal index
+  int32_t* inv0 = nullptr;       // [n0] internal index -> caller's vertex
+  int32_t* rp_user = nullptr;    // the caller's level-0 CSR, as validated
+  int32_t* col_user = nullptr;
+  float* omega_user = nullptr;
+  float* elen_user = nullptr;
+};
+mm_status renumber_levels(std::vector<Level>& levels, LevelOrder& ord, cudaStream_t s);
+// out[i] = in[idx[i]]
+mm_status permute_positions(int n, const int32_t* idx, const float2* in, float2* out,
+                            cudaStream_t s);
+
 // ----------------------------------------------------------- primitives --
 struct SortWS {
   uint32_t* counts = nullptr;  // [256 * max_tiles]
@@ -407,7 +423,9 @@ mm_status prolong(int n_fine, const int32_t* map, XSel xc, const float* cc, uint
 mm_status level_start(SweepState* st, double alpha0, int flip, cudaStream_t s);
 mm_status init_coarsest(int n, const float* c, const SEnt* s0, uint64_t seed, int level,
                         float R, float2* x0, SweepState* st, double alpha0, cudaStream_t s);
-mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s);
+// out[i] = current position of vertex perm[i] (perm NULL: of vertex i).
+mm_status copy_current(XSel x, int n, float2* out, cudaStream_t s,
+                       const int32_t* perm = nullptr);
 
 // ------------------------------------------------- fused small levels ---
 constexpr int kSmallMaxN = 2048;     // largest level the single-CTA kernel takes

@@ -57,7 +57,8 @@ class Params(ctypes.Structure):
         ("heavy_degree", ctypes.c_int32), ("traverse_warps", ctypes.c_int32),
         ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
         ("leaf_size", ctypes.c_int32), ("bh_group", ctypes.c_int32),
-        ("approx_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("approx_levels", ctypes.c_int32), ("level_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1),
     ]
 
 
