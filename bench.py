@@ -553,7 +553,10 @@ def main():
     # the final objective against the oracle's layout of the same graph
     ovo = None
     if rank == 0 and gp is None and not w.get("dynamic") and not w.get("learned"):
-        ovo = objective_vs_oracle(mm, args.workload, rp, col, kw, xbuf, M)
+        t0 = time.perf_counter()
+        Mb = mm.objective_bh(h, 0, xbuf, 0.008, float(kw.get("theta", 0.5)))[2]
+        mbh = (Mb, (time.perf_counter() - t0) * 1e3)
+        ovo = objective_vs_oracle(mm, args.workload, rp, col, kw, xbuf, M, mbh)
     # the other workloads of the same configuration family
     sides = [side_table(mm, o) for o in w.get("also", ())] if rank == 0 else []
 
@@ -867,7 +870,7 @@ def oracle_golden():
         return json.load(fh)
 
 
-def objective_vs_oracle(mm, wname, rp, col, kw, x_own, M_exact):
+def objective_vs_oracle(mm, wname, rp, col, kw, x_own, M_exact, M_bh=None):
     """Final maxent-stress (Eq. 1 at alpha = 0.008) of the GPU's layouts
     against the FP64 oracle's layout of the same graph (Sec. 3 algorithm on
     the oracle's own hierarchy, stored by tests/golden/make_oracle_layouts.py).
@@ -923,6 +926,10 @@ def objective_vs_oracle(mm, wname, rp, col, kw, x_own, M_exact):
         out["exact_vs_sampled"] = {"M_exact_gpu": M_exact, "M_sampled": e_own["M"],
                                    "se_M": e_own["se_M"],
                                    "z": (M_exact - e_own["M"]) / max(e_own["se_M"], 1e-300)}
+    if M_bh is not None:
+        out["barnes_hut_estimate"] = {"theta": kw.get("theta", 0.5), "M_bh_gpu": M_bh[0],
+                                      "rel_to_exact": (M_bh[0] - M_exact) / abs(M_exact)
+                                      if M_exact else None, "ms": M_bh[1]}
     out["seconds"] = round(time.perf_counter() - t0, 2)
     return out
 

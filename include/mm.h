@@ -488,6 +488,21 @@ mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x,
                        void* stream);
 
 /*
+ * The objective of Eq. 1 with the ln-sum estimated by Barnes-Hut (no exact
+ * O(n^2) pass; for levels too large for mm_objective): every vertex's log
+ * potential sum_{v != u} ln|x_u - x_v| comes from the quadtree walk at
+ * opening parameter theta >= 0 (an accepted cell adds count x ln of the
+ * centroid distance, leaves are exact, coincident points add 0; theta = 0
+ * is the exact sum through the tree), the all-pairs ln-sum is half their
+ * sum, and the stress and the ln-sum over S are exact, as in mm_objective.
+ * x device [2n] positions of `level`; outputs as mm_objective.
+ * Synchronises the stream.
+ */
+mm_status mm_objective_bh(mm_hierarchy* h, int32_t level, const float* x, double alpha,
+                          float theta, double* stress, double* lnsum, double* M,
+                          void* stream);
+
+/*
  * The k-hop pair set S of an arbitrary graph (Sec. 2.3 footnote): for every
  * u, all v != u within k hops (k = 1 or 2), d_uv = the shortest such path
  * with edge length edge_len (or 1) -- or sqrt(c_u) + sqrt(c_v) when node_c is

@@ -94,7 +94,47 @@ __global__ void __launch_bounds__(kT) s_pairs_kernel(const float2* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(kT) sum_phi_kernel(const float* __restrict__ phi, int n,
+                                                     double* partials) {
+  double acc = 0.0;
+  for (int u = blockIdx.x * kT + threadIdx.x; u < n; u += gridDim.x * kT) acc += phi[u];
+  const double b = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
 }  // namespace
+
+// Eq. 1 with the ln-sum over all pairs from per-vertex log potentials
+// Phi[u] = sum_{v != u} ln|x_u - x_v| (a Barnes-Hut estimate): all-pairs
+// ln-sum = (1/2) sum_u Phi[u]; stress and the ln-sum over S exact.
+mm_status objective_from_phi(const Level& L, const float2* x, const float* phi, double alpha,
+                             double out[3], cudaStream_t s) {
+  const int n = L.n;
+  const int pb = std::max(1, std::min(ceil_div(n, kT), num_sms() * 4));
+  const int sb = std::max(1, std::min(ceil_div(n, kT), num_sms() * 4));
+  double* parts = nullptr;
+  MM_CK(cudaMalloc(&parts, sizeof(double) * (size_t)(pb + 2 * sb)));
+  sum_phi_kernel<<<pb, kT, 0, s>>>(phi, n, parts);
+  s_pairs_kernel<<<sb, kT, 0, s>>>(x, n, L.sp, L.s, parts + pb);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> h((size_t)(pb + 2 * sb));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), parts, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(parts);
+  MM_CK(e);
+  double all = 0, stress = 0, lnS = 0;
+  for (int i = 0; i < pb; ++i) all += h[i];
+  all *= 0.5;
+  for (int i = 0; i < sb; ++i) {
+    stress += h[pb + 2 * i];
+    lnS += h[pb + 2 * i + 1];
+  }
+  out[0] = stress;
+  out[1] = all - lnS;
+  out[2] = stress - alpha * (all - lnS);
+  return MM_OK;
+}
 
 mm_status objective_exact(const Level& L, const float2* x, double alpha, double out[3],
                           cudaStream_t s) {

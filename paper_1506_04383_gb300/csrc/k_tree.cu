@@ -671,13 +671,18 @@ __device__ __forceinline__ float rcp_approx(float q) {
 // a zero offset, and the clamped squared distance keeps its term at zero);
 // and the position / offset / accumulator arithmetic is done on packed
 // (x, y) pairs.
-template <bool kCount, bool kSeeding>
+//
+// kPhi: the walk also sums the log potential phi_u = sum_{v != u} ln|x_u - x_v|
+// (the entropy term of Eq. 1) with the same decisions: an accepted cell
+// adds count * ln|x_u - centroid|, a leaf its points exactly, a coincident
+// point 0.
+template <bool kCount, bool kSeeding, bool kPhi = false>
 __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, int pos,
                                           unsigned long long xu, const float2* __restrict__ xs,
                                           const float4* __restrict__ nodeA,
                                           const int4* __restrict__ nodeB, unsigned long long& acc,
                                           int& budget, bool& broken, int* seeds, int& nseeds,
-                                          unsigned& visits, unsigned& inter) {
+                                          unsigned& visits, unsigned& inter, float& phi) {
   const unsigned nodes = 2u * (unsigned)n - 1u;
   const int lane = threadIdx.x & 31;
   const unsigned long long* xp = reinterpret_cast<const unsigned long long*>(xs);
@@ -697,6 +702,7 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
     // count / distance^2 of the accepted cell, 0 when the cell is not taken
     const float s = take ? A.w * rcp_approx(q) : 0.f;
     acc = fma2(pk2(s, s), d, acc);
+    if (kPhi && take) phi = fmaf(0.5f * A.w, __logf(q), phi);
     if (kCount && take) ++inter;
     const bool leaf = !take && B.x < 0;
     if (leaf) {  // uniform: every lane read the same record
@@ -705,8 +711,10 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
       for (int p = pb; p < pe; ++p) {
         const unsigned long long e = sub2(xu, __ldg(&xp[p]));
         const float2 ef = upk2(e);
-        const float r = rcp_approx(fmaxf(fmaf(ef.x, ef.x, ef.y * ef.y), 1e-30f));
+        const float eq = fmaf(ef.x, ef.x, ef.y * ef.y);
+        const float r = rcp_approx(fmaxf(eq, 1e-30f));
         acc = fma2(pk2(r, r), e, acc);
+        if (kPhi) phi += eq > 0.f ? 0.5f * __logf(eq) : 0.f;
       }
       if (kCount) inter += (unsigned)max(pe - pb, 0);
     }
@@ -722,11 +730,11 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
   }
 }
 
-template <bool kCount>
+template <bool kCount, bool kPhi = false>
 __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
     int n, int W, int seed, const float2* __restrict__ xs, const int32_t* __restrict__ vals,
     const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float2* __restrict__ F,
-    unsigned long long* counters, int* err) {
+    unsigned long long* counters, int* err, float* __restrict__ Phi = nullptr) {
   __shared__ GroupShared sh;
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int slot = wb / W, w = wb % W;
@@ -744,17 +752,18 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
   int* seeds = sh.seeds[slot];
   int& nseeds = sh.nseeds[slot];
   unsigned visits = 0, inter = 0;
+  float phi = 0.f;
   int budget = 2 * n + 2;
   bool broken = false;
   if (w == 0 && live) {
     if (lane == 0) nseeds = 0;
     __syncwarp();
     if (W > 1 && seed > 0)
-      vote_walk<kCount, true>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                              budget, broken, seeds, nseeds, visits, inter);
+      vote_walk<kCount, true, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                              budget, broken, seeds, nseeds, visits, inter, phi);
     else
-      vote_walk<kCount, false>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                               budget, broken, seeds, nseeds, visits, inter);
+      vote_walk<kCount, false, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                               budget, broken, seeds, nseeds, visits, inter, phi);
   }
   float2 f = upk2(acc);
   if (W > 1) {
@@ -762,8 +771,8 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
     const int ns = live ? nseeds : 0;
     for (int j = w; j < ns && !broken; j += W) {
       const int c = seeds[j];
-      vote_walk<kCount, false>(c, __ldg(&nodeB[c]).y, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                               budget, broken, seeds, nseeds, visits, inter);
+      vote_walk<kCount, false, kPhi>(c, __ldg(&nodeB[c]).y, n, seed, pos, xu, xs, nodeA, nodeB, acc,
+                               budget, broken, seeds, nseeds, visits, inter, phi);
     }
     f = upk2(acc);
     sh.part[wb][lane] = f;
@@ -776,9 +785,22 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
       }
       f = make_float2(sx, sy);
     }
+    if (kPhi) {
+      __syncthreads();
+      sh.part[wb][lane].x = phi;
+      __syncthreads();
+      if (w == 0) {
+        float sp = 0.f;
+        for (int k = 0; k < W; ++k) sp += sh.part[slot * W + k][lane].x;
+        phi = sp;
+      }
+    }
   }
   if (broken && lane == 0) atomicOr(err, 1);
-  if (w == 0 && valid) F[vals[p0]] = f;
+  if (w == 0 && valid) {
+    F[vals[p0]] = f;
+    if (kPhi) Phi[vals[p0]] = phi;
+  }
   if (kCount) {
     unsigned tot = valid ? inter : 0u;
 #pragma unroll
@@ -971,7 +993,7 @@ mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
     const int seed = W > 1 ? kSeedPoints : 0;
     auto kern = counters ? traverse_vote_kernel<true> : traverse_vote_kernel<false>;
     kern<<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(n, W, seed, ws.xs, ws.vals[0], ws.nodeA,
-                                                      ws.nodeB, F, counters, ws.err);
+                                                      ws.nodeB, F, counters, ws.err, nullptr);
   } else if (counters) {
     traverse_kernel<true><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB,
                                                        F, counters, ws.err);
@@ -979,6 +1001,20 @@ mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
     traverse_kernel<false><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA,
                                                         ws.nodeB, F, nullptr, ws.err);
   }
+  MM_CK(cudaGetLastError());
+  return MM_OK;
+}
+
+mm_status bh_potential(int n, const TreeWS& ws, float2* F, float* Phi, int warps_per_block,
+                       cudaStream_t s) {
+  if (n <= 0) return MM_OK;
+  const int wpb = warps_per_block > 0 ? warps_per_block : 4;
+  const int tasks = ceil_div(n, 32);
+  const int W = std::max(1, std::min(kGroupMaxWarps, wpb));
+  const int tpb = std::max(1, 8 / W);
+  const int seed = W > 1 ? kSeedPoints : 0;
+  traverse_vote_kernel<false, true><<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(
+      n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, nullptr, ws.err, Phi);
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

@@ -2349,6 +2349,37 @@ mm_status mm_objective(mm_hierarchy* h, int32_t level, const float* x, double al
   return MM_OK;
 }
 
+mm_status mm_objective_bh(mm_hierarchy* h, int32_t level, const float* x, double alpha,
+                          float theta, double* stress, double* lnsum, double* M, void* stream) {
+  g_err.clear();
+  MM_TRY(level_check(h, level));
+  if (!x || !(theta >= 0.f)) {
+    set_error("x is NULL or theta < 0");
+    return MM_ERR_INVALID_ARG;
+  }
+  DeviceGuard dg(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mm_status cst;
+  const float2* xi = x_in_internal(h, level, x, 0, s, &cst);
+  MM_TRY(cst);
+  const Level& L = h->levels[level];
+  float* phi = nullptr;
+  MM_CK(cudaMallocAsync(&phi, sizeof(float) * (size_t)std::max(L.n, 1), s));
+  XSel xs{xi, xi, h->zero};
+  // the group walk's decisions (leaf buckets, all 32 points of a task vote)
+  mm_status st = bh_build(xs, L.n, theta, leaf_of(h->p), h->tree, s, nullptr, true, true);
+  if (st == MM_OK) st = bh_potential(L.n, h->tree, h->F, phi, L.walk_warps, s);
+  double out[3] = {0, 0, 0};
+  if (st == MM_OK) st = objective_from_phi(L, xi, phi, alpha, out, s);
+  cudaFreeAsync(phi, s);
+  MM_TRY(st);
+  MM_TRY(tree_error(h, s));
+  if (stress) *stress = out[0];
+  if (lnsum) *lnsum = out[1];
+  if (M) *M = out[2];
+  return MM_OK;
+}
+
 mm_status mm_khop(int32_t n, const int64_t* row_ptr, const int32_t* col, const float* edge_len,
                   const float* node_c, int32_t k, int64_t* s_ptr, int64_t* nnz_S, int32_t* s_col,
                   float* s_d, float* rho, void* stream) {

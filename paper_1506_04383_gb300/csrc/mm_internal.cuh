@@ -363,6 +363,11 @@ constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
 inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
 // Tiled exact sum F[v] = sum_{u != v} r(v, u).
 mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
+// The group walk (bh_group = 1 decisions) over a built tree that also writes
+// Phi[u] = sum_{v != u} ln|x_u - x_v| (accepted cells: count x ln of the
+// centroid distance; leaves exact; coincident points 0), in input order.
+mm_status bh_potential(int n, const TreeWS& ws, float2* F, float* Phi, int warps_per_block,
+                       cudaStream_t s);
 // One block of the sort pass waits on a status word that nothing publishes;
 // *timed_out = 1 when the bounded wait gave up (error bit 2) as it must.
 mm_status lookback_selftest(int spin_limit, int* timed_out, cudaStream_t s);
@@ -560,6 +565,9 @@ mm_status net_adam_step(Net& net, float lr, cudaStream_t s);
 // ------------------------------------------------------------ objective --
 mm_status objective_exact(const Level& L, const float2* x, double alpha, double out[3],
                           cudaStream_t s);
+// As objective_exact, with the all-pairs ln-sum taken as (1/2) sum_u phi[u].
+mm_status objective_from_phi(const Level& L, const float2* x, const float* phi, double alpha,
+                             double out[3], cudaStream_t s);
 
 // ---------------------------------------------------------------- philox --
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 bijection.

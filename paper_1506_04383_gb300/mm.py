@@ -33,7 +33,7 @@ EXPORTS = ["mm_default_params", "mm_status_string", "mm_last_error", "mm_build_h
            "mm_net_forward", "mm_net_gradients", "mm_net_train_step", "mm_hierarchy_set_net",
            "mm_layout_levels", "mm_repulsion_h", "mm_full_stress",
            "mm_selftest_wait_timeout", "mm_measure_fp32_peak", "mm_gemm_bf16_tn",
-           "mm_net_gemm_profile"]
+           "mm_net_gemm_profile", "mm_objective_bh"]
 MM_NET_PARAMS = 17860
 
 
@@ -164,6 +164,7 @@ def load(path: str = LIB_PATH):
     lib.mm_measure_fp32_peak.argtypes = [i32, P, P, P]
     lib.mm_gemm_bf16_tn.argtypes = [i32, i32, P, P, P, P]
     lib.mm_net_gemm_profile.argtypes = [i32, i32, P, P]
+    lib.mm_objective_bh.argtypes = [P, i32, P, f64, f32, P, P, P, P]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("mm_default_params", "mm_free_hierarchy", "mm_status_string",
@@ -451,6 +452,17 @@ def gemm_bf16(A, B, bias=None, relu=False, out_bf16=False, stream=None):
     _check(load().mm_gemm_bf16(M, N, K, _ptr(A), _ptr(B), _ptr(bias), int(relu), _ptr(C),
                                _ptr(Cb), _stream(stream)))
     return (C, Cb) if out_bf16 else C
+
+
+def objective_bh(h: Hierarchy, level: int, x, alpha: float, theta: float, stream=None):
+    """Eq. 1 with the ln-sum from Barnes-Hut log potentials at theta;
+    returns (stress, ln-sum outside S, M)."""
+    x = _dev(x, torch.float32, "x")
+    st, ln, M = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().mm_objective_bh(h.handle, level, _ptr(x), float(alpha), float(theta),
+                                  ctypes.byref(st), ctypes.byref(ln), ctypes.byref(M),
+                                  _stream(stream)))
+    return st.value, ln.value, M.value
 
 
 def gemm_bf16_tn(A, B, stream=None):

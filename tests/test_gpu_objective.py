@@ -84,3 +84,36 @@ def test_del20_same_hierarchy_objective_within_1pct_of_stored_oracle_layout(mm):
     # exact M over all 5.5e11 pairs on the device vs the sampled estimate
     _, _, Mgpu = mm.objective(h, 0, x, 0.008)
     assert abs(Mgpu - est["M"]) <= 5 * est["se_M"], (Mgpu, est["M"], est["se_M"])
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.7])
+def test_barnes_hut_objective_against_the_oracle(mm, theta):
+    # mm_objective_bh: log potentials from the quadtree walk (accepted cells
+    # count x ln of the centroid distance) instead of the O(n^2) pass.  theta = 0
+    # opens every cell: the exact sum, to FP32 rounding (relative 1e-5 of M).
+    # theta > 0: about its centroid a cell's first-order term vanishes, and the
+    # second-order remainder of ln|1 - z| is at most |z|^2 / (2 (1 - |z|)) per
+    # point, |z| = (distance of a point from the centroid) / (distance of the
+    # centroid) <= sqrt(2) w / D < sqrt(2) theta for an accepted cell of side
+    # w (point and centroid both in the cell); so, for sqrt(2) theta < 1,
+    # |lnsum_bh - lnsum| <= pairs x that bound.
+    rp, col, _, _ = graphs.rgg(5000, 8.0, 44)
+    n = len(rp) - 1
+    h = mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(),
+                           mm.default_params(k=2, coarsest_n=100))
+    x, _ = mm.layout(h)
+    xs = x.cpu().numpy().astype(np.float64)
+    S = oracle.build_S(rp, col, 2)
+    so, lo, Mo = oracle.objective(xs, S, 0.008)
+    sb, lb, Mb = mm.objective_bh(h, 0, x, 0.008, theta)
+    assert sb == pytest.approx(so, rel=1e-6)
+    if theta == 0.0:
+        assert Mb == pytest.approx(Mo, rel=1e-5)
+        assert lb == pytest.approx(lo, rel=1e-5)
+    else:
+        z = theta * np.sqrt(2.0)
+        if z < 1.0:
+            bound = n * (n - 1) / 2 * z * z / (2 * (1 - z))
+            assert abs(lb - lo) <= bound
+        # in practice far inside that bound: a few parts in 10^4 of the sum
+        assert abs(lb - lo) <= 1e-3 * abs(lo), (lb, lo)
