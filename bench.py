@@ -376,6 +376,17 @@ def main():
                          "layout at equal objective (single-graph multilevel workloads)")
     ap.add_argument("--batch-compare", type=int, default=64,
                     help="graphs of the batch also laid out one by one for comparison")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="0: skip the oracle comparison, the second workloads and the "
+                         "level-by-level breakdown (a shorter run, e.g. for a launch list)")
+    ap.add_argument("--profile-level", type=int, default=-1,
+                    help="profiling aid (e.g. under ncu): build the workload's hierarchy, run "
+                         "one profiled sweep (mm_sweep_profile, 2 repetitions) of this level "
+                         "from uniform positions of the layout's scale, print its stage times "
+                         "and exit")
+    ap.add_argument("--profile-gemm", type=int, default=0,
+                    help="profiling aid: one launch each of the learned prolongation's two "
+                         "tensor-core kernels on this many vertices (after a warm-up), then exit")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -399,8 +410,26 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.profile_gemm > 0:
+        f_ms, b_ms = mm.net_gemm_profile(args.profile_gemm, reps=1)
+        print(json.dumps({"profile_gemm": args.profile_gemm, "layer_product_ms": f_ms,
+                          "weight_gradient_ms": b_ms}), flush=True)
+        return 0
     made = make_graph(w)
     rp, col = made[0], made[1]
+    if args.profile_level >= 0:
+        from paper_1506_04383_gb300 import graphs
+        hp = mm.build_hierarchy(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(),
+                                mm.default_params(**params_of(mm, w)))
+        lv = min(args.profile_level, hp.levels() - 1)
+        nl = hp.level_info(lv)[0]
+        xl = torch.from_numpy(graphs.uniform_positions(nl, 7, 0.0, math.sqrt(nl))
+                              .astype(np.float32)).cuda()
+        pr = mm.sweep_profile(hp, lv, xl, reps=2)
+        print(json.dumps({"profile_level": lv, "n": nl, "stage_ms": dict(zip(
+            pr["stage_names"], pr["stage_ms"])), "visits": pr["visits"],
+            "interactions": pr["interactions"], "nnz_S": pr["nnz_S"]}), flush=True)
+        return 0
     gp = made[2] if len(made) > 2 else None
     n = len(rp) - 1
     kw = params_of(mm, w)
@@ -512,7 +541,7 @@ def main():
         prof = mm.sweep_profile(h, 0, xbuf, reps=10)
         roof = roofline(prof, peaks, src, clk_sum, n, exact=bool(w.get("exact")),
                         workload=args.workload, fp32=fp32)
-        if not w.get("single"):
+        if not w.get("single") and args.extras:
             breakdown = layout_breakdown(mm, h, p, stats[-1], peaks, src, fp32_tf)
     else:
         big = int(np.argmax(np.diff(gp)))
@@ -552,13 +581,15 @@ def main():
 
     # the final objective against the oracle's layout of the same graph
     ovo = None
-    if rank == 0 and gp is None and not w.get("dynamic") and not w.get("learned"):
+    if (args.extras and rank == 0 and gp is None and not w.get("dynamic")
+            and not w.get("learned")):
         t0 = time.perf_counter()
         Mb = mm.objective_bh(h, 0, xbuf, 0.008, float(kw.get("theta", 0.5)))[2]
         mbh = (Mb, (time.perf_counter() - t0) * 1e3)
         ovo = objective_vs_oracle(mm, args.workload, rp, col, kw, xbuf, M, mbh)
     # the other workloads of the same configuration family
-    sides = [side_table(mm, o) for o in w.get("also", ())] if rank == 0 else []
+    sides = ([side_table(mm, o) for o in w.get("also", ())]
+             if rank == 0 and args.extras else [])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

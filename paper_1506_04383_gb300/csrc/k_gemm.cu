@@ -406,7 +406,11 @@ __global__ void sum_parts_kernel(int parts, int m, const float* __restrict__ par
 }
 }  // namespace
 
-int gemm_tn_parts(int n) { return std::max(1, std::min(num_sms(), ceil_div(n, kTnChunk))); }
+// Three CTAs per SM (24 KB of shared memory and 64 TMEM columns each) keep
+// enough operand loads in flight; at most kNetParts partials.
+int gemm_tn_parts(int n) {
+  return std::max(1, std::min(std::min(3 * num_sms(), kNetParts), ceil_div(n, kTnChunk)));
+}
 
 mm_status gemm_tn_bf16(const void* A, int n, int R, const void* B, float* out, float* part,
                        int* err, cudaStream_t s) {

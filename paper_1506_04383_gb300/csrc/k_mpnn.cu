@@ -508,7 +508,7 @@ mm_status net_backward(Net& net, const NetSample& smp, cudaStream_t s) {
         n * kH, net.dH, (const __nv_bfloat16*)net.H[l], (__nv_bfloat16*)net.dZb, net.dZ);
     // dW_l = Hcat^T dZ on the tensor cores (BF16 operands, FP32 accumulation
     // per vertex range, partials added in a fixed order); db_l = sum dZ
-    const int tparts = std::max(1, std::min(std::min(kNetParts, num_sms()), ceil_div(n, 64)));
+    const int tparts = gemm_tn_parts(n);
     MM_TRY(gemm_tn_partials(net.Hc, n, R, net.dZb, net.part, tparts, net.err, s));
     net_reduce_parts<<<ceil_div(R * kH, 256), 256, 0, s>>>(tparts, R * kH, net.part,
                                                            net.G + off[2 * l]);
