@@ -947,6 +947,11 @@ mm_status gather_config(Level& L, const mm_params& p, cudaStream_t s) {
   MM_CK(cudaStreamSynchronize(s));
   L.n_heavy = h[0];
   L.max_deg = h[1];
+  // the sums over S on a parallel branch of the sweep pay off where they
+  // are a large part of it (hubs, long rows); otherwise the extra update
+  // launch costs what the overlap saves (measured: R-MAT 2^20 -20 %,
+  // Delaunay 2^20 and the 100k RGG unchanged)
+  L.split_gather = L.n_heavy > 0 || avg >= 24.0;
   return MM_OK;
 }
 

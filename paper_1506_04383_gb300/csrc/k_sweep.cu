@@ -223,14 +223,21 @@ __device__ void update_tail(float s_dx, float s_x, float s_st, const Box& box, f
 }
 
 // G lanes per vertex; rows with more than `heavy` entries are skipped here.
-template <int G>
+// kMode 0: the whole update (sum over S_u, new position, reductions).
+// kMode 1: only the sum over S_u, stored per vertex in acc/acc_st (it needs
+//   nothing but x, so it can run beside the tree build and the walk).
+// kMode 2: the rest of the update from acc/acc_st.  Grid, vertex-to-thread
+//   assignment and arithmetic are those of kMode 0, so modes 1 + 2 give
+//   bit-identical positions, partial sums and schedule steps.
+template <int G, int kMode>
 __global__ void __launch_bounds__(kGatherThreads) gather_light(
     int n, const int32_t* __restrict__ sp, const SEnt* __restrict__ S,
     const float* __restrict__ rho, XSel xs, const float2* __restrict__ F,
-    const SweepState* st, int heavy, float4* partials, int nparts, int epi, SweepEpilogue ep) {
+    const SweepState* st, int heavy, float4* partials, int nparts, int epi, SweepEpilogue ep,
+    float4* __restrict__ acc, float* __restrict__ acc_st) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
-  const float alpha = (float)st->alpha;
+  const float alpha = kMode == 1 ? 0.f : (float)st->alpha;
   constexpr int kGroups = kGatherThreads / G;
   const int g = threadIdx.x / G, lg = threadIdx.x % G;
   float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
@@ -245,10 +252,10 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
       if (e - b <= heavy) {
         mine = true;
         xu = x[u];
-        accumulate_row<G>(a, xu, S, b, e, lg, x);
+        if (kMode != 2) accumulate_row<G>(a, xu, S, b, e, lg, x);
       }
     }
-    if (G > 1) {
+    if (kMode != 2 && G > 1) {
 #pragma unroll
       for (int o = G / 2; o; o >>= 1) {
         a.gx += __shfl_xor_sync(0xffffffffu, a.gx, o);
@@ -258,20 +265,32 @@ __global__ void __launch_bounds__(kGatherThreads) gather_light(
         a.st += __shfl_xor_sync(0xffffffffu, a.st, o);
       }
     }
-    if (mine && lg == 0) finish_vertex(u, a, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
+    if (mine && lg == 0) {
+      if (kMode == 1) {
+        acc[u] = make_float4(a.gx, a.gy, a.sx, a.sy);
+        acc_st[u] = a.st;
+      } else {
+        if (kMode == 2) {
+          const float4 q = acc[u];
+          a = RowAcc{q.x, q.y, q.z, q.w, acc_st[u]};
+        }
+        finish_vertex(u, a, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
+      }
+    }
   }
-  update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, 0, nparts, epi, ep);
+  if (kMode != 1) update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, 0, nparts, epi, ep);
 }
 
-// One block per heavy row (power-law hubs).
+// One block per heavy row (power-law hubs); kMode as for gather_light.
+template <int kMode>
 __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
     const int32_t* __restrict__ heavy_list, int n_heavy, const int32_t* __restrict__ sp,
     const SEnt* __restrict__ S, const float* __restrict__ rho, XSel xs,
     const float2* __restrict__ F, const SweepState* st, float4* partials, int part_off,
-    int nparts, int epi, SweepEpilogue ep) {
+    int nparts, int epi, SweepEpilogue ep, float4* __restrict__ acc, float* __restrict__ acc_st) {
   const float2* x = xs.cur();
   float2* xo = xs.next();
-  const float alpha = (float)st->alpha;
+  const float alpha = kMode == 1 ? 0.f : (float)st->alpha;
   __shared__ float red[5][kGatherThreads / 32];
   float s_dx = 0.f, s_x = 0.f, s_st = 0.f;
   Box box;
@@ -279,6 +298,14 @@ __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
   for (int h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const int u = heavy_list[h];
     const float2 xu = x[u];
+    if (kMode == 2) {
+      if (threadIdx.x == 0) {
+        const float4 q = acc[u];
+        const RowAcc t = {q.x, q.y, q.z, q.w, acc_st[u]};
+        finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
+      }
+      continue;
+    }
     RowAcc a = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = sp[u] + threadIdx.x; k < sp[u + 1]; k += blockDim.x) accumulate(a, xu, S[k], x);
 #pragma unroll
@@ -300,11 +327,17 @@ __global__ void __launch_bounds__(kGatherThreads) gather_heavy(
         t.gx += red[0][w]; t.gy += red[1][w]; t.sx += red[2][w];
         t.sy += red[3][w]; t.st += red[4][w];
       }
-      finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
+      if (kMode == 1) {
+        acc[u] = make_float4(t.gx, t.gy, t.sx, t.sy);
+        acc_st[u] = t.st;
+      } else {
+        finish_vertex(u, t, xu, alpha, rho, F, xo, s_dx, s_x, s_st, box);
+      }
     }
     __syncthreads();
   }
-  update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, part_off, nparts, epi, ep);
+  if (kMode != 1)
+    update_tail<kGatherThreads>(s_dx, s_x, s_st, box, partials, part_off, nparts, epi, ep);
 }
 
 constexpr int kCtlThreads = 256;
@@ -393,11 +426,43 @@ __global__ void copy_current_kernel(XSel xs, int n, const int32_t* __restrict__ 
   if (i < n) out[i] = xs.cur()[perm ? perm[i] : i];
 }
 
-template <int G>
+template <int G, int kMode>
 void launch_light(const Level& L, XSel x, const float2* F, const SweepState* st, float4* partials,
-                  int blocks, int nparts, int epi, const SweepEpilogue& ep, cudaStream_t s) {
-  gather_light<G><<<blocks, kGatherThreads, 0, s>>>(L.n, L.sp, L.s, L.rho, x, F, st,
-                                                    L.heavy_degree, partials, nparts, epi, ep);
+                  int blocks, int nparts, int epi, const SweepEpilogue& ep, float4* acc,
+                  float* acc_st, cudaStream_t s) {
+  gather_light<G, kMode><<<blocks, kGatherThreads, 0, s>>>(L.n, L.sp, L.s, L.rho, x, F, st,
+                                                           L.heavy_degree, partials, nparts, epi,
+                                                           ep, acc, acc_st);
+}
+
+template <int kMode>
+mm_status launch_gather(const Level& L, XSel x, const float2* F, const SweepState* st,
+                        float4* partials, const SweepEpilogue* epi, float4* acc, float* acc_st,
+                        cudaStream_t s) {
+  const int lb = gather_light_blocks(L);
+  const int hb = gather_heavy_blocks(L);
+  const int nparts = lb + hb;
+  SweepEpilogue ep{};
+  if (epi) ep = *epi;
+  // the epilogue runs in the last launch of the update
+  const int epi_light = epi && hb == 0 ? 1 : 0;
+  switch (L.lanes) {
+    case 1: launch_light<1, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    case 2: launch_light<2, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    case 4: launch_light<4, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    case 8: launch_light<8, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    case 16: launch_light<16, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    case 32: launch_light<32, kMode>(L, x, F, st, partials, lb, nparts, epi_light, ep, acc, acc_st, s); break;
+    default:
+      set_error("unsupported lanes per vertex %d", L.lanes);
+      return MM_ERR_INVALID_ARG;
+  }
+  if (hb > 0)
+    gather_heavy<kMode><<<hb, kGatherThreads, 0, s>>>(L.heavy, L.n_heavy, L.sp, L.s, L.rho, x, F,
+                                                      st, partials, lb, nparts, epi ? 1 : 0, ep,
+                                                      acc, acc_st);
+  MM_CK(cudaGetLastError());
+  return MM_OK;
 }
 
 }  // namespace
@@ -416,29 +481,20 @@ int gather_blocks(const Level& L) { return gather_light_blocks(L) + gather_heavy
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
                         float4* partials, cudaStream_t s, const SweepEpilogue* epi) {
   if (L.n <= 0) return MM_OK;
-  const int lb = gather_light_blocks(L);
-  const int hb = gather_heavy_blocks(L);
-  const int nparts = lb + hb;
-  SweepEpilogue ep{};
-  if (epi) ep = *epi;
-  // the epilogue runs in the last launch of the update
-  const int epi_light = epi && hb == 0 ? 1 : 0;
-  switch (L.lanes) {
-    case 1: launch_light<1>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    case 2: launch_light<2>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    case 4: launch_light<4>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    case 8: launch_light<8>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    case 16: launch_light<16>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    case 32: launch_light<32>(L, x, F, st, partials, lb, nparts, epi_light, ep, s); break;
-    default:
-      set_error("unsupported lanes per vertex %d", L.lanes);
-      return MM_ERR_INVALID_ARG;
-  }
-  if (hb > 0)
-    gather_heavy<<<hb, kGatherThreads, 0, s>>>(L.heavy, L.n_heavy, L.sp, L.s, L.rho, x, F, st,
-                                               partials, lb, nparts, epi ? 1 : 0, ep);
-  MM_CK(cudaGetLastError());
-  return MM_OK;
+  return launch_gather<0>(L, x, F, st, partials, epi, nullptr, nullptr, s);
+}
+
+mm_status gather_sum(const Level& L, XSel x, float4* acc, float* acc_st, cudaStream_t s) {
+  if (L.n <= 0) return MM_OK;
+  return launch_gather<1>(L, x, nullptr, nullptr, nullptr, nullptr, acc, acc_st, s);
+}
+
+mm_status update_from_sum(const Level& L, XSel x, const float2* F, const float4* acc,
+                          const float* acc_st, const SweepState* st, float4* partials,
+                          cudaStream_t s, const SweepEpilogue* epi) {
+  if (L.n <= 0) return MM_OK;
+  return launch_gather<2>(L, x, F, st, partials, epi, const_cast<float4*>(acc),
+                          const_cast<float*>(acc_st), s);
 }
 
 mm_status controller(int nblocks, const float4* partials, SweepState* st, SchedParams sp,

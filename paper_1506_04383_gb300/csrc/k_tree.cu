@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(kSortThreads) morton_hist_kernel(
 // err[0] |= 2 and treats the missing tile as empty, so the kernel always
 // finishes; every scatter stays inside [0, n) either way.
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookback = 8;  // status words read per look-back step
 
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
@@ -233,22 +234,42 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass(
     }
     uint32_t excl = 0;
     if (tile > 0) {
+      // the status words of the kLookback nearest preceding tiles are read
+      // together (independent loads), then added from the nearest back to
+      // the first inclusive prefix; a word not yet published stops the
+      // window and is polled again.  Walking back one tile per load would
+      // make the last tile wait about (tiles x load latency).
       int t = tile - 1;
       int spins = 0;
-      while (t >= 0) {
-        const unsigned long long w = vst[(size_t)t * 256 + d];
-        const uint32_t flag = (uint32_t)(w >> 30) & 3u;
-        if ((w & 0xffffffff00000000ull) != ep || flag == 0) {
+      bool done = false;
+      while (!done) {
+        unsigned long long w[kLookback];
+#pragma unroll
+        for (int k = 0; k < kLookback; ++k)
+          w[k] = t - k >= 0 ? vst[(size_t)(t - k) * 256 + d] : 0ull;
+        int used = 0;
+        bool stop = false;
+#pragma unroll
+        for (int k = 0; k < kLookback; ++k) {
+          if (stop) continue;
+          const uint32_t flag = (uint32_t)(w[k] >> 30) & 3u;
+          if (t - k < 0 || (w[k] & 0xffffffff00000000ull) != ep || flag == 0) {
+            stop = true;
+            continue;
+          }
+          excl += (uint32_t)(w[k] & 0x3fffffffull);
+          used = k + 1;
+          if (flag == 2) done = stop = true;
+        }
+        if (done) break;
+        t -= used;
+        if (used == 0) {
           if (++spins > spin_limit) {
             atomicOr(err, 2);
             break;
           }
           __nanosleep(32);
-          continue;
         }
-        excl += (uint32_t)(w & 0x3fffffffull);
-        if (flag == 2) break;
-        --t;
       }
       __threadfence();
       vst[(size_t)tile * 256 + d] = ep | (2ull << 30) | (excl + cnt);
@@ -329,76 +350,89 @@ __global__ void karras_kernel(const uint32_t* __restrict__ k, int n, int32_t* lo
   if (i < n - 1) karras_node(k, n, i, lo, hi, left, right, delta, owner, parent);
 }
 
-// Per tile of kSortThreads * IPT sorted positions: the FP64 inclusive prefix
-// sums of the sorted positions within the tile (the tile total goes to
-// tile_sum).
+// Position sums in fixed point: a coordinate becomes (v - v0) * 2^32 / side
+// (v0, side: the root square), an integer below 2^32 that keeps every bit of
+// the FP32 difference; up to 2^31 of them add up exactly in 64 bits, in any
+// order, at full integer rate (FP64 runs at a small fraction of the FP32
+// rate on this GPU).  A cell's centroid is the difference of two prefix sums
+// over its sorted range, divided by its count.
+__device__ __forceinline__ unsigned long long fixq(float v, float v0, float scale) {
+  const float f = fminf(fmaxf((v - v0) * scale, 0.f), 4294967040.f);  // largest float < 2^32
+  return (unsigned long long)(uint32_t)f;
+}
+
+// Per tile of kSortThreads * IPT sorted positions: the inclusive fixed-point
+// prefix sums within the tile (the tile total goes to tile_sum).
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) scan_xs_kernel(
-    XSel xs, const int32_t* __restrict__ vals, int n, float2* __restrict__ xsorted,
-    double2* __restrict__ incl, double2* __restrict__ tile_sum) {
+    XSel xs, const int32_t* __restrict__ vals, int n, const float4* __restrict__ root,
+    float2* __restrict__ xsorted, ulonglong2* __restrict__ incl,
+    ulonglong2* __restrict__ tile_sum) {
   const int base = blockIdx.x * (kSortThreads * IPT) + threadIdx.x * IPT;
   const float2* x = xs.cur();
-  float2 v[IPT];
-  double sx = 0.0, sy = 0.0;
+  const float4 r = *root;
+  const float scale = r.w * 65536.f;  // 2^32 / side
+  unsigned long long qx[IPT], qy[IPT];
+  unsigned long long sx = 0, sy = 0;
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const int i = base + j;
-    v[j] = make_float2(0.f, 0.f);
+    qx[j] = qy[j] = 0;
     if (i < n) {
-      v[j] = x[vals[i]];
-      xsorted[i] = v[j];
+      const float2 v = x[vals[i]];
+      xsorted[i] = v;
+      qx[j] = fixq(v.x, r.x, scale);
+      qy[j] = fixq(v.y, r.y, scale);
     }
-    sx += v[j].x;
-    sy += v[j].y;
+    sx += qx[j];
+    sy += qy[j];
   }
   // block exclusive scan of the per-thread sums
-  __shared__ double shx[kSortThreads / 32], shy[kSortThreads / 32];
+  __shared__ unsigned long long shx[kSortThreads / 32], shy[kSortThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double ix = sx, iy = sy;
+  unsigned long long ix = sx, iy = sy;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double tx = __shfl_up_sync(0xffffffffu, ix, o);
-    const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+    const unsigned long long tx = __shfl_up_sync(0xffffffffu, ix, o);
+    const unsigned long long ty = __shfl_up_sync(0xffffffffu, iy, o);
     if (lane >= o) { ix += tx; iy += ty; }
   }
   if (lane == 31) { shx[warp] = ix; shy[warp] = iy; }
   __syncthreads();
-  double wx = 0.0, wy = 0.0;
-  for (int w = 0; w < warp; ++w) { wx += shx[w]; wy += shy[w]; }
-  double rx = wx + ix - sx, ry = wy + iy - sy;
+  unsigned long long rx = ix - sx, ry = iy - sy;
+  for (int w = 0; w < warp; ++w) { rx += shx[w]; ry += shy[w]; }
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    rx += v[j].x;
-    ry += v[j].y;
-    if (base + j < n) incl[base + j] = make_double2(rx, ry);
+    rx += qx[j];
+    ry += qy[j];
+    if (base + j < n) incl[base + j] = make_ulonglong2(rx, ry);
   }
-  if (threadIdx.x == kSortThreads - 1) tile_sum[blockIdx.x] = make_double2(rx, ry);
+  if (threadIdx.x == kSortThreads - 1) tile_sum[blockIdx.x] = make_ulonglong2(rx, ry);
 }
 
 // Exclusive scan of the tile totals (one block).
-__global__ void __launch_bounds__(1024) tile_scan_kernel(double2* tile_sum, int tiles) {
-  __shared__ double shx[32], shy[32];
+__global__ void __launch_bounds__(1024) tile_scan_kernel(ulonglong2* tile_sum, int tiles) {
+  __shared__ unsigned long long shx[32], shy[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = (tiles + blockDim.x - 1) / blockDim.x;
   const int beg = threadIdx.x * per, end = min(beg + per, tiles);
-  double sx = 0.0, sy = 0.0;
+  unsigned long long sx = 0, sy = 0;
   for (int i = beg; i < end; ++i) { sx += tile_sum[i].x; sy += tile_sum[i].y; }
-  double ix = sx, iy = sy;
+  unsigned long long ix = sx, iy = sy;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double tx = __shfl_up_sync(0xffffffffu, ix, o);
-    const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+    const unsigned long long tx = __shfl_up_sync(0xffffffffu, ix, o);
+    const unsigned long long ty = __shfl_up_sync(0xffffffffu, iy, o);
     if (lane >= o) { ix += tx; iy += ty; }
   }
   if (lane == 31) { shx[warp] = ix; shy[warp] = iy; }
   __syncthreads();
-  double wx = 0.0, wy = 0.0;
-  for (int w = 0; w < warp; ++w) { wx += shx[w]; wy += shy[w]; }
-  double run_x = wx + ix - sx, run_y = wy + iy - sy;
+  unsigned long long run_x = ix - sx, run_y = iy - sy;
+  for (int w = 0; w < warp; ++w) { run_x += shx[w]; run_y += shy[w]; }
   __syncthreads();
   for (int i = beg; i < end; ++i) {
-    const double2 c = tile_sum[i];
-    tile_sum[i] = make_double2(run_x, run_y);
+    const ulonglong2 c = tile_sum[i];
+    tile_sum[i] = make_ulonglong2(run_x, run_y);
     run_x += c.x;
     run_y += c.y;
   }
@@ -426,13 +460,13 @@ __device__ __forceinline__ int escape_of(const TreeView& t, int h) {
   return resolve(t, t.right[t.owner[h]]);
 }
 
-__device__ void write_record(const TreeView& t, int id, double2 sum, float side, float theta,
+__device__ void write_record(const TreeView& t, int id, float2 c, float side, float theta,
                              int leaf, int maxdepth, float4* nodeA, int4* nodeB) {
   const int n = t.n;
   if (id >= n - 1) {  // leaf j
     const int j = id - (n - 1);
     if (n > 1 && t.delta[t.parent[id]] >= 32) return;  // inside a bucket
-    nodeA[id] = make_float4((float)sum.x, (float)sum.y, 0.f, 1.f);
+    nodeA[id] = make_float4(c.x, c.y, 0.f, 1.f);
     nodeB[id] = make_int4(-1, escape_of(t, j), j, j + 1);
     return;
   }
@@ -454,23 +488,24 @@ __device__ void write_record(const TreeView& t, int id, double2 sum, float side,
   const float cnt = (float)(b - a + 1);
   const float w = ldexpf(side, -depth);
   const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
-  // the FP64 sum is rounded once to FP32, the division is FP32
-  nodeA[id] = make_float4((float)sum.x / cnt, (float)sum.y / cnt, rc, cnt);
+  nodeA[id] = make_float4(c.x, c.y, rc, cnt);
   nodeB[id] = make_int4(first, escape_of(t, b), a, b + 1);
 }
 
-// Sum of the sorted positions [0, k): tile offset + inclusive sum in tile.
-__device__ __forceinline__ double2 prefix_at(const double2* __restrict__ incl,
-                                             const double2* __restrict__ tile_off, int tile,
-                                             int k) {
-  if (k == 0) return make_double2(0.0, 0.0);
-  const double2 a = tile_off[(k - 1) / tile];
-  const double2 b = incl[k - 1];
-  return make_double2(a.x + b.x, a.y + b.y);
+// Fixed-point sum of the sorted positions [0, k): tile offset + inclusive
+// sum in the tile.
+__device__ __forceinline__ ulonglong2 prefix_at(const ulonglong2* __restrict__ incl,
+                                                const ulonglong2* __restrict__ tile_off,
+                                                int tile, int k) {
+  if (k == 0) return make_ulonglong2(0, 0);
+  const ulonglong2 a = tile_off[(k - 1) / tile];
+  const ulonglong2 b = incl[k - 1];
+  return make_ulonglong2(a.x + b.x, a.y + b.y);
 }
 
 // Node-parallel records: a cell's position sum is the difference of two
-// prefix sums over its sorted range.
+// prefix sums over its sorted range (exact integers); the centroid is that
+// sum over the count, mapped back from fixed point in FP32.
 // kFold: tile_off holds the raw tile totals (no tile scan ran) and every
 // block scans them itself (few tiles: cheaper than one more launch): lane l
 // of warp 0 adds a run of kFoldTiles / 32 consecutive tiles, a warp scan
@@ -479,34 +514,34 @@ constexpr int kFoldTiles = 256;
 
 template <bool kFold>
 __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
-                               const double2* __restrict__ incl,
-                               const double2* __restrict__ tile_off, int tile,
+                               const ulonglong2* __restrict__ incl,
+                               const ulonglong2* __restrict__ tile_off, int tile,
                                const float4* __restrict__ root, float theta, int leaf,
                                int maxdepth, float4* nodeA, int4* nodeB) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
   if (kFold) {
     constexpr int kPer = kFoldTiles / 32;
-    __shared__ double2 off[kFoldTiles];
+    __shared__ ulonglong2 off[kFoldTiles];
     const int tiles = (n + tile - 1) / tile;
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x, b0 = lane * kPer;
-      double sx = 0.0, sy = 0.0;
+      unsigned long long sx = 0, sy = 0;
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
         if (b0 + q < tiles) { sx += tile_off[b0 + q].x; sy += tile_off[b0 + q].y; }
-      double ix = sx, iy = sy;
+      unsigned long long ix = sx, iy = sy;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const double tx = __shfl_up_sync(0xffffffffu, ix, o);
-        const double ty = __shfl_up_sync(0xffffffffu, iy, o);
+        const unsigned long long tx = __shfl_up_sync(0xffffffffu, ix, o);
+        const unsigned long long ty = __shfl_up_sync(0xffffffffu, iy, o);
         if (lane >= o) { ix += tx; iy += ty; }
       }
-      double rx = ix - sx, ry = iy - sy;
+      unsigned long long rx = ix - sx, ry = iy - sy;
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
         if (b0 + q < tiles) {
-          off[b0 + q] = make_double2(rx, ry);
+          off[b0 + q] = make_ulonglong2(rx, ry);
           rx += tile_off[b0 + q].x;
           ry += tile_off[b0 + q].y;
         }
@@ -515,16 +550,23 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
     tile_off = off;
   }
   if (id >= 2 * n - 1) return;
-  double2 sum;
+  const float4 r = *root;
+  float2 c;
   if (id >= n - 1) {
-    const float2 p = xsorted[id - (n - 1)];
-    sum = make_double2(p.x, p.y);
+    c = xsorted[id - (n - 1)];
   } else {
-    const double2 a = prefix_at(incl, tile_off, tile, t.lo[id]);
-    const double2 b = prefix_at(incl, tile_off, tile, t.hi[id] + 1);
-    sum = make_double2(b.x - a.x, b.y - a.y);
+    const int lo = t.lo[id], hi = t.hi[id];
+    const ulonglong2 a = prefix_at(incl, tile_off, tile, lo);
+    const ulonglong2 b = prefix_at(incl, tile_off, tile, hi + 1);
+    const float cnt = (float)(hi - lo + 1);
+    const float scale = r.w * 65536.f;
+    c = make_float2(r.x, r.y);  // all points coincide (side 0): the corner is each
+    if (scale > 0.f) {
+      c.x = r.x + ((float)(b.x - a.x) / cnt) / scale;
+      c.y = r.y + ((float)(b.y - a.y) / cnt) / scale;
+    }
   }
-  write_record(t, id, sum, root->z, theta, leaf, maxdepth, nodeA, nodeB);
+  write_record(t, id, c, r.z, theta, leaf, maxdepth, nodeA, nodeB);
 }
 
 // Guards: node ids must stay in [0, 2n-1) and a walk visits each node at
@@ -863,8 +905,8 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&ws.delta, sizeof(int32_t) * N, s));
   MM_CK(cudaMallocAsync(&ws.owner, sizeof(int32_t) * N, s));
   MM_CK(cudaMallocAsync(&ws.parent, sizeof(int32_t) * 2 * N, s));
-  MM_CK(cudaMallocAsync(&ws.incl, sizeof(double2) * N, s));
-  MM_CK(cudaMallocAsync(&ws.tile_sum, sizeof(double2) * tiles, s));
+  MM_CK(cudaMallocAsync(&ws.incl, sizeof(ulonglong2) * N, s));
+  MM_CK(cudaMallocAsync(&ws.tile_sum, sizeof(ulonglong2) * tiles, s));
   MM_CK(cudaMallocAsync(&ws.status, sizeof(unsigned long long) * tree_status_words(N), s));
   MM_CK(cudaMemsetAsync(ws.status, 0, sizeof(unsigned long long) * tree_status_words(N), s));
   MM_CK(cudaMallocAsync(&ws.hist, sizeof(uint32_t) * 4 * 256, s));
@@ -957,7 +999,8 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
                      : ipt == 4 ? scan_xs_kernel<4>
                      : ipt == 2 ? scan_xs_kernel<2>
                                 : scan_xs_kernel<1>;
-  scan_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.xs, ws.incl, ws.tile_sum);
+  scan_kernel<<<tiles, kSortThreads, 0, s>>>(x, ws.vals[0], n, ws.root, ws.xs, ws.incl,
+                                             ws.tile_sum);
   const bool fold = tiles <= kFoldTiles;
   if (!fold) tile_scan_kernel<<<1, 1024, 0, s>>>(ws.tile_sum, tiles);
   if (ws.aux) {

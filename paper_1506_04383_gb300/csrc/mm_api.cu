@@ -49,6 +49,11 @@ struct mm_hierarchy {
   float4* xc = nullptr;              // Eq. 3 midpoints and counts (approx_levels > 0)
   float4* box = nullptr;             // [kMaxGatherBlocks] update-block boxes
   unsigned* arrive = nullptr;        // update epilogue arrival counter
+  // Eq. 2's sums over S, computed on a parallel branch of each sweep
+  float4* gacc = nullptr;            // [n0] weighted targets and r(u,v) sums per vertex
+  float* gacc_st = nullptr;          // [n0] stress terms per vertex
+  cudaStream_t gs = nullptr;         // stream of that branch
+  cudaEvent_t gfork = nullptr, gjoin = nullptr;
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
   int32_t* lsw = nullptr;            // [2 MM_MAX_LEVELS] sweeps, last rel. change per level
   float* trace = nullptr;
@@ -301,10 +306,20 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   } else if (approx) {
     MM_TRY(approx_repulsion(L, x, h->xc, h->F, s));
   } else {
+    // the sums over S_u need only x: on levels where they are heavy, a
+    // parallel branch beside the tree build and the walk, joined before the
+    // update
+    if (L.split_gather) {
+      MM_CK(cudaEventRecord(h->gfork, s));
+      MM_CK(cudaStreamWaitEvent(h->gs, h->gfork, 0));
+      MM_TRY(gather_sum(L, x, h->gacc, h->gacc_st, h->gs));
+      MM_CK(cudaEventRecord(h->gjoin, h->gs));
+    }
     MM_TRY(bh_build(x, L.n, h->p.theta, leaf_of(h->p), h->tree, s, nullptr, !in_loop,
                     group_of(h->p)));
     MM_TRY(bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                        nullptr, s, h->p.bh_group));
+    if (L.split_gather) MM_CK(cudaStreamWaitEvent(s, h->gjoin, 0));
   }
   SweepEpilogue ep{};
   ep.st = st;
@@ -322,7 +337,10 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
     ep.counters = h->tree.counters;
     ep.tree_ticket = h->tree.ticket;
   }
-  MM_TRY(gather_update(L, x, h->F, st, h->partials, s, &ep));
+  if (exact || approx || !L.split_gather)
+    MM_TRY(gather_update(L, x, h->F, st, h->partials, s, &ep));
+  else
+    MM_TRY(update_from_sum(L, x, h->F, h->gacc, h->gacc_st, st, h->partials, s, &ep));
   return MM_OK;
 }
 
@@ -811,6 +829,11 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->arrive, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));
+  MM_CK(cudaMallocAsync(&h->gacc, sizeof(float4) * (size_t)n0, s));
+  MM_CK(cudaMallocAsync(&h->gacc_st, sizeof(float) * (size_t)n0, s));
+  MM_CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
+  MM_CK(cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming));
+  MM_CK(cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming));
   MM_CK(cudaMemsetAsync(h->state, 0, sizeof(SweepState), s));
   MM_CK(cudaMemsetAsync(h->sstate, 0, sizeof(SweepState), s));
   MM_CK(cudaMallocAsync(&h->zero, sizeof(int32_t), s));
@@ -1636,13 +1659,16 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   for (Level& L : h->levels) free_level(L);
   tree_ws_free(h->tree);
   void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart, h->xc,
-                  h->box, h->arrive,
+                  h->box, h->arrive, h->gacc, h->gacc_st,
                   h->zero, h->lsw, h->trace, h->pbuf[0], h->pbuf[1], h->ord.perm0,
                   h->ord.inv0, h->ord.rp_user, h->ord.col_user, h->ord.omega_user,
                   h->ord.elen_user};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gfork) cudaEventDestroy(h->gfork);
+  if (h->gjoin) cudaEventDestroy(h->gjoin);
+  if (h->gs) cudaStreamDestroy(h->gs);
   if (h->cs) cudaStreamDestroy(h->cs);
   for (mm_hierarchy* sub : h->subs) mm_free_hierarchy(sub);
   if (h->batch_args) cudaFree(h->batch_args);
@@ -1932,9 +1958,16 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
         st = bh_traverse(L.n, h->tree, h->F, L.walk_warps > 0 ? L.walk_warps : h->p.traverse_warps,
                          nullptr, s, h->p.bh_group);
     }
+    // gather stage: the fused update, or on split levels the sums over S
+    // alone; controller stage: then also the update from those sums
+    const bool split = !exact && L.split_gather;
     cudaEventRecord(ev[6], s);
-    if (st == MM_OK) st = gather_update(L, xs, h->F, h->sstate, h->partials, s);
+    if (st == MM_OK)
+      st = split ? gather_sum(L, xs, h->gacc, h->gacc_st, s)
+                 : gather_update(L, xs, h->F, h->sstate, h->partials, s);
     cudaEventRecord(ev[7], s);
+    if (st == MM_OK && split)
+      st = update_from_sum(L, xs, h->F, h->gacc, h->gacc_st, h->sstate, h->partials, s);
     if (st == MM_OK)
       st = controller(gather_blocks(L), h->partials, h->sstate, sp, nullptr, 0, nullptr, 0, false, s);
     cudaEventRecord(ev[8], s);

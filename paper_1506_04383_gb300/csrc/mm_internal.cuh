@@ -206,6 +206,7 @@ struct Level {
   int32_t heavy_degree = 0;
   int32_t walk_warps = 0;    // warps per block in the tree walk (0 = default)
   bool fused = false;        // whole level in the single-CTA kernel
+  bool split_gather = false; // sums over S beside the walk (gather_sum + update_from_sum)
   double sum_c = 0;
   // Eq. 3 (approx_levels = h > 0, all levels but the coarsest): the map to
   // the level h levels down (or the coarsest, nt vertices), the level's
@@ -308,8 +309,8 @@ struct TreeWS {
   int32_t* delta = nullptr;
   int32_t* owner = nullptr;   // owner[g] = internal node whose split is g
   int32_t* parent = nullptr;  // all nodes [2n-1]
-  double2* incl = nullptr;    // [n] inclusive position sums within each sort tile
-  double2* tile_sum = nullptr;// [tiles] tile totals, then their exclusive prefix
+  ulonglong2* incl = nullptr;     // [n] inclusive fixed-point position sums per sort tile
+  ulonglong2* tile_sum = nullptr; // [tiles] tile totals, then their exclusive prefix
   unsigned long long* status = nullptr;  // [4][tiles][256] look-back words
   uint32_t* hist = nullptr;   // [4][256] digit counts
   uint32_t* counters = nullptr;  // [4] tile tickets of the sort passes
@@ -394,6 +395,8 @@ constexpr int kMaxHeavyBlocks = kMaxSMs * 8;
 // Upper bound of gather_blocks() for any lanes setting (partials sizing).
 constexpr int kMaxGatherBlocks = kMaxLightBlocks + kMaxHeavyBlocks;
 int gather_blocks(const Level& L);
+int gather_light_blocks(const Level& L);
+int gather_heavy_blocks(const Level& L);
 // What the last block of an update launch does once every block's partial
 // sums are in (see gather_update): the controller's schedule step, and
 // optionally the next sweep's bounding square.
@@ -416,6 +419,15 @@ struct SweepEpilogue {
 // with `epi`, the update ends with the schedule step (no controller launch).
 mm_status gather_update(const Level& L, XSel x, const float2* F, const SweepState* st,
                         float4* partials, cudaStream_t s, const SweepEpilogue* epi = nullptr);
+// The same update in two launches: gather_sum stores each vertex's sums over
+// S_u (acc: [n] float4 of the w-weighted targets and of r(u,v); acc_st: [n]
+// stress terms) and reads only x, so it can run beside the tree build and
+// walk; update_from_sum then finishes the vertices from acc/acc_st and F with
+// gather_update's grid and arithmetic (bit-identical results).
+mm_status gather_sum(const Level& L, XSel x, float4* acc, float* acc_st, cudaStream_t s);
+mm_status update_from_sum(const Level& L, XSel x, const float2* F, const float4* acc,
+                          const float* acc_st, const SweepState* st, float4* partials,
+                          cudaStream_t s, const SweepEpilogue* epi = nullptr);
 // Reduces the partials, applies the alpha schedule, optionally sets the
 // graph loop condition.
 mm_status controller(int nblocks, const float4* partials, SweepState* st, SchedParams sp,

@@ -170,8 +170,8 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   ws.delta = (int32_t*)(b + c.delta);
   ws.owner = (int32_t*)(b + c.owner);
   ws.parent = (int32_t*)(b + c.parent);
-  ws.incl = (double2*)(b + c.incl);
-  ws.tile_sum = (double2*)(b + c.tile_sum);
+  ws.incl = (ulonglong2*)(b + c.incl);
+  ws.tile_sum = (ulonglong2*)(b + c.tile_sum);
   ws.status = (unsigned long long*)(b + c.status);
   ws.hist = (uint32_t*)(b + c.hist);
   ws.counters = (uint32_t*)(b + c.counters);
