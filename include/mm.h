@@ -382,7 +382,7 @@ mm_status mm_autotune(mm_hierarchy* h, const float* thetas, int32_t n_theta,
  * for testing (no paper counterpart): C = A * B^T on the tcgen05 tensor
  * cores with BF16 inputs and FP32 accumulation, optional bias[N] and ReLU.
  *   A device BF16 [M x K] row-major, B device BF16 [N x K] row-major,
- *   K a multiple of 16 in [16, 128], N = 64 or 128, all buffers 16-byte aligned;
+ *   K in {16, 32, 64, 128}, N = 64 or 128, all buffers 16-byte aligned;
  *   out_f32 (device FP32 [M x N]) and/or out_bf16 (device BF16 [M x N]).
  * Synchronises the stream (reports a tensor-core wait that gave up as
  * MM_ERR_TIMEOUT).

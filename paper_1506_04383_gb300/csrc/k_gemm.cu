@@ -3,18 +3,21 @@
 // prolongation: the layer products (gemm_tc_kernel, below) and the weight
 // gradients (gemm_tn_partial_kernel, further down).
 //   C[M x N] = A[M x K] * B[N x K]^T  (+ bias, ReLU)
-// A and B are row-major with K contiguous (both "K-major").  One CTA of 128
-// threads computes a 128-row tile:
-//   * warp 0 allocates N tensor-memory columns (128 lanes x N FP32);
-//   * all threads stage A (128 x K) and B (N x K) in shared memory in the
-//     canonical no-swizzle K-major layout of 8 x 16-byte core matrices
-//     (K-adjacent core matrices 128 B apart, M/N-adjacent ones 256 B apart,
-//     one 16-wide K slice after another);
-//   * one thread issues K/16 tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//     M = 128) and commits them to an mbarrier;
-//   * after the (bounded) wait every warp reads its 32 accumulator rows with
-//     tcgen05.ld 32x32b and runs the epilogue (bias, ReLU, BF16 or FP32
-//     store); warp 0 frees the tensor memory.
+// A and B are row-major with K contiguous (both "K-major").  The layer
+// product is persistent, one CTA of 256 threads per SM over 128-row tiles:
+//   * warp 0 allocates 2 N tensor-memory columns (two 128 x N FP32
+//     accumulators);
+//   * B (N x K) is staged once and the A tiles (128 x K) stream through a
+//     ring of shared-memory stages by cp.async, all in the canonical
+//     no-swizzle K-major layout of 8 x 16-byte core matrices (K-adjacent
+//     core matrices 128 B apart, M/N-adjacent ones 256 B apart, one 16-wide
+//     K slice after another);
+//   * per tile one thread issues K/16 tcgen05.mma (kind::f16, BF16 x BF16 ->
+//     FP32, M = 128) into the tile's accumulator and commits them to that
+//     accumulator's mbarrier;
+//   * while they run, every warp drains the previous tile's accumulator
+//     (bounded mbarrier wait, tcgen05.ld 32x32b, bias, ReLU, BF16 or FP32
+//     store); warp 0 frees the tensor memory at the end.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -26,7 +29,7 @@ namespace mm {
 
 namespace {
 
-constexpr int kGemmThreads = 128;
+constexpr int kGemmThreads = 128;  // weight-gradient CTAs
 constexpr int kTileM = 128;
 constexpr int kSpin = 1 << 26;
 
@@ -59,135 +62,197 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// Bytes of the staged tiles: A = (K/16) slices x 4096 B, B = (K/16) x N x 32 B.
+// Shared memory: B = (K/16) x N x 32 B once, then kPipeStages A stages of
+// (K/16) x 4096 B (128 rows).
+constexpr int kPipeStages = 5;  // A tiles in shared memory: 3 in flight, 1 in the MMA, 1 spare
 __host__ __device__ constexpr int gemm_smem_bytes(int n, int k) {
-  return (k / 16) * 4096 + (k / 16) * n * 32;
+  return (k / 16) * n * 32 + kPipeStages * (k / 16) * 4096;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+constexpr int kPipeThreads = 256;
+
+// The copies of A tile t (rows 128 t ...) into a stage, in the K-major core-
+// matrix layout; rows beyond M are zero-filled (no bytes read).  K / 8 is a
+// power of two (K in {16, 32, 64, 128}): lg_kc = log2(K / 8).
+__device__ __forceinline__ void load_a_tile(const __nv_bfloat16* __restrict__ A, int M, int K,
+                                            int lg_kc, int t, uint32_t sA, int tid) {
+  const int kc = K / 8;
+  const int m0 = t * kTileM;
+  for (int c = tid; c < kTileM * kc; c += kPipeThreads) {
+    const int m = c >> lg_kc, k8 = c & (kc - 1);
+    const int row = m0 + m;
+    const bool in = row < M;
+    const __nv_bfloat16* src = A + (size_t)(in ? row : 0) * K + k8 * 8;
+    const uint32_t off = (k8 >> 1) * 4096 + (m >> 3) * 256 + (k8 & 1) * 128 + (m & 7) * 16;
+    cp_async16(sA + off, src, in ? 16u : 0u);
+  }
+}
+
+// Persistent: CTA b takes the 128-row tiles b, b + grid, ... .  The A tiles
+// stream through a ring of kPipeStages shared-memory stages by cp.async
+// (three tiles ahead of the one in the MMA), B is staged once, and the
+// accumulator alternates between two TMEM buffers, so the MMAs of tile j run
+// while the epilogue of tile j - 1 drains the other buffer and later tiles
+// are in flight.  A stage is refilled only after the MMA that read it has
+// completed (its mbarrier was waited on one iteration earlier).  Eight warps:
+// warps w and w + 4 share TMEM lane quarter w (rows 32 w ..) and take one
+// half of the columns each.
 template <int N>
-__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(
+__global__ void __launch_bounds__(kPipeThreads, 1) gemm_tc_kernel(
     const __nv_bfloat16* __restrict__ A, int M, int K, const __nv_bfloat16* __restrict__ B,
     const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ outb,
     float* __restrict__ outf, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ float sbias[N];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kTileM;
+  const int quarter = warp & 3, half = warp >> 2;
   const int ks = K / 16;
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + ks * 4096;
+  const int lg_kc = __ffs(K / 8) - 1;
+  const int tiles = (M + kTileM - 1) / kTileM;
+  const int my = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int stage_bytes = ks * 4096;
+  unsigned char* sB = smem;
+  const uint32_t sA0 = smem_addr(smem + ks * N * 32);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_slot)),
-                 "r"(N));
+                 "r"(2 * N));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // stage A: 128 rows x K/8 chunks of 16 bytes (rows beyond M are zero)
+  for (int c = tid; c < N; c += kPipeThreads) sbias[c] = bias ? bias[c] : 0.f;
+  // B: N rows x K/8 chunks, once
   const int kc = K / 8;
-  for (int c = tid; c < kTileM * kc; c += kGemmThreads) {
-    const int m = c / kc, k8 = c % kc;
-    const int row = m0 + m;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (row < M) v = *reinterpret_cast<const uint4*>(A + (size_t)row * K + k8 * 8);
-    const int off = (k8 >> 1) * 4096 + (m >> 3) * 256 + (k8 & 1) * 128 + (m & 7) * 16;
-    *reinterpret_cast<uint4*>(sA + off) = v;
-  }
-  // stage B: N rows x K/8 chunks
-  for (int c = tid; c < N * kc; c += kGemmThreads) {
+  for (int c = tid; c < N * kc; c += kPipeThreads) {
     const int r = c / kc, k8 = c % kc;
     const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)r * K + k8 * 8);
     const int off = (k8 >> 1) * (N * 32) + (r >> 3) * 256 + (k8 & 1) * 128 + (r & 7) * 16;
     *reinterpret_cast<uint4*>(sB + off) = v;
   }
-  // generic-proxy shared stores -> visible to the tensor cores (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  constexpr int kAhead = kPipeStages - 2;
+  for (int j = 0; j < kAhead; ++j) {
+    if (j < my)
+      load_a_tile(A, M, K, lg_kc, blockIdx.x + j * gridDim.x,
+                  sA0 + (j % kPipeStages) * stage_bytes, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if (tid == 0) {
-    const uint32_t idesc = make_idesc(kTileM, N);
-    const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
-    for (int s = 0; s < ks; ++s) {
-      const uint64_t ad = make_desc(a0 + s * 4096, 128, 256);
-      const uint64_t bd = make_desc(b0 + s * (N * 32), 128, 256);
-      const uint32_t acc = s > 0 ? 1u : 0u;
+  const uint32_t idesc = make_idesc(kTileM, N);
+
+  // epilogue of tile jj: wait for its MMAs (bounded), drain its accumulator
+  auto epilogue = [&](int jj) {
+    const uint32_t bar = smem_addr(&mbar[jj & 1]);
+    const uint32_t parity = (uint32_t)((jj >> 1) & 1);
+    bool ok = false;
+    for (int spin = 0; spin < kSpin; ++spin) {
+      uint32_t done;
       asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.b32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity));
+      if (done) {
+        ok = true;
+        break;
+      }
     }
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(&mbar)));
-  }
-  // wait for the MMAs (phase 0), bounded
-  bool ok = false;
-  for (int spin = 0; spin < kSpin; ++spin) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-        " selp.b32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_addr(&mbar)));
-    if (done) {
-      ok = true;
-      break;
-    }
-  }
-  // tcgen05.ld is warp-collective: the whole warp reads or none of it
-  ok = __all_sync(0xffffffffu, ok);
-  if (!ok && lane == 0 && err) atomicOr(err, 4);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    // tcgen05.ld is warp-collective: the whole warp reads or none of it
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && lane == 0 && err) atomicOr(err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int row = (blockIdx.x + jj * gridDim.x) * kTileM + quarter * 32 + lane;
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((jj & 1) * N);
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t r[16];
-      ld16(tbase + (uint32_t)c0, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
-        // the lane's 16 consecutive outputs of its row, written as whole
-        // 16-byte vectors (every 32-byte sector filled by one thread)
-        float v[16];
+      for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 16) {
+        uint32_t r[16];
+        ld16(tbase + (uint32_t)c0, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M) {
+          // the lane's 16 consecutive outputs of its row, written as whole
+          // 16-byte vectors (every 32-byte sector filled by one thread)
+          float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          v[j] = __uint_as_float(r[j]);
-          if (bias) v[j] += bias[c0 + j];
-          if (relu) v[j] = fmaxf(v[j], 0.f);
-        }
-        if (outb) {
-          uint32_t pk[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-            pk[j] = *reinterpret_cast<const uint32_t*>(&h2);
+          for (int q = 0; q < 16; ++q) {
+            v[q] = __uint_as_float(r[q]) + sbias[c0 + q];
+            if (relu) v[q] = fmaxf(v[q], 0.f);
           }
-          uint4* dst = reinterpret_cast<uint4*>(outb + (size_t)row * N + c0);
-          dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        }
-        if (outf) {
-          float4* dst = reinterpret_cast<float4*>(outf + (size_t)row * N + c0);
+          if (outb) {
+            uint32_t pk[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int q = 0; q < 8; ++q) {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+              pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(outb + (size_t)row * N + c0);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          }
+          if (outf) {
+            float4* dst = reinterpret_cast<float4*>(outf + (size_t)row * N + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          }
         }
       }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+
+  for (int j = 0; j < my; ++j) {
+    // tile j + kAhead into the stage of tile j - 2, whose MMAs were waited
+    // for in the previous iteration's epilogue
+    const int jn = j + kAhead;
+    if (jn < my)
+      load_a_tile(A, M, K, lg_kc, blockIdx.x + jn * gridDim.x,
+                  sA0 + (jn % kPipeStages) * stage_bytes, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
+    // every thread's copies of tile j (and B) -> visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a0 = sA0 + (j % kPipeStages) * stage_bytes, b0 = smem_addr(sB);
+      const uint32_t d = tmem + (uint32_t)((j & 1) * N);
+      for (int s = 0; s < ks; ++s) {
+        const uint64_t ad = make_desc(a0 + s * 4096, 128, 256);
+        const uint64_t bd = make_desc(b0 + s * (N * 32), 128, 256);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar[j & 1])));
+    }
+    if (j > 0) epilogue(j - 1);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (my > 0) epilogue(my - 1);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * N));
   }
 }
 
@@ -360,8 +425,8 @@ mm_status launch_gemm(const __nv_bfloat16* A, int M, int K, const __nv_bfloat16*
                       const float* bias, int relu, __nv_bfloat16* outb, float* outf, int* err,
                       cudaStream_t s) {
   const int smem = gemm_smem_bytes(N, K);
-  gemm_tc_kernel<N><<<ceil_div(M, kTileM), kGemmThreads, smem, s>>>(A, M, K, B, bias, relu, outb,
-                                                                    outf, err);
+  const int grid = std::max(1, std::min(ceil_div(M, kTileM), num_sms()));
+  gemm_tc_kernel<N><<<grid, kPipeThreads, smem, s>>>(A, M, K, B, bias, relu, outb, outf, err);
   MM_CK(cudaGetLastError());
   return MM_OK;
 }
@@ -423,9 +488,9 @@ mm_status gemm_tn_bf16(const void* A, int n, int R, const void* B, float* out, f
 
 mm_status gemm_bf16(const void* A, int M, int K, const void* B, int N, const float* bias,
                     int relu, void* outb, float* outf, int* err, cudaStream_t s) {
-  if (M < 0 || K < 16 || K > 128 || K % 16 || (N != 64 && N != 128) || !A || !B ||
-      (!outb && !outf)) {
-    set_error("gemm: need 16 <= K <= 128 (multiple of 16), N in {64, 128}");
+  if (M < 0 || (K != 16 && K != 32 && K != 64 && K != 128) || (N != 64 && N != 128) || !A ||
+      !B || (!outb && !outf)) {
+    set_error("gemm: need K in {16, 32, 64, 128}, N in {64, 128}");
     return MM_ERR_INVALID_ARG;
   }
   if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)outb & 15) ||

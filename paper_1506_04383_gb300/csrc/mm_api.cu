@@ -2265,6 +2265,7 @@ mm_status mm_gemm_bf16_tn(int32_t n, int32_t R, const void* A, const void* B, fl
     MM_CK(cudaStreamSynchronize(s));
     return MM_OK;
   }
+  MM_TRY(gemm_setup());
   int* err = nullptr;
   float* part = nullptr;
   MM_CK(cudaMallocAsync(&err, sizeof(int), s));

@@ -58,3 +58,12 @@ def test_weight_gradient_gemm_matches_fp64(mm, n, R):
 def test_net_gemm_profile_reports_positive_times(mm):
     f, b = mm.net_gemm_profile(1 << 16, reps=3)
     assert f > 0 and b > 0
+
+
+def test_gemm_rejects_unsupported_k(mm):
+    # K is one of 16, 32, 64, 128 (the layer widths); anything else is an
+    # argument error, not a launch
+    A = torch.zeros(256, 48, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(64, 48, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(mm.MMError):
+        mm.gemm_bf16(A, B)
