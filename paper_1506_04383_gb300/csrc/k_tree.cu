@@ -517,9 +517,10 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const ulonglong2* __restrict__ incl,
                                const ulonglong2* __restrict__ tile_off, int tile,
                                const float4* __restrict__ root, float theta, int leaf,
-                               int maxdepth, float4* nodeA, int4* nodeB) {
+                               int maxdepth, float4* nodeA, int4* nodeB, unsigned* walk_next) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
+  if (id == 0) *walk_next = 0u;  // the walk that follows deals its tasks from 0
   if (kFold) {
     constexpr int kPer = kFoldTiles / 32;
     __shared__ ulonglong2 off[kFoldTiles];
@@ -854,6 +855,55 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
   }
 }
 
+// The group walk with one warp per task (W = 1, the large levels) as a
+// persistent grid: every warp takes the next 32-point task from a counter
+// (zeroed by the record kernel of the same build) until none is left, so
+// no SM idles in a last, partly filled wave while others still walk.  Each
+// task writes only its own points: the result does not depend on which
+// warp took it.
+template <bool kCount>
+__global__ void __launch_bounds__(256, 6) traverse_dyn_kernel(
+    int n, const float2* __restrict__ xs, const int32_t* __restrict__ vals,
+    const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float2* __restrict__ F,
+    unsigned* walk_next, unsigned long long* counters, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int tasks = (n + 31) / 32;
+  unsigned visits = 0, inter = 0;
+  int no_seed = 0;
+  for (;;) {
+    int task = 0;
+    if (lane == 0) task = (int)atomicAdd(walk_next, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= tasks) break;
+    const int p0 = task * 32 + lane;
+    const bool valid = p0 < n;
+    const int pos = valid ? p0 : -1;
+    const float2 x0 = valid ? xs[p0] : make_float2(CUDART_INF_F, CUDART_INF_F);
+    unsigned long long acc = pk2(0.f, 0.f);
+    unsigned v = 0, it = 0;
+    float phi = 0.f;
+    int budget = 2 * n + 2;
+    bool broken = false;
+    vote_walk<kCount, false, false>(n > 1 ? 0 : -1, -1, n, 0, pos, pk2(x0.x, x0.y), xs, nodeA,
+                                    nodeB, acc, budget, broken, nullptr, no_seed, v, it, phi);
+    if (broken && lane == 0) atomicOr(err, 1);
+    if (valid) F[vals[p0]] = upk2(acc);
+    if (kCount) {
+      visits += v;
+      inter += valid ? it : 0u;
+    }
+  }
+  if (kCount) {
+    unsigned tot = inter;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) {
+      atomicAdd(&counters[0], (unsigned long long)visits);
+      atomicAdd(&counters[1], (unsigned long long)tot);
+    }
+  }
+}
+
 constexpr int kExactThreads = 256;
 
 __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, float2* F) {
@@ -889,6 +939,14 @@ size_t tree_status_words(int64_t n) {
   return (size_t)4 * ceil_div(n > 1 ? n : 2, kSortMinTile) * 256;
 }
 
+mm_status walk_setup(TreeWS& ws) {
+  int per_sm = 0;
+  MM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traverse_dyn_kernel<false>, 256,
+                                                      0));
+  ws.walk_resident = std::max(1, per_sm) * num_sms();
+  return MM_OK;
+}
+
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   const size_t N = (size_t)(n > 1 ? n : 2);
   const size_t tiles = (size_t)ceil_div((int64_t)N, kSortMinTile);
@@ -911,6 +969,8 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   MM_CK(cudaMemsetAsync(ws.status, 0, sizeof(unsigned long long) * tree_status_words(N), s));
   MM_CK(cudaMallocAsync(&ws.hist, sizeof(uint32_t) * 4 * 256, s));
   MM_CK(cudaMallocAsync(&ws.counters, sizeof(uint32_t) * 4, s));
+  MM_CK(cudaMallocAsync(&ws.walk_next, sizeof(unsigned), s));
+  MM_CK(cudaMemsetAsync(ws.walk_next, 0, sizeof(unsigned), s));
   MM_CK(cudaMallocAsync(&ws.nodeA, sizeof(float4) * 2 * N, s));
   MM_CK(cudaMallocAsync(&ws.nodeB, sizeof(int4) * 2 * N, s));
   MM_CK(cudaMallocAsync(&ws.partials, sizeof(float4) * kBBoxMaxBlocks, s));
@@ -921,6 +981,7 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   // unwritten records read as leaves whose escape ends the walk
   MM_CK(cudaMemsetAsync(ws.nodeB, 0xff, sizeof(int4) * 2 * N, s));
+  MM_TRY(walk_setup(ws));
   MM_CK(cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking));
   MM_CK(cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming));
   MM_CK(cudaEventCreateWithFlags(&ws.join, cudaEventDisableTiming));
@@ -930,7 +991,7 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
 void tree_ws_free(TreeWS& ws) {
   void* ptrs[] = {ws.keys[0], ws.keys[1], ws.vals[0], ws.vals[1], ws.xs, ws.lo, ws.hi,
                   ws.left, ws.right, ws.delta, ws.owner, ws.parent, ws.incl, ws.tile_sum,
-                  ws.status, ws.hist, ws.counters, ws.nodeA, ws.nodeB, ws.partials, ws.root,
+                  ws.status, ws.hist, ws.counters, ws.walk_next, ws.nodeA, ws.nodeB, ws.partials, ws.root,
                   ws.ticket, ws.err};
   for (void* p : ptrs) cudaFree(p);
   if (ws.fork) cudaEventDestroy(ws.fork);
@@ -1012,11 +1073,11 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   if (fold)
     records_kernel<true><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
         tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
-        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB);
+        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB, ws.walk_next);
   else
     records_kernel<false><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
         tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
-        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB);
+        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB, ws.walk_next);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;
@@ -1034,6 +1095,16 @@ mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
     const int W = std::max(1, std::min(kGroupMaxWarps, wpb));
     const int tpb = std::max(1, 8 / W);
     const int seed = W > 1 ? kSeedPoints : 0;
+    if (W == 1) {
+      // persistent: as many 256-thread blocks as fit (walk_setup), tasks
+      // dealt by a counter
+      const int grid = std::max(1, std::min(std::max(ws.walk_resident, 1), ceil_div(tasks, 8)));
+      auto kern = counters ? traverse_dyn_kernel<true> : traverse_dyn_kernel<false>;
+      kern<<<grid, 256, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, ws.walk_next,
+                                counters, ws.err);
+      MM_CK(cudaGetLastError());
+      return MM_OK;
+    }
     auto kern = counters ? traverse_vote_kernel<true> : traverse_vote_kernel<false>;
     kern<<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(n, W, seed, ws.xs, ws.vals[0], ws.nodeA,
                                                       ws.nodeB, F, counters, ws.err, nullptr);

@@ -314,6 +314,8 @@ struct TreeWS {
   unsigned long long* status = nullptr;  // [4][tiles][256] look-back words
   uint32_t* hist = nullptr;   // [4][256] digit counts
   uint32_t* counters = nullptr;  // [4] tile tickets of the sort passes
+  unsigned* walk_next = nullptr;  // next task of the persistent walk (reset by each build)
+  int walk_resident = 0;          // blocks of the persistent walk that fit on the device
   float4* nodeA = nullptr;    // (cx, cy, r_crit^2, count)
   int4* nodeB = nullptr;      // (first child | -1, escape | -1, lo, hi+1)
   float4* partials = nullptr; // bbox partial results
@@ -330,6 +332,8 @@ size_t tree_status_words(int64_t n);
 // Whether the tree build of n points scans its tile totals in a kernel of
 // its own (else the record kernel folds them in).
 bool tree_tile_scan(int64_t n);
+// Sizes the persistent walk's grid (occupancy query; no allocation).
+mm_status walk_setup(TreeWS& ws);
 mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s);
 void tree_ws_free(TreeWS& ws);
 

@@ -49,7 +49,8 @@ constexpr size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 // Byte offsets of the workspace pieces inside the array.
 struct Carve {
   size_t keys0, keys1, vals0, vals1, xs, lo, hi, left, right, delta, owner, parent, incl,
-      tile_sum, status, hist, counters, nodeA, nodeB, partials, root, ticket, err, zero, total;
+      tile_sum, status, hist, counters, walk_next, nodeA, nodeB, partials, root, ticket, err, zero,
+      total;
 };
 
 constexpr Carve carve() {
@@ -74,6 +75,7 @@ constexpr Carve carve() {
   c.status = o; o += up(8 * 4 * tiles * 256);
   c.hist = o; o += up(4 * 4 * 256);
   c.counters = o; o += up(4 * 4);
+  c.walk_next = o; o += up(4);
   c.nodeA = o; o += up(16 * 2 * N);
   c.nodeB = o; o += up(16 * 2 * N);
   c.partials = o; o += up(16 * 2 * kMaxSMs);
@@ -175,6 +177,7 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   ws.status = (unsigned long long*)(b + c.status);
   ws.hist = (uint32_t*)(b + c.hist);
   ws.counters = (uint32_t*)(b + c.counters);
+  ws.walk_next = (unsigned*)(b + c.walk_next);
   ws.nodeA = (float4*)(b + c.nodeA);
   ws.nodeB = (int4*)(b + c.nodeB);
   ws.partials = (float4*)(b + c.partials);
@@ -191,6 +194,7 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   // mm_repulsion on a hierarchy built with mm_default_params
   mm_params d;
   mm_default_params(&d);
+  MM_TRY(walk_setup(ws));
   MM_TRY(bh_build(xs, n, theta, leaf_of(d), ws, s, nullptr, true, group_of(d)));
   MM_TRY(bh_traverse(n, ws, (float2*)F_out, 0, nullptr, s, group_of(d)));
   int err = 0;

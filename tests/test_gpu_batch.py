@@ -60,7 +60,8 @@ def test_autotune_keeps_objective(mm):
     assert r["theta"] in (0.5, np.float32(0.6), np.float32(0.7))
     assert abs(r["objective"] - r["objective_ref"]) <= 0.01 * abs(r["objective_ref"]) + 1e-9
     for lanes, warps in zip(r["gather_lanes"], r["traverse_warps"]):
-        assert lanes in (0, 1, 2, 4, 8, 16, 32) and warps in (0, 2, 4, 8, 16)
+        # the tuner times 1, 2, 4, 8 and 16 warps per walk task
+        assert lanes in (0, 1, 2, 4, 8, 16, 32) and warps in (0, 1, 2, 4, 8, 16)
     x, st = mm.layout(h)
     assert np.all(np.isfinite(x.cpu().numpy()))
 
