@@ -98,7 +98,12 @@ typedef struct mm_params {
                             /* the coarser level (memory locality of the      */
                             /* sweeps; level-0 positions still cross the ABI  */
                             /* in the caller's numbering); 0: input numbering */
-  int32_t reserved[1];
+  int32_t exact_max_n;      /* multilevel layouts: levels with at most this   */
+                            /* many vertices (other than Eq. 3 levels) take   */
+                            /* the exact O(n^2) entropy sum (the coarsest     */
+                            /* level always does); 0 = only the coarsest;    */
+                            /* default 8192 (below it the O(n^2) sum costs   */
+                            /* less than the tree build and walk)             */
 } mm_params;
 
 /* A graph on the device (the input of mm_build_hierarchy). */

@@ -929,6 +929,57 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
   if (u < n) F[u] = make_float2(fx, fy);
 }
 
+// The same sum for levels too small to fill the GPU one vertex per thread:
+// block (vb, c) sums the sources of chunk c for vertices 128 vb ..; each
+// block stores its partial, and the last block of a vertex block to arrive
+// adds the chunk partials in chunk order (reproducible) and resets the
+// arrival counter for the next sweep.
+constexpr int kExactSplitThreads = 128;
+
+__global__ void __launch_bounds__(kExactSplitThreads) exact_split_kernel(
+    XSel xs, int n, int chunk, int chunks, float2* __restrict__ part, unsigned* arrive,
+    float2* __restrict__ F) {
+  __shared__ float2 tile[kExactSplitThreads];
+  __shared__ bool last;
+  const float2* x = xs.cur();
+  const int vb = blockIdx.x, c = blockIdx.y;
+  const int u = vb * kExactSplitThreads + threadIdx.x;
+  const float2 xu = u < n ? x[u] : make_float2(0.f, 0.f);
+  float fx = 0.f, fy = 0.f;
+  const int j0 = c * chunk, j1 = min(n, j0 + chunk);
+  for (int t0 = j0; t0 < j1; t0 += kExactSplitThreads) {
+    const int cnt = min(kExactSplitThreads, j1 - t0);
+    if (threadIdx.x < cnt) tile[threadIdx.x] = x[t0 + threadIdx.x];
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < cnt; ++k) {
+      const float dx = xu.x - tile[k].x, dy = xu.y - tile[k].y;
+      const float q = fmaf(dx, dx, dy * dy);
+      const float inv = q > 0.f ? __fdividef(1.f, q) : 0.f;
+      fx = fmaf(inv, dx, fx);
+      fy = fmaf(inv, dy, fy);
+    }
+    __syncthreads();
+  }
+  if (u < n) part[(size_t)c * n + u] = make_float2(fx, fy);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&arrive[vb], 1u) == (unsigned)(chunks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (u < n) {
+    float sx = 0.f, sy = 0.f;
+    for (int q = 0; q < chunks; ++q) {
+      const float2 pq = __ldcg(&part[(size_t)q * n + u]);
+      sx += pq.x;
+      sy += pq.y;
+    }
+    F[u] = make_float2(sx, sy);
+  }
+  if (threadIdx.x == 0) arrive[vb] = 0u;
+}
+
 }  // namespace
 
 bool tree_tile_scan(int64_t n) {
@@ -1133,9 +1184,26 @@ mm_status bh_potential(int n, const TreeWS& ws, float2* F, float* Phi, int warps
   return MM_OK;
 }
 
-mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s) {
+int exact_chunks(int n) {
+  // split the sources until about four blocks per SM are busy, within the
+  // partial-sum buffer (kExactPartCap float2)
+  const int vblocks = ceil_div(std::max(n, 1), kExactSplitThreads);
+  const int want = ceil_div(4 * num_sms(), vblocks);
+  return std::max(1, std::min(want, kExactPartCap / std::max(n, 1)));
+}
+
+mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s, float2* part,
+                          unsigned* arrive) {
   if (n <= 0) return MM_OK;
-  exact_kernel<<<ceil_div(n, kExactThreads), kExactThreads, 0, s>>>(x, n, F);
+  const int chunks = part && arrive ? exact_chunks(n) : 1;
+  if (chunks <= 1) {
+    exact_kernel<<<ceil_div(n, kExactThreads), kExactThreads, 0, s>>>(x, n, F);
+  } else {
+    const int chunk = ceil_div(ceil_div(n, chunks), 32) * 32;
+    const int c = ceil_div(n, chunk);
+    exact_split_kernel<<<dim3(ceil_div(n, kExactSplitThreads), c), kExactSplitThreads, 0, s>>>(
+        x, n, chunk, c, part, arrive, F);
+  }
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

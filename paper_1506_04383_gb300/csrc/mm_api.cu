@@ -54,6 +54,8 @@ struct mm_hierarchy {
   float* gacc_st = nullptr;          // [n0] stress terms per vertex
   cudaStream_t gs = nullptr;         // stream of that branch
   cudaEvent_t gfork = nullptr, gjoin = nullptr;
+  float2* xpart = nullptr;           // [kExactPartCap] chunk partials of the exact sum
+  unsigned* xarrive = nullptr;       // [ceil(n0 / 128)] their arrival counters (zero between sweeps)
   int32_t* zero = nullptr;           // device int 0 (parity of standalone calls)
   int32_t* lsw = nullptr;            // [2 MM_MAX_LEVELS] sweeps, last rel. change per level
   float* trace = nullptr;
@@ -154,7 +156,8 @@ mm_status check_params(const mm_params* p) {
       !(p->alpha_min > 0) || !(p->alpha0 > 0) || !(p->alpha_factor > 0 && p->alpha_factor < 1) ||
       p->max_levels < 1 || p->max_levels > MM_MAX_LEVELS || p->leaf_size < 0 ||
       p->leaf_size > kMaxLeaf || p->approx_levels < 0 || p->approx_levels > MM_MAX_LEVELS ||
-      p->bh_group < 0 || p->bh_group > 1 || p->level_order < 0 || p->level_order > 1) {
+      p->bh_group < 0 || p->bh_group > 1 || p->level_order < 0 || p->level_order > 1 ||
+      p->exact_max_n < 0) {
     set_error("parameter out of range");
     return MM_ERR_INVALID_ARG;
   }
@@ -229,10 +232,16 @@ mm_status tree_error(mm_hierarchy* h, cudaStream_t s) {
   return MM_OK;
 }
 
+bool level_approx(const mm_hierarchy* h, int level);
+
 bool level_exact(const mm_hierarchy* h, int level, bool single) {
   if (h->p.exact_repulsion) return true;
-  // the coarsest level of a multilevel run is refined with the exact sum
-  return !single && level == (int)h->levels.size() - 1;
+  if (single) return false;
+  // the coarsest level of a multilevel run is refined with the exact sum,
+  // and so is every level of at most exact_max_n vertices (below that size
+  // the O(n^2) sum costs less than a tree build and walk)
+  if (level == (int)h->levels.size() - 1) return true;
+  return !level_approx(h, level) && h->levels[level].n <= h->p.exact_max_n;
 }
 
 // The level takes its entropy sum from Eq. 3 (a map to a coarser level).
@@ -244,9 +253,10 @@ bool level_approx(const mm_hierarchy* h, int level) {
 // sweep_body with in_loop = true).
 int64_t kernels_per_sweep(const mm_hierarchy* h, int level, bool exact) {
   const Level& L = h->levels[level];
-  int64_t k = 1 + (L.n_heavy > 0 ? 1 : 0);  // update (+ heavy rows), epilogue fused
-  if (exact) return k + 1;                   // tiled exact sum
-  if (level_approx(h, level)) return k + 2;  // midpoints, Eq. 3 sums
+  const int64_t upd = 1 + (L.n_heavy > 0 ? 1 : 0);  // update (+ heavy rows), epilogue fused
+  if (exact) return upd + 1;                   // tiled exact sum
+  if (level_approx(h, level)) return upd + 2;  // midpoints, Eq. 3 sums
+  int64_t k = L.split_gather ? 2 * upd : upd;  // sums over S on their branch, then the update
   k += 1 + (group_of(h->p) ? 3 : 4);         // Morton keys + histograms, sort passes
   if (L.n > 1) k += 1;                       // radix tree
   k += 1;                                    // position prefix sums
@@ -302,7 +312,7 @@ mm_status sweep_body(mm_hierarchy* h, int level, bool exact, XSel x, SweepState*
   const Level& L = h->levels[level];
   const bool approx = !exact && level_approx(h, level);
   if (exact) {
-    MM_TRY(exact_repulsion(x, L.n, h->F, s));
+    MM_TRY(exact_repulsion(x, L.n, h->F, s, h->xpart, h->xarrive));
   } else if (approx) {
     MM_TRY(approx_repulsion(L, x, h->xc, h->F, s));
   } else {
@@ -829,6 +839,9 @@ mm_status finish_levels(mm_hierarchy* h, const mm_params* p, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&h->box, sizeof(float4) * (size_t)kMaxGatherBlocks, s));
   MM_CK(cudaMallocAsync(&h->arrive, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(h->arrive, 0, sizeof(unsigned), s));
+  MM_CK(cudaMallocAsync(&h->xpart, sizeof(float2) * (size_t)kExactPartCap, s));
+  MM_CK(cudaMallocAsync(&h->xarrive, sizeof(unsigned) * (size_t)ceil_div(n0, 128), s));
+  MM_CK(cudaMemsetAsync(h->xarrive, 0, sizeof(unsigned) * (size_t)ceil_div(n0, 128), s));
   MM_CK(cudaMallocAsync(&h->gacc, sizeof(float4) * (size_t)n0, s));
   MM_CK(cudaMallocAsync(&h->gacc_st, sizeof(float) * (size_t)n0, s));
   MM_CK(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking));
@@ -1580,6 +1593,7 @@ void mm_default_params(mm_params* p) {
   p->leaf_size = 16;
   p->bh_group = 1;
   p->level_order = 1;
+  p->exact_max_n = 8192;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1659,7 +1673,7 @@ void mm_free_hierarchy(mm_hierarchy* h) {
   for (Level& L : h->levels) free_level(L);
   tree_ws_free(h->tree);
   void* ptrs[] = {h->xb[0], h->xb[1], h->F, h->partials, h->state, h->sstate, h->spart, h->xc,
-                  h->box, h->arrive, h->gacc, h->gacc_st,
+                  h->box, h->arrive, h->gacc, h->gacc_st, h->xpart, h->xarrive,
                   h->zero, h->lsw, h->trace, h->pbuf[0], h->pbuf[1], h->ord.perm0,
                   h->ord.inv0, h->ord.rp_user, h->ord.col_user, h->ord.omega_user,
                   h->ord.elen_user};
@@ -1951,7 +1965,7 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
     if (exact) {
       cudaEventRecord(ev[0], s);
       for (int i = 1; i <= 5; ++i) cudaEventRecord(ev[i], s);
-      st = exact_repulsion(xs, L.n, h->F, s);
+      st = exact_repulsion(xs, L.n, h->F, s, h->xpart, h->xarrive);
     } else {
       st = bh_build(xs, L.n, h->p.theta, leaf_of(h->p), h->tree, s, ev, true, group_of(h->p));
       if (st == MM_OK)

@@ -366,8 +366,13 @@ constexpr int kMaxWalkWarps = 16;  // warps per block of the tree walk
 
 // Group acceptance of a parameter set.
 inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
-// Tiled exact sum F[v] = sum_{u != v} r(v, u).
-mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s);
+// Tiled exact sum F[v] = sum_{u != v} r(v, u).  With part ([kExactPartCap]
+// float2) and arrive ([ceil(n / 128)] counters, zero between calls) small n
+// split the sources over several blocks per vertex block (partials added in
+// a fixed order).
+constexpr int kExactPartCap = 1 << 18;
+mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s, float2* part = nullptr,
+                          unsigned* arrive = nullptr);
 // The group walk (bh_group = 1 decisions) over a built tree that also writes
 // Phi[u] = sum_{v != u} ln|x_u - x_v| (accepted cells: count x ln of the
 // centroid distance; leaves exact; coincident points 0), in input order.

@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
         ("fused_max_n", ctypes.c_int32), ("learned_prolong", ctypes.c_int32),
         ("leaf_size", ctypes.c_int32), ("bh_group", ctypes.c_int32),
         ("approx_levels", ctypes.c_int32), ("level_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1),
+        ("exact_max_n", ctypes.c_int32),
     ]
 
 

@@ -66,8 +66,8 @@ def test_struct_layout_matches_c(tmp_path):
           printf("%zu %zu %zu %zu %zu\\n", sizeof(mm_prolong_sample),
                  offsetof(mm_prolong_sample, n_coarse), offsetof(mm_prolong_sample, seed),
                  offsetof(mm_prolong_sample, level), offsetof(mm_prolong_sample, x_target));
-          printf("%zu %zu\\n", offsetof(mm_params, learned_prolong),
-                 offsetof(mm_params, approx_levels));
+          printf("%zu %zu %zu\\n", offsetof(mm_params, learned_prolong),
+                 offsetof(mm_params, approx_levels), offsetof(mm_params, exact_max_n));
           return 0;
         }
     """))
@@ -85,7 +85,8 @@ def test_struct_layout_matches_c(tmp_path):
     Q = mm.ProlongSample
     assert [int(t) for t in c.split()] == [ctypes.sizeof(Q), Q.n_coarse.offset, Q.seed.offset,
                                            Q.level.offset, Q.x_target.offset]
-    assert [int(t) for t in d.split()] == [P.learned_prolong.offset, P.approx_levels.offset]
+    assert [int(t) for t in d.split()] == [P.learned_prolong.offset, P.approx_levels.offset,
+                                           P.exact_max_n.offset]
 
 
 def test_product_path_does_not_import_oracle():
@@ -101,7 +102,7 @@ def test_product_path_does_not_import_oracle():
 @pytest.mark.parametrize("field,value,status", [
     ("struct_version", 0, 1), ("k", 3, 7), ("theta", -0.5, 1), ("coarsest_n", 0, 1),
     ("alpha_factor", 1.5, 1), ("max_levels", 0, 1), ("leaf_size", 65, 1),
-    ("approx_levels", -1, 1), ("approx_levels", 1000, 1)])
+    ("approx_levels", -1, 1), ("approx_levels", 1000, 1), ("exact_max_n", -1, 1)])
 def test_parameters_are_checked_before_any_device_work(lib, field, value, status):
     # host-only: the parameter check runs before the graph or the device is
     # touched, so a descriptor without buffers is enough

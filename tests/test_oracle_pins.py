@@ -706,6 +706,34 @@ def test_sweep_h_with_identity_map_is_the_exact_sweep():
     assert np.allclose(sth, ste, rtol=1e-12)
 
 
+def test_exact_max_n_selects_the_exact_sum_by_level_size():
+    # levels of at most exact_max_n vertices take the exact entropy sum: with
+    # the threshold above every level the layout is the exact_repulsion = 1
+    # layout bit for bit; with threshold 0 only the coarsest level is exact
+    # and the Barnes-Hut levels give a different layout; a threshold between
+    # two level sizes makes exactly the levels below it exact
+    rp, col = graphs.grid(12, 12)
+    base = dict(k=2, theta=0.5, coarsest_n=2, seed=4)
+    levels = oracle.build_hierarchy(rp, col, oracle.params(**base))
+    x_all, _ = oracle.layout(rp, col, oracle.params(**base, exact_max_n=144), levels=levels)
+    x_ex, _ = oracle.layout(rp, col, oracle.params(**base, exact_repulsion=1), levels=levels)
+    x_bh, _ = oracle.layout(rp, col, oracle.params(**base, exact_max_n=0), levels=levels)
+    assert np.array_equal(x_all, x_ex)
+    assert not np.array_equal(x_all, x_bh)
+    # threshold = the size of level 1: the coarse levels are exact (the same
+    # sweeps as the all-exact run, step for step), level 0 is Barnes-Hut
+    n1 = int(levels[1]["n"])
+    tr_mid, tr_ex = [], []
+    _, info_mid = oracle.layout(rp, col, oracle.params(**base, exact_max_n=n1), levels=levels,
+                                trace=tr_mid)
+    _, info_ex = oracle.layout(rp, col, oracle.params(**base, exact_repulsion=1), levels=levels,
+                               trace=tr_ex)
+    assert info_mid["sweeps"][1:] == info_ex["sweeps"][1:]
+    coarse = sum(info_ex["sweeps"][1:])
+    assert tr_mid[:coarse] == tr_ex[:coarse]
+    assert tr_mid[coarse:] != tr_ex[coarse:]
+
+
 def test_layout_h_runs_and_maps_compose():
     rp, col = graphs.grid(12, 12)
     p = oracle.params(k=2, coarsest_n=2, seed=4, approx_levels=2)
