@@ -911,22 +911,27 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
   const float2* x = xs.cur();
   const int u = blockIdx.x * kExactThreads + threadIdx.x;
   const float2 xu = u < n ? x[u] : make_float2(0.f, 0.f);
-  float fx = 0.f, fy = 0.f;
+  const unsigned long long xu2 = pk2(xu.x, xu.y);
+  const unsigned long long* tp = reinterpret_cast<const unsigned long long*>(tile);
+  unsigned long long acc = pk2(0.f, 0.f);
   for (int t0 = 0; t0 < n; t0 += kExactThreads) {
     const int cnt = min(kExactThreads, n - t0);
     if (threadIdx.x < cnt) tile[threadIdx.x] = x[t0 + threadIdx.x];
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < cnt; ++k) {
-      const float dx = xu.x - tile[k].x, dy = xu.y - tile[k].y;
-      const float q = fmaf(dx, dx, dy * dy);
-      const float inv = q > 0.f ? __fdividef(1.f, q) : 0.f;
-      fx = fmaf(inv, dx, fx);
-      fy = fmaf(inv, dy, fy);
+      // packed (x, y) offset and accumulator; a coincident point (its own
+      // included) has a zero offset, and the clamped distance keeps its
+      // term at zero
+      const unsigned long long d = sub2(xu2, tp[k]);
+      const float2 df = upk2(d);
+      const float q = fmaf(df.x, df.x, df.y * df.y);
+      const float r = rcp_approx(fmaxf(q, 1e-30f));
+      acc = fma2(pk2(r, r), d, acc);
     }
     __syncthreads();
   }
-  if (u < n) F[u] = make_float2(fx, fy);
+  if (u < n) F[u] = upk2(acc);
 }
 
 // The same sum for levels too small to fill the GPU one vertex per thread:
@@ -945,7 +950,9 @@ __global__ void __launch_bounds__(kExactSplitThreads) exact_split_kernel(
   const int vb = blockIdx.x, c = blockIdx.y;
   const int u = vb * kExactSplitThreads + threadIdx.x;
   const float2 xu = u < n ? x[u] : make_float2(0.f, 0.f);
-  float fx = 0.f, fy = 0.f;
+  const unsigned long long xu2 = pk2(xu.x, xu.y);
+  const unsigned long long* tp = reinterpret_cast<const unsigned long long*>(tile);
+  unsigned long long acc = pk2(0.f, 0.f);
   const int j0 = c * chunk, j1 = min(n, j0 + chunk);
   for (int t0 = j0; t0 < j1; t0 += kExactSplitThreads) {
     const int cnt = min(kExactSplitThreads, j1 - t0);
@@ -953,15 +960,18 @@ __global__ void __launch_bounds__(kExactSplitThreads) exact_split_kernel(
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < cnt; ++k) {
-      const float dx = xu.x - tile[k].x, dy = xu.y - tile[k].y;
-      const float q = fmaf(dx, dx, dy * dy);
-      const float inv = q > 0.f ? __fdividef(1.f, q) : 0.f;
-      fx = fmaf(inv, dx, fx);
-      fy = fmaf(inv, dy, fy);
+      // packed (x, y) offset and accumulator; a coincident point (its own
+      // included) has a zero offset, and the clamped distance keeps its
+      // term at zero
+      const unsigned long long d = sub2(xu2, tp[k]);
+      const float2 df = upk2(d);
+      const float q = fmaf(df.x, df.x, df.y * df.y);
+      const float r = rcp_approx(fmaxf(q, 1e-30f));
+      acc = fma2(pk2(r, r), d, acc);
     }
     __syncthreads();
   }
-  if (u < n) part[(size_t)c * n + u] = make_float2(fx, fy);
+  if (u < n) part[(size_t)c * n + u] = upk2(acc);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&arrive[vb], 1u) == (unsigned)(chunks - 1);
