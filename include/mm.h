@@ -102,7 +102,7 @@ typedef struct mm_params {
                             /* many vertices (other than Eq. 3 levels) take   */
                             /* the exact O(n^2) entropy sum (the coarsest     */
                             /* level always does); 0 = only the coarsest;    */
-                            /* default 8192 (below it the O(n^2) sum costs   */
+                            /* default 16384 (below it the O(n^2) sum costs  */
                             /* less than the tree build and walk)             */
 } mm_params;
 

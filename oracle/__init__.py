@@ -313,7 +313,7 @@ DEFAULTS = dict(
     k=2, theta=0.5, exact_repulsion=0, coarsest_n=2, f=20.0, b=2.0, lp_rounds=10,
     iters_per_alpha=2, alpha0=1.0, alpha_factor=0.3, alpha_min=0.008, eps=1e-4,
     eps_final=1e-4, max_iters_at_min=100, early_exit=1, seed=1506, max_levels=64,
-    max_stalls=10, approx_levels=0, exact_max_n=8192,
+    max_stalls=10, approx_levels=0, exact_max_n=16384,
 )
 
 

@@ -1593,7 +1593,7 @@ void mm_default_params(mm_params* p) {
   p->leaf_size = 16;
   p->bh_group = 1;
   p->level_order = 1;
-  p->exact_max_n = 8192;
+  p->exact_max_n = 16384;
 }
 
 const char* mm_status_string(mm_status s) {
