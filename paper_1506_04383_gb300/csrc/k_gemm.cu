@@ -263,8 +263,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) gemm_tc_kernel(
 // the caller adds the per-CTA partials in a fixed order.  In GEMM terms the
 // contraction runs over the vertices, so both operands arrive with the
 // contracted index slowest (row-major over vertices).  Each CTA (128
-// threads, one per SM, a contiguous range of vertices) stages 64 vertices at
-// a time, transposing 8 x 8 blocks of BF16 in registers so that A^T (R rows,
+// threads, three per SM, a contiguous range of vertices) stages 64 vertices
+// at a time: the warps load 8 x 8 BF16 blocks in the matrix-fragment layout
+// and store them transposed with stmatrix .trans, so that A^T (R rows,
 // padded to 128 with zeros) and B^T (64 rows) land in the same K-major
 // no-swizzle layout as gemm_tc_kernel's operands; one thread issues the four
 // K = 16 MMAs (M = 128, N = 64) of the chunk into one FP32 accumulator in
@@ -274,26 +275,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) gemm_tc_kernel(
 constexpr int kTnChunk = 64;                              // vertices per stage
 constexpr int kTnSmem = (kTnChunk / 16) * (4096 + 64 * 32);  // A + B tiles
 
-// Transposes an 8 x 8 block of BF16 held as 8 rows of 8 (row i = u[i]):
-// out[j] holds column j, element i from u[i].
-__device__ __forceinline__ void transpose8x8(const uint4 (&u)[8], uint4 (&out)[8]) {
-  uint32_t w[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    w[i][0] = u[i].x; w[i][1] = u[i].y; w[i][2] = u[i].z; w[i][3] = u[i].w;
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int word = j >> 1;
-    const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;  // high or low halves of two words
-    uint32_t o[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) o[p] = __byte_perm(w[2 * p][word], w[2 * p + 1][word], sel);
-    out[j] = make_uint4(o[0], o[1], o[2], o[3]);
-  }
-}
-
-__global__ void __launch_bounds__(kGemmThreads) gemm_tn_partial_kernel(
+__global__ void __launch_bounds__(kGemmThreads, 3) gemm_tn_partial_kernel(
     const __nv_bfloat16* __restrict__ A, int n, int R, const __nv_bfloat16* __restrict__ B,
     float* __restrict__ part, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -323,35 +305,60 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tn_partial_kernel(
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = make_idesc(kTileM, N);
+  // The chunk's R + 64 blocks of 8 vertices x 8 columns (of A, then of B),
+  // four per warp operation: lane t holds the 32-bit pair (vertex t / 4,
+  // columns 2 (t % 4) ..) of each of the operation's blocks -- the fragment
+  // layout of an 8 x 8 BF16 matrix -- and stmatrix .trans stores each block
+  // transposed, its row j (16 bytes: column j over the 8 vertices) at the
+  // address lane 8 i + j gives for block i: row m of the K-major operand,
+  // K chunk vg.  The eight rows of a block are 128 contiguous bytes, so the
+  // stores do not conflict.  A chunk's fragments are loaded into registers
+  // while the previous chunk's MMAs run.
+  const int na = (R / 8) * 8;  // A blocks: R/8 column groups x 8 vertex groups
+  const int nops = (na + 64) / 4;
+  constexpr int kWarpsTn = kGemmThreads / 32;
+  constexpr int kOps = (128 + 64) / 4 / kWarpsTn;  // operations per warp, at most
+  uint32_t frag[kOps][4];
+  auto load_chunk = [&](int base) {
+#pragma unroll
+    for (int k = 0; k < kOps; ++k) {
+      const int op = warp + k * kWarpsTn;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int tb = op * 4 + i;
+        const bool isA = tb < na;
+        const int t = isA ? tb : tb - na;
+        const int cg = t >> 3, vg = t & 7;  // column group, vertex group
+        const int v = base + vg * 8 + (lane >> 2);
+        // element offset in 32 bits (n x 128 < 2^31 for every level the
+        // network sees); one base pointer per operand
+        const int off = v * (isA ? R : N) + cg * 8 + 2 * (lane & 3);
+        frag[k][i] = op < nops && v < v1
+                         ? __ldg(reinterpret_cast<const uint32_t*>((isA ? A : B) + off))
+                         : 0u;
+      }
+    }
+  };
   bool ok = true;
   int chunks = 0;
+  if (v0 < v1) load_chunk(v0);
   for (int base = v0; base < v1 && ok; base += kTnChunk, ++chunks) {
-    // stage: each of the R + 64 blocks of 8 vertices x 8 columns (of A,
-    // then of B) is loaded, transposed and stored by one thread
-    const int na = (R / 8) * 8;  // A blocks: R/8 column groups x 8 vertex groups
-    for (int tb = tid; tb < na + 64; tb += kGemmThreads) {
+#pragma unroll
+    for (int k = 0; k < kOps; ++k) {
+      const int op = warp + k * kWarpsTn;
+      if (op >= nops) continue;  // warp-uniform
+      const int tb = op * 4 + (lane >> 3);
       const bool isA = tb < na;
       const int t = isA ? tb : tb - na;
-      const int cg = t >> 3, vg = t & 7;  // column group, vertex group
-      const int ld = isA ? R : N;
-      const __nv_bfloat16* src = isA ? A : B;
-      uint4 u[8], o[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int v = base + vg * 8 + i;
-        u[i] = v < v1 ? *reinterpret_cast<const uint4*>(src + (size_t)v * ld + cg * 8)
-                      : make_uint4(0u, 0u, 0u, 0u);
-      }
-      transpose8x8(u, o);
-      // o[j] = row (cg * 8 + j) of the transposed operand, K chunk vg
-      unsigned char* dst = isA ? sA : sB;
+      const int cg = t >> 3, vg = t & 7;
+      const int m = cg * 8 + (lane & 7);
       const int slice = isA ? 4096 : N * 32;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int m = cg * 8 + j;
-        const int off = (vg >> 1) * slice + (m >> 3) * 256 + (vg & 1) * 128 + (m & 7) * 16;
-        *reinterpret_cast<uint4*>(dst + off) = o[j];
-      }
+      const uint32_t addr = smem_addr((isA ? sA : sB) + (vg >> 1) * slice + (m >> 3) * 256 +
+                                      (vg & 1) * 128 + (m & 7) * 16);
+      asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(
+                       addr),
+                   "r"(frag[k][0]), "r"(frag[k][1]), "r"(frag[k][2]), "r"(frag[k][3])
+                   : "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -373,6 +380,8 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tn_partial_kernel(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_addr(&mbar)));
     }
+    // the next chunk's fragments in flight while these MMAs run
+    if (base + kTnChunk < v1) load_chunk(base + kTnChunk);
     // the chunk's MMAs done (phase = chunk parity) before the buffers are
     // refilled or the accumulator read; bounded
     bool done = false;
