@@ -705,7 +705,11 @@ def ctypes_copy(dst, src):
 # ncu capture of the kernel on level 0 of the workload, with the source file
 # of the kernel and its SHA-256 prefix at capture time: reported only while
 # that source is unchanged (null otherwise).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/traverse_dyn_kernel_del20.md and profiles/gather_light_del20.md
+    ("del20", "traverse"): (36.70e6, "paper_1506_04383_gb300/csrc/k_tree.cu", "da118a20008c07dc"),
+    ("del20", "gather"): (77.58e6, "paper_1506_04383_gb300/csrc/k_sweep.cu", "195d1391b37d2281"),
+}
 
 
 def ncu_traffic(workload, kernel):

@@ -293,11 +293,13 @@ mm_status mm_layout(mm_hierarchy* h, const mm_params* p, const float* x_init,
 
 /*
  * Per-stage timing of one sweep on `level` (no paper counterpart; a
- * measurement aid): the sweep of mm_sweep is run `reps` times from x with
- * CUDA events between its stages, and the mean milliseconds per stage are
- * written to stage_ms (host [8]): bbox, Morton keys + digit histograms, sort
- * passes, radix tree + prefix sums, node records, traverse (or the exact
- * O(n^2) kernel), gather, controller.  work (host
+ * measurement aid): one sweep of the level as the multilevel layout runs it
+ * (the exact O(n^2) sum on the coarsest level, on levels of at most
+ * exact_max_n vertices and with exact_repulsion; else the tree) is run `reps`
+ * times from x with CUDA events between its stages, and the mean
+ * milliseconds per stage are written to stage_ms (host [8]): bbox, Morton
+ * keys + digit histograms, sort passes, radix tree + prefix sums, node
+ * records, traverse (or the exact kernel), gather, controller.  work (host
  * [4]) receives the walk's warp node visits and lane interactions (from one
  * instrumented walk), |S| and n.  alpha = 0.3.  x device [2n], unchanged.
  */

@@ -1889,7 +1889,8 @@ mm_status mm_sweep_profile(mm_hierarchy* h, int32_t level, const float* x, int32
   DeviceGuard dg(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const Level& L = h->levels[level];
-  const bool exact = h->p.exact_repulsion != 0;
+  // the entropy sum the multilevel layout uses on this level
+  const bool exact = level_exact(h, level, false);
   // level 0 in the hierarchy's own order (as the layout runs it)
   mm_status cst;
   const float2* xi = x_in_internal(h, level, x, 0, s, &cst);
