@@ -1195,10 +1195,11 @@ mm_status bh_potential(int n, const TreeWS& ws, float2* F, float* Phi, int warps
 }
 
 int exact_chunks(int n) {
-  // split the sources until about four blocks per SM are busy, within the
-  // partial-sum buffer (kExactPartCap float2)
+  // split the sources until about sixteen 4-warp blocks per SM are busy
+  // (the loop is latency-bound at fewer), within the partial-sum buffer
+  // (kExactPartCap float2)
   const int vblocks = ceil_div(std::max(n, 1), kExactSplitThreads);
-  const int want = ceil_div(4 * num_sms(), vblocks);
+  const int want = ceil_div(16 * num_sms(), vblocks);
   return std::max(1, std::min(want, kExactPartCap / std::max(n, 1)));
 }
 

@@ -370,7 +370,7 @@ inline bool group_of(const mm_params& p) { return p.bh_group != 0; }
 // float2) and arrive ([ceil(n / 128)] counters, zero between calls) small n
 // split the sources over several blocks per vertex block (partials added in
 // a fixed order).
-constexpr int kExactPartCap = 1 << 18;
+constexpr int kExactPartCap = 1 << 20;
 mm_status exact_repulsion(XSel x, int n, float2* F, cudaStream_t s, float2* part = nullptr,
                           unsigned* arrive = nullptr);
 // The group walk (bh_group = 1 decisions) over a built tree that also writes
