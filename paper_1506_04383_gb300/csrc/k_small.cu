@@ -8,10 +8,11 @@
 // every per-sweep structure lives in shared memory:
 //   bounding square -> Morton keys (16 bits per axis, the same cells as the
 //   multi-kernel path) -> bitonic sort of (key, index) -> Karras radix tree
-//   -> centroids from FP64 prefix sums of the sorted positions -> 32-byte
-//   node records -> warp-synchronous stackless walk (per-lane acceptance,
-//   as in the multi-kernel walk) -> Eq. 2 update over S (rows read from
-//   global memory) -> FP64 block reductions -> the schedule step.
+//   -> centroids from float-float prefix sums of the sorted positions ->
+//   32-byte node records -> warp-synchronous stackless walk (per-lane
+//   acceptance, as in the multi-kernel walk) -> Eq. 2 update over S (rows
+//   read from global memory) -> block reductions (FP32 within a warp,
+//   float-float across warps) -> the schedule step.
 // With exact repulsion (the coarsest level) the walk is replaced by the
 // all-pairs sum over the staged positions.
 #include <cuda_runtime.h>

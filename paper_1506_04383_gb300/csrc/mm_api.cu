@@ -1590,7 +1590,7 @@ void mm_default_params(mm_params* p) {
   p->gather_lanes = 0;
   p->heavy_degree = 0;
   p->traverse_warps = 0;
-  p->leaf_size = 16;
+  p->leaf_size = 24;
   p->bh_group = 1;
   p->level_order = 1;
   p->exact_max_n = 16384;

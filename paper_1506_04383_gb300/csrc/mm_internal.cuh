@@ -338,8 +338,8 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s);
 void tree_ws_free(TreeWS& ws);
 
 // Rebuilds the quadtree from the current positions (bbox, Morton keys and
-// digit histograms, four look-back sort passes, radix tree with FP64 prefix
-// sums, node records).
+// digit histograms, look-back sort passes, radix tree, 64-bit fixed-point
+// prefix sums of the sorted positions, node records).
 // ev (nullable, 6 events) records the stage boundaries for profiling.
 // leaf: cells with at most `leaf` points become leaves (1..kMaxLeaf).
 // with_bbox = false: the root square (and the zeroed sort state) was left

@@ -177,7 +177,7 @@ def test_bh_matches_oracle_clustered_and_duplicates(mm):
     _bh_check(mm, f32(x), 0.5)
 
 
-@pytest.mark.parametrize("leaf", [8, 16])
+@pytest.mark.parametrize("leaf", [8, 16, 24])
 def test_bh_leaf_buckets_within_oracle_error(mm, leaf):
     x = f32(graphs.uniform_positions(3001, 77, 0.0, 50.0))
     _bh_check(mm, x, 0.5, leaf)
@@ -194,7 +194,7 @@ def test_bh_leaf_buckets_within_oracle_error(mm, leaf):
     assert np.all(np.abs(F - ref) <= 2e-4 * inv_dist_sum(x)[:, None] + 1e-12)
 
 
-@pytest.mark.parametrize("leaf", [1, 16])
+@pytest.mark.parametrize("leaf", [1, 16, 24])
 def test_bh_group_acceptance_within_oracle_error(mm, leaf):
     # a cell accepted for all 32 points of a warp passes every point's test:
     # each point's sum refines its per-point Barnes-Hut sum
@@ -214,7 +214,7 @@ def test_bh_group_acceptance_within_oracle_error(mm, leaf):
 
 @pytest.mark.parametrize("fused", [0, -1])
 def test_sweep_default_barnes_hut_within_oracle_error(mm, fused):
-    # default walk (leaf buckets of 16, group acceptance): one sweep is at
+    # default walk (leaf buckets of 24, group acceptance): one sweep is at
     # least as close to the exact sweep as the oracle's Barnes-Hut sweep
     rp, col, pts, _ = graphs.rgg(2000 if fused == 0 else 6000, 8.0, 31)
     n = len(rp) - 1
