@@ -461,13 +461,13 @@ __device__ __forceinline__ int escape_of(const TreeView& t, int h) {
 }
 
 __device__ void write_record(const TreeView& t, int id, float2 c, float side, float theta,
-                             int leaf, int maxdepth, float4* nodeA, int4* nodeB) {
+                             int leaf, int maxdepth, NodeRec* node) {
   const int n = t.n;
   if (id >= n - 1) {  // leaf j
     const int j = id - (n - 1);
     if (n > 1 && t.delta[t.parent[id]] >= 32) return;  // inside a bucket
-    nodeA[id] = make_float4(c.x, c.y, 0.f, 1.f);
-    nodeB[id] = make_int4(-1, escape_of(t, j), j, j + 1);
+    node[id].a = make_float4(c.x, c.y, 0.f, 1.f);
+    node[id].b = make_int4(-1, escape_of(t, j), j, j + 1);
     return;
   }
   const int dd = t.delta[id];
@@ -488,8 +488,8 @@ __device__ void write_record(const TreeView& t, int id, float2 c, float side, fl
   const float cnt = (float)(b - a + 1);
   const float w = ldexpf(side, -depth);
   const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
-  nodeA[id] = make_float4(c.x, c.y, rc, cnt);
-  nodeB[id] = make_int4(first, escape_of(t, b), a, b + 1);
+  node[id].a = make_float4(c.x, c.y, rc, cnt);
+  node[id].b = make_int4(first, escape_of(t, b), a, b + 1);
 }
 
 // Fixed-point sum of the sorted positions [0, k): tile offset + inclusive
@@ -517,7 +517,7 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
                                const ulonglong2* __restrict__ incl,
                                const ulonglong2* __restrict__ tile_off, int tile,
                                const float4* __restrict__ root, float theta, int leaf,
-                               int maxdepth, float4* nodeA, int4* nodeB, unsigned* walk_next) {
+                               int maxdepth, NodeRec* node, unsigned* walk_next) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = t.n;
   if (id == 0) *walk_next = 0u;  // the walk that follows deals its tasks from 0
@@ -567,7 +567,18 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
       c.y = r.y + ((float)(b.y - a.y) / cnt) / scale;
     }
   }
-  write_record(t, id, c, r.z, theta, leaf, maxdepth, nodeA, nodeB);
+  write_record(t, id, c, r.z, theta, leaf, maxdepth, node);
+}
+
+// A cell record in one 256-bit load through the read-only path (the
+// records are written by an earlier launch and only read by the walks).
+__device__ __forceinline__ void ld_node(const NodeRec* __restrict__ p, float4& A, int4& B) {
+  unsigned a0, a1, a2, a3;
+  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(B.x), "=r"(B.y), "=r"(B.z), "=r"(B.w)
+      : "l"(p));
+  A = make_float4(__uint_as_float(a0), __uint_as_float(a1), __uint_as_float(a2),
+                  __uint_as_float(a3));
 }
 
 // Guards: node ids must stay in [0, 2n-1) and a walk visits each node at
@@ -577,8 +588,7 @@ __global__ void records_kernel(TreeView t, const float2* __restrict__ xsorted,
 template <bool kCount>
 __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
                                 const int32_t* __restrict__ vals,
-                                const float4* __restrict__ nodeA,
-                                const int4* __restrict__ nodeB, float2* __restrict__ F,
+                                const NodeRec* __restrict__ node, float2* __restrict__ F,
                                 unsigned long long* counters, int* err) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -597,8 +607,9 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
       if (lane == 0) atomicOr(err, 1);
       break;
     }
-    const float4 A = __ldg(&nodeA[cur]);
-    const int4 B = __ldg(&nodeB[cur]);
+    float4 A;
+    int4 B;
+    ld_node(node + cur, A, B);
     if (wait == cur) wait = kNone;
     bool desc = false;
     if (wait == kNone) {
@@ -711,7 +722,8 @@ __device__ __forceinline__ float rcp_approx(float q) {
 // comparison; the accepted-cell term is computed on every visit and masked
 // (no branch), the next cell is a select, and only the exact leaf sum is a
 // (warp-uniform) branch; the leaf sum has no branch (a coincident point has
-// a zero offset, and the clamped squared distance keeps its term at zero);
+// a zero offset, and 1e-30 added to its squared distance keeps its term at
+// zero); the record is one 256-bit load;
 // and the position / offset / accumulator arithmetic is done on packed
 // (x, y) pairs.
 //
@@ -722,8 +734,8 @@ __device__ __forceinline__ float rcp_approx(float q) {
 template <bool kCount, bool kSeeding, bool kPhi = false>
 __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, int pos,
                                           unsigned long long xu, const float2* __restrict__ xs,
-                                          const float4* __restrict__ nodeA,
-                                          const int4* __restrict__ nodeB, unsigned long long& acc,
+                                          const NodeRec* __restrict__ node,
+                                          unsigned long long& acc,
                                           int& budget, bool& broken, int* seeds, int& nseeds,
                                           unsigned& visits, unsigned& inter, float& phi) {
   const unsigned nodes = 2u * (unsigned)n - 1u;
@@ -734,8 +746,9 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
       broken = true;
       return;
     }
-    const float4 A = __ldg(&nodeA[cur]);
-    const int4 B = __ldg(&nodeB[cur]);
+    float4 A;
+    int4 B;
+    ld_node(node + cur, A, B);
     if (kCount) ++visits;
     const unsigned long long d = sub2(xu, pk2(A.x, A.y));
     const float2 df = upk2(d);
@@ -754,10 +767,16 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
       for (int p = pb; p < pe; ++p) {
         const unsigned long long e = sub2(xu, __ldg(&xp[p]));
         const float2 ef = upk2(e);
-        const float eq = fmaf(ef.x, ef.x, ef.y * ef.y);
-        const float r = rcp_approx(fmaxf(eq, 1e-30f));
+        // |e|^2 + 1e-30: the same float as |e|^2 for any two points that are
+        // not (nearly) coincident, and a coincident point's zero offset keeps
+        // its term at zero
+        const float eq = fmaf(ef.x, ef.x, fmaf(ef.y, ef.y, 1e-30f));
+        const float r = rcp_approx(eq);
         acc = fma2(pk2(r, r), e, acc);
-        if (kPhi) phi += eq > 0.f ? 0.5f * __logf(eq) : 0.f;
+        if (kPhi) {
+          const float e2 = fmaf(ef.x, ef.x, ef.y * ef.y);
+          phi += e2 > 0.f ? 0.5f * __logf(e2) : 0.f;
+        }
       }
       if (kCount) inter += (unsigned)max(pe - pb, 0);
     }
@@ -776,8 +795,8 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
 template <bool kCount, bool kPhi = false>
 __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
     int n, int W, int seed, const float2* __restrict__ xs, const int32_t* __restrict__ vals,
-    const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float2* __restrict__ F,
-    unsigned long long* counters, int* err, float* __restrict__ Phi = nullptr) {
+    const NodeRec* __restrict__ node, float2* __restrict__ F, unsigned long long* counters,
+    int* err, float* __restrict__ Phi = nullptr) {
   __shared__ GroupShared sh;
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int slot = wb / W, w = wb % W;
@@ -802,11 +821,11 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
     if (lane == 0) nseeds = 0;
     __syncwarp();
     if (W > 1 && seed > 0)
-      vote_walk<kCount, true, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                              budget, broken, seeds, nseeds, visits, inter, phi);
+      vote_walk<kCount, true, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, node, acc, budget,
+                                    broken, seeds, nseeds, visits, inter, phi);
     else
-      vote_walk<kCount, false, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                               budget, broken, seeds, nseeds, visits, inter, phi);
+      vote_walk<kCount, false, kPhi>(n > 1 ? 0 : -1, -1, n, seed, pos, xu, xs, node, acc, budget,
+                                     broken, seeds, nseeds, visits, inter, phi);
   }
   float2 f = upk2(acc);
   if (W > 1) {
@@ -814,8 +833,8 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
     const int ns = live ? nseeds : 0;
     for (int j = w; j < ns && !broken; j += W) {
       const int c = seeds[j];
-      vote_walk<kCount, false, kPhi>(c, __ldg(&nodeB[c]).y, n, seed, pos, xu, xs, nodeA, nodeB, acc,
-                               budget, broken, seeds, nseeds, visits, inter, phi);
+      vote_walk<kCount, false, kPhi>(c, __ldg(&node[c].b.y), n, seed, pos, xu, xs, node, acc,
+                                     budget, broken, seeds, nseeds, visits, inter, phi);
     }
     f = upk2(acc);
     sh.part[wb][lane] = f;
@@ -864,8 +883,8 @@ __global__ void __launch_bounds__(512, 3) traverse_vote_kernel(
 template <bool kCount>
 __global__ void __launch_bounds__(256, 6) traverse_dyn_kernel(
     int n, const float2* __restrict__ xs, const int32_t* __restrict__ vals,
-    const float4* __restrict__ nodeA, const int4* __restrict__ nodeB, float2* __restrict__ F,
-    unsigned* walk_next, unsigned long long* counters, int* err) {
+    const NodeRec* __restrict__ node, float2* __restrict__ F, unsigned* walk_next,
+    unsigned long long* counters, int* err) {
   const int lane = threadIdx.x & 31;
   const int tasks = (n + 31) / 32;
   unsigned visits = 0, inter = 0;
@@ -884,8 +903,8 @@ __global__ void __launch_bounds__(256, 6) traverse_dyn_kernel(
     float phi = 0.f;
     int budget = 2 * n + 2;
     bool broken = false;
-    vote_walk<kCount, false, false>(n > 1 ? 0 : -1, -1, n, 0, pos, pk2(x0.x, x0.y), xs, nodeA,
-                                    nodeB, acc, budget, broken, nullptr, no_seed, v, it, phi);
+    vote_walk<kCount, false, false>(n > 1 ? 0 : -1, -1, n, 0, pos, pk2(x0.x, x0.y), xs, node,
+                                    acc, budget, broken, nullptr, no_seed, v, it, phi);
     if (broken && lane == 0) atomicOr(err, 1);
     if (valid) F[vals[p0]] = upk2(acc);
     if (kCount) {
@@ -921,12 +940,12 @@ __global__ void __launch_bounds__(kExactThreads) exact_kernel(XSel xs, int n, fl
 #pragma unroll 8
     for (int k = 0; k < cnt; ++k) {
       // packed (x, y) offset and accumulator; a coincident point (its own
-      // included) has a zero offset, and the clamped distance keeps its
-      // term at zero
+      // included) has a zero offset, and the 1e-30 added to the squared
+      // distance (lost in rounding for any other pair) keeps its term at zero
       const unsigned long long d = sub2(xu2, tp[k]);
       const float2 df = upk2(d);
-      const float q = fmaf(df.x, df.x, df.y * df.y);
-      const float r = rcp_approx(fmaxf(q, 1e-30f));
+      const float q = fmaf(df.x, df.x, fmaf(df.y, df.y, 1e-30f));
+      const float r = rcp_approx(q);
       acc = fma2(pk2(r, r), d, acc);
     }
     __syncthreads();
@@ -961,12 +980,12 @@ __global__ void __launch_bounds__(kExactSplitThreads) exact_split_kernel(
 #pragma unroll 8
     for (int k = 0; k < cnt; ++k) {
       // packed (x, y) offset and accumulator; a coincident point (its own
-      // included) has a zero offset, and the clamped distance keeps its
-      // term at zero
+      // included) has a zero offset, and the 1e-30 added to the squared
+      // distance (lost in rounding for any other pair) keeps its term at zero
       const unsigned long long d = sub2(xu2, tp[k]);
       const float2 df = upk2(d);
-      const float q = fmaf(df.x, df.x, df.y * df.y);
-      const float r = rcp_approx(fmaxf(q, 1e-30f));
+      const float q = fmaf(df.x, df.x, fmaf(df.y, df.y, 1e-30f));
+      const float r = rcp_approx(q);
       acc = fma2(pk2(r, r), d, acc);
     }
     __syncthreads();
@@ -1032,8 +1051,7 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&ws.counters, sizeof(uint32_t) * 4, s));
   MM_CK(cudaMallocAsync(&ws.walk_next, sizeof(unsigned), s));
   MM_CK(cudaMemsetAsync(ws.walk_next, 0, sizeof(unsigned), s));
-  MM_CK(cudaMallocAsync(&ws.nodeA, sizeof(float4) * 2 * N, s));
-  MM_CK(cudaMallocAsync(&ws.nodeB, sizeof(int4) * 2 * N, s));
+  MM_CK(cudaMallocAsync(&ws.node, sizeof(NodeRec) * 2 * N, s));
   MM_CK(cudaMallocAsync(&ws.partials, sizeof(float4) * kBBoxMaxBlocks, s));
   MM_CK(cudaMallocAsync(&ws.root, sizeof(float4), s));
   MM_CK(cudaMallocAsync(&ws.ticket, 2 * sizeof(unsigned), s));
@@ -1041,7 +1059,7 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
   MM_CK(cudaMallocAsync(&ws.err, sizeof(int), s));
   MM_CK(cudaMemsetAsync(ws.err, 0, sizeof(int), s));
   // unwritten records read as leaves whose escape ends the walk
-  MM_CK(cudaMemsetAsync(ws.nodeB, 0xff, sizeof(int4) * 2 * N, s));
+  MM_CK(cudaMemsetAsync(ws.node, 0xff, sizeof(NodeRec) * 2 * N, s));
   MM_TRY(walk_setup(ws));
   MM_CK(cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking));
   MM_CK(cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming));
@@ -1052,7 +1070,7 @@ mm_status tree_ws_alloc(TreeWS& ws, int64_t n, cudaStream_t s) {
 void tree_ws_free(TreeWS& ws) {
   void* ptrs[] = {ws.keys[0], ws.keys[1], ws.vals[0], ws.vals[1], ws.xs, ws.lo, ws.hi,
                   ws.left, ws.right, ws.delta, ws.owner, ws.parent, ws.incl, ws.tile_sum,
-                  ws.status, ws.hist, ws.counters, ws.walk_next, ws.nodeA, ws.nodeB, ws.partials, ws.root,
+                  ws.status, ws.hist, ws.counters, ws.walk_next, ws.node, ws.partials, ws.root,
                   ws.ticket, ws.err};
   for (void* p : ptrs) cudaFree(p);
   if (ws.fork) cudaEventDestroy(ws.fork);
@@ -1134,11 +1152,11 @@ mm_status bh_build(XSel x, int n, float theta, int leaf, TreeWS& ws, cudaStream_
   if (fold)
     records_kernel<true><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
         tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
-        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB, ws.walk_next);
+        coarse_keys ? 12 : kKeyBits, ws.node, ws.walk_next);
   else
     records_kernel<false><<<ceil_div(2 * n - 1, 256), 256, 0, s>>>(
         tv, ws.xs, ws.incl, ws.tile_sum, tile, ws.root, theta, leaf,
-        coarse_keys ? 12 : kKeyBits, ws.nodeA, ws.nodeB, ws.walk_next);
+        coarse_keys ? 12 : kKeyBits, ws.node, ws.walk_next);
   mark(5);
   MM_CK(cudaGetLastError());
   return MM_OK;
@@ -1161,20 +1179,20 @@ mm_status bh_traverse(int n, const TreeWS& ws, float2* F, int warps_per_block,
       // dealt by a counter
       const int grid = std::max(1, std::min(std::max(ws.walk_resident, 1), ceil_div(tasks, 8)));
       auto kern = counters ? traverse_dyn_kernel<true> : traverse_dyn_kernel<false>;
-      kern<<<grid, 256, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, ws.walk_next,
-                                counters, ws.err);
+      kern<<<grid, 256, 0, s>>>(n, ws.xs, ws.vals[0], ws.node, F, ws.walk_next, counters,
+                                ws.err);
       MM_CK(cudaGetLastError());
       return MM_OK;
     }
     auto kern = counters ? traverse_vote_kernel<true> : traverse_vote_kernel<false>;
-    kern<<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(n, W, seed, ws.xs, ws.vals[0], ws.nodeA,
-                                                      ws.nodeB, F, counters, ws.err, nullptr);
+    kern<<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(n, W, seed, ws.xs, ws.vals[0], ws.node, F,
+                                                      counters, ws.err, nullptr);
   } else if (counters) {
-    traverse_kernel<true><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB,
-                                                       F, counters, ws.err);
+    traverse_kernel<true><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.node, F,
+                                                       counters, ws.err);
   } else {
-    traverse_kernel<false><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.nodeA,
-                                                        ws.nodeB, F, nullptr, ws.err);
+    traverse_kernel<false><<<blocks, wpb * 32, 0, s>>>(n, ws.xs, ws.vals[0], ws.node, F,
+                                                        nullptr, ws.err);
   }
   MM_CK(cudaGetLastError());
   return MM_OK;
@@ -1189,7 +1207,7 @@ mm_status bh_potential(int n, const TreeWS& ws, float2* F, float* Phi, int warps
   const int tpb = std::max(1, 8 / W);
   const int seed = W > 1 ? kSeedPoints : 0;
   traverse_vote_kernel<false, true><<<ceil_div(tasks, tpb), tpb * W * 32, 0, s>>>(
-      n, W, seed, ws.xs, ws.vals[0], ws.nodeA, ws.nodeB, F, nullptr, ws.err, Phi);
+      n, W, seed, ws.xs, ws.vals[0], ws.node, F, nullptr, ws.err, Phi);
   MM_CK(cudaGetLastError());
   return MM_OK;
 }

@@ -296,6 +296,14 @@ mm_status read_scalar(const void* dev, T* host, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ quadtree --
+// One quadtree cell as the walk reads it: a = (cx, cy, r_crit^2, count),
+// b = (first child | -1, escape | -1, lo, hi+1).  Both halves share one
+// 32-byte sector, so a visit is a single 256-bit load.
+struct __align__(32) NodeRec {
+  float4 a;
+  int4 b;
+};
+
 // Workspace of the Barnes-Hut tree, sized for the largest level.
 struct TreeWS {
   int64_t cap = 0;
@@ -316,8 +324,7 @@ struct TreeWS {
   uint32_t* counters = nullptr;  // [4] tile tickets of the sort passes
   unsigned* walk_next = nullptr;  // next task of the persistent walk (reset by each build)
   int walk_resident = 0;          // blocks of the persistent walk that fit on the device
-  float4* nodeA = nullptr;    // (cx, cy, r_crit^2, count)
-  int4* nodeB = nullptr;      // (first child | -1, escape | -1, lo, hi+1)
+  NodeRec* node = nullptr;    // [2n-1] cell records (one 32-byte sector each)
   float4* partials = nullptr; // bbox partial results
   float4* root = nullptr;     // (min x, min y, side, key scale)
   uint32_t* ticket = nullptr; // [0] last-block ticket, [1] build epoch

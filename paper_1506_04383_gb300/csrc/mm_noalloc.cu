@@ -49,7 +49,7 @@ constexpr size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 // Byte offsets of the workspace pieces inside the array.
 struct Carve {
   size_t keys0, keys1, vals0, vals1, xs, lo, hi, left, right, delta, owner, parent, incl,
-      tile_sum, status, hist, counters, walk_next, nodeA, nodeB, partials, root, ticket, err, zero,
+      tile_sum, status, hist, counters, walk_next, node, partials, root, ticket, err, zero,
       total;
 };
 
@@ -76,8 +76,7 @@ constexpr Carve carve() {
   c.hist = o; o += up(4 * 4 * 256);
   c.counters = o; o += up(4 * 4);
   c.walk_next = o; o += up(4);
-  c.nodeA = o; o += up(16 * 2 * N);
-  c.nodeB = o; o += up(16 * 2 * N);
+  c.node = o; o += up(32 * 2 * N);
   c.partials = o; o += up(16 * 2 * kMaxSMs);
   c.root = o; o += up(16);
   c.ticket = o; o += up(8);
@@ -178,8 +177,7 @@ extern "C" mm_status mm_repulsion_noalloc(int32_t n, const float* x, float theta
   ws.hist = (uint32_t*)(b + c.hist);
   ws.counters = (uint32_t*)(b + c.counters);
   ws.walk_next = (unsigned*)(b + c.walk_next);
-  ws.nodeA = (float4*)(b + c.nodeA);
-  ws.nodeB = (int4*)(b + c.nodeB);
+  ws.node = (NodeRec*)(b + c.node);
   ws.partials = (float4*)(b + c.partials);
   ws.root = (float4*)(b + c.root);
   ws.ticket = (uint32_t*)(b + c.ticket);
