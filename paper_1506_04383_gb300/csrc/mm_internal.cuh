@@ -303,6 +303,8 @@ struct __align__(32) NodeRec {
   float4 a;
   int4 b;
 };
+static_assert(sizeof(NodeRec) == 32 && alignof(NodeRec) == 32,
+              "a cell record is one aligned 32-byte sector");
 
 // Workspace of the Barnes-Hut tree, sized for the largest level.
 struct TreeWS {

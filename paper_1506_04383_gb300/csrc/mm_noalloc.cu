@@ -89,6 +89,7 @@ constexpr Carve carve() {
 constexpr Carve kCarve = carve();
 constexpr size_t kScratchBytes = kCarve.total;
 static_assert(kScratchBytes < (8u << 20), "no-allocation scratch stays under 8 MiB");
+static_assert(kCarve.node % alignof(NodeRec) == 0, "cell records are read with 256-bit loads");
 
 // The scratch array (zero at module load).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
