@@ -467,7 +467,7 @@ __device__ void write_record(const TreeView& t, int id, float2 c, float side, fl
     const int j = id - (n - 1);
     if (n > 1 && t.delta[t.parent[id]] >= 32) return;  // inside a bucket
     node[id].a = make_float4(c.x, c.y, 0.f, 1.f);
-    node[id].b = make_int4(-1, escape_of(t, j), j, j + 1);
+    node[id].b = make_int4(-1, escape_of(t, j), j, 1);
     return;
   }
   const int dd = t.delta[id];
@@ -489,7 +489,7 @@ __device__ void write_record(const TreeView& t, int id, float2 c, float side, fl
   const float w = ldexpf(side, -depth);
   const float rc = theta > 0.f ? (w / theta) * (w / theta) : CUDART_INF_F;
   node[id].a = make_float4(c.x, c.y, rc, cnt);
-  node[id].b = make_int4(first, escape_of(t, b), a, b + 1);
+  node[id].b = make_int4(first, escape_of(t, b), a, b - a + 1);
 }
 
 // Fixed-point sum of the sorted positions [0, k): tile offset + inclusive
@@ -615,7 +615,7 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
     if (wait == kNone) {
       const float dx = xu.x - A.x, dy = xu.y - A.y;
       const float q = fmaf(dx, dx, dy * dy);
-      const bool inside = pos >= B.z && pos < B.w;
+      const bool inside = (unsigned)(pos - B.z) < (unsigned)B.w;
       if (!inside && q > A.z) {
         const float sc = __fdividef(A.w, q);
         fx = fmaf(sc, dx, fx);
@@ -623,7 +623,7 @@ __global__ void traverse_kernel(int n, const float2* __restrict__ xs,
         wait = B.y;
         if (kCount) ++inter;
       } else if (B.x < 0) {
-        const int pb = max(B.z, 0), pe = min(B.w, n);
+        const int pb = max(B.z, 0), pe = min(B.z + B.w, n);
         for (int p = pb; p < pe; ++p) {
           if (p == pos) continue;
           const float2 xv = xs[p];
@@ -753,7 +753,7 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
     const unsigned long long d = sub2(xu, pk2(A.x, A.y));
     const float2 df = upk2(d);
     const float q = fmaf(df.x, df.x, df.y * df.y);
-    const bool far = (unsigned)(pos - B.z) >= (unsigned)(B.w - B.z) && q > A.z;
+    const bool far = (unsigned)(pos - B.z) >= (unsigned)B.w && q > A.z;
     const bool take = __all_sync(0xffffffffu, far);
     // count / distance^2 of the accepted cell, 0 when the cell is not taken
     const float s = take ? A.w * rcp_approx(q) : 0.f;
@@ -762,7 +762,7 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
     if (kCount && take) ++inter;
     const bool leaf = !take && B.x < 0;
     if (leaf) {  // uniform: every lane read the same record
-      const int pb = max(B.z, 0), pe = min(B.w, n);
+      const int pb = max(B.z, 0), pe = min(B.z + B.w, n);
 #pragma unroll 4
       for (int p = pb; p < pe; ++p) {
         const unsigned long long e = sub2(xu, __ldg(&xp[p]));
@@ -780,7 +780,7 @@ __device__ __forceinline__ void vote_walk(int cur, int stop, int n, int seed, in
       }
       if (kCount) inter += (unsigned)max(pe - pb, 0);
     }
-    if (kSeeding && !take && !leaf && B.w - B.z <= seed && nseeds < kSeedMax) {
+    if (kSeeding && !take && !leaf && B.w <= seed && nseeds < kSeedMax) {
       if (lane == 0) seeds[nseeds] = cur;
       __syncwarp();
       if (lane == 0) ++nseeds;

@@ -297,8 +297,10 @@ mm_status read_scalar(const void* dev, T* host, cudaStream_t s) {
 
 // ------------------------------------------------------------ quadtree --
 // One quadtree cell as the walk reads it: a = (cx, cy, r_crit^2, count),
-// b = (first child | -1, escape | -1, lo, hi+1).  Both halves share one
-// 32-byte sector, so a visit is a single 256-bit load.
+// b = (first child | -1, escape | -1, first point lo, point count).  Both
+// halves share one 32-byte sector, so a visit is a single 256-bit load; the
+// integer count makes the point-in-cell test one subtraction and one
+// unsigned comparison.
 struct __align__(32) NodeRec {
   float4 a;
   int4 b;
